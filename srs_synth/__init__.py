@@ -1,0 +1,123 @@
+"""Seeded synthetic inputs shared by the tests, the oracle checks and bench.py.
+
+This module only makes data: Gaussian noise, Newtonian (0PN) chirps injected
+into it, and template lists.  It holds none of the search's arithmetic (no
+resampling, transform, power or statistic), so it can feed both the CUDA path
+and the oracle without tying them together.
+
+The chirp follows the paper's signal model: Sec. III.A Eq. (f) for the
+frequency and Eq. (phi) for the phase, with the chirp parameter of Sec. II
+Eq. (beta).  The phase is written with its constant removed
+(phi(t) - phi(0)), which only shifts phi0.
+
+Workload shapes (30 s segments, 40-60 Hz band, chirp masses 5e-4..1e-1 Msun)
+follow the paper's search (abstract, Sec. III.C, Sec. IV).
+"""
+import math
+
+import numpy as np
+
+# G*Msun / c^3 in seconds (IAU nominal G*Msun = 1.32712440018e20 m^3/s^2).
+_GMSUN_C3 = 1.32712440018e20 / 299792458.0 ** 3
+
+
+def chirp_beta(mc_msun, f0):
+    """Sec. II Eq. (beta): chirp rate parameter for chirp mass mc at frequency f0."""
+    return (96.0 / 5.0) * math.pi ** (8.0 / 3.0) * (_GMSUN_C3 * mc_msun) ** (5.0 / 3.0) * f0 ** (8.0 / 3.0)
+
+
+def mc_for_beta(beta, f0):
+    """Inverse of chirp_beta in mc at fixed f0."""
+    k = (96.0 / 5.0) * math.pi ** (8.0 / 3.0) * _GMSUN_C3 ** (5.0 / 3.0) * f0 ** (8.0 / 3.0)
+    return (beta / k) ** 0.6
+
+
+def white_noise(n, seed, dtype=np.float64):
+    """n samples of N(0, 1) from numpy's PCG64 stream `seed`."""
+    return np.random.default_rng(seed).standard_normal(n).astype(dtype, copy=False)
+
+
+def chirp(n, fs, mc_msun, f0, amp, phi0=0.0, t_start=0.0):
+    """A cos(phi(t)) for t = t_start + j/fs, j < n, zero before t_start.
+
+    phi(t) - phi0 = 2 pi f0 * (3 / (5 beta)) * (1 - (1 - (8/3) beta (t - t_start))^(5/8))
+    (Eq. (phi) minus its value at t_start); zero after coalescence."""
+    beta = chirp_beta(mc_msun, f0)
+    t = np.arange(n, dtype=np.float64) / fs - t_start
+    x = (8.0 / 3.0) * beta * t
+    out = np.zeros(n)
+    live = (t >= 0) & (x < 1.0)
+    core = -np.expm1(0.625 * np.log1p(-x[live]))
+    phase = 2.0 * np.pi * f0 * (3.0 / (5.0 * beta)) * core + phi0
+    out[live] = amp * np.cos(phase)
+    return out
+
+
+def log_templates(mc_lo, mc_hi, count):
+    """count chirp masses log-spaced over [mc_lo, mc_hi]."""
+    if count == 1:
+        return np.array([float(mc_lo)])
+    return np.exp(np.linspace(np.log(mc_lo), np.log(mc_hi), count))
+
+
+def strain_with_chirps(n, fs, seed, injections, dtype=np.float64, noise=True):
+    """Noise (seed) plus the listed chirps; each injection is a dict with keys
+    mc, f0, amp and optionally phi0, t_start."""
+    x = white_noise(n, seed) if noise else np.zeros(n)
+    for inj in injections:
+        x = x + chirp(n, fs, inj["mc"], inj["f0"], inj["amp"], inj.get("phi0", 0.0),
+                      inj.get("t_start", 0.0))
+    return x.astype(dtype, copy=False)
+
+
+def random_injections(count, seed, mc_lo, mc_hi, f_lo, f_hi, amp):
+    """count injections: chirp mass log-uniform in [mc_lo, mc_hi], f0 uniform in
+    [f_lo, f_hi), phi0 uniform in [0, 2 pi); amp a number or a (lo, hi) pair for
+    a uniform draw."""
+    r = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        a = amp if np.isscalar(amp) else r.uniform(amp[0], amp[1])
+        out.append({"mc": float(np.exp(r.uniform(np.log(mc_lo), np.log(mc_hi)))),
+                    "f0": float(r.uniform(f_lo, f_hi)), "amp": float(a),
+                    "phi0": float(r.uniform(0, 2 * np.pi))})
+    return out
+
+
+# Workloads of the paper's search shape (T_coh = 30 s, 40-60 Hz).
+WORKLOADS = {
+    # single segment, single exact template, full mode set at 128 Hz
+    "single": dict(fs=128.0, t_obs=30.0, t_coh=30.0, f_lo=-64.0, f_hi=64.0, f_ref=50.0,
+                   mc=[1e-2], eps=1e-9, seed=0, dtype="f64",
+                   injections=[{"mc": 1e-2, "f0": 50.0, "amp": 0.5}]),
+    # 2 h, 64 templates 2e-2..5e-2, one loud chirp
+    "semicoherent_2h": dict(fs=256.0, t_obs=7200.0, t_coh=30.0, f_lo=40.0, f_hi=60.0, f_ref=40.0,
+                            mc=("log", 2e-2, 5e-2, 64), eps=1e-6, seed=0, dtype="f64", top_k=32,
+                            injections=[{"mc": 3e-2, "f0": 45.0, "amp": 0.05}]),
+    # 6 h, 1024 templates 5e-4..1e-1, 8 injections
+    "batched_6h": dict(fs=256.0, t_obs=21600.0, t_coh=30.0, f_lo=40.0, f_hi=60.0, f_ref=40.0,
+                       mc=("log", 5e-4, 1e-1, 1024), eps=1e-6, seed=0, dtype="f64", top_k=32,
+                       injections=("random", 8, 1, 0.05)),
+    # 24 h float32, 4096 templates, 64 injections
+    "large_24h": dict(fs=256.0, t_obs=86400.0, t_coh=30.0, f_lo=40.0, f_hi=60.0, f_ref=40.0,
+                      mc=("log", 5e-4, 1e-1, 4096), eps=1e-6, seed=0, dtype="f32", top_k=32,
+                      injections=("random", 64, 1, 0.05)),
+}
+
+
+def make_workload(name, **over):
+    """Materialise a named workload: returns dict with strain (numpy), mc list
+    and the search parameters."""
+    w = dict(WORKLOADS[name]); w.update(over)
+    n = int(round(w["t_obs"] * w["fs"]))
+    mc = w["mc"]
+    if isinstance(mc, tuple) and mc[0] == "log":
+        mc = log_templates(mc[1], mc[2], mc[3])
+    mc = np.asarray(mc, dtype=np.float64)
+    inj = w["injections"]
+    if isinstance(inj, tuple) and inj[0] == "random":
+        inj = random_injections(inj[1], inj[2], 5e-4, 1e-1, w["f_lo"], w["f_hi"], inj[3])
+    dtype = np.float32 if w["dtype"] == "f32" else np.float64
+    x = strain_with_chirps(n, w["fs"], w["seed"], inj, dtype=dtype)
+    w.update(strain=x, mc=mc, injections=inj, n_samples=n)
+    return w

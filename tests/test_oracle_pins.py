@@ -1,0 +1,193 @@
+"""Pins of the FP64 oracle against the paper's printed numbers, closed forms,
+library routines in limiting cases, and statistics.  CPU only."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import srs_synth
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))
+
+
+def _one_sig(x):
+    e = np.floor(np.log10(abs(x)))
+    return round(x / 10 ** e) * 10 ** e
+
+
+def test_beta_range_matches_paper():
+    g = GOLD["beta_range"]
+    lo = oracle.beta(g["mc_lo"], g["f_lo"])
+    hi = oracle.beta(g["mc_hi"], g["f_hi"])
+    assert _one_sig(lo) == pytest.approx(g["beta_lo_printed"])
+    assert _one_sig(hi) == pytest.approx(g["beta_hi_printed"])
+
+
+def test_injection_segment_count_matches_paper():
+    g = GOLD["injection_segments"]
+    b = oracle.beta(g["mc"], g["f0"])
+    assert oracle.nseg(b, g["f0"], g["f_end"], g["t_coh"], 10 ** 6) == g["n_seg"]
+    # 35 whole segments = 1050 s < 0PN band time < 36 segments
+    t = oracle.duration(b, g["f0"], g["f_end"])
+    assert 35 * 30.0 < t < 36 * 30.0
+
+
+def test_band_crossing_times_match_paper():
+    g = GOLD["band_crossing_times"]
+    b1 = oracle.beta(g["cases"][0]["mc"], g["f_lo"])
+    hours = oracle.duration(b1, g["f_lo"], g["f_hi"]) / 3600.0
+    assert round(hours) == g["cases"][0]["hours_printed"]
+    b2 = oracle.beta(g["cases"][1]["mc"], g["f_lo"])
+    years = oracle.duration(b2, g["f_lo"], g["f_hi"]) / (365.25 * 86400.0)
+    assert round(years) == g["cases"][1]["years_printed"]
+
+
+def test_nseg_cut_rule_and_clamps():
+    b = oracle.beta(0.1, 40.0)
+    assert oracle.nseg(b, 40.0, 60.0, 30.0, 10) == 10      # clamped to the data
+    assert oracle.nseg(b, 40.0, 60.0, 30.0, 100, cut=False) == 100
+    heavy = oracle.beta(5.0, 40.0)                            # leaves band in < 30 s
+    assert oracle.nseg(heavy, 40.0, 60.0, 30.0, 100) == 1
+
+
+def test_frequency_reaches_f_end_after_duration():
+    """Eq. (f) and the Sec. II duration are two separate formulas; they must agree."""
+    for mc in (5e-4, 1e-2, 1e-1):
+        b = oracle.beta(mc, 40.0)
+        t = oracle.duration(b, 40.0, 60.0)
+        assert oracle.freq(b, 40.0, t) == pytest.approx(60.0, rel=1e-12)
+
+
+def test_delta_matches_high_precision_eq_new_t():
+    """delta = tau(t_i0 + s) - tau(t_i0) with tau from Eq. (new_t) evaluated
+    literally at 60 digits; the oracle's cancellation-free form must agree to
+    ~1e-15 relative."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 60
+    for mc, i0 in ((5e-4, 2879), (1e-2, 100), (1e-1, 34), (3e-2, 0)):
+        b = oracle.beta(mc, 40.0)
+        t_i0 = i0 * 30.0
+        B = mpmath.mpf(b)
+        tau = lambda t: -mpmath.mpf(3) / 5 * (1 - mpmath.mpf(8) / 3 * B * t) ** (mpmath.mpf(5) / 8) / B
+        for s in (0.0, 1.0 / 256, 7.3, 29.99609375):
+            ref = tau(mpmath.mpf(t_i0) + mpmath.mpf(s)) - tau(mpmath.mpf(t_i0))
+            got = oracle.delta(b, t_i0, s)[0]
+            assert abs(got - float(ref)) <= 2e-15 * max(abs(float(ref)), 1e-300) + 1e-300
+
+
+def test_delta_derivative_is_frequency_ratio():
+    """d tau / dt = f(t) / f0 (Eq. (new_t) differentiated against Eq. (f))."""
+    b = oracle.beta(1e-1, 40.0)
+    t_i0, h = 900.0, 1e-3
+    for s in (0.5, 12.0, 29.0):
+        d = oracle.delta(b, t_i0, [s - h, s + h])
+        slope = (d[1] - d[0]) / (2 * h)
+        assert slope == pytest.approx(oracle.freq(b, 40.0, t_i0 + s) / 40.0, rel=1e-8)
+
+
+def _theta_mp(beta, t_i0, fs, n, f):
+    """2 pi f delta_j for j < n, computed at high precision from Eq. (new_t)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    B = mpmath.mpf(beta)
+    tau = lambda t: -mpmath.mpf(3) / 5 * (1 - mpmath.mpf(8) / 3 * B * t) ** (mpmath.mpf(5) / 8) / B
+    t0 = tau(mpmath.mpf(t_i0))
+    out = np.empty(n)
+    for j in range(n):
+        cyc = mpmath.mpf(f) * (tau(mpmath.mpf(t_i0) + mpmath.mpf(j) / fs) - t0)
+        out[j] = float(2 * mpmath.pi * (cyc - mpmath.floor(cyc)))
+    return out
+
+
+def test_tone_in_tau_gives_exactly_n():
+    """Monochromatic in tau (Eq. (monochromatic)): x = cos(theta), y = sin(theta),
+    theta_j = 2 pi f_b delta_j.  Then F_x(f_b) + i F_y(f_b) = sum_j 1 = N exactly,
+    and F_x - i F_y = sum_j exp(-2 i theta_j)."""
+    fs, T, f_lo, n_b = 64.0, 4.0, 10.0, 40
+    n = int(fs * T)
+    b = oracle.beta(0.05, 12.0)
+    t_i0 = 3 * T
+    bin0 = 9
+    f0 = f_lo + bin0 / T
+    th = _theta_mp(b, t_i0, fs, n, f0)
+    strain = np.zeros(4 * n)
+    strain[3 * n:] = np.cos(th)
+    Fx = oracle.spectra(strain, fs, T, f_lo, n_b, [b], [(0, 3)])[0]
+    strain[3 * n:] = np.sin(th)
+    Fy = oracle.spectra(strain, fs, T, f_lo, n_b, [b], [(0, 3)])[0]
+    assert abs(Fx[bin0] + 1j * Fy[bin0] - n) < 1e-9
+    assert abs((Fx[bin0] - 1j * Fy[bin0]) - np.exp(-2j * th).sum()) < 1e-9
+
+
+def test_uniform_limit_is_the_fft():
+    """beta -> 0 makes delta_j = j / fs, so with the full mode set the NDFT is the
+    plain DFT: F(f_b) = fft(x)[(b - N/2) mod N] for f_b = (b - N/2) / T."""
+    fs, T = 32.0, 8.0
+    n = int(fs * T)
+    x = srs_synth.white_noise(n, seed=3)
+    F = oracle.spectra(x, fs, T, -fs / 2, n, [1e-30], [(0, 0)])[0]
+    ref = np.fft.fft(x)
+    k = (np.arange(n) - n // 2) % n
+    assert np.max(np.abs(F - ref[k])) < 1e-9 * np.max(np.abs(ref))
+    # Parseval over the full mode set
+    assert np.sum(np.abs(F) ** 2) == pytest.approx(n * np.sum(x ** 2), rel=1e-12)
+
+
+def test_real_input_conjugate_symmetry():
+    """Real x: F(-f) = conj F(f) for any beta."""
+    fs, T = 32.0, 4.0
+    n = int(fs * T)
+    x = srs_synth.white_noise(2 * n, seed=5)
+    b = oracle.beta(0.08, 8.0)
+    F = oracle.spectra(x, fs, T, -8.0, 65, [b], [(0, 1)])[0]   # f_b = -8 .. +8 Hz
+    assert np.max(np.abs(F[::-1] - np.conj(F))) < 1e-9 * np.max(np.abs(F))
+
+
+def test_noiseless_exact_template_chirp_concentrates_power():
+    """A 0PN chirp resampled with its own beta is a tone at f0 in every segment
+    (Sec. III.B): the peak bin is f0's and its power is A^2 N / 2 up to the
+    O(1/N) cross term."""
+    fs, T, f_lo, f_hi = 256.0, 30.0, 40.0, 60.0
+    mc, f0, A = 3e-2, 45.0, 0.05
+    n_s = int(fs * T)
+    nseg = 6
+    x = srs_synth.chirp(nseg * n_s, fs, mc, f0, A)
+    b = oracle.beta(mc, f0)
+    n_b = int((f_hi - f_lo) * T)
+    F = oracle.spectra(x, fs, T, f_lo, n_b, [b], [(0, i) for i in range(nseg)])
+    P = oracle.power(F, n_s)
+    b0 = int(round((f0 - f_lo) * T))
+    assert np.all(np.argmax(P, axis=1) == b0)
+    assert np.allclose(P[:, b0], A * A * n_s / 2, rtol=5e-3)
+    # everything off the peak is leakage-free to O(A^2): a tiny fraction
+    off = np.delete(P, b0, axis=1)
+    assert off.max() < 1e-3 * P[:, b0].min()
+
+
+def test_noise_power_moments_and_n_sigma_null():
+    """Gaussian N(0,1) noise: P ~ chi^2_2 (mean 2, std 2), n_sigma ~ (0, 1)."""
+    g = GOLD["noise_power_moments"]
+    fs, T, f_lo, f_hi = 256.0, 30.0, 40.0, 60.0
+    n_s = int(fs * T)
+    nseg = 8
+    x = srs_synth.white_noise(nseg * n_s, seed=11)
+    bets = [oracle.beta(m, 40.0) for m in (1e-3, 2e-2, 9e-2)]
+    n_b = 600
+    items = [(m, i) for m in range(3) for i in range(nseg)]
+    P = oracle.power(oracle.spectra(x, fs, T, f_lo, n_b, bets, items), n_s)
+    se = g["std"] / np.sqrt(P.size)
+    assert abs(P.mean() - g["mean"]) < 4 * se * 2
+    assert abs(P.std() - g["std"]) < 0.05 * g["std"]
+    S = P.reshape(3, nseg, n_b).sum(axis=1)
+    ns = oracle.n_sigma(S, [nseg] * 3)
+    assert abs(ns.mean()) < 0.1 and abs(ns.std() - 1.0) < 0.1
+
+
+def test_topk_order_against_brute_force():
+    r = np.random.default_rng(0)
+    M = r.integers(0, 6, size=(7, 9)).astype(np.float64)   # many ties
+    v, m, b = oracle.topk(M, 20)
+    brute = sorted(((-M[i, j], i, j) for i in range(7) for j in range(9)))[:20]
+    assert [(-a, i, j) for a, i, j in brute] == list(zip(v, m, b))
