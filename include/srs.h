@@ -1,0 +1,203 @@
+/*
+ * srs.h -- C ABI of the GB300 semicoherent resampling search (libsrs.so).
+ *
+ * The search follows arXiv:2609.12476 (Lu, Palomba, Piccinni, Sun):
+ *   Sec. III.B  resample each coherent segment with the 0PN time tau(t; beta)
+ *               (Eq. new_t) so that a chirp becomes monochromatic
+ *               (Eq. monochromatic), and take the segment's spectrum with a
+ *               type-1 non-uniform FFT;
+ *   Sec. III.C  normalise the powers (Eq. normalized_power), sum them over
+ *               segments with equal weights (Eq. weights) into the
+ *               semicoherent statistic n_sigma (Eq. semicoherent_statistic);
+ *   and keep the top-k (template, bin) cells.
+ *
+ * Conventions shared by every call
+ *   - Templates are chirp masses mc[m] (solar masses) quoted at f_ref; the
+ *     resampling parameter is beta_m = beta(f_ref, mc[m]) of Eq. (beta).
+ *   - Time t = 0 is the first strain sample; segment i covers samples
+ *     [i*n_s, (i+1)*n_s) with n_s = t_coh*fs.  Within segment i the
+ *     resampled time is delta_j = tau(t_i0 + j/fs) - tau(t_i0) (Eq. new_t,
+ *     referenced to the segment start).
+ *   - Bins b = 0..n_bins-1 are the frequencies f_b = f_lo + b/t_coh with
+ *     n_bins = (f_hi - f_lo)*t_coh.  The spectrum of a segment is
+ *     F_b = sum_j x_j exp(-2 pi i f_b delta_j), no 1/N factor.
+ *   - Power P = 2 |F_b|^2 / n_s (Eq. normalized_power for unit-variance white
+ *     noise); template m sums its first nseg_m segments, nseg_m = whole
+ *     30 s segments its 0PN track spends below f_hi (Sec. II duration,
+ *     Sec. V), clamped to [1, segments in the data]; with equal weights and
+ *     mu = sigma = 2, n_sigma[m][b] = (sum_i P - 2 nseg_m) / (2 sqrt(nseg_m)).
+ *   - Top-k ordering: n_sigma descending, then template ascending, then bin
+ *     ascending.
+ *
+ * Ownership and memory
+ *   - The caller owns every buffer passed in or out.  With
+ *     params.io_on_device = 1 the strain, map, candidate and spectra
+ *     pointers are device pointers on the context's device; with 0 they are
+ *     host pointers and the call copies them.  Template lists (mc) are always
+ *     host pointers.
+ *   - The context owns its device workspace (allocated on first use, grown
+ *     when a larger problem arrives, freed by srs_destroy) and its stream.
+ *   - Every call is synchronous with respect to the host: it returns after
+ *     the results are in the caller's buffers.
+ *
+ * Errors
+ *   - Every call returns an srs_status; nothing throws or aborts across the
+ *     ABI.  srs_last_error() gives the context's last message.
+ *   - SRS_ERR_ARG: a NULL pointer where one is needed, a non-integer
+ *     t_coh*fs or band width, f_hi > fs/2, eps outside [1e-12, 1e-1], top_k
+ *     outside [1, 1024] or larger than the map, fewer samples than one
+ *     segment.
+ *   - SRS_ERR_DOMAIN: a computed segment reaches coalescence
+ *     (1 - (8/3) beta t <= 0, Sec. II), possible with cut_segments = 0.
+ *   - SRS_ERR_UNSUPPORTED: a combination this build does not run (e.g. the
+ *     mixed form below its FP32 floor, eps < 1e-7).
+ *   - SRS_ERR_CUDA / SRS_ERR_OOM: a CUDA call failed / device memory ran out;
+ *     the context stays usable for smaller problems.
+ *   - Threading: one context per host thread.
+ */
+#ifndef SRS_H
+#define SRS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct srs_ctx srs_ctx;
+
+typedef enum {
+  SRS_OK = 0,
+  SRS_ERR_ARG = -1,
+  SRS_ERR_OOM = -2,
+  SRS_ERR_CUDA = -3,
+  SRS_ERR_TIMEOUT = -4,
+  SRS_ERR_UNSUPPORTED = -5,
+  SRS_ERR_DOMAIN = -6
+} srs_status;
+
+/* Element type of the strain buffer. */
+typedef enum { SRS_F32 = 0, SRS_F64 = 1 } srs_dtype;
+
+/* Arithmetic of the segment transform.
+ * SRS_PLAIN_FP64: every step in FP64, one CTA per spectrum, tau evaluated
+ *   per sample (the comparison form).
+ * SRS_MIXED: tau and the per-segment phase reference in FP64 at a few anchor
+ *   samples per segment, sample offsets as 32-bit fixed-point phase plus an
+ *   FP32 polynomial, spreading / FFT / power in FP32 with FP32 accumulation,
+ *   persistent kernels over (template, segment-chunk) work. */
+typedef enum { SRS_PLAIN_FP64 = 0, SRS_MIXED = 1 } srs_precision;
+
+/* Search parameters (Sec. III; defaults in brackets are the paper's search). */
+typedef struct {
+  double fs;           /* strain sample rate [Hz] */
+  double t_coh;        /* coherent segment length [s] [30]; t_coh*fs integer */
+  double f_lo;         /* band start [Hz] [40] */
+  double f_hi;         /* band end (exclusive) [Hz] [60] */
+  double f_ref;        /* frequency at which template chirp masses give beta [Hz] [40] */
+  double eps;          /* NUFFT relative tolerance (FINUFFT sense) [1e-6] */
+  double sigma;        /* fine-grid oversampling; 0 = choose from eps and shared memory */
+  int32_t top_k;       /* candidates to return [32] */
+  int32_t precision;   /* srs_precision */
+  int32_t cut_segments;/* 1: template m sums its nseg_m in-band segments; 0: all segments */
+  int32_t io_on_device;/* 1: strain / outputs are device pointers; 0: host pointers */
+  int32_t chunk;       /* segments per work item in the mixed form; 0 = autotune */
+  int32_t deterministic; /* reserved, must be 0 or 1; the reduction is always ordered */
+} srs_params;
+
+/* Host-side plan (no GPU needed): what srs_plan chose. */
+typedef struct {
+  int64_t n_s;            /* samples per segment */
+  int32_t n_seg_total;    /* whole segments in the strain */
+  int32_t n_bins;         /* bins per spectrum */
+  int32_t n_fine;         /* fine (oversampled) grid size, a 2^a 3^b 5^c number */
+  int32_t w;              /* spreading kernel width in fine-grid cells */
+  double beta_es;         /* exponential-of-semicircle shape parameter */
+  double sigma;           /* n_fine / n_bins */
+  int64_t n_spectra;      /* sum over templates of nseg_m */
+  int32_t chunk;          /* segments per work item (mixed form) */
+  int32_t n_items;        /* work items (mixed form) */
+} srs_plan_info;
+
+/* One candidate cell of the statistic map. */
+typedef struct {
+  float value;            /* n_sigma */
+  int32_t template_idx;   /* m */
+  int32_t bin;            /* b, frequency f_lo + b/t_coh */
+} srs_candidate;
+
+/* Timings and choices of the last call (all optional to read). */
+typedef struct {
+  double device_ms;       /* device time of the transform + statistic + top-k */
+  double spectra_per_s;   /* n_spectra / device time */
+  int64_t n_spectra;
+  int32_t w;
+  int32_t n_fine;
+  double sigma;
+  double beta_es;
+  int32_t chunk;
+  int32_t n_items;
+  int32_t kernel_launches;/* kernels this call launched */
+  double spread_ms;       /* device time of the transform kernel alone (k_mixed / k_plain) */
+} srs_report;
+
+/* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
+ * the context will use (NULL: the context creates its own non-blocking
+ * stream).  *out receives the context.  Errors: SRS_ERR_ARG, SRS_ERR_CUDA. */
+srs_status srs_create(srs_ctx** out, int device, void* cuda_stream);
+
+/* Free the workspace and the context (NULL is allowed). */
+void srs_destroy(srs_ctx* ctx);
+
+/* Last error message of `ctx` (static text when ctx is NULL).  Owned by the
+ * context; valid until the next call on it. */
+const char* srs_last_error(const srs_ctx* ctx);
+
+/* Host-only planner (Sec. II Eq. beta and duration; Sec. III.B NUFFT sizes):
+ * fills `info`, beta_out[n_templates] (may be NULL) and nseg_out[n_templates]
+ * (may be NULL) for a strain of n_samples.  No GPU is touched. */
+srs_status srs_plan(const srs_params* params, const double* mc, int32_t n_templates,
+                    int64_t n_samples, srs_plan_info* info, double* beta_out,
+                    int32_t* nseg_out);
+
+/* The semicoherent search (Sec. III.B-C): for every template m and its
+ * nseg_m segments, the segment spectra, powers, their sum, n_sigma and the
+ * top-k cells.
+ *   strain     [n_samples] of `dtype`, host or device per params.io_on_device
+ *   mc         [n_templates] host, chirp masses (solar masses) at f_ref
+ *   stat_map   [n_templates][n_bins] float n_sigma, or NULL to skip
+ *   cands      [top_k] candidates, ordered as above
+ *   n_cands    host int32: number of candidates written (min(top_k, map size))
+ *   report     host, may be NULL */
+srs_status srs_search(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype,
+                      const double* mc, int32_t n_templates, const srs_params* params,
+                      float* stat_map, srs_candidate* cands, int32_t* n_cands,
+                      srs_report* report);
+
+/* Segment spectra F_b for templates [0, n_templates) and segments
+ * [seg_begin, seg_end) (Sec. III.B), through the same time map, spreader,
+ * FFT and deconvolution as srs_search.
+ *   F  [n_templates][seg_end-seg_begin][n_bins] complex double (re, im
+ *      interleaved), host or device per params.io_on_device.
+ * Segments past a template's nseg_m are still computed (the cut applies
+ * only to the sum); SRS_ERR_DOMAIN if any reaches coalescence. */
+srs_status srs_segment_spectra(srs_ctx* ctx, const void* strain, int64_t n_samples,
+                               int32_t dtype, const double* mc, int32_t n_templates,
+                               int32_t seg_begin, int32_t seg_end, const srs_params* params,
+                               double* F, srs_report* report);
+
+/* The time map alone (Sec. III.B Eq. new_t), as the chosen precision form
+ * evaluates it inside the spreader, for n_items (template, segment) pairs:
+ *   psi_out   [n_items][n_s]  delta_j / t_coh modulo 1 (fine-grid phase, periods)
+ *   theta_out [n_items][n_s]  f_c delta_j modulo 1, f_c = (f_lo + f_hi)/2 (cycles)
+ * both host double arrays; item_m / item_i host int32 arrays. */
+srs_status srs_time_map(srs_ctx* ctx, const double* mc, int32_t n_templates,
+                        const int32_t* item_m, const int32_t* item_i, int32_t n_items,
+                        const srs_params* params, int64_t n_samples, double* psi_out,
+                        double* theta_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRS_H */

@@ -1,0 +1,254 @@
+"""ctypes binding of libsrs.so (include/srs.h): argument marshalling only.
+
+Every step of the search runs in the library's CUDA kernels; this module
+converts numpy arrays (host) or torch CUDA tensors (device) into pointers and
+sizes, calls the C entry point of the same name, and raises SrsError on a
+non-zero status.  There is no CPU path: if the library cannot be built or
+loaded, the first call raises.
+"""
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+SRS_OK = 0
+STATUS = {0: "SRS_OK", -1: "SRS_ERR_ARG", -2: "SRS_ERR_OOM", -3: "SRS_ERR_CUDA", -4: "SRS_ERR_TIMEOUT",
+          -5: "SRS_ERR_UNSUPPORTED", -6: "SRS_ERR_DOMAIN"}
+SRS_F32, SRS_F64 = 0, 1
+SRS_PLAIN_FP64, SRS_MIXED = 0, 1
+
+# Entry points declared in include/srs.h (checked by the tests).
+EXPORTS = ("srs_create", "srs_destroy", "srs_last_error", "srs_plan", "srs_search",
+           "srs_segment_spectra", "srs_time_map")
+
+
+class SrsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("fs", ctypes.c_double), ("t_coh", ctypes.c_double), ("f_lo", ctypes.c_double),
+                ("f_hi", ctypes.c_double), ("f_ref", ctypes.c_double), ("eps", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("top_k", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("cut_segments", ctypes.c_int32), ("io_on_device", ctypes.c_int32),
+                ("chunk", ctypes.c_int32), ("deterministic", ctypes.c_int32)]
+
+
+class _PlanInfo(ctypes.Structure):
+    _fields_ = [("n_s", ctypes.c_int64), ("n_seg_total", ctypes.c_int32), ("n_bins", ctypes.c_int32),
+                ("n_fine", ctypes.c_int32), ("w", ctypes.c_int32), ("beta_es", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("n_spectra", ctypes.c_int64), ("chunk", ctypes.c_int32),
+                ("n_items", ctypes.c_int32)]
+
+
+class Candidate(ctypes.Structure):
+    _fields_ = [("value", ctypes.c_float), ("template_idx", ctypes.c_int32), ("bin", ctypes.c_int32)]
+
+
+class _Report(ctypes.Structure):
+    _fields_ = [("device_ms", ctypes.c_double), ("spectra_per_s", ctypes.c_double),
+                ("n_spectra", ctypes.c_int64), ("w", ctypes.c_int32), ("n_fine", ctypes.c_int32),
+                ("sigma", ctypes.c_double), ("beta_es", ctypes.c_double), ("chunk", ctypes.c_int32),
+                ("n_items", ctypes.c_int32), ("kernel_launches", ctypes.c_int32), ("spread_ms", ctypes.c_double)]
+
+
+CAND_DTYPE = np.dtype([("value", np.float32), ("template_idx", np.int32), ("bin", np.int32)])
+
+
+@dataclass
+class Params:
+    """srs_params (include/srs.h).  Defaults are the paper's search: 30 s
+    segments, 40-60 Hz band, chirp masses quoted at 40 Hz, eps = 1e-6."""
+    fs: float = 256.0
+    t_coh: float = 30.0
+    f_lo: float = 40.0
+    f_hi: float = 60.0
+    f_ref: float = 40.0
+    eps: float = 1e-6
+    sigma: float = 0.0
+    top_k: int = 32
+    precision: int = SRS_MIXED
+    cut_segments: int = 1
+    io_on_device: int = 0
+    chunk: int = 0
+    deterministic: int = 1
+
+    def c(self):
+        return _Params(self.fs, self.t_coh, self.f_lo, self.f_hi, self.f_ref, self.eps, self.sigma,
+                       self.top_k, self.precision, self.cut_segments, self.io_on_device, self.chunk,
+                       self.deterministic)
+
+
+_LIB = None
+
+
+def lib():
+    """Load libsrs.so, building it first if it is missing or stale."""
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.srs_create.restype = i32
+        L.srs_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp]
+        L.srs_destroy.restype = None
+        L.srs_destroy.argtypes = [vp]
+        L.srs_last_error.restype = ctypes.c_char_p
+        L.srs_last_error.argtypes = [vp]
+        L.srs_plan.restype = i32
+        L.srs_plan.argtypes = [ctypes.POINTER(_Params), vp, i32, i64, ctypes.POINTER(_PlanInfo), vp, vp]
+        L.srs_search.restype = i32
+        L.srs_search.argtypes = [vp, vp, i64, i32, vp, i32, ctypes.POINTER(_Params), vp, vp,
+                                 ctypes.POINTER(i32), ctypes.POINTER(_Report)]
+        L.srs_segment_spectra.restype = i32
+        L.srs_segment_spectra.argtypes = [vp, vp, i64, i32, vp, i32, i32, i32, ctypes.POINTER(_Params), vp,
+                                          ctypes.POINTER(_Report)]
+        L.srs_time_map.restype = i32
+        L.srs_time_map.argtypes = [vp, vp, i32, vp, vp, i32, ctypes.POINTER(_Params), i64, vp, vp]
+        _LIB = L
+    return _LIB
+
+
+def _report_dict(r):
+    return {k: getattr(r, k) for k, _ in _Report._fields_}
+
+
+def srs_plan(params, mc, n_samples):
+    """Host planner: returns (info dict, beta[m], nseg[m]).  No GPU needed."""
+    mc = np.ascontiguousarray(mc, dtype=np.float64)
+    info = _PlanInfo()
+    beta = np.zeros(mc.size)
+    nseg = np.zeros(mc.size, dtype=np.int32)
+    p = params.c()
+    st = lib().srs_plan(ctypes.byref(p), mc.ctypes.data, mc.size, int(n_samples), ctypes.byref(info),
+                        beta.ctypes.data, nseg.ctypes.data)
+    if st != SRS_OK:
+        raise SrsError(st, "srs_plan rejected the parameters")
+    return {k: getattr(info, k) for k, _ in _PlanInfo._fields_}, beta, nseg
+
+
+def _is_torch_cuda(x):
+    return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
+
+
+def _dtype_code(x):
+    if _is_torch_cuda(x):
+        import torch
+        if x.dtype == torch.float64:
+            return SRS_F64
+        if x.dtype == torch.float32:
+            return SRS_F32
+        raise TypeError("strain must be float32 or float64")
+    if x.dtype == np.float64:
+        return SRS_F64
+    if x.dtype == np.float32:
+        return SRS_F32
+    raise TypeError("strain must be float32 or float64")
+
+
+class Context:
+    """srs_ctx: one CUDA device, one stream, a reusable device workspace."""
+
+    def __init__(self, device=0, stream=None):
+        self._lib = lib()
+        self._h = ctypes.c_void_p()
+        st = self._lib.srs_create(ctypes.byref(self._h), int(device), stream)
+        if st != SRS_OK:
+            raise SrsError(st, "srs_create failed (no CUDA device?)")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            self._lib.srs_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != SRS_OK:
+            raise SrsError(st, self._lib.srs_last_error(self._h).decode())
+
+    def search(self, strain, mc, params, stat_map=True, out=None):
+        """srs_search.  Host numpy strain (params.io_on_device = 0) returns numpy
+        results; a torch CUDA tensor (io_on_device = 1) returns torch tensors on
+        its device.  Returns (candidates structured array / dict of tensors,
+        map or None, report dict)."""
+        mc = np.ascontiguousarray(mc, dtype=np.float64)
+        dt = _dtype_code(strain)
+        p = params.c()
+        n_cands = ctypes.c_int32(0)
+        rep = _Report()
+        if _is_torch_cuda(strain):
+            import torch
+            p.io_on_device = 1
+            n_bins = int(round((params.f_hi - params.f_lo) * params.t_coh))
+            if out is None:
+                out = {"map": torch.empty((mc.size, n_bins), dtype=torch.float32, device=strain.device)
+                       if stat_map else None,
+                       "cands": torch.empty((params.top_k, 3), dtype=torch.int32, device=strain.device)}
+            mp = out["map"].data_ptr() if out.get("map") is not None else None
+            st = self._lib.srs_search(self._h, strain.data_ptr(), strain.numel(), dt, mc.ctypes.data, mc.size,
+                                      ctypes.byref(p), mp, out["cands"].data_ptr(), ctypes.byref(n_cands),
+                                      ctypes.byref(rep))
+            self._check(st)
+            return out, _report_dict(rep)
+        strain = np.ascontiguousarray(strain)
+        p.io_on_device = 0
+        n_bins = int(round((params.f_hi - params.f_lo) * params.t_coh))
+        m = np.empty((mc.size, n_bins), dtype=np.float32) if stat_map else None
+        c = np.zeros(params.top_k, dtype=CAND_DTYPE)
+        st = self._lib.srs_search(self._h, strain.ctypes.data, strain.size, dt, mc.ctypes.data, mc.size,
+                                  ctypes.byref(p), m.ctypes.data if m is not None else None, c.ctypes.data,
+                                  ctypes.byref(n_cands), ctypes.byref(rep))
+        self._check(st)
+        return c[:n_cands.value], m, _report_dict(rep)
+
+    def segment_spectra(self, strain, mc, seg_begin, seg_end, params):
+        """srs_segment_spectra: complex128 [templates, seg_end - seg_begin, n_bins]
+        (numpy for host strain, torch for a CUDA tensor)."""
+        mc = np.ascontiguousarray(mc, dtype=np.float64)
+        dt = _dtype_code(strain)
+        p = params.c()
+        rep = _Report()
+        n_bins = int(round((params.f_hi - params.f_lo) * params.t_coh))
+        shape = (mc.size, seg_end - seg_begin, n_bins)
+        if _is_torch_cuda(strain):
+            import torch
+            p.io_on_device = 1
+            F = torch.empty(shape, dtype=torch.complex128, device=strain.device)
+            st = self._lib.srs_segment_spectra(self._h, strain.data_ptr(), strain.numel(), dt, mc.ctypes.data,
+                                               mc.size, int(seg_begin), int(seg_end), ctypes.byref(p),
+                                               F.data_ptr(), ctypes.byref(rep))
+            self._check(st)
+            return F, _report_dict(rep)
+        strain = np.ascontiguousarray(strain)
+        p.io_on_device = 0
+        F = np.empty(shape, dtype=np.complex128)
+        st = self._lib.srs_segment_spectra(self._h, strain.ctypes.data, strain.size, dt, mc.ctypes.data, mc.size,
+                                           int(seg_begin), int(seg_end), ctypes.byref(p), F.ctypes.data,
+                                           ctypes.byref(rep))
+        self._check(st)
+        return F, _report_dict(rep)
+
+    def time_map(self, mc, items, params, n_samples):
+        """srs_time_map: (psi, theta) float64 [len(items), n_s] for (m, i) items."""
+        mc = np.ascontiguousarray(mc, dtype=np.float64)
+        items = np.asarray(items, dtype=np.int32).reshape(-1, 2)
+        im = np.ascontiguousarray(items[:, 0]); ii = np.ascontiguousarray(items[:, 1])
+        n_s = int(round(params.t_coh * params.fs))
+        psi = np.empty((items.shape[0], n_s)); th = np.empty((items.shape[0], n_s))
+        p = params.c()
+        st = self._lib.srs_time_map(self._h, mc.ctypes.data, mc.size, im.ctypes.data, ii.ctypes.data,
+                                    items.shape[0], ctypes.byref(p), int(n_samples), psi.ctypes.data,
+                                    th.ctypes.data)
+        self._check(st)
+        return psi, th

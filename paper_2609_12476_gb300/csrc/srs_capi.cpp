@@ -1,0 +1,586 @@
+// srs_capi.cpp -- the extern "C" entry points of libsrs (include/srs.h).
+//
+// Owns the per-context device workspace and stream, turns a host plan
+// (srs_plan.cpp) into kernel launches (srs_kernels.cu), and copies results to
+// the caller's buffers.  No exception crosses the ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "srs_internal.h"
+#include "srs_kernels.h"
+
+using namespace srs;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t b = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e == cudaSuccess) cap = b;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+}  // namespace
+
+struct srs_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int n_sm = 0;
+  std::string err;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+  // last plan whose tables are on the device (key: call kind, sizes, params, templates)
+  bool have_plan = false;
+  std::vector<unsigned char> plan_key;
+  Plan plan;
+  DevBuf items, anchors, partial, betas, nseg, item_off, corr, tw, keys, topk_a, topk_b, cands, queue, strain,
+      map, S, F, psi, th, im, ii;
+};
+
+namespace {
+
+srs_status set_err(srs_ctx* c, srs_status s, const std::string& m) {
+  if (c) c->err = m;
+  return s;
+}
+
+srs_status cuda_err(srs_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();  // clear a sticky-free error so the context stays usable
+  return set_err(c, e == cudaErrorMemoryAllocation ? SRS_ERR_OOM : SRS_ERR_CUDA, m);
+}
+
+#define SRS_CK(call, where)                         \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_err(ctx, e_, where); \
+  } while (0)
+
+void fill_radices(const Plan& pl, int8_t* r) {
+  for (int k = 0; k < 16; ++k) r[k] = 0;
+  for (size_t k = 0; k < pl.radices.size() && k < 16; ++k) r[k] = (int8_t)pl.radices[k];
+}
+
+MixedArgs mixed_args(const Plan& pl, const srs_ctx* ctx, int seg_begin, int seg_range) {
+  MixedArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.n_s = (int)pl.n_s;
+  a.n_fine = pl.n_fine;
+  a.n_bins = pl.n_bins;
+  a.half_bins = pl.half_bins;
+  a.run = pl.run;
+  a.span = pl.span;
+  a.n_anchor = pl.n_anchor;
+  a.n_pass = (int)pl.radices.size();
+  a.seg_begin = seg_begin;
+  a.seg_range = seg_range;
+  a.kc = (float)pl.k_c;
+  a.inv_ns = (float)(1.0 / (double)pl.n_s);
+  a.es_beta_log2e = (float)(pl.beta_es * 1.4426950408889634074);
+  a.two_over_w = (float)(2.0 / pl.w);
+  a.corr = ctx->corr.as<float>();
+  a.tw = ctx->tw.as<float>();
+  fill_radices(pl, a.radices);
+  return a;
+}
+
+PlainArgs plain_args(const Plan& pl, const srs_ctx* ctx, int seg_begin, int seg_range) {
+  PlainArgs p;
+  std::memset(&p, 0, sizeof p);
+  p.fs = pl.fs;
+  p.t_coh = pl.t_coh;
+  p.f_c = pl.f_c;
+  p.beta_es = pl.beta_es;
+  p.n_s = (int)pl.n_s;
+  p.n_fine = pl.n_fine;
+  p.n_bins = pl.n_bins;
+  p.half_bins = pl.half_bins;
+  p.w = pl.w;
+  p.n_pass = (int)pl.radices.size();
+  p.seg_begin = seg_begin;
+  p.seg_range = seg_range;
+  p.corr = ctx->corr.as<double>();
+  p.tw = ctx->tw.as<double>();
+  fill_radices(pl, p.radices);
+  return p;
+}
+
+AnchorArgs anchor_args(const Plan& pl) {
+  AnchorArgs aa;
+  aa.fs = pl.fs;
+  aa.t_coh = pl.t_coh;
+  aa.f_c = pl.f_c;
+  aa.n_s = pl.n_s;
+  aa.span = pl.span;
+  aa.n_anchor = pl.n_anchor;
+  return aa;
+}
+
+// Upload the tables of a plan (deconvolution, twiddles, templates).
+srs_status upload_tables(srs_ctx* ctx, const Plan& pl) {
+  const bool mixed = pl.precision == SRS_MIXED;
+  if (mixed) {
+    std::vector<float> corr(pl.corr.begin(), pl.corr.end());
+    std::vector<float> tw(2 * pl.n_fine);
+    for (int m = 0; m < pl.n_fine; ++m) { tw[2 * m] = (float)pl.tw_re[m]; tw[2 * m + 1] = (float)pl.tw_im[m]; }
+    SRS_CK(ctx->corr.ensure(corr.size() * 4), "alloc corr");
+    SRS_CK(ctx->tw.ensure(tw.size() * 4), "alloc tw");
+    SRS_CK(cudaMemcpyAsync(ctx->corr.p, corr.data(), corr.size() * 4, cudaMemcpyHostToDevice, ctx->stream), "copy corr");
+    SRS_CK(cudaMemcpyAsync(ctx->tw.p, tw.data(), tw.size() * 4, cudaMemcpyHostToDevice, ctx->stream), "copy tw");
+    SRS_CK(cudaStreamSynchronize(ctx->stream), "sync tables");
+  } else {
+    std::vector<double> tw(2 * pl.n_fine);
+    for (int m = 0; m < pl.n_fine; ++m) { tw[2 * m] = pl.tw_re[m]; tw[2 * m + 1] = pl.tw_im[m]; }
+    SRS_CK(ctx->corr.ensure(pl.corr.size() * 8), "alloc corr");
+    SRS_CK(ctx->tw.ensure(tw.size() * 8), "alloc tw");
+    SRS_CK(cudaMemcpyAsync(ctx->corr.p, pl.corr.data(), pl.corr.size() * 8, cudaMemcpyHostToDevice, ctx->stream), "copy corr");
+    SRS_CK(cudaMemcpyAsync(ctx->tw.p, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice, ctx->stream), "copy tw");
+    SRS_CK(cudaStreamSynchronize(ctx->stream), "sync tables");
+  }
+  SRS_CK(ctx->betas.ensure(pl.beta.size() * 8), "alloc betas");
+  SRS_CK(ctx->nseg.ensure(pl.nseg.size() * 4), "alloc nseg");
+  SRS_CK(cudaMemcpyAsync(ctx->betas.p, pl.beta.data(), pl.beta.size() * 8, cudaMemcpyHostToDevice, ctx->stream), "copy betas");
+  SRS_CK(cudaMemcpyAsync(ctx->nseg.p, pl.nseg.data(), pl.nseg.size() * 4, cudaMemcpyHostToDevice, ctx->stream), "copy nseg");
+  if (mixed && !pl.items.empty()) {
+    SRS_CK(ctx->items.ensure(pl.items.size() * sizeof(Item)), "alloc items");
+    SRS_CK(ctx->item_off.ensure(pl.item_off.size() * 4), "alloc item_off");
+    SRS_CK(cudaMemcpyAsync(ctx->items.p, pl.items.data(), pl.items.size() * sizeof(Item), cudaMemcpyHostToDevice, ctx->stream), "copy items");
+    SRS_CK(cudaMemcpyAsync(ctx->item_off.p, pl.item_off.data(), pl.item_off.size() * 4, cudaMemcpyHostToDevice, ctx->stream), "copy item_off");
+  }
+  SRS_CK(cudaStreamSynchronize(ctx->stream), "sync tables");
+  return SRS_OK;
+}
+
+// Strain on the device: the caller's pointer, or a copy of the first
+// `samples` samples of the caller's host array.
+srs_status stage_strain(srs_ctx* ctx, const void* strain, int64_t samples, int32_t dtype, int on_device,
+                        const void** dev) {
+  if (on_device) {
+    *dev = strain;
+    return SRS_OK;
+  }
+  size_t bytes = (size_t)samples * (dtype == SRS_F64 ? 8 : 4);
+  SRS_CK(ctx->strain.ensure(bytes), "alloc strain");
+  SRS_CK(cudaMemcpyAsync(ctx->strain.p, strain, bytes, cudaMemcpyHostToDevice, ctx->stream), "copy strain");
+  *dev = ctx->strain.p;
+  return SRS_OK;
+}
+
+srs_status check_common(srs_ctx* ctx, const void* strain, int32_t dtype, const srs_params* params) {
+  if (!ctx) return SRS_ERR_ARG;
+  if (!strain) return set_err(ctx, SRS_ERR_ARG, "strain is NULL");
+  if (!params) return set_err(ctx, SRS_ERR_ARG, "params is NULL");
+  if (dtype != SRS_F32 && dtype != SRS_F64) return set_err(ctx, SRS_ERR_ARG, "dtype must be SRS_F32 or SRS_F64");
+  if (params->io_on_device != 0 && params->io_on_device != 1) return set_err(ctx, SRS_ERR_ARG, "io_on_device must be 0 or 1");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_err(ctx, cudaGetLastError(), "cudaSetDevice");
+  return SRS_OK;
+}
+
+std::vector<unsigned char> make_key(int kind, const srs_params* p, int64_t n_samples, int32_t dtype, const double* mc,
+                                    int32_t n_templates, int32_t a, int32_t b) {
+  std::vector<unsigned char> k;
+  auto put = [&](const void* d, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(d);
+    k.insert(k.end(), c, c + n);
+  };
+  put(&kind, sizeof kind);
+  put(p, sizeof *p);
+  put(&n_samples, sizeof n_samples);
+  put(&dtype, sizeof dtype);
+  put(&a, sizeof a);
+  put(&b, sizeof b);
+  put(&n_templates, sizeof n_templates);
+  if (mc && n_templates > 0) put(mc, sizeof(double) * (size_t)n_templates);
+  return k;
+}
+
+// Plan for this call, reusing the context's last plan (and its device tables)
+// when the call kind, sizes, parameters and templates are the same.
+srs_status get_plan(srs_ctx* ctx, int kind, const srs_params* params, const double* mc, int32_t n_templates,
+                    int64_t n_samples, int32_t dtype, bool spectra_mode, int32_t a, int32_t b, const Plan** out) {
+  srs_params key_p = *params;
+  key_p.io_on_device = 0;
+  std::vector<unsigned char> key = make_key(kind, &key_p, n_samples, dtype, mc, n_templates, a, b);
+  if (ctx->have_plan && key == ctx->plan_key) {
+    *out = &ctx->plan;
+    return SRS_OK;
+  }
+  ctx->have_plan = false;
+  std::string msg;
+  srs_status s = make_plan(*params, mc, n_templates, n_samples, spectra_mode, a, b, ctx->plan, msg);
+  if (s != SRS_OK) return set_err(ctx, s, msg);
+  s = upload_tables(ctx, ctx->plan);
+  if (s != SRS_OK) return s;
+  ctx->plan_key.swap(key);
+  ctx->have_plan = true;
+  *out = &ctx->plan;
+  return SRS_OK;
+}
+
+srs_status search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype, const double* mc,
+                       int32_t n_templates, const srs_params* params, float* stat_map, srs_candidate* cands,
+                       int32_t* n_cands, srs_report* report) {
+  srs_status s = check_common(ctx, strain, dtype, params);
+  if (s != SRS_OK) return s;
+  if (!cands || !n_cands) return set_err(ctx, SRS_ERR_ARG, "cands and n_cands are required");
+  const Plan* plp = nullptr;
+  s = get_plan(ctx, 1, params, mc, n_templates, n_samples, dtype, false, 0, 0, &plp);
+  if (s != SRS_OK) return s;
+  const Plan& pl = *plp;
+  const bool mixed = pl.precision == SRS_MIXED;
+  const bool f64 = dtype == SRS_F64;
+  const int on_dev = params->io_on_device;
+  int32_t max_seg = *std::max_element(pl.nseg.begin(), pl.nseg.end());
+  const void* dstrain = nullptr;
+  s = stage_strain(ctx, strain, (int64_t)max_seg * pl.n_s, dtype, on_dev, &dstrain);
+  if (s != SRS_OK) return s;
+
+  const long long n_map = (long long)n_templates * pl.n_bins;
+  const int k = (int)std::min<long long>(pl.top_k, n_map);
+  float* dmap = nullptr;
+  if (stat_map) {
+    if (on_dev) {
+      dmap = stat_map;
+    } else {
+      SRS_CK(ctx->map.ensure(n_map * 4), "alloc map");
+      dmap = ctx->map.as<float>();
+    }
+  }
+  SRS_CK(ctx->keys.ensure(n_map * 8), "alloc keys");
+  long long tiles = (n_map + kTopkTile - 1) / kTopkTile;
+  SRS_CK(ctx->topk_a.ensure(std::max<long long>(tiles, 1) * k * 8), "alloc topk");
+  SRS_CK(ctx->topk_b.ensure(std::max<long long>(tiles, 1) * k * 8), "alloc topk");
+  srs_candidate* dc = on_dev ? cands : nullptr;
+  if (!on_dev) {
+    SRS_CK(ctx->cands.ensure((size_t)k * sizeof(srs_candidate)), "alloc cands");
+    dc = ctx->cands.as<srs_candidate>();
+  }
+  int launches = 0;
+  const long long n_items = (long long)pl.items.size();
+  if (mixed) {
+    const long long n_anch = pl.n_spectra * pl.n_anchor;
+    SRS_CK(ctx->anchors.ensure(n_anch * sizeof(Anchor)), "alloc anchors");
+    SRS_CK(ctx->partial.ensure(n_items * pl.n_bins * 4), "alloc partial");
+    SRS_CK(ctx->queue.ensure(64), "alloc queue");
+  } else {
+    SRS_CK(ctx->S.ensure(n_map * 8), "alloc S");
+  }
+
+  SRS_CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
+  if (mixed) {
+    MixedArgs a = mixed_args(pl, ctx, 0, 0);
+    SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
+    SRS_CK(launch_anchors(ctx->items.as<Item>(), (int)n_items, ctx->betas.as<double>(), anchor_args(pl),
+                          ctx->anchors.as<Anchor>(), pl.n_spectra * pl.n_anchor, ctx->n_sm, ctx->stream), "k_anchors");
+    ++launches;
+    SRS_CK(cudaEventRecord(ctx->ev2, ctx->stream), "event");
+    SRS_CK(launch_mixed(f64, false, pl.w, dstrain, ctx->items.as<Item>(), (int)n_items, ctx->anchors.as<Anchor>(),
+                        ctx->queue.as<int>(), a, ctx->partial.as<float>(), nullptr, ctx->n_sm, 0, ctx->stream), "k_mixed");
+    SRS_CK(cudaEventRecord(ctx->ev3, ctx->stream), "event");
+    ++launches;
+    SRS_CK(launch_reduce_mixed(ctx->partial.as<float>(), ctx->item_off.as<int>(), ctx->nseg.as<int>(), n_templates,
+                               pl.n_bins, dmap, ctx->keys.as<unsigned long long>(), ctx->stream), "k_reduce_mixed");
+    ++launches;
+  } else {
+    PlainArgs p = plain_args(pl, ctx, 0, 0);
+    SRS_CK(cudaMemsetAsync(ctx->S.p, 0, n_map * 8, ctx->stream), "memset S");
+    SRS_CK(cudaEventRecord(ctx->ev2, ctx->stream), "event");
+    SRS_CK(launch_plain(f64, false, dstrain, ctx->betas.as<double>(), ctx->nseg.as<int>(), p, max_seg, n_templates,
+                        ctx->S.as<double>(), nullptr, ctx->stream), "k_plain");
+    SRS_CK(cudaEventRecord(ctx->ev3, ctx->stream), "event");
+    ++launches;
+    SRS_CK(launch_finish_plain(ctx->S.as<double>(), ctx->nseg.as<int>(), n_templates, pl.n_bins, dmap,
+                               ctx->keys.as<unsigned long long>(), ctx->n_sm, ctx->stream), "k_finish_plain");
+    ++launches;
+  }
+  const unsigned long long* top = nullptr;
+  SRS_CK(launch_topk(ctx->keys.as<unsigned long long>(), n_map, k, ctx->topk_a.as<unsigned long long>(),
+                     ctx->topk_b.as<unsigned long long>(), &top, &launches, ctx->stream), "k_topk_tile");
+  SRS_CK(launch_keys_to_cands(top, k, pl.n_bins, dc, ctx->stream), "k_keys_to_cands");
+  ++launches;
+  SRS_CK(cudaEventRecord(ctx->ev1, ctx->stream), "event");
+  if (!on_dev) {
+    SRS_CK(cudaMemcpyAsync(cands, dc, (size_t)k * sizeof(srs_candidate), cudaMemcpyDeviceToHost, ctx->stream), "copy cands");
+    if (stat_map) SRS_CK(cudaMemcpyAsync(stat_map, dmap, n_map * 4, cudaMemcpyDeviceToHost, ctx->stream), "copy map");
+  }
+  SRS_CK(cudaStreamSynchronize(ctx->stream), "search");
+  *n_cands = k;
+  if (report) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    report->device_ms = ms;
+    report->n_spectra = pl.n_spectra;
+    report->spectra_per_s = ms > 0 ? pl.n_spectra / (ms * 1e-3) : 0.0;
+    report->w = pl.w;
+    report->n_fine = pl.n_fine;
+    report->sigma = pl.sigma;
+    report->beta_es = pl.beta_es;
+    report->chunk = mixed ? pl.chunk : 1;
+    report->n_items = mixed ? (int32_t)n_items : (int32_t)pl.n_spectra;
+    report->kernel_launches = launches;
+    float sms = 0.f;
+    cudaEventElapsedTime(&sms, ctx->ev2, ctx->ev3);
+    report->spread_ms = sms;
+  }
+  return SRS_OK;
+}
+
+srs_status spectra_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype, const double* mc,
+                        int32_t n_templates, int32_t seg_begin, int32_t seg_end, const srs_params* params,
+                        double* F, srs_report* report) {
+  srs_status s = check_common(ctx, strain, dtype, params);
+  if (s != SRS_OK) return s;
+  if (!F) return set_err(ctx, SRS_ERR_ARG, "F is NULL");
+  const Plan* plp = nullptr;
+  s = get_plan(ctx, 2, params, mc, n_templates, n_samples, dtype, true, seg_begin, seg_end, &plp);
+  if (s != SRS_OK) return s;
+  const Plan& pl = *plp;
+  const bool mixed = pl.precision == SRS_MIXED;
+  const bool f64 = dtype == SRS_F64;
+  const int on_dev = params->io_on_device;
+  const void* dstrain = nullptr;
+  s = stage_strain(ctx, strain, (int64_t)seg_end * pl.n_s, dtype, on_dev, &dstrain);
+  if (s != SRS_OK) return s;
+  const int range = seg_end - seg_begin;
+  const size_t fbytes = (size_t)n_templates * range * pl.n_bins * 16;
+  double2* dF = reinterpret_cast<double2*>(F);
+  if (!on_dev) {
+    SRS_CK(ctx->F.ensure(fbytes), "alloc F");
+    dF = ctx->F.as<double2>();
+  }
+  int launches = 0;
+  SRS_CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
+  if (mixed) {
+    const long long n_items = (long long)pl.items.size();
+    SRS_CK(ctx->anchors.ensure(pl.n_spectra * pl.n_anchor * sizeof(Anchor)), "alloc anchors");
+    SRS_CK(ctx->queue.ensure(64), "alloc queue");
+    SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
+    SRS_CK(launch_anchors(ctx->items.as<Item>(), (int)n_items, ctx->betas.as<double>(), anchor_args(pl),
+                          ctx->anchors.as<Anchor>(), pl.n_spectra * pl.n_anchor, ctx->n_sm, ctx->stream), "k_anchors");
+    MixedArgs a = mixed_args(pl, ctx, seg_begin, range);
+    SRS_CK(launch_mixed(f64, true, pl.w, dstrain, ctx->items.as<Item>(), (int)n_items, ctx->anchors.as<Anchor>(),
+                        ctx->queue.as<int>(), a, nullptr, dF, ctx->n_sm, 0, ctx->stream), "k_mixed");
+    launches += 2;
+  } else {
+    PlainArgs p = plain_args(pl, ctx, seg_begin, range);
+    SRS_CK(launch_plain(f64, true, dstrain, ctx->betas.as<double>(), ctx->nseg.as<int>(), p, range, n_templates,
+                        nullptr, dF, ctx->stream), "k_plain");
+    launches += 1;
+  }
+  SRS_CK(cudaEventRecord(ctx->ev1, ctx->stream), "event");
+  if (!on_dev) SRS_CK(cudaMemcpyAsync(F, dF, fbytes, cudaMemcpyDeviceToHost, ctx->stream), "copy F");
+  SRS_CK(cudaStreamSynchronize(ctx->stream), "spectra");
+  if (report) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    std::memset(report, 0, sizeof *report);
+    report->device_ms = ms;
+    report->n_spectra = pl.n_spectra;
+    report->spectra_per_s = ms > 0 ? pl.n_spectra / (ms * 1e-3) : 0.0;
+    report->w = pl.w;
+    report->n_fine = pl.n_fine;
+    report->sigma = pl.sigma;
+    report->beta_es = pl.beta_es;
+    report->chunk = pl.chunk;
+    report->n_items = (int32_t)pl.items.size();
+    report->kernel_launches = launches;
+  }
+  return SRS_OK;
+}
+
+srs_status time_map_impl(srs_ctx* ctx, const double* mc, int32_t n_templates, const int32_t* item_m,
+                         const int32_t* item_i, int32_t n_items, const srs_params* params, int64_t n_samples,
+                         double* psi_out, double* theta_out) {
+  if (!ctx) return SRS_ERR_ARG;
+  if (!params || !item_m || !item_i || !psi_out || !theta_out || n_items <= 0)
+    return set_err(ctx, SRS_ERR_ARG, "time_map: NULL argument or no items");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_err(ctx, cudaGetLastError(), "cudaSetDevice");
+  int32_t max_i = 0;
+  for (int32_t k = 0; k < n_items; ++k) {
+    if (item_m[k] < 0 || item_m[k] >= n_templates || item_i[k] < 0) return set_err(ctx, SRS_ERR_ARG, "time_map: item out of range");
+    max_i = std::max(max_i, item_i[k]);
+  }
+  Plan pl;
+  std::string msg;
+  srs_status s = make_plan(*params, mc, n_templates, n_samples, true, 0, 1, pl, msg);
+  if (s != SRS_OK) return set_err(ctx, s, msg);
+  if (max_i >= pl.n_seg_total) return set_err(ctx, SRS_ERR_ARG, "time_map: segment beyond the strain");
+  for (int32_t k = 0; k < n_items; ++k) {
+    // Sec. II: every sample of the segment must precede coalescence
+    double t_last = ((double)(item_i[k] + 1) * (double)pl.n_s - 1.0) / pl.fs;
+    if (!(1.0 - 8.0 / 3.0 * pl.beta[item_m[k]] * t_last > 0.0))
+      return set_err(ctx, SRS_ERR_DOMAIN, "time_map: a segment reaches coalescence (1 - 8/3 beta t <= 0)");
+  }
+  ctx->have_plan = false;
+  s = upload_tables(ctx, pl);
+  if (s != SRS_OK) return s;
+  const size_t out_bytes = (size_t)n_items * pl.n_s * 8;
+  SRS_CK(ctx->psi.ensure(out_bytes), "alloc psi");
+  SRS_CK(ctx->th.ensure(out_bytes), "alloc th");
+  if (pl.precision == SRS_MIXED) {
+    std::vector<Item> its(n_items);
+    for (int32_t k = 0; k < n_items; ++k) its[k] = Item{item_m[k], item_i[k], item_i[k] + 1, k};
+    SRS_CK(ctx->items.ensure(its.size() * sizeof(Item)), "alloc items");
+    SRS_CK(cudaMemcpyAsync(ctx->items.p, its.data(), its.size() * sizeof(Item), cudaMemcpyHostToDevice, ctx->stream), "copy items");
+    SRS_CK(ctx->anchors.ensure((size_t)n_items * pl.n_anchor * sizeof(Anchor)), "alloc anchors");
+    SRS_CK(launch_anchors(ctx->items.as<Item>(), n_items, ctx->betas.as<double>(), anchor_args(pl),
+                          ctx->anchors.as<Anchor>(), (long long)n_items * pl.n_anchor, ctx->n_sm, ctx->stream), "k_anchors");
+    MixedArgs a = mixed_args(pl, ctx, 0, 0);
+    SRS_CK(launch_time_map_mixed(ctx->anchors.as<Anchor>(), n_items, a, ctx->psi.as<double>(), ctx->th.as<double>(),
+                                 ctx->stream), "k_time_map_mixed");
+  } else {
+    SRS_CK(ctx->im.ensure((size_t)n_items * 4), "alloc im");
+    SRS_CK(ctx->ii.ensure((size_t)n_items * 4), "alloc ii");
+    SRS_CK(cudaMemcpyAsync(ctx->im.p, item_m, (size_t)n_items * 4, cudaMemcpyHostToDevice, ctx->stream), "copy im");
+    SRS_CK(cudaMemcpyAsync(ctx->ii.p, item_i, (size_t)n_items * 4, cudaMemcpyHostToDevice, ctx->stream), "copy ii");
+    PlainArgs p = plain_args(pl, ctx, 0, 0);
+    SRS_CK(launch_time_map_plain(ctx->im.as<int>(), ctx->ii.as<int>(), n_items, ctx->betas.as<double>(), p,
+                                 ctx->psi.as<double>(), ctx->th.as<double>(), ctx->stream), "k_time_map_plain");
+  }
+  SRS_CK(cudaMemcpyAsync(psi_out, ctx->psi.p, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy psi");
+  SRS_CK(cudaMemcpyAsync(theta_out, ctx->th.p, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy th");
+  SRS_CK(cudaStreamSynchronize(ctx->stream), "time_map");
+  return SRS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+srs_status srs_create(srs_ctx** out, int device, void* cuda_stream) {
+  if (!out) return SRS_ERR_ARG;
+  *out = nullptr;
+  srs_ctx* c = new (std::nothrow) srs_ctx();
+  if (!c) return SRS_ERR_OOM;
+  int n_dev = 0;
+  if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) {
+    cudaGetLastError();
+    delete c;
+    return device < 0 ? SRS_ERR_ARG : SRS_ERR_CUDA;
+  }
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return SRS_ERR_CUDA;
+  }
+  if (cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return SRS_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+      cudaEventCreate(&c->ev2) != cudaSuccess || cudaEventCreate(&c->ev3) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return SRS_ERR_CUDA;
+  }
+  *out = c;
+  return SRS_OK;
+}
+
+void srs_destroy(srs_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (DevBuf* b : {&c->items, &c->anchors, &c->partial, &c->betas, &c->nseg, &c->item_off, &c->corr, &c->tw,
+                    &c->keys, &c->topk_a, &c->topk_b, &c->cands, &c->queue, &c->strain, &c->map, &c->S, &c->F,
+                    &c->psi, &c->th, &c->im, &c->ii})
+    b->release();
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->ev2) cudaEventDestroy(c->ev2);
+  if (c->ev3) cudaEventDestroy(c->ev3);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* srs_last_error(const srs_ctx* c) {
+  if (!c) return "no context";
+  return c->err.c_str();
+}
+
+srs_status srs_plan(const srs_params* params, const double* mc, int32_t n_templates, int64_t n_samples,
+                    srs_plan_info* info, double* beta_out, int32_t* nseg_out) {
+  if (!params) return SRS_ERR_ARG;
+  try {
+    Plan pl;
+    std::string msg;
+    srs_status s = make_plan(*params, mc, n_templates, n_samples, false, 0, 0, pl, msg);
+    if (s != SRS_OK) return s;
+    fill_info(pl, info);
+    for (int32_t m = 0; m < n_templates; ++m) {
+      if (beta_out) beta_out[m] = pl.beta[m];
+      if (nseg_out) nseg_out[m] = pl.nseg[m];
+    }
+    return SRS_OK;
+  } catch (...) {
+    return SRS_ERR_OOM;
+  }
+}
+
+srs_status srs_search(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype, const double* mc,
+                      int32_t n_templates, const srs_params* params, float* stat_map, srs_candidate* cands,
+                      int32_t* n_cands, srs_report* report) {
+  try {
+    return search_impl(ctx, strain, n_samples, dtype, mc, n_templates, params, stat_map, cands, n_cands, report);
+  } catch (const std::bad_alloc&) {
+    return set_err(ctx, SRS_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return set_err(ctx, SRS_ERR_ARG, "unexpected host error");
+  }
+}
+
+srs_status srs_segment_spectra(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype,
+                               const double* mc, int32_t n_templates, int32_t seg_begin, int32_t seg_end,
+                               const srs_params* params, double* F, srs_report* report) {
+  try {
+    return spectra_impl(ctx, strain, n_samples, dtype, mc, n_templates, seg_begin, seg_end, params, F, report);
+  } catch (const std::bad_alloc&) {
+    return set_err(ctx, SRS_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return set_err(ctx, SRS_ERR_ARG, "unexpected host error");
+  }
+}
+
+srs_status srs_time_map(srs_ctx* ctx, const double* mc, int32_t n_templates, const int32_t* item_m,
+                        const int32_t* item_i, int32_t n_items, const srs_params* params, int64_t n_samples,
+                        double* psi_out, double* theta_out) {
+  try {
+    return time_map_impl(ctx, mc, n_templates, item_m, item_i, n_items, params, n_samples, psi_out, theta_out);
+  } catch (const std::bad_alloc&) {
+    return set_err(ctx, SRS_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return set_err(ctx, SRS_ERR_ARG, "unexpected host error");
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// srs_internal.h -- structures shared by the host planner, the C ABI layer and
+// the CUDA kernels of libsrs.  Not part of the public ABI (include/srs.h is).
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "../../include/srs.h"
+
+namespace srs {
+
+// Threads per CTA of the mixed-precision spreader; each thread owns a run of
+// consecutive samples, each warp one FP64 anchor (see Anchor).
+constexpr int kSpreadThreads = 256;
+constexpr int kSpreadWarps = kSpreadThreads / 32;
+// Largest kernel width the mixed form is compiled for (eps >= 1e-7 needs <= 8).
+constexpr int kMixedMaxW = 8;
+// Largest kernel width of the plain FP64 form.
+constexpr int kPlainMaxW = 16;
+
+// One work item of the mixed form: segments [i0, i1) of template m; their
+// anchors start at row g0 of the anchor table.
+struct Item {
+  int32_t m, i0, i1, g0;
+};
+
+// FP64-derived description of the resampled time over one warp's span of
+// samples l = 0 .. span-1 from sample index l_a of a segment (Sec. III.B,
+// Eq. new_t expanded around the anchor):
+//   delta(l_a + l)/t_coh = psi0 + P1 l + P2 l^2 + P3 l^3 + P4 l^4 + P5 l^5   [periods]
+//   f_c * delta(l_a + l)   = th0 + M1 l + k_c (P2 l^2 + ... + P5 l^5)          [cycles]
+// psi0, th0: fractions of a period / cycle as unsigned 32-bit fixed point;
+// n1, m1: the linear coefficients as 32-bit fixed point (mod 1) with the
+// rounding residual kept in p1lo / m1lo (FP32); P2..P5 in FP32.
+struct Anchor {
+  uint32_t psi0, n1, th0, m1;
+  float p1lo, m1lo, p2, p3;
+  float p4, p5, pad0, pad1;
+};
+static_assert(sizeof(Anchor) == 48, "anchor layout");
+
+// Everything the kernels need about one call, resolved on the host.
+struct Plan {
+  // problem
+  double fs = 0, t_coh = 0, f_lo = 0, f_hi = 0, f_ref = 0, eps = 0;
+  int64_t n_samples = 0, n_s = 0;
+  int32_t n_seg_total = 0, n_bins = 0, half_bins = 0;  // k = b - half_bins
+  double f_c = 0, k_c = 0;                               // demodulation frequency, f_c * t_coh
+  int32_t n_templates = 0, top_k = 0, precision = 1, cut = 1;
+  // NUFFT
+  int32_t n_fine = 0, w = 0;
+  double sigma = 0, beta_es = 0;
+  std::vector<int32_t> radices;                          // Stockham passes, product n_fine
+  // templates
+  std::vector<double> beta;                              // per template
+  std::vector<int32_t> nseg;                             // per template
+  int64_t n_spectra = 0;
+  // mixed form work decomposition
+  int32_t run = 0, span = 0, n_anchor = 0;               // samples per thread / per warp / anchors per segment
+  int32_t chunk = 0;
+  std::vector<Item> items;
+  std::vector<int32_t> item_off;                         // [n_templates+1] first item of template m
+  // tables (FP64, converted by the launcher)
+  std::vector<double> corr;                              // [n_bins] deconvolution factor
+  std::vector<double> tw_re, tw_im;                      // [n_fine] exp(-2 pi i m / n_fine)
+};
+
+// Host planner (srs_plan.cpp).  Returns SRS_OK or an error with `msg` set.
+srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
+                     int64_t n_samples, bool need_segments_all, int32_t seg_begin,
+                     int32_t seg_end, Plan& out, std::string& msg);
+void fill_info(const Plan& pl, srs_plan_info* info);
+// Work items of the mixed form for a given chunk size (search: each template's
+// first nseg_m segments; spectra: [seg_begin, seg_end) of every template).
+void make_items(Plan& pl, int32_t chunk, bool spectra_mode, int32_t seg_begin, int32_t seg_end);
+
+}  // namespace srs

@@ -1,0 +1,684 @@
+// srs_kernels.cu -- sm_103a kernels of the semicoherent NUFFT resampling search.
+//
+// Sec. III.B of arXiv:2609.12476: each coherent segment is resampled with the
+// 0PN time tau(t; beta) of Eq. (new_t) and its spectrum is taken with a type-1
+// NUFFT (spread onto an oversampled grid with an exponential-of-semicircle
+// kernel, FFT, divide by the kernel's transform).  Sec. III.C: powers
+// (Eq. normalized_power), equal-weight sum over segments into n_sigma
+// (Eqs. weights, semicoherent_statistic), then top-k.
+//
+// Two forms:
+//   mixed  -- k_anchors (FP64, a few samples per segment) + k_mixed (FP32
+//             spreading, shared-memory Stockham FFT, FP32 power/sum) as a
+//             persistent kernel over (template, segment-chunk) items, then an
+//             ordered reduction and top-k;
+//   plain  -- k_plain: one CTA per spectrum, every step in FP64.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "srs_internal.h"
+#include "srs_kernels.h"
+
+namespace srs {
+
+// ---------------------------------------------------------------------------
+// small complex helpers
+// ---------------------------------------------------------------------------
+template <typename R> struct cplx;
+template <> struct cplx<float> { using T = float2; };
+template <> struct cplx<double> { using T = double2; };
+
+template <typename C> __device__ __forceinline__ C cmk(decltype(C::x) a, decltype(C::x) b) { C c; c.x = a; c.y = b; return c; }
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) { return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return cmk<C>(a.x * s, a.y * s); }
+// i * a
+template <typename C> __device__ __forceinline__ C cmuli(C a) { return cmk<C>(-a.y, a.x); }
+
+// ---------------------------------------------------------------------------
+// R-point forward DFTs, y_k = sum_r v_r exp(-2 pi i r k / R)
+// ---------------------------------------------------------------------------
+template <typename C, int R> struct Dft;
+template <typename C> struct Dft<C, 2> {
+  static __device__ __forceinline__ void run(C* v) { C a = v[0], b = v[1]; v[0] = cadd(a, b); v[1] = csub(a, b); }
+};
+template <typename C> struct Dft<C, 3> {
+  static __device__ __forceinline__ void run(C* v) {
+    using R_ = decltype(C::x);
+    const R_ c = R_(-0.5), s = R_(-0.86602540378443864676);   // cos, sin of -2pi/3... sin(-2pi/3)
+    C t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+    C m = cadd(v[0], cscale(t1, c));
+    C is = cmuli(cscale(t2, s));
+    v[0] = cadd(v[0], t1);
+    v[1] = cadd(m, is);
+    v[2] = csub(m, is);
+  }
+};
+template <typename C> struct Dft<C, 4> {
+  static __device__ __forceinline__ void run(C* v) {
+    C a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+    C c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+    C id = cmuli(d);
+    v[0] = cadd(a, c);
+    v[2] = csub(a, c);
+    v[1] = csub(b, id);   // b - i d
+    v[3] = cadd(b, id);   // b + i d
+  }
+};
+template <typename C> struct Dft<C, 5> {
+  static __device__ __forceinline__ void run(C* v) {
+    using R_ = decltype(C::x);
+    // cos(2pi/5), cos(4pi/5), -sin(2pi/5), -sin(4pi/5)
+    const R_ c1 = R_(0.30901699437494742410), c2 = R_(-0.80901699437494742410);
+    const R_ s1 = R_(-0.95105651629515357212), s2 = R_(-0.58778525229247312917);
+    C t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+    C t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+    C a1 = cadd(v[0], cadd(cscale(t1, c1), cscale(t2, c2)));
+    C a2 = cadd(v[0], cadd(cscale(t1, c2), cscale(t2, c1)));
+    C b1 = cmuli(cadd(cscale(t3, s1), cscale(t4, s2)));
+    C b2 = cmuli(csub(cscale(t3, s2), cscale(t4, s1)));
+    v[0] = cadd(v[0], cadd(t1, t2));
+    v[1] = cadd(a1, b1);
+    v[4] = csub(a1, b1);
+    v[2] = cadd(a2, b2);
+    v[3] = csub(a2, b2);
+  }
+};
+
+// One Stockham autosort pass of radix R over n points (Ns = product of the
+// radices already applied).  Butterfly j reads in[j + r n/R], multiplies by
+// the twiddles exp(-2 pi i (j mod Ns) r / (Ns R)), transforms, and writes
+// out[(j - j mod Ns) R + j mod Ns + r Ns].
+template <typename C, int R>
+__device__ __forceinline__ void stockham_pass(const C* __restrict__ in, C* __restrict__ out, int n, int Ns,
+                                              const C* __restrict__ tw) {
+  const int nR = n / R;
+  const int step = n / (Ns * R);
+  for (int j = threadIdx.x; j < nR; j += blockDim.x) {
+    const int jm = j % Ns;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in[j + r * nR];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[jm * r * step]);
+    }
+    Dft<C, R>::run(v);
+    const int idxD = (j - jm) * R + jm;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[idxD + r * Ns] = v[r];
+  }
+}
+
+// Forward FFT of a[0..n) in shared memory, ping-ponging with b.  Returns the
+// buffer that holds the result.  Every thread of the block must call it.
+template <typename C>
+__device__ C* fft_smem(C* a, C* b, int n, const int8_t* radices, int n_pass, const C* __restrict__ tw) {
+  int Ns = 1;
+  for (int p = 0; p < n_pass; ++p) {
+    const int R = radices[p];
+    switch (R) {
+      case 2: stockham_pass<C, 2>(a, b, n, Ns, tw); break;
+      case 3: stockham_pass<C, 3>(a, b, n, Ns, tw); break;
+      case 4: stockham_pass<C, 4>(a, b, n, Ns, tw); break;
+      default: stockham_pass<C, 5>(a, b, n, Ns, tw); break;
+    }
+    __syncthreads();
+    C* t = a; a = b; b = t;
+    Ns *= R;
+  }
+  return a;
+}
+
+// ---------------------------------------------------------------------------
+// PTX helpers (documented single instructions)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// ---------------------------------------------------------------------------
+// K1: FP64 anchors of the resampled time (Eq. new_t), one thread per
+// (segment, anchor).  Segment g belongs to the item with the largest g0 <= g.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t frac_to_u32(double f) {  // f in [0, 1)
+  long long v = __double2ll_rn(f * 4294967296.0);
+  return (uint32_t)(v & 0xffffffffLL);
+}
+
+__global__ void k_anchors(const Item* __restrict__ items, int n_items, const double* __restrict__ betas,
+                          AnchorArgs aa, Anchor* __restrict__ out, long long total) {
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long g = idx / aa.n_anchor;
+    const int ai = (int)(idx - g * aa.n_anchor);
+    int lo = 0, hi = n_items - 1;
+    while (lo < hi) {  // largest q with items[q].g0 <= g
+      int mid = (lo + hi + 1) >> 1;
+      if (items[mid].g0 <= g) lo = mid; else hi = mid - 1;
+    }
+    const Item it = items[lo];
+    const int i = it.i0 + (int)(g - it.g0);
+    const double b = betas[it.m];
+    const double t_i0 = (double)i * (double)aa.n_s / aa.fs;
+    const double a = 1.0 - (8.0 / 3.0) * b * t_i0;
+    const double a58 = exp(0.625 * log(a));                       // a^(5/8)
+    const double s0 = (double)ai * (double)aa.span / aa.fs;
+    const double x = (8.0 / 3.0) * b * s0 / a;
+    const double L = log1p(-x);                                     // log(A / a)
+    const double d0 = 3.0 * a58 / (5.0 * b) * (-expm1(0.625 * L)); // delta(s0)
+    const double e1 = (a58 / a) * exp(-0.375 * L);                  // A^(-3/8) = d delta / ds
+    const double A = a * (1.0 - x);                                 // 1 - 8/3 beta (t_i0 + s0)
+    Anchor an;
+    double psi = d0 / aa.t_coh;
+    an.psi0 = frac_to_u32(psi - floor(psi));
+    double P1 = e1 / (aa.fs * aa.t_coh);
+    double P1f = P1 - floor(P1);
+    double N1 = rint(P1f * 4294967296.0);
+    an.n1 = (uint32_t)((long long)N1 & 0xffffffffLL);
+    an.p1lo = (float)(P1f - N1 * 2.3283064365386962890625e-10);
+    double th = aa.f_c * d0;
+    an.th0 = frac_to_u32(th - floor(th));
+    double M1 = aa.f_c * e1 / aa.fs;
+    double M1f = M1 - floor(M1);
+    double Mr = rint(M1f * 4294967296.0);
+    an.m1 = (uint32_t)((long long)Mr & 0xffffffffLL);
+    an.m1lo = (float)(M1f - Mr * 2.3283064365386962890625e-10);
+    // Taylor coefficients of delta around the anchor, per sample, in periods:
+    // E_{k+1} = E_k * (8/3)(3/8 + k - 1) beta / (A fs (k + 1)).
+    const double r = b / (A * aa.fs);
+    const double E1 = e1 / aa.fs;
+    const double E2 = E1 * r * 0.5;
+    const double E3 = E2 * r * (11.0 / 9.0);
+    const double E4 = E3 * r * (19.0 / 12.0);
+    const double E5 = E4 * r * (9.0 / 5.0);
+    an.p2 = (float)(E2 / aa.t_coh);
+    an.p3 = (float)(E3 / aa.t_coh);
+    an.p4 = (float)(E4 / aa.t_coh);
+    an.p5 = (float)(E5 / aa.t_coh);
+    an.pad0 = 0.f;
+    an.pad1 = 0.f;
+    out[idx] = an;
+  }
+}
+
+// Phase of sample l (0 <= l < span) of an anchor's span: the fine-grid phase
+// Psi (unsigned 32-bit fixed point, periods of t_coh) and the demodulation
+// phase th = f_c delta mod 1 in [-0.5, 0.5] (cycles).
+__device__ __forceinline__ void mixed_phase(const Anchor& A, int l, float kc, uint32_t& Psi, float& th) {
+  const float lf = (float)l;
+  const float cq = fmaf(fmaf(fmaf(A.p5, lf, A.p4), lf, A.p3), lf, A.p2) * (lf * lf);
+  const float cpsi = fmaf(A.p1lo, lf, cq);
+  Psi = A.psi0 + (uint32_t)l * A.n1 + (uint32_t)__float2int_rn(cpsi * 4294967296.0f);
+  const float cth = fmaf(A.m1lo, lf, kc * cq);
+  float t = (float)(int32_t)(A.th0 + (uint32_t)l * A.m1) * 2.3283064365386963e-10f + cth;
+  th = t - rintf(t);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed form: persistent spread + FFT + deconvolution + power/segment sum.
+// ---------------------------------------------------------------------------
+template <int W>
+__device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2* __restrict__ grid,
+                                           const Anchor& A, int j_begin, int j_end, int l_base,
+                                           const MixedArgs& a) {
+  float acc_re[W], acc_im[W];
+#pragma unroll
+  for (int t = 0; t < W; ++t) { acc_re[t] = 0.f; acc_im[t] = 0.f; }
+  const int n = a.n_fine;
+  int Bm = -1;  // fine-grid cell of acc[0]
+  for (int j = j_begin; j < j_end; ++j) {
+    uint32_t Psi;
+    float th;
+    mixed_phase(A, j - l_base, a.kc, Psi, th);
+    const int cell = (int)__umulhi(Psi, (uint32_t)n);
+    const float fr = (float)(Psi * (uint32_t)n) * 2.3283064365386963e-10f;
+    float sn, cs;
+    __sincosf(6.28318530717958647692f * th, &sn, &cs);
+    const float xv = xs[j];
+    const float cre = xv * cs, cim = -xv * sn;
+    const float off = ceilf(fr - 0.5f * (float)W);
+    int l0 = cell + (int)off;
+    if (l0 < 0) l0 += n; else if (l0 >= n) l0 -= n;
+    if (Bm < 0) Bm = l0;
+    int d = l0 - Bm;
+    if (d < -(n >> 1)) d += n;
+    // slide the register window forward to l0, flushing cells that leave it
+    for (int s = 0; s < W && d > 0; ++s, --d) {
+      atomicAdd(&grid[Bm].x, acc_re[0]);
+      atomicAdd(&grid[Bm].y, acc_im[0]);
+#pragma unroll
+      for (int t = 0; t < W - 1; ++t) { acc_re[t] = acc_re[t + 1]; acc_im[t] = acc_im[t + 1]; }
+      acc_re[W - 1] = 0.f;
+      acc_im[W - 1] = 0.f;
+      Bm = (Bm + 1 == n) ? 0 : Bm + 1;
+    }
+    if (d > 0) { Bm += d; if (Bm >= n) Bm -= n; }
+    float z = (off - fr) * a.two_over_w;
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+      const float q = fmaxf(fmaf(-z, z, 1.0f), 0.0f);
+      const float ph = ex2_approx(a.es_beta_log2e * (sqrt_approx(q) - 1.0f));
+      acc_re[t] = fmaf(ph, cre, acc_re[t]);
+      acc_im[t] = fmaf(ph, cim, acc_im[t]);
+      z += a.two_over_w;
+    }
+  }
+  if (Bm >= 0) {
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+      int c = Bm + t;
+      if (c >= n) c -= n;
+      atomicAdd(&grid[c].x, acc_re[t]);
+      atomicAdd(&grid[c].y, acc_im[t]);
+    }
+  }
+}
+
+template <typename TIN, int W, bool SPECTRA>
+__global__ void __launch_bounds__(kSpreadThreads)
+k_mixed(const TIN* __restrict__ strain, const Item* __restrict__ items, int n_items,
+        const Anchor* __restrict__ anchors, int* __restrict__ queue, MixedArgs a,
+        float* __restrict__ partial, double2* __restrict__ Fout) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* g0 = reinterpret_cast<float2*>(smem);
+  float2* g1 = g0 + a.n_fine;
+  float* Z = reinterpret_cast<float*>(g1 + a.n_fine);
+  Anchor* anc = reinterpret_cast<Anchor*>(Z + ((a.n_bins + 3) & ~3));
+  float* xs = reinterpret_cast<float*>(anc + kSpreadWarps);
+  __shared__ int s_item;
+  __shared__ int8_t s_rad[16];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid < 16) s_rad[tid] = a.radices[tid];
+  const float2* __restrict__ tw = reinterpret_cast<const float2*>(a.tw);
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(queue, 1);
+    __syncthreads();
+    const int q = s_item;
+    if (q >= n_items) break;
+    const Item it = items[q];
+    if (!SPECTRA)
+      for (int b = tid; b < a.n_bins; b += blockDim.x) Z[b] = 0.f;
+    for (int i = it.i0; i < it.i1; ++i) {
+      const long long g = (long long)it.g0 + (i - it.i0);
+      const TIN* src = strain + (long long)i * a.n_s;
+      for (int j = tid; j < a.n_s; j += blockDim.x) xs[j] = (float)src[j];
+      for (int j = tid; j < a.n_fine; j += blockDim.x) g0[j] = make_float2(0.f, 0.f);
+      if (tid < a.n_anchor) anc[tid] = anchors[g * a.n_anchor + tid];
+      __syncthreads();
+      {
+        const int j0 = (warp * 32 + lane) * a.run;
+        const int j1 = min(j0 + a.run, a.n_s);
+        if (j0 < a.n_s) spread_run<W>(xs, g0, anc[warp], j0, j1, warp * a.span, a);
+      }
+      __syncthreads();
+      float2* res = fft_smem<float2>(g0, g1, a.n_fine, s_rad, a.n_pass, tw);
+      for (int b = tid; b < a.n_bins; b += blockDim.x) {
+        int k = b - a.half_bins;
+        int idx = k < 0 ? k + a.n_fine : k;
+        const float2 G = res[idx];
+        const float c = a.corr[b];
+        const float fx = G.x * c, fy = G.y * c;
+        if (SPECTRA) {
+          Fout[((long long)it.m * a.seg_range + (i - a.seg_begin)) * a.n_bins + b] = make_double2(fx, fy);
+        } else {
+          // (P - 2) / 2 with P = 2 |F|^2 / n_s (mu = sigma = 2)
+          Z[b] += fmaf(fx, fx, fy * fy) * a.inv_ns - 1.0f;
+        }
+      }
+      __syncthreads();
+    }
+    if (!SPECTRA)
+      for (int b = tid; b < a.n_bins; b += blockDim.x) partial[(long long)q * a.n_bins + b] = Z[b];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Plain FP64 form: one CTA per (template, segment) spectrum.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void plain_phase(double b, double a, double pre, double s, const PlainArgs& p,
+                                            double& psi, double& th) {
+  const double x = (8.0 / 3.0) * b * s / a;
+  const double d = pre * (-expm1(0.625 * log1p(-x)));   // delta(s), Eq. (new_t) referenced to t_i0
+  psi = d / p.t_coh;
+  psi -= floor(psi);
+  th = p.f_c * d;
+  th -= floor(th);
+}
+
+template <typename TIN, bool SPECTRA>
+__global__ void __launch_bounds__(256)
+k_plain(const TIN* __restrict__ strain, const double* __restrict__ betas, const int* __restrict__ nseg,
+        PlainArgs p, double* __restrict__ S, double2* __restrict__ Fout) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double2* g0 = reinterpret_cast<double2*>(smem);
+  double2* g1 = g0 + p.n_fine;
+  __shared__ int8_t s_rad[16];
+  const int m = blockIdx.y;
+  const int i = blockIdx.x + p.seg_begin;
+  if (!SPECTRA && i >= nseg[m]) return;
+  const int tid = threadIdx.x;
+  if (tid < 16) s_rad[tid] = p.radices[tid];
+  const int n = p.n_fine;
+  for (int j = tid; j < n; j += blockDim.x) g0[j] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const double b = betas[m];
+  const double t_i0 = (double)i * (double)p.n_s / p.fs;
+  const double a = 1.0 - (8.0 / 3.0) * b * t_i0;
+  const double pre = 3.0 * pow(a, 0.625) / (5.0 * b);
+  const TIN* src = strain + (long long)i * p.n_s;
+  const double hw = 0.5 * p.w;
+  for (int j = tid; j < p.n_s; j += blockDim.x) {
+    double psi, th;
+    plain_phase(b, a, pre, (double)j / p.fs, p, psi, th);
+    double sn, cs;
+    sincospi(2.0 * th, &sn, &cs);
+    const double xv = (double)src[j];
+    const double cre = xv * cs, cim = -xv * sn;
+    const double U = psi * n;
+    const double l0 = ceil(U - hw);
+    int cell = (int)l0;
+    if (cell < 0) cell += n;
+    for (int t = 0; t < p.w; ++t) {
+      const double z = (l0 + t - U) / hw;
+      const double ph = exp(p.beta_es * (sqrt(fmax(1.0 - z * z, 0.0)) - 1.0));
+      int c = cell + t;
+      if (c >= n) c -= n;
+      atomicAdd(&g0[c].x, ph * cre);
+      atomicAdd(&g0[c].y, ph * cim);
+    }
+  }
+  __syncthreads();
+  const double2* __restrict__ tw = reinterpret_cast<const double2*>(p.tw);
+  double2* res = fft_smem<double2>(g0, g1, n, s_rad, p.n_pass, tw);
+  for (int bb = tid; bb < p.n_bins; bb += blockDim.x) {
+    int k = bb - p.half_bins;
+    int idx = k < 0 ? k + n : k;
+    const double2 G = res[idx];
+    const double c = p.corr[bb];
+    const double fx = G.x * c, fy = G.y * c;
+    if (SPECTRA) {
+      Fout[((long long)m * p.seg_range + (i - p.seg_begin)) * p.n_bins + bb] = make_double2(fx, fy);
+    } else {
+      atomicAdd(&S[(long long)m * p.n_bins + bb], 2.0 * (fx * fx + fy * fy) / (double)p.n_s);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Statistic and top-k keys
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long make_key(float v, uint32_t flat) {
+  uint32_t u = __float_as_uint(v);
+  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  return ((unsigned long long)u << 32) | (unsigned long long)(~flat);
+}
+__device__ __forceinline__ float key_value(unsigned long long k) {
+  uint32_t u = (uint32_t)(k >> 32);
+  u = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+  return __uint_as_float(u);
+}
+
+// Mixed form: n_sigma[m][b] = (sum over the template's items of Z) / sqrt(nseg_m),
+// items summed in order (FP64) so the result does not depend on scheduling.
+__global__ void k_reduce_mixed(const float* __restrict__ partial, const int* __restrict__ item_off,
+                               const int* __restrict__ nseg, int n_bins, float* __restrict__ map,
+                               unsigned long long* __restrict__ keys) {
+  const int m = blockIdx.x;
+  const int q0 = item_off[m], q1 = item_off[m + 1];
+  const double inv = 1.0 / sqrt((double)nseg[m]);
+  for (int b = threadIdx.x; b < n_bins; b += blockDim.x) {
+    double z = 0.0;
+    for (int q = q0; q < q1; ++q) z += (double)partial[(long long)q * n_bins + b];
+    const float v = (float)(z * inv);
+    const uint32_t flat = (uint32_t)m * (uint32_t)n_bins + (uint32_t)b;
+    if (map) map[flat] = v;
+    keys[flat] = make_key(v, flat);
+  }
+}
+
+// Plain form: n_sigma = (S - 2 N) / (2 sqrt(N)) in FP64.
+__global__ void k_finish_plain(const double* __restrict__ S, const int* __restrict__ nseg, int n_templates,
+                               int n_bins, float* __restrict__ map, unsigned long long* __restrict__ keys) {
+  const long long total = (long long)n_templates * n_bins;
+  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < total;
+       f += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(f / n_bins);
+    const double N = (double)nseg[m];
+    const float v = (float)((S[f] - 2.0 * N) / (2.0 * sqrt(N)));
+    if (map) map[f] = v;
+    keys[f] = make_key(v, (uint32_t)f);
+  }
+}
+
+// Top-k of each tile of kTopkTile keys: bitonic sort (descending) in shared
+// memory, first k written to out[blockIdx.x * k ...].  Missing keys are 0,
+// which sorts below every real key.
+__global__ void __launch_bounds__(1024)
+k_topk_tile(const unsigned long long* __restrict__ in, long long n, int k, unsigned long long* __restrict__ out) {
+  __shared__ unsigned long long s[kTopkTile];
+  const long long base = (long long)blockIdx.x * kTopkTile;
+  for (int t = threadIdx.x; t < kTopkTile; t += blockDim.x) {
+    const long long g = base + t;
+    s[t] = g < n ? in[g] : 0ull;
+  }
+  __syncthreads();
+  for (int size = 2; size <= kTopkTile; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < kTopkTile / 2; t += blockDim.x) {
+        const int lo = 2 * t - (t & (stride - 1));
+        const int hi = lo + stride;
+        const bool desc = ((lo & size) == 0);
+        const unsigned long long x = s[lo], y = s[hi];
+        if ((x < y) == desc) { s[lo] = y; s[hi] = x; }
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = threadIdx.x; t < k; t += blockDim.x) out[(long long)blockIdx.x * k + t] = s[t];
+}
+
+__global__ void k_keys_to_cands(const unsigned long long* __restrict__ keys, int k, int n_bins,
+                                srs_candidate* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= k) return;
+  const unsigned long long key = keys[t];
+  const uint32_t flat = ~(uint32_t)(key & 0xffffffffull);
+  srs_candidate c;
+  c.value = key_value(key);
+  c.template_idx = (int32_t)(flat / (uint32_t)n_bins);
+  c.bin = (int32_t)(flat % (uint32_t)n_bins);
+  out[t] = c;
+}
+
+// ---------------------------------------------------------------------------
+// Time map alone (the same per-sample arithmetic as the spreaders)
+// ---------------------------------------------------------------------------
+__global__ void k_time_map_mixed(const Anchor* __restrict__ anchors, int n_items, MixedArgs a,
+                                 double* __restrict__ psi_out, double* __restrict__ th_out) {
+  const long long total = (long long)n_items * a.n_s;
+  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < total;
+       f += (long long)gridDim.x * blockDim.x) {
+    const long long it = f / a.n_s;
+    const int j = (int)(f - it * a.n_s);
+    const int ai = j / a.span;
+    const Anchor A = anchors[it * a.n_anchor + ai];
+    uint32_t Psi;
+    float th;
+    mixed_phase(A, j - ai * a.span, a.kc, Psi, th);
+    psi_out[f] = (double)Psi * 2.3283064365386962890625e-10;
+    th_out[f] = th < 0.f ? (double)th + 1.0 : (double)th;
+  }
+}
+
+__global__ void k_time_map_plain(const int* __restrict__ item_m, const int* __restrict__ item_i, int n_items,
+                                 const double* __restrict__ betas, PlainArgs p, double* __restrict__ psi_out,
+                                 double* __restrict__ th_out) {
+  const long long total = (long long)n_items * p.n_s;
+  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < total;
+       f += (long long)gridDim.x * blockDim.x) {
+    const long long it = f / p.n_s;
+    const int j = (int)(f - it * p.n_s);
+    const double b = betas[item_m[it]];
+    const double t_i0 = (double)item_i[it] * (double)p.n_s / p.fs;
+    const double a = 1.0 - (8.0 / 3.0) * b * t_i0;
+    const double pre = 3.0 * pow(a, 0.625) / (5.0 * b);
+    double psi, th;
+    plain_phase(b, a, pre, (double)j / p.fs, p, psi, th);
+    psi_out[f] = psi;
+    th_out[f] = th;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+size_t mixed_smem_bytes(const MixedArgs& a) {
+  size_t s = (size_t)a.n_fine * 2 * sizeof(float2);
+  s += (size_t)((a.n_bins + 3) & ~3) * sizeof(float);
+  s += kSpreadWarps * sizeof(Anchor);
+  s += (size_t)((a.n_s + 3) & ~3) * sizeof(float);
+  return s;
+}
+
+cudaError_t launch_anchors(const Item* items, int n_items, const double* betas, const AnchorArgs& aa,
+                           Anchor* out, long long total, int n_sm, cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  long long blocks = (total + 255) / 256;
+  if (blocks > (long long)n_sm * 32) blocks = (long long)n_sm * 32;
+  k_anchors<<<(unsigned)blocks, 256, 0, st>>>(items, n_items, betas, aa, out, total);
+  return cudaGetLastError();
+}
+
+template <typename TIN, int W, bool SP>
+static cudaError_t launch_mixed_t(const void* strain, const Item* items, int n_items, const Anchor* anchors,
+                                  int* queue, const MixedArgs& a, float* partial, double2* Fout, int n_sm,
+                                  int ctas_per_sm, cudaStream_t st) {
+  const size_t smem = mixed_smem_bytes(a);
+  auto kern = k_mixed<TIN, W, SP>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kSpreadThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
+  long long grid = (long long)n_sm * occ;
+  if (grid > n_items) grid = n_items;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, kSpreadThreads, smem, st>>>(static_cast<const TIN*>(strain), items, n_items, anchors,
+                                                      queue, a, partial, Fout);
+  return cudaGetLastError();
+}
+
+template <typename TIN, bool SP>
+static cudaError_t launch_mixed_w(int w, const void* strain, const Item* items, int n_items, const Anchor* anchors,
+                                  int* queue, const MixedArgs& a, float* partial, double2* Fout, int n_sm,
+                                  int ctas_per_sm, cudaStream_t st) {
+  switch (w) {
+#define SRS_W(WW) \
+  case WW: return launch_mixed_t<TIN, WW, SP>(strain, items, n_items, anchors, queue, a, partial, Fout, n_sm, ctas_per_sm, st);
+    SRS_W(2) SRS_W(3) SRS_W(4) SRS_W(5) SRS_W(6) SRS_W(7) SRS_W(8)
+#undef SRS_W
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_mixed(bool f64_in, bool spectra, int w, const void* strain, const Item* items, int n_items,
+                         const Anchor* anchors, int* queue, const MixedArgs& a, float* partial, double2* Fout,
+                         int n_sm, int ctas_per_sm, cudaStream_t st) {
+  if (f64_in)
+    return spectra ? launch_mixed_w<double, true>(w, strain, items, n_items, anchors, queue, a, partial, Fout, n_sm, ctas_per_sm, st)
+                   : launch_mixed_w<double, false>(w, strain, items, n_items, anchors, queue, a, partial, Fout, n_sm, ctas_per_sm, st);
+  return spectra ? launch_mixed_w<float, true>(w, strain, items, n_items, anchors, queue, a, partial, Fout, n_sm, ctas_per_sm, st)
+                 : launch_mixed_w<float, false>(w, strain, items, n_items, anchors, queue, a, partial, Fout, n_sm, ctas_per_sm, st);
+}
+
+cudaError_t launch_plain(bool f64_in, bool spectra, const void* strain, const double* betas, const int* nseg,
+                         const PlainArgs& p, int grid_x, int n_templates, double* S, double2* Fout,
+                         cudaStream_t st) {
+  const size_t smem = (size_t)p.n_fine * 2 * sizeof(double2);
+  dim3 grid(grid_x, n_templates);
+  cudaError_t e;
+#define SRS_PLAIN(TIN, SP)                                                                              \
+  do {                                                                                                  \
+    auto kern = k_plain<TIN, SP>;                                                                       \
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);             \
+    if (e != cudaSuccess) return e;                                                                     \
+    kern<<<grid, 256, smem, st>>>(static_cast<const TIN*>(strain), betas, nseg, p, S, Fout);            \
+  } while (0)
+  if (f64_in) {
+    if (spectra) SRS_PLAIN(double, true); else SRS_PLAIN(double, false);
+  } else {
+    if (spectra) SRS_PLAIN(float, true); else SRS_PLAIN(float, false);
+  }
+#undef SRS_PLAIN
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_mixed(const float* partial, const int* item_off, const int* nseg, int n_templates,
+                                int n_bins, float* map, unsigned long long* keys, cudaStream_t st) {
+  k_reduce_mixed<<<n_templates, 256, 0, st>>>(partial, item_off, nseg, n_bins, map, keys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_plain(const double* S, const int* nseg, int n_templates, int n_bins, float* map,
+                                unsigned long long* keys, int n_sm, cudaStream_t st) {
+  long long total = (long long)n_templates * n_bins;
+  long long blocks = (total + 255) / 256;
+  if (blocks > (long long)n_sm * 16) blocks = (long long)n_sm * 16;
+  k_finish_plain<<<(unsigned)blocks, 256, 0, st>>>(S, nseg, n_templates, n_bins, map, keys);
+  return cudaGetLastError();
+}
+
+// Reduce n keys to the top k (k <= kTopkTile / 2) through tiles; result in
+// whichever of buf_a / buf_b the last level wrote, returned in *result.
+cudaError_t launch_topk(const unsigned long long* keys, long long n, int k, unsigned long long* buf_a,
+                        unsigned long long* buf_b, const unsigned long long** result, int* launches,
+                        cudaStream_t st) {
+  const unsigned long long* src = keys;
+  unsigned long long* dst = buf_a;
+  long long cur = n;
+  for (;;) {
+    long long tiles = (cur + kTopkTile - 1) / kTopkTile;
+    k_topk_tile<<<(unsigned)tiles, 1024, 0, st>>>(src, cur, k, dst);
+    ++*launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    cur = tiles * k;
+    src = dst;
+    if (tiles == 1) break;
+    dst = (dst == buf_a) ? buf_b : buf_a;
+  }
+  *result = src;
+  return cudaSuccess;
+}
+
+cudaError_t launch_keys_to_cands(const unsigned long long* keys, int k, int n_bins, srs_candidate* out,
+                                 cudaStream_t st) {
+  k_keys_to_cands<<<(k + 255) / 256, 256, 0, st>>>(keys, k, n_bins, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_time_map_mixed(const Anchor* anchors, int n_items, const MixedArgs& a, double* psi,
+                                  double* th, cudaStream_t st) {
+  k_time_map_mixed<<<1024, 256, 0, st>>>(anchors, n_items, a, psi, th);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_time_map_plain(const int* item_m, const int* item_i, int n_items, const double* betas,
+                                  const PlainArgs& p, double* psi, double* th, cudaStream_t st) {
+  k_time_map_plain<<<1024, 256, 0, st>>>(item_m, item_i, n_items, betas, p, psi, th);
+  return cudaGetLastError();
+}
+
+}  // namespace srs

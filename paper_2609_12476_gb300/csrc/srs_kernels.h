@@ -1,0 +1,65 @@
+// srs_kernels.h -- kernel argument blocks and launchers of libsrs (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "srs_internal.h"
+
+namespace srs {
+
+constexpr int kTopkTile = 4096;  // keys per top-k tile (k <= kTopkTile / 2)
+
+struct AnchorArgs {
+  double fs, t_coh, f_c;
+  long long n_s;
+  int span, n_anchor;
+};
+
+struct MixedArgs {
+  int n_s, n_fine, n_bins, half_bins;
+  int run, span, n_anchor, n_pass;
+  int seg_begin, seg_range;       // spectra output: first segment, segments per template
+  float kc;                       // f_c * t_coh
+  float inv_ns;                   // 1 / n_s
+  float es_beta_log2e;            // ES shape parameter * log2(e)
+  float two_over_w;
+  const float* corr;              // [n_bins] deconvolution factors
+  const float* tw;                // [2 n_fine] interleaved exp(-2 pi i m / n_fine)
+  int8_t radices[16];
+};
+
+struct PlainArgs {
+  double fs, t_coh, f_c, beta_es;
+  int n_s, n_fine, n_bins, half_bins;
+  int w, n_pass, seg_begin, seg_range;
+  const double* corr;             // [n_bins]
+  const double* tw;               // [2 n_fine]
+  int8_t radices[16];
+};
+
+size_t mixed_smem_bytes(const MixedArgs& a);
+
+cudaError_t launch_anchors(const Item* items, int n_items, const double* betas, const AnchorArgs& aa,
+                           Anchor* out, long long total, int n_sm, cudaStream_t st);
+cudaError_t launch_mixed(bool f64_in, bool spectra, int w, const void* strain, const Item* items, int n_items,
+                         const Anchor* anchors, int* queue, const MixedArgs& a, float* partial, double2* Fout,
+                         int n_sm, int ctas_per_sm, cudaStream_t st);
+cudaError_t launch_plain(bool f64_in, bool spectra, const void* strain, const double* betas, const int* nseg,
+                         const PlainArgs& p, int grid_x, int n_templates, double* S, double2* Fout,
+                         cudaStream_t st);
+cudaError_t launch_reduce_mixed(const float* partial, const int* item_off, const int* nseg, int n_templates,
+                                int n_bins, float* map, unsigned long long* keys, cudaStream_t st);
+cudaError_t launch_finish_plain(const double* S, const int* nseg, int n_templates, int n_bins, float* map,
+                                unsigned long long* keys, int n_sm, cudaStream_t st);
+cudaError_t launch_topk(const unsigned long long* keys, long long n, int k, unsigned long long* buf_a,
+                        unsigned long long* buf_b, const unsigned long long** result, int* launches,
+                        cudaStream_t st);
+cudaError_t launch_keys_to_cands(const unsigned long long* keys, int k, int n_bins, srs_candidate* out,
+                                 cudaStream_t st);
+cudaError_t launch_time_map_mixed(const Anchor* anchors, int n_items, const MixedArgs& a, double* psi,
+                                  double* th, cudaStream_t st);
+cudaError_t launch_time_map_plain(const int* item_m, const int* item_i, int n_items, const double* betas,
+                                  const PlainArgs& p, double* psi, double* th, cudaStream_t st);
+
+}  // namespace srs

@@ -1,0 +1,98 @@
+"""The C ABI library on the host: it builds, loads, exports every entry point
+of include/srs.h, and its planner (no GPU) agrees with the pinned oracle and
+rejects bad arguments with the documented status codes."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import srs_synth
+from paper_2609_12476_gb300 import _capi
+from paper_2609_12476_gb300 import Params, SrsError, srs_plan, SRS_MIXED, SRS_PLAIN_FP64
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "srs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(srs_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_entry_point():
+    L = _capi.lib()
+    names = _declared()
+    assert set(names) == set(_capi.EXPORTS)
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_plan_matches_oracle_beta_and_segments():
+    w = srs_synth.WORKLOADS["semicoherent_2h"]
+    mc = srs_synth.log_templates(2e-2, 5e-2, 64)
+    info, beta, nseg = srs_plan(Params(), mc, int(7200 * 256))
+    for m in range(64):
+        b = oracle.beta(mc[m], 40.0)
+        assert beta[m] == pytest.approx(b, rel=1e-13)
+        assert nseg[m] == oracle.nseg(b, 40.0, 60.0, 30.0, 240)
+    assert nseg.min() == 112 and nseg.max() == 240 and nseg.sum() == 13022
+    assert info["n_spectra"] == 13022
+    assert info["n_bins"] == 600 and info["n_s"] == 7680 and info["n_seg_total"] == 240
+
+
+def test_plan_nufft_sizes_from_eps():
+    mc = [1e-2]
+    info, _, _ = srs_plan(Params(eps=1e-6), mc, 7680 * 4)
+    assert info["w"] == 7 and info["n_fine"] == 1200 and info["sigma"] == pytest.approx(2.0)
+    assert info["beta_es"] == pytest.approx(2.30 * 7)
+    info, _, _ = srs_plan(Params(eps=1e-3), mc, 7680 * 4)
+    assert info["w"] == 4
+    info, _, _ = srs_plan(Params(eps=1e-9, precision=SRS_PLAIN_FP64), mc, 7680 * 4)
+    assert info["w"] == 10 and info["n_fine"] == 1200
+    # the full-band single-segment case needs a smaller sigma to fit shared memory
+    p = Params(fs=128.0, f_lo=-64.0, f_hi=64.0, f_ref=50.0, eps=1e-9, precision=SRS_PLAIN_FP64)
+    info, _, _ = srs_plan(p, mc, 3840)
+    assert info["n_bins"] == 3840 and info["n_fine"] * 32 <= 200 * 1024
+    assert info["n_fine"] >= 1.25 * 3840
+
+
+def test_plan_rejects_bad_arguments():
+    mc = [1e-2]
+    bad = [Params(fs=250.01), Params(f_hi=60.01), Params(f_hi=200.0), Params(eps=1e-13), Params(eps=0.5),
+           Params(top_k=0), Params(top_k=2000), Params(f_lo=60.0, f_hi=40.0), Params(sigma=1.0)]
+    for p in bad:
+        with pytest.raises(SrsError) as e:
+            srs_plan(p, mc, 7680 * 4)
+        assert e.value.status == -1, p
+    with pytest.raises(SrsError) as e:
+        srs_plan(Params(), mc, 100)                       # shorter than a segment
+    assert e.value.status == -1
+    with pytest.raises(SrsError) as e:
+        srs_plan(Params(), [-1.0], 7680)
+    assert e.value.status == -1
+
+
+def test_plan_domain_error_past_coalescence():
+    # 2 h with cut_segments = 0: the heaviest template of the 2e-2..5e-2 bank
+    # coalesces at 3/(8 beta) ~ 5.1e3 s < 7200 s.
+    mc = srs_synth.log_templates(2e-2, 5e-2, 64)
+    with pytest.raises(SrsError) as e:
+        srs_plan(Params(cut_segments=0), mc, 7200 * 256)
+    assert e.value.status == -6
+    srs_plan(Params(cut_segments=1), mc, 7200 * 256)
+
+
+def test_plan_mixed_form_floor():
+    with pytest.raises(SrsError) as e:
+        srs_plan(Params(eps=1e-9, precision=SRS_MIXED), [1e-2], 7680)
+    assert e.value.status == -5
+
+
+def test_plan_items_cover_every_segment_once():
+    mc = srs_synth.log_templates(5e-4, 1e-1, 32)
+    for chunk in (1, 3, 16):
+        info, _, nseg = srs_plan(Params(chunk=chunk), mc, 720 * 7680)
+        assert info["chunk"] == chunk
+        assert info["n_items"] == sum((int(n) + chunk - 1) // chunk for n in nseg)

@@ -1,0 +1,211 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances: spectra within relative L2 <= 10 eps per spectrum (the NUFFT's
+FINUFFT-sense tolerance, oracle = exact non-uniform DFT); the time map to
+the phase accuracy each form is built for; n_sigma within the bound that the
+per-spectrum error implies; top-k identical up to swaps inside that bound."""
+import numpy as np
+import pytest
+
+import oracle
+import srs_synth
+from paper_2609_12476_gb300 import Context, Params, SrsError, SRS_MIXED, SRS_PLAIN_FP64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def rel_l2(a, b, axis=-1):
+    return np.linalg.norm(a - b, axis=axis) / np.linalg.norm(b, axis=axis)
+
+
+@pytest.fixture(scope="module")
+def two_hours():
+    return srs_synth.make_workload("semicoherent_2h")
+
+
+def _oracle_phase(beta, i, n_s, fs, T, f_c):
+    d = oracle.delta(beta, i * n_s / fs, np.arange(n_s) / fs)
+    psi = d / T
+    th = f_c * d
+    return psi - np.floor(psi), th - np.floor(th)
+
+
+def _cyc(a, b):
+    d = np.abs(a - b)
+    return np.minimum(d, 1.0 - d)
+
+
+@pytest.mark.parametrize("precision,tol_psi,tol_th", [(SRS_MIXED, 2e-9, 2e-7), (SRS_PLAIN_FP64, 1e-12, 1e-11)])
+def test_time_map_against_oracle(ctx, two_hours, precision, tol_psi, tol_th):
+    w = two_hours
+    p = Params(precision=precision)
+    mc = w["mc"]
+    _, beta, nseg = __import__("paper_2609_12476_gb300").srs_plan(p, mc, w["n_samples"])
+    items = [(0, 0), (0, 239), (63, 0), (63, int(nseg[63]) - 1), (31, 57)]
+    psi, th = ctx.time_map(mc, items, p, w["n_samples"])
+    for k, (m, i) in enumerate(items):
+        rp, rt = _oracle_phase(beta[m], i, 7680, 256.0, 30.0, 50.0)
+        assert _cyc(psi[k], rp).max() < tol_psi, (m, i, _cyc(psi[k], rp).max())
+        assert _cyc(th[k], rt).max() < tol_th, (m, i, _cyc(th[k], rt).max())
+
+
+def test_single_segment_full_band_plain_fp64(ctx):
+    """Single segment, exact template, 3840 modes at eps = 1e-9 in FP64."""
+    w = srs_synth.make_workload("single")
+    p = Params(fs=128.0, f_lo=-64.0, f_hi=64.0, f_ref=50.0, eps=1e-9, precision=SRS_PLAIN_FP64)
+    F, _ = ctx.segment_spectra(w["strain"], w["mc"], 0, 1, p)
+    b = oracle.beta(1e-2, 50.0)
+    R = oracle.spectra(w["strain"], 128.0, 30.0, -64.0, 3840, [b], [(0, 0)])
+    assert rel_l2(F[0], R).max() <= 1e-8
+    # the injected chirp sits in the 50 Hz bin
+    assert np.argmax(np.abs(F[0, 0])) in (1920 + 1500, 1920 - 1500)
+
+
+def test_single_segment_full_band_mixed(ctx):
+    w = srs_synth.make_workload("single")
+    p = Params(fs=128.0, f_lo=-64.0, f_hi=64.0, f_ref=50.0, eps=1e-6, precision=SRS_MIXED)
+    F, _ = ctx.segment_spectra(w["strain"], w["mc"], 0, 1, p)
+    R = oracle.spectra(w["strain"], 128.0, 30.0, -64.0, 3840, [oracle.beta(1e-2, 50.0)], [(0, 0)])
+    assert rel_l2(F[0], R).max() <= 1e-5
+
+
+@pytest.mark.parametrize("precision", [SRS_MIXED, SRS_PLAIN_FP64])
+def test_spectra_two_hours_subset(ctx, two_hours, precision):
+    w = two_hours
+    p = Params(precision=precision, eps=1e-6)
+    mc = w["mc"][[0, 31, 63]]
+    segs = (0, 3)
+    F, _ = ctx.segment_spectra(w["strain"], mc, segs[0], segs[1], p)
+    betas = [oracle.beta(m, 40.0) for m in mc]
+    items = [(m, i) for m in range(3) for i in range(*segs)]
+    R = oracle.spectra(w["strain"], 256.0, 30.0, 40.0, 600, betas, items).reshape(3, 3, 600)
+    err = rel_l2(F, R)
+    assert err.max() <= 1e-5, err
+    # last in-band segment of the heaviest template: its tau span exceeds one period (wrap)
+    F2, _ = ctx.segment_spectra(w["strain"], mc[2:], 110, 112, p)
+    R2 = oracle.spectra(w["strain"], 256.0, 30.0, 40.0, 600, betas[2:], [(0, 110), (0, 111)])
+    assert rel_l2(F2[0], R2).max() <= 1e-5
+
+
+@pytest.mark.parametrize("precision,eps", [(SRS_MIXED, 1e-2), (SRS_MIXED, 1e-3), (SRS_MIXED, 1e-4),
+                                           (SRS_MIXED, 1e-5), (SRS_PLAIN_FP64, 1e-3), (SRS_PLAIN_FP64, 1e-7),
+                                           (SRS_PLAIN_FP64, 1e-10)])
+def test_eps_sweep(ctx, two_hours, precision, eps):
+    w = two_hours
+    mc = w["mc"][[5, 60]]
+    p = Params(precision=precision, eps=eps)
+    F, _ = ctx.segment_spectra(w["strain"], mc, 20, 22, p)
+    betas = [oracle.beta(m, 40.0) for m in mc]
+    R = oracle.spectra(w["strain"], 256.0, 30.0, 40.0, 600, betas,
+                       [(0, 20), (0, 21), (1, 20), (1, 21)]).reshape(2, 2, 600)
+    assert rel_l2(F, R).max() <= 10 * eps
+
+
+def test_ragged_segment_and_noninteger_demodulation(ctx):
+    """6000-sample segments (not a multiple of the 256-thread run layout) and a
+    band whose centre is not a whole number of cycles per segment."""
+    fs, T = 200.0, 30.0
+    f_lo = 40.0 + 1.0 / 60.0
+    p = Params(fs=fs, t_coh=T, f_lo=f_lo, f_hi=f_lo + 20.0, eps=1e-6)
+    x = srs_synth.strain_with_chirps(4 * 6000, fs, 7, [{"mc": 5e-2, "f0": 47.0, "amp": 0.1}])
+    mc = np.array([5e-2, 8e-3])
+    F, _ = ctx.segment_spectra(x, mc, 1, 4, p)
+    betas = [oracle.beta(m, 40.0) for m in mc]
+    R = oracle.spectra(x, fs, T, f_lo, 600, betas, [(m, i) for m in range(2) for i in range(1, 4)]).reshape(2, 3, 600)
+    assert rel_l2(F, R).max() <= 1e-5
+    Fp, _ = ctx.segment_spectra(x, mc, 1, 4, Params(fs=fs, t_coh=T, f_lo=f_lo, f_hi=f_lo + 20.0, eps=1e-6,
+                                                    precision=SRS_PLAIN_FP64))
+    assert rel_l2(Fp, R).max() <= 1e-5
+
+
+def _search_case():
+    fs, T, nseg_tot = 256.0, 30.0, 40
+    mc = srs_synth.log_templates(6e-2, 1e-1, 6)
+    inj = [{"mc": 8e-2, "f0": 44.0, "amp": 0.03}]
+    x = srs_synth.strain_with_chirps(nseg_tot * 7680, fs, 21, inj)
+    return x, mc
+
+
+def _map_tolerance(P, items, nsegs, eps, n_s, shape):
+    """Bound on |n_sigma_gpu - n_sigma_oracle| implied by rel-L2(F) <= 10 eps per
+    spectrum: |dF_b| <= 10 eps ||F||, |dP_b| <= (4 |F_b| |dF_b| + 2 |dF_b|^2) / n_s."""
+    tol = np.zeros(shape)
+    e = 10 * eps
+    for k, (m, _i) in enumerate(items):
+        Fb = np.sqrt(P[k] * n_s / 2.0)
+        Fn = np.sqrt(P[k].sum() * n_s / 2.0)
+        tol[m] += (4 * Fb * e * Fn + 2 * (e * Fn) ** 2) / n_s
+    return tol / (2.0 * np.sqrt(np.asarray(nsegs, dtype=float)).reshape(-1, 1))
+
+
+@pytest.mark.parametrize("precision", [SRS_MIXED, SRS_PLAIN_FP64])
+def test_search_against_oracle(ctx, precision):
+    x, mc = _search_case()
+    eps = 1e-6
+    p = Params(precision=precision, eps=eps, top_k=32)
+    cands, smap, rep = ctx.search(x, mc, p)
+    betas = [oracle.beta(m, 40.0) for m in mc]
+    nsegs = [oracle.nseg(b, 40.0, 60.0, 30.0, 40) for b in betas]
+    items = [(m, i) for m in range(len(mc)) for i in range(nsegs[m])]
+    F = oracle.spectra(x, 256.0, 30.0, 40.0, 600, betas, items)
+    P = oracle.power(F, 7680)
+    S = np.zeros((len(mc), 600))
+    for k, (m, _i) in enumerate(items):
+        S[m] += P[k]
+    ns = oracle.n_sigma(S, nsegs)
+    tol = _map_tolerance(P, items, nsegs, eps, 7680, ns.shape) + 1e-5 * np.abs(ns) + 1e-6
+    assert np.all(np.abs(smap - ns) <= tol), np.max(np.abs(smap - ns) / tol)
+    assert rep["n_spectra"] == sum(nsegs)
+    # top-k: identical cells except swaps whose oracle values lie within tolerance
+    ov, om, ob = oracle.topk(ns, 32)
+    kth = ov[-1]
+    for c in cands:
+        m, b = int(c["template_idx"]), int(c["bin"])
+        assert abs(c["value"] - ns[m, b]) <= tol[m, b]
+        assert ns[m, b] >= kth - tol[m, b] - tol[om[-1], ob[-1]]
+    for pos in range(32):
+        gm, gb = int(cands[pos]["template_idx"]), int(cands[pos]["bin"])
+        if (gm, gb) != (om[pos], ob[pos]):
+            assert abs(ns[gm, gb] - ov[pos]) <= tol[gm, gb] + tol[om[pos], ob[pos]]
+    # the loud injection is the top candidate
+    assert cands[0]["value"] > 20
+
+
+def test_device_io_matches_host_io(ctx):
+    torch = pytest.importorskip("torch")
+    x, mc = _search_case()
+    p = Params(eps=1e-6, top_k=16)
+    c_host, m_host, _ = ctx.search(x, mc, p)
+    xd = torch.from_numpy(x).cuda()
+    out, _ = ctx.search(xd, mc, p)
+    torch.cuda.synchronize()
+    m_dev = out["map"].cpu().numpy()
+    assert np.array_equal(m_dev, m_host)
+    cd = out["cands"].cpu().numpy()
+    assert np.array_equal(cd[:, 1], c_host["template_idx"]) and np.array_equal(cd[:, 2], c_host["bin"])
+    # float32 strain through the same path
+    c32, m32, _ = ctx.search(x.astype(np.float32), mc, p)
+    assert np.max(np.abs(m32 - m_host)) < 1e-2
+
+
+def test_errors_are_status_codes(ctx):
+    x = np.zeros(7680 * 2)
+    with pytest.raises(SrsError) as e:
+        ctx.search(x, [1e-2], Params(fs=250.01))
+    assert e.value.status == -1
+    with pytest.raises(SrsError) as e:
+        ctx.search(x[:100], [1e-2], Params())
+    assert e.value.status == -1
+    with pytest.raises(SrsError) as e:
+        ctx.segment_spectra(x, [1e-2], 0, 1, Params(eps=1e-9, precision=SRS_MIXED))
+    assert e.value.status == -5
+    # the context is still usable afterwards
+    c, m, _ = ctx.search(np.random.default_rng(0).standard_normal(7680 * 2), [1e-2], Params(top_k=4))
+    assert len(c) == 4 and np.isfinite(m).all()
