@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -55,7 +56,7 @@ struct srs_ctx {
   std::vector<unsigned char> plan_key;
   Plan plan;
   DevBuf items, anchors, partial, betas, nseg, item_off, corr, tw, keys, topk_a, topk_b, cands, queue, strain,
-      map, S, F, psi, th, im, ii;
+      strain32, errflag, map, S, F, psi, th, im, ii;
 };
 
 namespace {
@@ -95,6 +96,16 @@ MixedArgs mixed_args(const Plan& pl, const srs_ctx* ctx, int seg_begin, int seg_
   a.n_pass = (int)pl.radices.size();
   a.seg_begin = seg_begin;
   a.seg_range = seg_range;
+  a.ns4 = (int)((pl.n_s + 3) & ~3LL);
+  a.nb4 = (pl.n_bins + 3) & ~3;
+  a.chunk = pl.chunk;
+  a.use_tma = 0;
+  a.aa.fs = pl.fs;
+  a.aa.t_coh = pl.t_coh;
+  a.aa.f_c = pl.f_c;
+  a.aa.n_s = pl.n_s;
+  a.aa.span = pl.span;
+  a.aa.n_anchor = pl.n_anchor;
   a.kc = (float)pl.k_c;
   a.inv_ns = (float)(1.0 / (double)pl.n_s);
   a.es_beta_log2e = (float)(pl.beta_es * 1.4426950408889634074);
@@ -238,6 +249,39 @@ srs_status get_plan(srs_ctx* ctx, int kind, const srs_params* params, const doub
   return SRS_OK;
 }
 
+// The mixed form reads FP32 samples: convert FP64 strain once per call, and
+// use FP32 strain in place when TMA can read it (16-byte aligned, n_s % 4 == 0).
+srs_status strain_f32(srs_ctx* ctx, const void* dstrain, int32_t dtype, int64_t samples, int64_t n_s,
+                      const float** out, int* use_tma) {
+  // SRS_NO_TMA=1 in the environment selects plain shared-memory staging.
+  const char* no_tma = std::getenv("SRS_NO_TMA");
+  const bool tma_ok_len = (n_s % 4) == 0 && !(no_tma && no_tma[0] == '1');
+  if (dtype == SRS_F64) {
+    SRS_CK(ctx->strain32.ensure((size_t)samples * 4), "alloc strain32");
+    SRS_CK(launch_to_f32(static_cast<const double*>(dstrain), ctx->strain32.as<float>(), samples, ctx->n_sm,
+                         ctx->stream), "k_to_f32");
+    *out = ctx->strain32.as<float>();
+    *use_tma = tma_ok_len ? 1 : 0;
+    return SRS_OK;
+  }
+  const bool aligned = ((uintptr_t)dstrain % 16) == 0;
+  *out = static_cast<const float*>(dstrain);
+  *use_tma = (tma_ok_len && aligned) ? 1 : 0;
+  return SRS_OK;
+}
+
+srs_status check_err_flag(srs_ctx* ctx) {
+  int flag[5] = {0, 0, 0, 0, 0};
+  SRS_CK(cudaMemcpy(flag, ctx->errflag.p, sizeof flag, cudaMemcpyDeviceToHost), "read error flag");
+  if (flag[0]) {
+    char buf[200];
+    std::snprintf(buf, sizeof buf, "a device wait gave up (TMA copy did not complete in time): item %d segment %d parity %d block %d",
+                  flag[1], flag[2], flag[3], flag[4]);
+    return set_err(ctx, SRS_ERR_TIMEOUT, buf);
+  }
+  return SRS_OK;
+}
+
 srs_status search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype, const double* mc,
                        int32_t n_templates, const srs_params* params, float* stat_map, srs_candidate* cands,
                        int32_t* n_cands, srs_report* report) {
@@ -268,9 +312,9 @@ srs_status search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
     }
   }
   SRS_CK(ctx->keys.ensure(n_map * 8), "alloc keys");
-  long long tiles = (n_map + kTopkTile - 1) / kTopkTile;
-  SRS_CK(ctx->topk_a.ensure(std::max<long long>(tiles, 1) * k * 8), "alloc topk");
-  SRS_CK(ctx->topk_b.ensure(std::max<long long>(tiles, 1) * k * 8), "alloc topk");
+  const long long scratch = topk_scratch_keys(n_map, k);
+  SRS_CK(ctx->topk_a.ensure(scratch * 8), "alloc topk");
+  SRS_CK(ctx->topk_b.ensure(scratch * 8), "alloc topk");
   srs_candidate* dc = on_dev ? cands : nullptr;
   if (!on_dev) {
     SRS_CK(ctx->cands.ensure((size_t)k * sizeof(srs_candidate)), "alloc cands");
@@ -279,10 +323,9 @@ srs_status search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
   int launches = 0;
   const long long n_items = (long long)pl.items.size();
   if (mixed) {
-    const long long n_anch = pl.n_spectra * pl.n_anchor;
-    SRS_CK(ctx->anchors.ensure(n_anch * sizeof(Anchor)), "alloc anchors");
     SRS_CK(ctx->partial.ensure(n_items * pl.n_bins * 4), "alloc partial");
     SRS_CK(ctx->queue.ensure(64), "alloc queue");
+    SRS_CK(ctx->errflag.ensure(64), "alloc error flag");
   } else {
     SRS_CK(ctx->S.ensure(n_map * 8), "alloc S");
   }
@@ -290,17 +333,20 @@ srs_status search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
   SRS_CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
   if (mixed) {
     MixedArgs a = mixed_args(pl, ctx, 0, 0);
+    const float* s32 = nullptr;
+    s = strain_f32(ctx, dstrain, dtype, (int64_t)max_seg * pl.n_s, pl.n_s, &s32, &a.use_tma);
+    if (s != SRS_OK) return s;
+    if (f64) ++launches;
     SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
-    SRS_CK(launch_anchors(ctx->items.as<Item>(), (int)n_items, ctx->betas.as<double>(), anchor_args(pl),
-                          ctx->anchors.as<Anchor>(), pl.n_spectra * pl.n_anchor, ctx->n_sm, ctx->stream), "k_anchors");
-    ++launches;
+    SRS_CK(cudaMemsetAsync(ctx->errflag.p, 0, 64, ctx->stream), "memset error flag");
     SRS_CK(cudaEventRecord(ctx->ev2, ctx->stream), "event");
-    SRS_CK(launch_mixed(f64, false, pl.w, dstrain, ctx->items.as<Item>(), (int)n_items, ctx->anchors.as<Anchor>(),
-                        ctx->queue.as<int>(), a, ctx->partial.as<float>(), nullptr, ctx->n_sm, 0, ctx->stream), "k_mixed");
+    SRS_CK(launch_mixed(false, pl.w, s32, ctx->items.as<Item>(), (int)n_items, ctx->betas.as<double>(),
+                        ctx->queue.as<int>(), a, ctx->partial.as<float>(), nullptr, ctx->errflag.as<int>(), ctx->n_sm,
+                        0, ctx->stream), "k_mixed");
     SRS_CK(cudaEventRecord(ctx->ev3, ctx->stream), "event");
     ++launches;
     SRS_CK(launch_reduce_mixed(ctx->partial.as<float>(), ctx->item_off.as<int>(), ctx->nseg.as<int>(), n_templates,
-                               pl.n_bins, dmap, ctx->keys.as<unsigned long long>(), ctx->stream), "k_reduce_mixed");
+                               pl.n_bins, dmap, ctx->keys.as<unsigned long long>(), ctx->n_sm, ctx->stream), "k_reduce_mixed");
     ++launches;
   } else {
     PlainArgs p = plain_args(pl, ctx, 0, 0);
@@ -325,6 +371,10 @@ srs_status search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
     if (stat_map) SRS_CK(cudaMemcpyAsync(stat_map, dmap, n_map * 4, cudaMemcpyDeviceToHost, ctx->stream), "copy map");
   }
   SRS_CK(cudaStreamSynchronize(ctx->stream), "search");
+  if (mixed) {
+    s = check_err_flag(ctx);
+    if (s != SRS_OK) return s;
+  }
   *n_cands = k;
   if (report) {
     float ms = 0.f;
@@ -373,15 +423,19 @@ srs_status spectra_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int
   SRS_CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
   if (mixed) {
     const long long n_items = (long long)pl.items.size();
-    SRS_CK(ctx->anchors.ensure(pl.n_spectra * pl.n_anchor * sizeof(Anchor)), "alloc anchors");
     SRS_CK(ctx->queue.ensure(64), "alloc queue");
-    SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
-    SRS_CK(launch_anchors(ctx->items.as<Item>(), (int)n_items, ctx->betas.as<double>(), anchor_args(pl),
-                          ctx->anchors.as<Anchor>(), pl.n_spectra * pl.n_anchor, ctx->n_sm, ctx->stream), "k_anchors");
+    SRS_CK(ctx->errflag.ensure(64), "alloc error flag");
     MixedArgs a = mixed_args(pl, ctx, seg_begin, range);
-    SRS_CK(launch_mixed(f64, true, pl.w, dstrain, ctx->items.as<Item>(), (int)n_items, ctx->anchors.as<Anchor>(),
-                        ctx->queue.as<int>(), a, nullptr, dF, ctx->n_sm, 0, ctx->stream), "k_mixed");
-    launches += 2;
+    const float* s32 = nullptr;
+    s = strain_f32(ctx, dstrain, dtype, (int64_t)seg_end * pl.n_s, pl.n_s, &s32, &a.use_tma);
+    if (s != SRS_OK) return s;
+    if (f64) ++launches;
+    SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
+    SRS_CK(cudaMemsetAsync(ctx->errflag.p, 0, 64, ctx->stream), "memset error flag");
+    SRS_CK(launch_mixed(true, pl.w, s32, ctx->items.as<Item>(), (int)n_items, ctx->betas.as<double>(),
+                        ctx->queue.as<int>(), a, nullptr, dF, ctx->errflag.as<int>(), ctx->n_sm, 0, ctx->stream),
+           "k_mixed");
+    launches += 1;
   } else {
     PlainArgs p = plain_args(pl, ctx, seg_begin, range);
     SRS_CK(launch_plain(f64, true, dstrain, ctx->betas.as<double>(), ctx->nseg.as<int>(), p, range, n_templates,
@@ -391,6 +445,10 @@ srs_status spectra_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int
   SRS_CK(cudaEventRecord(ctx->ev1, ctx->stream), "event");
   if (!on_dev) SRS_CK(cudaMemcpyAsync(F, dF, fbytes, cudaMemcpyDeviceToHost, ctx->stream), "copy F");
   SRS_CK(cudaStreamSynchronize(ctx->stream), "spectra");
+  if (mixed) {
+    s = check_err_flag(ctx);
+    if (s != SRS_OK) return s;
+  }
   if (report) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
@@ -512,8 +570,8 @@ void srs_destroy(srs_ctx* c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   for (DevBuf* b : {&c->items, &c->anchors, &c->partial, &c->betas, &c->nseg, &c->item_off, &c->corr, &c->tw,
-                    &c->keys, &c->topk_a, &c->topk_b, &c->cands, &c->queue, &c->strain, &c->map, &c->S, &c->F,
-                    &c->psi, &c->th, &c->im, &c->ii})
+                    &c->keys, &c->topk_a, &c->topk_b, &c->cands, &c->queue, &c->strain, &c->strain32,
+                    &c->errflag, &c->map, &c->S, &c->F, &c->psi, &c->th, &c->im, &c->ii})
     b->release();
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);

@@ -154,6 +154,52 @@ __device__ __forceinline__ uint32_t frac_to_u32(double f) {  // f in [0, 1)
   return (uint32_t)(v & 0xffffffffLL);
 }
 
+// Anchor ai of segment i of a template with chirp parameter b (Eq. new_t
+// expanded around the anchor sample l_a = ai * span): the segment-local
+// resampled time delta(s) = tau(t_i0 + s) - tau(t_i0) at s0 = l_a / fs, written
+// without cancellation, its derivative A^(-3/8) (= f / f0, Eq. f), and the
+// Taylor coefficients of delta in the sample index.
+__device__ __forceinline__ Anchor compute_anchor(double b, int i, int ai, const AnchorArgs& aa) {
+  const double t_i0 = (double)i * (double)aa.n_s / aa.fs;
+  const double a = 1.0 - (8.0 / 3.0) * b * t_i0;
+  const double a58 = exp(0.625 * log(a));                       // a^(5/8)
+  const double s0 = (double)ai * (double)aa.span / aa.fs;
+  const double x = (8.0 / 3.0) * b * s0 / a;
+  const double L = log1p(-x);                                     // log(A / a)
+  const double d0 = 3.0 * a58 / (5.0 * b) * (-expm1(0.625 * L)); // delta(s0)
+  const double e1 = (a58 / a) * exp(-0.375 * L);                  // A^(-3/8) = d delta / ds
+  const double A = a * (1.0 - x);                                 // 1 - 8/3 beta (t_i0 + s0)
+  Anchor an;
+  double psi = d0 / aa.t_coh;
+  an.psi0 = frac_to_u32(psi - floor(psi));
+  double P1 = e1 / (aa.fs * aa.t_coh);
+  double P1f = P1 - floor(P1);
+  double N1 = rint(P1f * 4294967296.0);
+  an.n1 = (uint32_t)((long long)N1 & 0xffffffffLL);
+  an.p1lo = (float)(P1f - N1 * 2.3283064365386962890625e-10);
+  double th = aa.f_c * d0;
+  an.th0 = frac_to_u32(th - floor(th));
+  double M1 = aa.f_c * e1 / aa.fs;
+  double M1f = M1 - floor(M1);
+  double Mr = rint(M1f * 4294967296.0);
+  an.m1 = (uint32_t)((long long)Mr & 0xffffffffLL);
+  an.m1lo = (float)(M1f - Mr * 2.3283064365386962890625e-10);
+  // E_{k+1} = E_k * (8/3)(3/8 + k - 1) beta / (A fs (k + 1)), per sample, in periods
+  const double r = b / (A * aa.fs);
+  const double E1 = e1 / aa.fs;
+  const double E2 = E1 * r * 0.5;
+  const double E3 = E2 * r * (11.0 / 9.0);
+  const double E4 = E3 * r * (19.0 / 12.0);
+  const double E5 = E4 * r * (9.0 / 5.0);
+  an.p2 = (float)(E2 / aa.t_coh);
+  an.p3 = (float)(E3 / aa.t_coh);
+  an.p4 = (float)(E4 / aa.t_coh);
+  an.p5 = (float)(E5 / aa.t_coh);
+  an.pad0 = 0.f;
+  an.pad1 = 0.f;
+  return an;
+}
+
 __global__ void k_anchors(const Item* __restrict__ items, int n_items, const double* __restrict__ betas,
                           AnchorArgs aa, Anchor* __restrict__ out, long long total) {
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -166,47 +212,7 @@ __global__ void k_anchors(const Item* __restrict__ items, int n_items, const dou
       if (items[mid].g0 <= g) lo = mid; else hi = mid - 1;
     }
     const Item it = items[lo];
-    const int i = it.i0 + (int)(g - it.g0);
-    const double b = betas[it.m];
-    const double t_i0 = (double)i * (double)aa.n_s / aa.fs;
-    const double a = 1.0 - (8.0 / 3.0) * b * t_i0;
-    const double a58 = exp(0.625 * log(a));                       // a^(5/8)
-    const double s0 = (double)ai * (double)aa.span / aa.fs;
-    const double x = (8.0 / 3.0) * b * s0 / a;
-    const double L = log1p(-x);                                     // log(A / a)
-    const double d0 = 3.0 * a58 / (5.0 * b) * (-expm1(0.625 * L)); // delta(s0)
-    const double e1 = (a58 / a) * exp(-0.375 * L);                  // A^(-3/8) = d delta / ds
-    const double A = a * (1.0 - x);                                 // 1 - 8/3 beta (t_i0 + s0)
-    Anchor an;
-    double psi = d0 / aa.t_coh;
-    an.psi0 = frac_to_u32(psi - floor(psi));
-    double P1 = e1 / (aa.fs * aa.t_coh);
-    double P1f = P1 - floor(P1);
-    double N1 = rint(P1f * 4294967296.0);
-    an.n1 = (uint32_t)((long long)N1 & 0xffffffffLL);
-    an.p1lo = (float)(P1f - N1 * 2.3283064365386962890625e-10);
-    double th = aa.f_c * d0;
-    an.th0 = frac_to_u32(th - floor(th));
-    double M1 = aa.f_c * e1 / aa.fs;
-    double M1f = M1 - floor(M1);
-    double Mr = rint(M1f * 4294967296.0);
-    an.m1 = (uint32_t)((long long)Mr & 0xffffffffLL);
-    an.m1lo = (float)(M1f - Mr * 2.3283064365386962890625e-10);
-    // Taylor coefficients of delta around the anchor, per sample, in periods:
-    // E_{k+1} = E_k * (8/3)(3/8 + k - 1) beta / (A fs (k + 1)).
-    const double r = b / (A * aa.fs);
-    const double E1 = e1 / aa.fs;
-    const double E2 = E1 * r * 0.5;
-    const double E3 = E2 * r * (11.0 / 9.0);
-    const double E4 = E3 * r * (19.0 / 12.0);
-    const double E5 = E4 * r * (9.0 / 5.0);
-    an.p2 = (float)(E2 / aa.t_coh);
-    an.p3 = (float)(E3 / aa.t_coh);
-    an.p4 = (float)(E4 / aa.t_coh);
-    an.p5 = (float)(E5 / aa.t_coh);
-    an.pad0 = 0.f;
-    an.pad1 = 0.f;
-    out[idx] = an;
+    out[idx] = compute_anchor(betas[it.m], it.i0 + (int)(g - it.g0), ai, aa);
   }
 }
 
@@ -226,6 +232,32 @@ __device__ __forceinline__ void mixed_phase(const Anchor& A, int l, float kc, ui
 // ---------------------------------------------------------------------------
 // Mixed form: persistent spread + FFT + deconvolution + power/segment sum.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// One TMA bulk copy global -> shared completing on `bar` (16-byte aligned, size % 16 == 0).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(d), "l"(src), "r"(bytes), "r"(b) : "memory");
+}
+// Wait for phase `parity` of `bar`, giving up after ~2^31 cycles (about a second).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(b), "r"(parity) : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+}
+
 template <int W>
 __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2* __restrict__ grid,
                                            const Anchor& A, int j_begin, int j_end, int l_base,
@@ -234,6 +266,8 @@ __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2*
 #pragma unroll
   for (int t = 0; t < W; ++t) { acc_re[t] = 0.f; acc_im[t] = 0.f; }
   const int n = a.n_fine;
+  const float h = a.two_over_w;
+  const float esb = a.es_beta_log2e;
   int Bm = -1;  // fine-grid cell of acc[0]
   for (int j = j_begin; j < j_end; ++j) {
     uint32_t Psi;
@@ -251,25 +285,37 @@ __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2*
     if (Bm < 0) Bm = l0;
     int d = l0 - Bm;
     if (d < -(n >> 1)) d += n;
-    // slide the register window forward to l0, flushing cells that leave it
-    for (int s = 0; s < W && d > 0; ++s, --d) {
-      atomicAdd(&grid[Bm].x, acc_re[0]);
-      atomicAdd(&grid[Bm].y, acc_im[0]);
+    if (d != 0) {
+      if (d == 1) {
+        // the window moves one cell: acc[0]'s cell is complete
+        atomicAdd(&grid[Bm].x, acc_re[0]);
+        atomicAdd(&grid[Bm].y, acc_im[0]);
 #pragma unroll
-      for (int t = 0; t < W - 1; ++t) { acc_re[t] = acc_re[t + 1]; acc_im[t] = acc_im[t + 1]; }
-      acc_re[W - 1] = 0.f;
-      acc_im[W - 1] = 0.f;
-      Bm = (Bm + 1 == n) ? 0 : Bm + 1;
+        for (int t = 0; t < W - 1; ++t) { acc_re[t] = acc_re[t + 1]; acc_im[t] = acc_im[t + 1]; }
+        acc_re[W - 1] = 0.f;
+        acc_im[W - 1] = 0.f;
+      } else {
+        // jump (more than one cell per sample): flush the whole window
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+          int c = Bm + t;
+          if (c >= n) c -= n;
+          atomicAdd(&grid[c].x, acc_re[t]);
+          atomicAdd(&grid[c].y, acc_im[t]);
+          acc_re[t] = 0.f;
+          acc_im[t] = 0.f;
+        }
+      }
+      Bm = l0;
     }
-    if (d > 0) { Bm += d; if (Bm >= n) Bm -= n; }
-    float z = (off - fr) * a.two_over_w;
+    const float z0 = fmaxf((off - fr) * h, -1.0f);
 #pragma unroll
     for (int t = 0; t < W; ++t) {
-      const float q = fmaxf(fmaf(-z, z, 1.0f), 0.0f);
-      const float ph = ex2_approx(a.es_beta_log2e * (sqrt_approx(q) - 1.0f));
+      const float z = fmaf((float)t, h, z0);
+      const float q = fmaf(-z, z, 1.0f);
+      const float ph = ex2_approx(fmaf(esb, sqrt_approx(q), -esb));
       acc_re[t] = fmaf(ph, cre, acc_re[t]);
       acc_im[t] = fmaf(ph, cim, acc_im[t]);
-      z += a.two_over_w;
     }
   }
   if (Bm >= 0) {
@@ -283,22 +329,32 @@ __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2*
   }
 }
 
-template <typename TIN, int W, bool SPECTRA>
+// Persistent CTAs take (template, segment-chunk) items from `queue`.  Per
+// item: FP64 anchors of all its segments; per segment: samples staged in
+// shared memory by a TMA bulk copy (the next segment's copy overlaps this
+// segment's FFT), spread, FFT, deconvolve, then either write F (SPECTRA) or
+// add (P - 2) / 2 into the item's running sum Z.
+template <int W, bool SPECTRA>
 __global__ void __launch_bounds__(kSpreadThreads)
-k_mixed(const TIN* __restrict__ strain, const Item* __restrict__ items, int n_items,
-        const Anchor* __restrict__ anchors, int* __restrict__ queue, MixedArgs a,
-        float* __restrict__ partial, double2* __restrict__ Fout) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  float2* g0 = reinterpret_cast<float2*>(smem);
-  float2* g1 = g0 + a.n_fine;
-  float* Z = reinterpret_cast<float*>(g1 + a.n_fine);
-  Anchor* anc = reinterpret_cast<Anchor*>(Z + ((a.n_bins + 3) & ~3));
-  float* xs = reinterpret_cast<float*>(anc + kSpreadWarps);
-  __shared__ int s_item;
+k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_items,
+        const double* __restrict__ betas, int* __restrict__ queue, MixedArgs a,
+        float* __restrict__ partial, double2* __restrict__ Fout, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* xs = reinterpret_cast<float*>(smem);                       // [ns4]
+  float2* g0 = reinterpret_cast<float2*>(xs + a.ns4);               // [n_fine]
+  float2* g1 = g0 + a.n_fine;                                       // [n_fine]
+  float* Z = reinterpret_cast<float*>(g1 + a.n_fine);               // [nb4]
+  Anchor* anc = reinterpret_cast<Anchor*>(Z + a.nb4);               // [chunk * n_anchor]
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ int s_item, s_abort;
   __shared__ int8_t s_rad[16];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid < 16) s_rad[tid] = a.radices[tid];
+  if (tid == 0) { mbar_init(&s_bar); s_abort = 0; }
+  __syncthreads();
   const float2* __restrict__ tw = reinterpret_cast<const float2*>(a.tw);
+  const uint32_t seg_bytes = (uint32_t)a.n_s * 4u;
+  uint32_t parity = 0;
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(queue, 1);
@@ -306,21 +362,42 @@ k_mixed(const TIN* __restrict__ strain, const Item* __restrict__ items, int n_it
     const int q = s_item;
     if (q >= n_items) break;
     const Item it = items[q];
+    if (tid == 0 && a.use_tma) bulk_load(xs, strain + (long long)it.i0 * a.n_s, seg_bytes, &s_bar);
+    {
+      const int na = (it.i1 - it.i0) * a.n_anchor;
+      const double b = betas[it.m];
+      for (int t = tid; t < na; t += blockDim.x)
+        anc[t] = compute_anchor(b, it.i0 + t / a.n_anchor, t % a.n_anchor, a.aa);
+    }
     if (!SPECTRA)
       for (int b = tid; b < a.n_bins; b += blockDim.x) Z[b] = 0.f;
     for (int i = it.i0; i < it.i1; ++i) {
-      const long long g = (long long)it.g0 + (i - it.i0);
-      const TIN* src = strain + (long long)i * a.n_s;
-      for (int j = tid; j < a.n_s; j += blockDim.x) xs[j] = (float)src[j];
       for (int j = tid; j < a.n_fine; j += blockDim.x) g0[j] = make_float2(0.f, 0.f);
-      if (tid < a.n_anchor) anc[tid] = anchors[g * a.n_anchor + tid];
+      if (a.use_tma) {
+        if (tid == 0 && !mbar_wait(&s_bar, parity)) {
+          // record where the wait gave up: flag, item, segment, parity, block
+          s_abort = 1;
+          if (atomicExch(err, 1) == 0) { err[1] = q; err[2] = i; err[3] = (int)parity; err[4] = blockIdx.x; }
+        }
+        parity ^= 1u;
+      } else {
+        const float* src = strain + (long long)i * a.n_s;
+        for (int j = tid; j < a.n_s; j += blockDim.x) xs[j] = src[j];
+      }
       __syncthreads();
+      if (s_abort) {
+        // give the copy in flight one more bounded wait before leaving
+        if (tid == 0) mbar_wait(&s_bar, parity ^ 1u);
+        __syncthreads();
+        return;
+      }
       {
         const int j0 = (warp * 32 + lane) * a.run;
         const int j1 = min(j0 + a.run, a.n_s);
-        if (j0 < a.n_s) spread_run<W>(xs, g0, anc[warp], j0, j1, warp * a.span, a);
+        if (j0 < a.n_s) spread_run<W>(xs, g0, anc[(i - it.i0) * a.n_anchor + warp], j0, j1, warp * a.span, a);
       }
       __syncthreads();
+      if (tid == 0 && a.use_tma && i + 1 < it.i1) bulk_load(xs, strain + (long long)(i + 1) * a.n_s, seg_bytes, &s_bar);
       float2* res = fft_smem<float2>(g0, g1, a.n_fine, s_rad, a.n_pass, tw);
       for (int b = tid; b < a.n_bins; b += blockDim.x) {
         int k = b - a.half_bins;
@@ -340,6 +417,12 @@ k_mixed(const TIN* __restrict__ strain, const Item* __restrict__ items, int n_it
     if (!SPECTRA)
       for (int b = tid; b < a.n_bins; b += blockDim.x) partial[(long long)q * a.n_bins + b] = Z[b];
   }
+}
+
+// Strain as FP32 (the mixed form's working precision for samples).
+__global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out, long long n) {
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    out[k] = (float)in[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -430,19 +513,21 @@ __device__ __forceinline__ float key_value(unsigned long long k) {
 
 // Mixed form: n_sigma[m][b] = (sum over the template's items of Z) / sqrt(nseg_m),
 // items summed in order (FP64) so the result does not depend on scheduling.
+// One thread per (template, bin).
 __global__ void k_reduce_mixed(const float* __restrict__ partial, const int* __restrict__ item_off,
-                               const int* __restrict__ nseg, int n_bins, float* __restrict__ map,
+                               const int* __restrict__ nseg, int n_templates, int n_bins, float* __restrict__ map,
                                unsigned long long* __restrict__ keys) {
-  const int m = blockIdx.x;
-  const int q0 = item_off[m], q1 = item_off[m + 1];
-  const double inv = 1.0 / sqrt((double)nseg[m]);
-  for (int b = threadIdx.x; b < n_bins; b += blockDim.x) {
+  const long long total = (long long)n_templates * n_bins;
+  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < total;
+       f += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(f / n_bins);
+    const int b = (int)(f - (long long)m * n_bins);
+    const int q0 = item_off[m], q1 = item_off[m + 1];
     double z = 0.0;
     for (int q = q0; q < q1; ++q) z += (double)partial[(long long)q * n_bins + b];
-    const float v = (float)(z * inv);
-    const uint32_t flat = (uint32_t)m * (uint32_t)n_bins + (uint32_t)b;
-    if (map) map[flat] = v;
-    keys[flat] = make_key(v, flat);
+    const float v = (float)(z / sqrt((double)nseg[m]));
+    if (map) map[f] = v;
+    keys[f] = make_key(v, (uint32_t)f);
   }
 }
 
@@ -460,21 +545,22 @@ __global__ void k_finish_plain(const double* __restrict__ S, const int* __restri
   }
 }
 
-// Top-k of each tile of kTopkTile keys: bitonic sort (descending) in shared
-// memory, first k written to out[blockIdx.x * k ...].  Missing keys are 0,
-// which sorts below every real key.
-__global__ void __launch_bounds__(1024)
-k_topk_tile(const unsigned long long* __restrict__ in, long long n, int k, unsigned long long* __restrict__ out) {
-  __shared__ unsigned long long s[kTopkTile];
-  const long long base = (long long)blockIdx.x * kTopkTile;
-  for (int t = threadIdx.x; t < kTopkTile; t += blockDim.x) {
+// Top-k of each tile of `tile` keys (a power of two, >= 2k): bitonic sort
+// (descending) in shared memory, first k written to out[blockIdx.x * k ...].
+// Missing keys are 0, which sorts below every real key.
+__global__ void __launch_bounds__(512)
+k_topk_tile(const unsigned long long* __restrict__ in, long long n, int k, int tile,
+            unsigned long long* __restrict__ out) {
+  extern __shared__ unsigned long long s[];
+  const long long base = (long long)blockIdx.x * tile;
+  for (int t = threadIdx.x; t < tile; t += blockDim.x) {
     const long long g = base + t;
     s[t] = g < n ? in[g] : 0ull;
   }
   __syncthreads();
-  for (int size = 2; size <= kTopkTile; size <<= 1) {
+  for (int size = 2; size <= tile; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int t = threadIdx.x; t < kTopkTile / 2; t += blockDim.x) {
+      for (int t = threadIdx.x; t < tile / 2; t += blockDim.x) {
         const int lo = 2 * t - (t & (stride - 1));
         const int hi = lo + stride;
         const bool desc = ((lo & size) == 0);
@@ -543,10 +629,10 @@ __global__ void k_time_map_plain(const int* __restrict__ item_m, const int* __re
 // Launchers
 // ---------------------------------------------------------------------------
 size_t mixed_smem_bytes(const MixedArgs& a) {
-  size_t s = (size_t)a.n_fine * 2 * sizeof(float2);
-  s += (size_t)((a.n_bins + 3) & ~3) * sizeof(float);
-  s += kSpreadWarps * sizeof(Anchor);
-  s += (size_t)((a.n_s + 3) & ~3) * sizeof(float);
+  size_t s = (size_t)a.ns4 * sizeof(float);
+  s += (size_t)a.n_fine * 2 * sizeof(float2);
+  s += (size_t)a.nb4 * sizeof(float);
+  s += (size_t)a.chunk * a.n_anchor * sizeof(Anchor);
   return s;
 }
 
@@ -559,12 +645,19 @@ cudaError_t launch_anchors(const Item* items, int n_items, const double* betas, 
   return cudaGetLastError();
 }
 
-template <typename TIN, int W, bool SP>
-static cudaError_t launch_mixed_t(const void* strain, const Item* items, int n_items, const Anchor* anchors,
-                                  int* queue, const MixedArgs& a, float* partial, double2* Fout, int n_sm,
+cudaError_t launch_to_f32(const double* in, float* out, long long n, int n_sm, cudaStream_t st) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > (long long)n_sm * 16) blocks = (long long)n_sm * 16;
+  k_to_f32<<<(unsigned)blocks, 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+template <int W, bool SP>
+static cudaError_t launch_mixed_t(const float* strain, const Item* items, int n_items, const double* betas,
+                                  int* queue, const MixedArgs& a, float* partial, double2* Fout, int* err, int n_sm,
                                   int ctas_per_sm, cudaStream_t st) {
   const size_t smem = mixed_smem_bytes(a);
-  auto kern = k_mixed<TIN, W, SP>;
+  auto kern = k_mixed<W, SP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -575,32 +668,24 @@ static cudaError_t launch_mixed_t(const void* strain, const Item* items, int n_i
   long long grid = (long long)n_sm * occ;
   if (grid > n_items) grid = n_items;
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, kSpreadThreads, smem, st>>>(static_cast<const TIN*>(strain), items, n_items, anchors,
-                                                      queue, a, partial, Fout);
+  kern<<<(unsigned)grid, kSpreadThreads, smem, st>>>(strain, items, n_items, betas, queue, a, partial, Fout, err);
   return cudaGetLastError();
 }
 
-template <typename TIN, bool SP>
-static cudaError_t launch_mixed_w(int w, const void* strain, const Item* items, int n_items, const Anchor* anchors,
-                                  int* queue, const MixedArgs& a, float* partial, double2* Fout, int n_sm,
-                                  int ctas_per_sm, cudaStream_t st) {
+cudaError_t launch_mixed(bool spectra, int w, const float* strain, const Item* items, int n_items,
+                         const double* betas, int* queue, const MixedArgs& a, float* partial, double2* Fout,
+                         int* err, int n_sm, int ctas_per_sm, cudaStream_t st) {
   switch (w) {
-#define SRS_W(WW) \
-  case WW: return launch_mixed_t<TIN, WW, SP>(strain, items, n_items, anchors, queue, a, partial, Fout, n_sm, ctas_per_sm, st);
+#define SRS_W(WW)                                                                                          \
+  case WW:                                                                                                 \
+    return spectra ? launch_mixed_t<WW, true>(strain, items, n_items, betas, queue, a, partial, Fout, err,  \
+                                              n_sm, ctas_per_sm, st)                                       \
+                   : launch_mixed_t<WW, false>(strain, items, n_items, betas, queue, a, partial, Fout, err, \
+                                               n_sm, ctas_per_sm, st);
     SRS_W(2) SRS_W(3) SRS_W(4) SRS_W(5) SRS_W(6) SRS_W(7) SRS_W(8)
 #undef SRS_W
     default: return cudaErrorInvalidValue;
   }
-}
-
-cudaError_t launch_mixed(bool f64_in, bool spectra, int w, const void* strain, const Item* items, int n_items,
-                         const Anchor* anchors, int* queue, const MixedArgs& a, float* partial, double2* Fout,
-                         int n_sm, int ctas_per_sm, cudaStream_t st) {
-  if (f64_in)
-    return spectra ? launch_mixed_w<double, true>(w, strain, items, n_items, anchors, queue, a, partial, Fout, n_sm, ctas_per_sm, st)
-                   : launch_mixed_w<double, false>(w, strain, items, n_items, anchors, queue, a, partial, Fout, n_sm, ctas_per_sm, st);
-  return spectra ? launch_mixed_w<float, true>(w, strain, items, n_items, anchors, queue, a, partial, Fout, n_sm, ctas_per_sm, st)
-                 : launch_mixed_w<float, false>(w, strain, items, n_items, anchors, queue, a, partial, Fout, n_sm, ctas_per_sm, st);
 }
 
 cudaError_t launch_plain(bool f64_in, bool spectra, const void* strain, const double* betas, const int* nseg,
@@ -626,8 +711,11 @@ cudaError_t launch_plain(bool f64_in, bool spectra, const void* strain, const do
 }
 
 cudaError_t launch_reduce_mixed(const float* partial, const int* item_off, const int* nseg, int n_templates,
-                                int n_bins, float* map, unsigned long long* keys, cudaStream_t st) {
-  k_reduce_mixed<<<n_templates, 256, 0, st>>>(partial, item_off, nseg, n_bins, map, keys);
+                                int n_bins, float* map, unsigned long long* keys, int n_sm, cudaStream_t st) {
+  long long total = (long long)n_templates * n_bins;
+  long long blocks = (total + 255) / 256;
+  if (blocks > (long long)n_sm * 16) blocks = (long long)n_sm * 16;
+  k_reduce_mixed<<<(unsigned)blocks, 256, 0, st>>>(partial, item_off, nseg, n_templates, n_bins, map, keys);
   return cudaGetLastError();
 }
 
@@ -640,17 +728,49 @@ cudaError_t launch_finish_plain(const double* S, const int* nseg, int n_template
   return cudaGetLastError();
 }
 
-// Reduce n keys to the top k (k <= kTopkTile / 2) through tiles; result in
-// whichever of buf_a / buf_b the last level wrote, returned in *result.
+static int pow2_at_least(long long v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Tile of the next top-k level for `cur` keys: a power of two >= 2k, at most
+// 1024 keys (4096 when 2k > 1024).
+static int topk_tile(long long cur, int k) {
+  const int kp = pow2_at_least(2 * (long long)k);
+  int tile = pow2_at_least(cur);
+  if (tile < kp) tile = kp;
+  const int cap = kp > 1024 ? kTopkTile : 1024;
+  if (tile > cap) tile = cap;
+  return tile;
+}
+
+// Keys each of the two scratch buffers of launch_topk must hold (the first
+// level writes the most).
+long long topk_scratch_keys(long long n, int k) {
+  const int tile = topk_tile(n, k);
+  return ((n + tile - 1) / tile) * (long long)k;
+}
+
+// Reduce n keys to the top k (k <= 1024) through tiles; result in whichever
+// of buf_a / buf_b (each topk_scratch_keys(n, k) keys) the last level wrote,
+// returned in *result.
 cudaError_t launch_topk(const unsigned long long* keys, long long n, int k, unsigned long long* buf_a,
                         unsigned long long* buf_b, const unsigned long long** result, int* launches,
                         cudaStream_t st) {
   const unsigned long long* src = keys;
   unsigned long long* dst = buf_a;
   long long cur = n;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_topk_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, kTopkTile * 8);
+    attr_set = true;
+  }
   for (;;) {
-    long long tiles = (cur + kTopkTile - 1) / kTopkTile;
-    k_topk_tile<<<(unsigned)tiles, 1024, 0, st>>>(src, cur, k, dst);
+    const int tile = topk_tile(cur, k);
+    const long long tiles = (cur + tile - 1) / tile;
+    const int threads = tile / 2 < 512 ? tile / 2 : 512;
+    k_topk_tile<<<(unsigned)tiles, threads, (size_t)tile * 8, st>>>(src, cur, k, tile, dst);
     ++*launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

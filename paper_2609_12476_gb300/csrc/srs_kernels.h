@@ -19,7 +19,11 @@ struct AnchorArgs {
 struct MixedArgs {
   int n_s, n_fine, n_bins, half_bins;
   int run, span, n_anchor, n_pass;
+  int ns4, nb4;                   // n_s, n_bins rounded up to multiples of 4 (shared-memory layout)
+  int chunk;                      // most segments in one item
+  int use_tma;                    // 1: samples staged by TMA bulk copies (n_s % 4 == 0, 16-byte aligned strain)
   int seg_begin, seg_range;       // spectra output: first segment, segments per template
+  AnchorArgs aa;                  // FP64 anchor inputs
   float kc;                       // f_c * t_coh
   float inv_ns;                   // 1 / n_s
   float es_beta_log2e;            // ES shape parameter * log2(e)
@@ -42,16 +46,18 @@ size_t mixed_smem_bytes(const MixedArgs& a);
 
 cudaError_t launch_anchors(const Item* items, int n_items, const double* betas, const AnchorArgs& aa,
                            Anchor* out, long long total, int n_sm, cudaStream_t st);
-cudaError_t launch_mixed(bool f64_in, bool spectra, int w, const void* strain, const Item* items, int n_items,
-                         const Anchor* anchors, int* queue, const MixedArgs& a, float* partial, double2* Fout,
-                         int n_sm, int ctas_per_sm, cudaStream_t st);
+cudaError_t launch_to_f32(const double* in, float* out, long long n, int n_sm, cudaStream_t st);
+cudaError_t launch_mixed(bool spectra, int w, const float* strain, const Item* items, int n_items,
+                         const double* betas, int* queue, const MixedArgs& a, float* partial, double2* Fout,
+                         int* err, int n_sm, int ctas_per_sm, cudaStream_t st);
 cudaError_t launch_plain(bool f64_in, bool spectra, const void* strain, const double* betas, const int* nseg,
                          const PlainArgs& p, int grid_x, int n_templates, double* S, double2* Fout,
                          cudaStream_t st);
 cudaError_t launch_reduce_mixed(const float* partial, const int* item_off, const int* nseg, int n_templates,
-                                int n_bins, float* map, unsigned long long* keys, cudaStream_t st);
+                                int n_bins, float* map, unsigned long long* keys, int n_sm, cudaStream_t st);
 cudaError_t launch_finish_plain(const double* S, const int* nseg, int n_templates, int n_bins, float* map,
                                 unsigned long long* keys, int n_sm, cudaStream_t st);
+long long topk_scratch_keys(long long n, int k);
 cudaError_t launch_topk(const unsigned long long* keys, long long n, int k, unsigned long long* buf_a,
                         unsigned long long* buf_b, const unsigned long long** result, int* launches,
                         cudaStream_t st);

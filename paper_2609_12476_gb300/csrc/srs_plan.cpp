@@ -119,7 +119,7 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
   if (p.precision != SRS_PLAIN_FP64 && p.precision != SRS_MIXED) return fail(SRS_ERR_ARG, "unknown precision");
   if (p.deterministic != 0 && p.deterministic != 1) return fail(SRS_ERR_ARG, "deterministic must be 0 or 1");
   if (p.sigma != 0 && !(p.sigma >= 1.2 && p.sigma <= 4.0)) return fail(SRS_ERR_ARG, "sigma must be 0 (auto) or in [1.2, 4]");
-  if (p.chunk < 0 || p.chunk > 4096) return fail(SRS_ERR_ARG, "chunk must be in [0, 4096]");
+  if (p.chunk < 0) return fail(SRS_ERR_ARG, "chunk must be in [0, 16]");
 
   pl = Plan();
   pl.fs = p.fs; pl.t_coh = p.t_coh; pl.f_lo = p.f_lo; pl.f_hi = p.f_hi; pl.f_ref = p.f_ref; pl.eps = p.eps;
@@ -191,7 +191,8 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
     if (pl.w > kMixedMaxW) return fail(SRS_ERR_UNSUPPORTED, "kernel width above the mixed form's maximum (raise eps or sigma)");
     pl.n_fine = next_smooth(std::max((int32_t)std::ceil(pl.sigma * pl.n_bins - 1e-9), 2 * pl.w));
     // shared memory of the mixed spreader: staged samples + grid + FFT scratch + Z
-    size_t need = (size_t)pl.n_s * 4 + (size_t)pl.n_fine * 16 + (size_t)pl.n_bins * 4 + 1024;
+    // + anchors of one item (at most 16 segments)
+    size_t need = (size_t)pl.n_s * 4 + (size_t)pl.n_fine * 16 + (size_t)pl.n_bins * 4 + 16 * 8 * 48 + 1024;
     if (need > smem_cap) return fail(SRS_ERR_UNSUPPORTED, "segment too long or band too wide for the mixed form's shared memory");
   } else {
     const double sig_try[3] = {2.0, 1.5, 1.25};
@@ -262,6 +263,7 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
   }
 
   // Default chunk: enough items to keep ~8 per resident CTA of a 152-SM part.
+  if (p.chunk > 16) return fail(SRS_ERR_ARG, "chunk must be in [0, 16]");
   int32_t chunk = p.chunk;
   if (chunk == 0) {
     int64_t per = pl.n_spectra / (8 * 152 * 4);
