@@ -58,6 +58,7 @@
 #ifndef SRS_H
 #define SRS_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -195,6 +196,42 @@ srs_status srs_time_map(srs_ctx* ctx, const double* mc, int32_t n_templates,
                         const int32_t* item_m, const int32_t* item_i, int32_t n_items,
                         const srs_params* params, int64_t n_samples, double* psi_out,
                         double* theta_out);
+
+/* Size of the fixed device scratch used by srs_segment_spectra_static(). */
+#define SRS_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* Segment spectra without allocating device memory.  The paper has no
+ * counterpart: this is a service for callers that must not let a library
+ * call cudaMalloc / cudaFree -- pipelines whose device memory is all handed
+ * to their own allocator at start-up, and low-latency paths that cannot take
+ * the stall or the device-wide synchronisation of allocating and freeing.
+ *
+ * It computes exactly what srs_segment_spectra() computes in the mixed form
+ * (params->precision must be SRS_MIXED), with the same kernel, but the
+ * kernel's scratch -- its tables, work queue and error flag, and the float32
+ * copy of float64 strain -- lives in one fixed array of
+ * SRS_STATIC_SCRATCH_BYTES that is part of the library and is held on every
+ * GPU that loads the library until the process exits.  No context is used.
+ *   cuda_stream  cudaStream_t to run on (NULL: the legacy default stream), on
+ *                the current device
+ *   strain       device pointer, [n_samples] of `dtype`
+ *   mc           host, [n_templates] chirp masses at params->f_ref
+ *   F            device pointer, [n_templates][seg_end-seg_begin][n_bins]
+ *                complex double (re, im interleaved), caller-owned
+ *   err_msg      optional host buffer of err_len bytes for a message
+ * Returns SRS_ERR_ARG (with a message) when the request needs more scratch
+ * than SRS_STATIC_SCRATCH_BYTES (many templates x segments, or long float64
+ * strain), when a pointer is not a device pointer, or for any argument
+ * srs_segment_spectra() would reject.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) for that device; make
+ * that first call before any stream capture.  Every call reuses the same
+ * array and clears what must start at zero; calls that overlap on the GPU
+ * (other streams, other host threads) race on it and must be serialised by
+ * the caller.  Synchronous with respect to the host. */
+srs_status srs_segment_spectra_static(void* cuda_stream, const void* strain, int64_t n_samples,
+                                      int32_t dtype, const double* mc, int32_t n_templates,
+                                      int32_t seg_begin, int32_t seg_end, const srs_params* params,
+                                      double* F, char* err_msg, size_t err_len);
 
 #ifdef __cplusplus
 }

@@ -22,7 +22,7 @@ SRS_PLAIN_FP64, SRS_MIXED = 0, 1
 
 # Entry points declared in include/srs.h (checked by the tests).
 EXPORTS = ("srs_create", "srs_destroy", "srs_last_error", "srs_plan", "srs_search",
-           "srs_segment_spectra", "srs_time_map")
+           "srs_segment_spectra", "srs_time_map", "srs_segment_spectra_static")
 
 
 class SrsError(RuntimeError):
@@ -110,6 +110,9 @@ def lib():
                                           ctypes.POINTER(_Report)]
         L.srs_time_map.restype = i32
         L.srs_time_map.argtypes = [vp, vp, i32, vp, vp, i32, ctypes.POINTER(_Params), i64, vp, vp]
+        L.srs_segment_spectra_static.restype = i32
+        L.srs_segment_spectra_static.argtypes = [vp, vp, i64, i32, vp, i32, i32, i32, ctypes.POINTER(_Params),
+                                                 vp, ctypes.c_char_p, ctypes.c_size_t]
         _LIB = L
     return _LIB
 
@@ -252,3 +255,28 @@ class Context:
                                     th.ctypes.data)
         self._check(st)
         return psi, th
+
+
+def segment_spectra_static(strain, mc, seg_begin, seg_end, params, F=None, stream=None):
+    """srs_segment_spectra_static: the mixed-form segment spectra for callers
+    that cannot let the library allocate device memory.  `strain` is a torch
+    CUDA tensor (float32 or float64); F, if given, a complex128 CUDA tensor
+    [templates, seg_end - seg_begin, n_bins] that receives the result; stream
+    a torch.cuda.Stream (default: the current stream).  Returns F."""
+    import torch
+    if not _is_torch_cuda(strain):
+        raise TypeError("strain must be a CUDA tensor")
+    mc = np.ascontiguousarray(mc, dtype=np.float64)
+    n_bins = int(round((params.f_hi - params.f_lo) * params.t_coh))
+    if F is None:
+        F = torch.empty((mc.size, seg_end - seg_begin, n_bins), dtype=torch.complex128, device=strain.device)
+    s = stream if stream is not None else torch.cuda.current_stream(strain.device)
+    p = params.c()
+    p.io_on_device = 1
+    buf = ctypes.create_string_buffer(256)
+    st = lib().srs_segment_spectra_static(ctypes.c_void_p(s.cuda_stream), strain.data_ptr(), strain.numel(),
+                                          _dtype_code(strain), mc.ctypes.data, mc.size, int(seg_begin),
+                                          int(seg_end), ctypes.byref(p), F.data_ptr(), buf, 256)
+    if st != SRS_OK:
+        raise SrsError(st, buf.value.decode())
+    return F
