@@ -106,6 +106,7 @@ MixedArgs mixed_args(const Plan& pl, const srs_ctx* ctx, int seg_begin, int seg_
   a.aa.n_s = pl.n_s;
   a.aa.span = pl.span;
   a.aa.n_anchor = pl.n_anchor;
+  a.fft_fixed = (pl.n_fine == 1200 && pl.radices == std::vector<int32_t>{4, 4, 3, 5, 5}) ? 1200 : 0;
   a.kc = (float)pl.k_c;
   a.inv_ns = (float)(1.0 / (double)pl.n_s);
   a.es_beta_log2e = (float)(pl.beta_es * 1.4426950408889634074);

@@ -111,6 +111,46 @@ __device__ __forceinline__ void stockham_pass(const C* __restrict__ in, C* __res
   }
 }
 
+// One Stockham pass with the radix, stride and size known at compile time
+// (index arithmetic folds to multiplies and shifts).
+template <typename C, int R, int Ns, int N>
+__device__ __forceinline__ void stockham_pass_c(const C* __restrict__ in, C* __restrict__ out,
+                                                const C* __restrict__ tw) {
+  constexpr int nR = N / R;
+  constexpr int step = N / (Ns * R);
+  for (int j = threadIdx.x; j < nR; j += blockDim.x) {
+    const int jm = j % Ns;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in[j + r * nR];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[jm * r * step]);
+    }
+    Dft<C, R>::run(v);
+    const int idxD = (j - jm) * R + jm;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[idxD + r * Ns] = v[r];
+  }
+}
+
+// n = 1200 = 4 * 4 * 3 * 5 * 5 (the 40-60 Hz band at oversampling 2), five
+// passes ending in b.
+template <typename C>
+__device__ __forceinline__ C* fft_1200(C* a, C* b, const C* __restrict__ tw) {
+  stockham_pass_c<C, 4, 1, 1200>(a, b, tw);
+  __syncthreads();
+  stockham_pass_c<C, 4, 4, 1200>(b, a, tw);
+  __syncthreads();
+  stockham_pass_c<C, 3, 16, 1200>(a, b, tw);
+  __syncthreads();
+  stockham_pass_c<C, 5, 48, 1200>(b, a, tw);
+  __syncthreads();
+  stockham_pass_c<C, 5, 240, 1200>(a, b, tw);
+  __syncthreads();
+  return b;
+}
+
 // Forward FFT of a[0..n) in shared memory, ping-ponging with b.  Returns the
 // buffer that holds the result.  Every thread of the block must call it.
 template <typename C>
@@ -258,6 +298,40 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
+// Tap inputs of one sample: first fine-grid cell l0 (wrapped into [0, n)),
+// the kernel argument of tap 0, and the demodulated sample c = x exp(-2 pi i th).
+struct TapIn {
+  int l0;
+  float z0, cre, cim;
+};
+
+__device__ __forceinline__ TapIn tap_inputs(const Anchor& A, const float* __restrict__ xs, int j, int l_base,
+                                            int W, const MixedArgs& a) {
+  uint32_t Psi;
+  float th;
+  mixed_phase(A, j - l_base, a.kc, Psi, th);
+  const int n = a.n_fine;
+  const int cell = (int)__umulhi(Psi, (uint32_t)n);
+  const float fr = (float)(Psi * (uint32_t)n) * 2.3283064365386963e-10f;
+  float sn, cs;
+  __sincosf(6.28318530717958647692f * th, &sn, &cs);
+  const float xv = xs[j];
+  const float off = ceilf(fr - 0.5f * (float)W);
+  TapIn t;
+  int l0 = cell + (int)off;
+  if (l0 < 0) l0 += n; else if (l0 >= n) l0 -= n;
+  t.l0 = l0;
+  t.z0 = fmaxf((off - fr) * a.two_over_w, -1.0f);
+  t.cre = xv * cs;
+  t.cim = -xv * sn;
+  return t;
+}
+
+// Spread the samples [j_begin, j_end) of one lane into `grid`.  The lane keeps
+// the W cells [Bm, Bm + W) of its kernel footprint in registers.  The warp
+// walks cell by cell: each lane adds all of its samples whose first cell is
+// Bm, then every lane moves its window one cell on (flushing acc[0] with a
+// shared-memory atomic), so the shift is warp-uniform.
 template <int W>
 __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2* __restrict__ grid,
                                            const Anchor& A, int j_begin, int j_end, int l_base,
@@ -268,61 +342,42 @@ __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2*
   const int n = a.n_fine;
   const float h = a.two_over_w;
   const float esb = a.es_beta_log2e;
-  int Bm = -1;  // fine-grid cell of acc[0]
-  for (int j = j_begin; j < j_end; ++j) {
-    uint32_t Psi;
-    float th;
-    mixed_phase(A, j - l_base, a.kc, Psi, th);
-    const int cell = (int)__umulhi(Psi, (uint32_t)n);
-    const float fr = (float)(Psi * (uint32_t)n) * 2.3283064365386963e-10f;
-    float sn, cs;
-    __sincosf(6.28318530717958647692f * th, &sn, &cs);
-    const float xv = xs[j];
-    const float cre = xv * cs, cim = -xv * sn;
-    const float off = ceilf(fr - 0.5f * (float)W);
-    int l0 = cell + (int)off;
-    if (l0 < 0) l0 += n; else if (l0 >= n) l0 -= n;
-    if (Bm < 0) Bm = l0;
-    int d = l0 - Bm;
-    if (d < -(n >> 1)) d += n;
-    if (d != 0) {
-      if (d == 1) {
-        // the window moves one cell: acc[0]'s cell is complete
-        atomicAdd(&grid[Bm].x, acc_re[0]);
-        atomicAdd(&grid[Bm].y, acc_im[0]);
+  const unsigned mask = __activemask();
+  int j = j_begin;
+  bool live = j < j_end;
+  TapIn p = {0, 0.f, 0.f, 0.f};
+  if (live) p = tap_inputs(A, xs, j, l_base, W, a);
+  int Bm = p.l0;  // fine-grid cell of acc[0]
+  while (__any_sync(mask, live)) {
+    while (live && p.l0 == Bm) {
 #pragma unroll
-        for (int t = 0; t < W - 1; ++t) { acc_re[t] = acc_re[t + 1]; acc_im[t] = acc_im[t + 1]; }
-        acc_re[W - 1] = 0.f;
-        acc_im[W - 1] = 0.f;
-      } else {
-        // jump (more than one cell per sample): flush the whole window
-#pragma unroll
-        for (int t = 0; t < W; ++t) {
-          int c = Bm + t;
-          if (c >= n) c -= n;
-          atomicAdd(&grid[c].x, acc_re[t]);
-          atomicAdd(&grid[c].y, acc_im[t]);
-          acc_re[t] = 0.f;
-          acc_im[t] = 0.f;
-        }
+      for (int t = 0; t < W; ++t) {
+        const float z = fmaf((float)t, h, p.z0);
+        const float q = fmaf(-z, z, 1.0f);
+        const float ph = ex2_approx(fmaf(esb, sqrt_approx(q), -esb));
+        acc_re[t] = fmaf(ph, p.cre, acc_re[t]);
+        acc_im[t] = fmaf(ph, p.cim, acc_im[t]);
       }
-      Bm = l0;
+      ++j;
+      live = j < j_end;
+      if (live) p = tap_inputs(A, xs, j, l_base, W, a);
     }
-    const float z0 = fmaxf((off - fr) * h, -1.0f);
+    // cell Bm is complete for this lane
+    if (acc_re[0] != 0.f || acc_im[0] != 0.f) {
+      atomicAdd(&grid[Bm].x, acc_re[0]);
+      atomicAdd(&grid[Bm].y, acc_im[0]);
+    }
 #pragma unroll
-    for (int t = 0; t < W; ++t) {
-      const float z = fmaf((float)t, h, z0);
-      const float q = fmaf(-z, z, 1.0f);
-      const float ph = ex2_approx(fmaf(esb, sqrt_approx(q), -esb));
-      acc_re[t] = fmaf(ph, cre, acc_re[t]);
-      acc_im[t] = fmaf(ph, cim, acc_im[t]);
-    }
+    for (int t = 0; t < W - 1; ++t) { acc_re[t] = acc_re[t + 1]; acc_im[t] = acc_im[t + 1]; }
+    acc_re[W - 1] = 0.f;
+    acc_im[W - 1] = 0.f;
+    Bm = (Bm + 1 == n) ? 0 : Bm + 1;
   }
-  if (Bm >= 0) {
 #pragma unroll
-    for (int t = 0; t < W; ++t) {
-      int c = Bm + t;
-      if (c >= n) c -= n;
+  for (int t = 0; t < W - 1; ++t) {
+    int c = Bm + t;
+    if (c >= n) c -= n;
+    if (acc_re[t] != 0.f || acc_im[t] != 0.f) {
       atomicAdd(&grid[c].x, acc_re[t]);
       atomicAdd(&grid[c].y, acc_im[t]);
     }
@@ -335,7 +390,7 @@ __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2*
 // segment's FFT), spread, FFT, deconvolve, then either write F (SPECTRA) or
 // add (P - 2) / 2 into the item's running sum Z.
 template <int W, bool SPECTRA>
-__global__ void __launch_bounds__(kSpreadThreads)
+__global__ void __launch_bounds__(kSpreadThreads, 4)
 k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_items,
         const double* __restrict__ betas, int* __restrict__ queue, MixedArgs a,
         float* __restrict__ partial, double2* __restrict__ Fout, int* __restrict__ err) {
@@ -398,7 +453,8 @@ k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_
       }
       __syncthreads();
       if (tid == 0 && a.use_tma && i + 1 < it.i1) bulk_load(xs, strain + (long long)(i + 1) * a.n_s, seg_bytes, &s_bar);
-      float2* res = fft_smem<float2>(g0, g1, a.n_fine, s_rad, a.n_pass, tw);
+      float2* res = a.fft_fixed == 1200 ? fft_1200<float2>(g0, g1, tw)
+                                        : fft_smem<float2>(g0, g1, a.n_fine, s_rad, a.n_pass, tw);
       for (int b = tid; b < a.n_bins; b += blockDim.x) {
         int k = b - a.half_bins;
         int idx = k < 0 ? k + a.n_fine : k;
@@ -442,7 +498,7 @@ template <typename TIN, bool SPECTRA>
 __global__ void __launch_bounds__(256)
 k_plain(const TIN* __restrict__ strain, const double* __restrict__ betas, const int* __restrict__ nseg,
         PlainArgs p, double* __restrict__ S, double2* __restrict__ Fout) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   double2* g0 = reinterpret_cast<double2*>(smem);
   double2* g1 = g0 + p.n_fine;
   __shared__ int8_t s_rad[16];

@@ -22,6 +22,7 @@ struct MixedArgs {
   int ns4, nb4;                   // n_s, n_bins rounded up to multiples of 4 (shared-memory layout)
   int chunk;                      // most segments in one item
   int use_tma;                    // 1: samples staged by TMA bulk copies (n_s % 4 == 0, 16-byte aligned strain)
+  int fft_fixed;                  // 1200: the compile-time 4-4-3-5-5 plan applies; 0: generic passes
   int seg_begin, seg_range;       // spectra output: first segment, segments per template
   AnchorArgs aa;                  // FP64 anchor inputs
   float kc;                       // f_c * t_coh

@@ -173,6 +173,7 @@ srs_status run(void* stream_v, const void* strain, int64_t n_samples, int32_t dt
   a.aa.n_s = pl.n_s;
   a.aa.span = pl.span;
   a.aa.n_anchor = pl.n_anchor;
+  a.fft_fixed = (pl.n_fine == 1200 && pl.radices == std::vector<int32_t>{4, 4, 3, 5, 5}) ? 1200 : 0;
   a.kc = (float)pl.k_c;
   a.inv_ns = (float)(1.0 / (double)pl.n_s);
   a.es_beta_log2e = (float)(pl.beta_es * 1.4426950408889634074);
