@@ -197,6 +197,110 @@ srs_status srs_time_map(srs_ctx* ctx, const double* mc, int32_t n_templates,
                         const srs_params* params, int64_t n_samples, double* psi_out,
                         double* theta_out);
 
+/* ------------------------------------------------------------------------
+ * Learned proposal.  A small network looks at a coarse-template n_sigma map
+ * and proposes which fine (template, bin) cells to compute; the full
+ * fine-template search stays the fallback and the judge.
+ *   input   a 9 x 33 patch of the coarse map around a cell (templates m-4..m+4,
+ *           bins b-16..b+16, zero outside the map), each value through asinh
+ *   network 297 -> 64 (ReLU) -> 1 logit; weights used in FP16, sums in FP32;
+ *           parameters travel as FP32 master values, one vector of
+ *           SRS_MLP_PARAMS floats: W1[64][297] row-major, b1[64], w2[64], b2
+ *   loss    binary cross entropy with logits, mean over the batch
+ * ------------------------------------------------------------------------ */
+#define SRS_MLP_TEMPLATES 9
+#define SRS_MLP_BINS 33
+#define SRS_MLP_INPUTS 297
+#define SRS_MLP_HIDDEN 64
+#define SRS_MLP_PARAMS 19137
+
+/* One injected 0PN chirp (Sec. III.A Eqs. f and phi): chirp mass mc (Msun),
+ * frequency f0 at t = 0, amplitude amp per sample, phase phi0 (rad). */
+typedef struct {
+  double mc;
+  double f0;
+  double amp;
+  double phi0;
+} srs_injection;
+
+typedef struct {
+  int32_t epochs;
+  int32_t batch;
+  float lr;          /* Adam step size */
+  float beta1;       /* Adam first-moment decay */
+  float beta2;       /* Adam second-moment decay */
+  float adam_eps;
+  uint64_t seed;     /* minibatch order */
+} srs_train_cfg;
+
+typedef struct {
+  double device_ms;          /* coarse search + scoring + refinement */
+  int64_t coarse_spectra;    /* spectra of the coarse search */
+  int32_t proposed_coarse;   /* coarse cells above the score threshold */
+  int32_t fine_cells;        /* fine (template, bin) cells evaluated */
+  int64_t fine_segment_bins; /* (segment, bin) direct sums evaluated */
+  int32_t fine_templates;    /* distinct fine templates touched */
+} srs_proposal_report;
+
+/* Synthetic strain for training and evaluation, written on the device:
+ * out[j] = (noise ? N(0,1) : 0) + sum over injections of
+ * amp cos(phi(j/fs)), where each chirp starts at t = 0 with frequency f0 and
+ * stops where its 0PN frequency (Eq. f) reaches f_hi.  The noise is a
+ * counter-based Philox-4x32 (10 rounds) stream `seed` with Box-Muller.
+ *   out  device, [n] float; inj host, [n_inj]. */
+srs_status srs_make_strain(srs_ctx* ctx, float* out, int64_t n, double fs, uint64_t seed, int32_t noise,
+                           const srs_injection* inj, int32_t n_inj, double f_hi);
+
+/* Network inputs for listed cells of a map [n_templates][n_bins]:
+ * out[k][r][c] = asinh(map[cell_m[k] + r - 4][cell_b[k] + c - 16]) (0 outside).
+ * map, cell_m, cell_b, out on the device when io_on_device = 1, else host. */
+srs_status srs_patches(srs_ctx* ctx, const float* map, int32_t n_templates, int32_t n_bins,
+                       const int32_t* cell_m, const int32_t* cell_b, int32_t n_cells, float* out,
+                       int32_t io_on_device);
+
+/* Logits of n inputs X[n][297]; params host [SRS_MLP_PARAMS]. */
+srs_status srs_mlp_forward(srs_ctx* ctx, const float* X, int32_t n, const float* params, float* logits,
+                           int32_t io_on_device);
+
+/* Loss and its gradient with respect to every parameter (same layout as
+ * params) over the batch X[n][297], labels y[n] in {0, 1}; grad and loss are
+ * host pointers. */
+srs_status srs_mlp_grad(srs_ctx* ctx, const float* X, const float* y, int32_t n, const float* params,
+                        float* grad, float* loss, int32_t io_on_device);
+
+/* Train in place: shuffled minibatches of the device set X[n][297], y[n],
+ * Adam on the FP32 master parameters (host, in/out); mean training loss of
+ * each epoch in loss_per_epoch (host, [cfg->epochs], may be NULL). */
+srs_status srs_mlp_train(srs_ctx* ctx, const float* X, const float* y, int32_t n, const srs_train_cfg* cfg,
+                         float* params, float* loss_per_epoch);
+
+/* Network score (logit) of every cell of a device map; scores on the device,
+ * [n_templates][n_bins]. */
+srs_status srs_score_map(srs_ctx* ctx, const float* map, int32_t n_templates, int32_t n_bins,
+                         const float* params, float* scores);
+
+/* n_sigma of listed (template, bin) cells, each over its template's nseg_m
+ * segments, from direct sums of the segment samples at those bins (the
+ * transform the NUFFT approximates, Sec. III.B), in the mixed precision
+ * (FP64 anchors, fixed-point phase, FP32 sums).  nsigma host, [n_cells]. */
+srs_status srs_refine(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype, const double* mc,
+                      int32_t n_templates, const srs_params* params, const int32_t* cell_m,
+                      const int32_t* cell_b, int32_t n_cells, float* nsigma, srs_report* report);
+
+/* The proposal search: the coarse search over coarse_mc, network scores of
+ * all its cells, every cell scoring above score_threshold proposes the fine
+ * templates whose nearest coarse template (in log Mc) is within one of it and
+ * bins within one of its bin; those fine cells are evaluated with
+ * srs_refine.  Outputs (host): up to max_cells evaluated cells (cell_m,
+ * cell_b, cell_nsigma; *n_cells_out = how many were evaluated, possibly more
+ * than max_cells), the top-k of them in cands, and a report. */
+srs_status srs_search_proposed(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype,
+                               const double* coarse_mc, int32_t n_coarse, const double* fine_mc,
+                               int32_t n_fine, const srs_params* params, const float* mlp_params,
+                               float score_threshold, int32_t max_cells, int32_t* cell_m, int32_t* cell_b,
+                               float* cell_nsigma, int32_t* n_cells_out, srs_candidate* cands,
+                               int32_t* n_cands, srs_proposal_report* report);
+
 /* Size of the fixed device scratch used by srs_segment_spectra_static(). */
 #define SRS_STATIC_SCRATCH_BYTES (16u << 20)
 

@@ -22,7 +22,10 @@ SRS_PLAIN_FP64, SRS_MIXED = 0, 1
 
 # Entry points declared in include/srs.h (checked by the tests).
 EXPORTS = ("srs_create", "srs_destroy", "srs_last_error", "srs_plan", "srs_search",
-           "srs_segment_spectra", "srs_time_map", "srs_segment_spectra_static")
+           "srs_segment_spectra", "srs_time_map", "srs_segment_spectra_static", "srs_make_strain",
+           "srs_patches", "srs_mlp_forward", "srs_mlp_grad", "srs_mlp_train", "srs_score_map", "srs_refine",
+           "srs_search_proposed")
+MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 297, 64, 19137
 
 
 class SrsError(RuntimeError):
@@ -55,6 +58,23 @@ class _Report(ctypes.Structure):
                 ("n_spectra", ctypes.c_int64), ("w", ctypes.c_int32), ("n_fine", ctypes.c_int32),
                 ("sigma", ctypes.c_double), ("beta_es", ctypes.c_double), ("chunk", ctypes.c_int32),
                 ("n_items", ctypes.c_int32), ("kernel_launches", ctypes.c_int32), ("spread_ms", ctypes.c_double)]
+
+
+class _Injection(ctypes.Structure):
+    _fields_ = [("mc", ctypes.c_double), ("f0", ctypes.c_double), ("amp", ctypes.c_double),
+                ("phi0", ctypes.c_double)]
+
+
+class _TrainCfg(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("adam_eps", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
+
+
+class _ProposalReport(ctypes.Structure):
+    _fields_ = [("device_ms", ctypes.c_double), ("coarse_spectra", ctypes.c_int64),
+                ("proposed_coarse", ctypes.c_int32), ("fine_cells", ctypes.c_int32),
+                ("fine_segment_bins", ctypes.c_int64), ("fine_templates", ctypes.c_int32)]
 
 
 CAND_DTYPE = np.dtype([("value", np.float32), ("template_idx", np.int32), ("bin", np.int32)])
@@ -110,6 +130,26 @@ def lib():
                                           ctypes.POINTER(_Report)]
         L.srs_time_map.restype = i32
         L.srs_time_map.argtypes = [vp, vp, i32, vp, vp, i32, ctypes.POINTER(_Params), i64, vp, vp]
+        f32p = ctypes.POINTER(ctypes.c_float)
+        L.srs_make_strain.restype = i32
+        L.srs_make_strain.argtypes = [vp, vp, i64, ctypes.c_double, ctypes.c_uint64, i32, vp, i32, ctypes.c_double]
+        L.srs_patches.restype = i32
+        L.srs_patches.argtypes = [vp, vp, i32, i32, vp, vp, i32, vp, i32]
+        L.srs_mlp_forward.restype = i32
+        L.srs_mlp_forward.argtypes = [vp, vp, i32, vp, vp, i32]
+        L.srs_mlp_grad.restype = i32
+        L.srs_mlp_grad.argtypes = [vp, vp, vp, i32, vp, vp, vp, i32]
+        L.srs_mlp_train.restype = i32
+        L.srs_mlp_train.argtypes = [vp, vp, vp, i32, ctypes.POINTER(_TrainCfg), vp, vp]
+        L.srs_score_map.restype = i32
+        L.srs_score_map.argtypes = [vp, vp, i32, i32, vp, vp]
+        L.srs_refine.restype = i32
+        L.srs_refine.argtypes = [vp, vp, i64, i32, vp, i32, ctypes.POINTER(_Params), vp, vp, i32, vp,
+                                 ctypes.POINTER(_Report)]
+        L.srs_search_proposed.restype = i32
+        L.srs_search_proposed.argtypes = [vp, vp, i64, i32, vp, i32, vp, i32, ctypes.POINTER(_Params), vp,
+                                          ctypes.c_float, i32, vp, vp, vp, ctypes.POINTER(i32), vp,
+                                          ctypes.POINTER(i32), ctypes.POINTER(_ProposalReport)]
         L.srs_segment_spectra_static.restype = i32
         L.srs_segment_spectra_static.argtypes = [vp, vp, i64, i32, vp, i32, i32, i32, ctypes.POINTER(_Params),
                                                  vp, ctypes.c_char_p, ctypes.c_size_t]
@@ -241,6 +281,146 @@ class Context:
                                            ctypes.byref(rep))
         self._check(st)
         return F, _report_dict(rep)
+
+    # ----- learned proposal -----------------------------------------------
+    def make_strain(self, n, fs, seed, injections=(), f_hi=60.0, noise=True, out=None):
+        """srs_make_strain: float32 CUDA tensor [n] of seeded noise plus 0PN
+        chirps (dicts with mc, f0, amp and optional phi0)."""
+        import torch
+        if out is None:
+            out = torch.empty(int(n), dtype=torch.float32, device="cuda:%d" % self.device)
+        arr = (_Injection * max(1, len(injections)))()
+        for k, inj in enumerate(injections):
+            arr[k] = _Injection(inj["mc"], inj["f0"], inj["amp"], inj.get("phi0", 0.0))
+        st = self._lib.srs_make_strain(self._h, out.data_ptr(), int(n), float(fs), int(seed) & (2 ** 64 - 1),
+                                       1 if noise else 0, ctypes.cast(arr, ctypes.c_void_p), len(injections),
+                                       float(f_hi))
+        self._check(st)
+        return out
+
+    def patches(self, stat_map, cells):
+        """srs_patches for (m, b) cells of a map: numpy map -> numpy [n, 297];
+        torch CUDA map -> torch CUDA [n, 297]."""
+        cells = np.asarray(cells, dtype=np.int32).reshape(-1, 2)
+        n = cells.shape[0]
+        if _is_torch_cuda(stat_map):
+            import torch
+            M, NB = stat_map.shape
+            cm = torch.from_numpy(np.ascontiguousarray(cells[:, 0])).to(stat_map.device)
+            cb = torch.from_numpy(np.ascontiguousarray(cells[:, 1])).to(stat_map.device)
+            out = torch.empty((n, MLP_INPUTS), dtype=torch.float32, device=stat_map.device)
+            torch.cuda.synchronize()
+            st = self._lib.srs_patches(self._h, stat_map.data_ptr(), M, NB, cm.data_ptr(), cb.data_ptr(), n,
+                                       out.data_ptr(), 1)
+            self._check(st)
+            return out
+        stat_map = np.ascontiguousarray(stat_map, dtype=np.float32)
+        M, NB = stat_map.shape
+        cm = np.ascontiguousarray(cells[:, 0]); cb = np.ascontiguousarray(cells[:, 1])
+        out = np.empty((n, MLP_INPUTS), dtype=np.float32)
+        st = self._lib.srs_patches(self._h, stat_map.ctypes.data, M, NB, cm.ctypes.data, cb.ctypes.data, n,
+                                   out.ctypes.data, 0)
+        self._check(st)
+        return out
+
+    def mlp_forward(self, X, params):
+        """srs_mlp_forward: logits of inputs X [n, 297] (numpy or torch CUDA)."""
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        if _is_torch_cuda(X):
+            import torch
+            out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+            st = self._lib.srs_mlp_forward(self._h, X.data_ptr(), X.shape[0], params.ctypes.data, out.data_ptr(), 1)
+            self._check(st)
+            return out
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        out = np.empty(X.shape[0], dtype=np.float32)
+        st = self._lib.srs_mlp_forward(self._h, X.ctypes.data, X.shape[0], params.ctypes.data, out.ctypes.data, 0)
+        self._check(st)
+        return out
+
+    def mlp_grad(self, X, y, params):
+        """srs_mlp_grad: (gradient [19137], mean loss) over host X [n, 297], y [n]."""
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        g = np.empty(MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_float(0.0)
+        st = self._lib.srs_mlp_grad(self._h, X.ctypes.data, y.ctypes.data, X.shape[0], params.ctypes.data,
+                                    g.ctypes.data, ctypes.byref(loss), 0)
+        self._check(st)
+        return g, loss.value
+
+    def mlp_train(self, X, y, params, epochs=20, batch=256, lr=1e-3, seed=0, beta1=0.9, beta2=0.999, eps=1e-8):
+        """srs_mlp_train on a CUDA training set X [n, 297], y [n]; returns
+        (trained FP32 parameters, mean loss of each epoch)."""
+        p = np.array(params, dtype=np.float32)
+        losses = np.zeros(epochs, dtype=np.float32)
+        cfg = _TrainCfg(int(epochs), int(batch), float(lr), float(beta1), float(beta2), float(eps),
+                        int(seed) & (2 ** 64 - 1))
+        st = self._lib.srs_mlp_train(self._h, X.data_ptr(), y.data_ptr(), X.shape[0], ctypes.byref(cfg),
+                                     p.ctypes.data, losses.ctypes.data)
+        self._check(st)
+        return p, losses
+
+    def score_map(self, stat_map, params):
+        """srs_score_map: logits of every cell of a CUDA map [templates, bins]."""
+        import torch
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        M, NB = stat_map.shape
+        out = torch.empty((M, NB), dtype=torch.float32, device=stat_map.device)
+        st = self._lib.srs_score_map(self._h, stat_map.data_ptr(), M, NB, params.ctypes.data, out.data_ptr())
+        self._check(st)
+        return out
+
+    def refine(self, strain, mc, params, cells):
+        """srs_refine: n_sigma (numpy) of listed (m, b) cells by direct sums."""
+        mc = np.ascontiguousarray(mc, dtype=np.float64)
+        cells = np.asarray(cells, dtype=np.int32).reshape(-1, 2)
+        cm = np.ascontiguousarray(cells[:, 0]); cb = np.ascontiguousarray(cells[:, 1])
+        ns = np.empty(cells.shape[0], dtype=np.float32)
+        p = params.c()
+        rep = _Report()
+        if _is_torch_cuda(strain):
+            p.io_on_device = 1
+            ptr, n = strain.data_ptr(), strain.numel()
+        else:
+            strain = np.ascontiguousarray(strain)
+            p.io_on_device = 0
+            ptr, n = strain.ctypes.data, strain.size
+        st = self._lib.srs_refine(self._h, ptr, n, _dtype_code(strain), mc.ctypes.data, mc.size, ctypes.byref(p),
+                                  cm.ctypes.data, cb.ctypes.data, cells.shape[0], ns.ctypes.data,
+                                  ctypes.byref(rep))
+        self._check(st)
+        return ns, _report_dict(rep)
+
+    def search_proposed(self, strain, coarse_mc, fine_mc, params, mlp_params, threshold, max_cells=1 << 20):
+        """srs_search_proposed: returns dict(cells [n, 2], nsigma [n], cands,
+        report)."""
+        cmc = np.ascontiguousarray(coarse_mc, dtype=np.float64)
+        fmc = np.ascontiguousarray(fine_mc, dtype=np.float64)
+        mp = np.ascontiguousarray(mlp_params, dtype=np.float32)
+        cm = np.empty(max_cells, dtype=np.int32); cb = np.empty(max_cells, dtype=np.int32)
+        ns = np.empty(max_cells, dtype=np.float32)
+        nout = ctypes.c_int32(0); nc = ctypes.c_int32(0)
+        cands = np.zeros(max(1, params.top_k), dtype=CAND_DTYPE)
+        rep = _ProposalReport()
+        p = params.c()
+        if _is_torch_cuda(strain):
+            p.io_on_device = 1
+            ptr, n = strain.data_ptr(), strain.numel()
+        else:
+            strain = np.ascontiguousarray(strain)
+            p.io_on_device = 0
+            ptr, n = strain.ctypes.data, strain.size
+        st = self._lib.srs_search_proposed(self._h, ptr, n, _dtype_code(strain), cmc.ctypes.data, cmc.size,
+                                           fmc.ctypes.data, fmc.size, ctypes.byref(p), mp.ctypes.data,
+                                           float(threshold), max_cells, cm.ctypes.data, cb.ctypes.data,
+                                           ns.ctypes.data, ctypes.byref(nout), cands.ctypes.data,
+                                           ctypes.byref(nc), ctypes.byref(rep))
+        self._check(st)
+        k = min(nout.value, max_cells)
+        return {"cells": np.stack([cm[:k], cb[:k]], axis=1), "nsigma": ns[:k], "n_cells": nout.value,
+                "cands": cands[:nc.value], "report": {f: getattr(rep, f) for f, _ in _ProposalReport._fields_}}
 
     def time_map(self, mc, items, params, n_samples):
         """srs_time_map: (psi, theta) float64 [len(items), n_s] for (m, i) items."""

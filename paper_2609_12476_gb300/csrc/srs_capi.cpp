@@ -14,69 +14,13 @@
 #include <string>
 #include <vector>
 
+#include "srs_ctx.h"
 #include "srs_internal.h"
 #include "srs_kernels.h"
 
 using namespace srs;
 
 namespace {
-
-struct DevBuf {
-  void* p = nullptr;
-  size_t cap = 0;
-  cudaError_t ensure(size_t bytes) {
-    if (bytes <= cap && p) return cudaSuccess;
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-    size_t b = std::max<size_t>(bytes, 256);
-    cudaError_t e = cudaMalloc(&p, b);
-    if (e == cudaSuccess) cap = b;
-    return e;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-  }
-  template <typename T> T* as() const { return static_cast<T*>(p); }
-};
-
-}  // namespace
-
-struct srs_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int n_sm = 0;
-  std::string err;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
-  // last plan whose tables are on the device (key: call kind, sizes, params, templates)
-  bool have_plan = false;
-  std::vector<unsigned char> plan_key;
-  Plan plan;
-  DevBuf items, anchors, partial, betas, nseg, item_off, corr, tw, keys, topk_a, topk_b, cands, queue, strain,
-      strain32, errflag, map, S, F, psi, th, im, ii;
-};
-
-namespace {
-
-srs_status set_err(srs_ctx* c, srs_status s, const std::string& m) {
-  if (c) c->err = m;
-  return s;
-}
-
-srs_status cuda_err(srs_ctx* c, cudaError_t e, const char* where) {
-  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
-  cudaGetLastError();  // clear a sticky-free error so the context stays usable
-  return set_err(c, e == cudaErrorMemoryAllocation ? SRS_ERR_OOM : SRS_ERR_CUDA, m);
-}
-
-#define SRS_CK(call, where)                         \
-  do {                                              \
-    cudaError_t e_ = (call);                        \
-    if (e_ != cudaSuccess) return cuda_err(ctx, e_, where); \
-  } while (0)
 
 void fill_radices(const Plan& pl, int8_t* r) {
   for (int k = 0; k < 16; ++k) r[k] = 0;
@@ -250,6 +194,10 @@ srs_status get_plan(srs_ctx* ctx, int kind, const srs_params* params, const doub
   return SRS_OK;
 }
 
+}  // namespace
+
+namespace srs {
+
 // The mixed form reads FP32 samples: convert FP64 strain once per call, and
 // use FP32 strain in place when TMA can read it (16-byte aligned, n_s % 4 == 0).
 srs_status strain_f32(srs_ctx* ctx, const void* dstrain, int32_t dtype, int64_t samples, int64_t n_s,
@@ -271,6 +219,10 @@ srs_status strain_f32(srs_ctx* ctx, const void* dstrain, int32_t dtype, int64_t 
   return SRS_OK;
 }
 
+}  // namespace srs
+
+namespace {
+
 srs_status check_err_flag(srs_ctx* ctx) {
   int flag[5] = {0, 0, 0, 0, 0};
   SRS_CK(cudaMemcpy(flag, ctx->errflag.p, sizeof flag, cudaMemcpyDeviceToHost), "read error flag");
@@ -283,9 +235,11 @@ srs_status check_err_flag(srs_ctx* ctx) {
   return SRS_OK;
 }
 
-srs_status search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype, const double* mc,
-                       int32_t n_templates, const srs_params* params, float* stat_map, srs_candidate* cands,
-                       int32_t* n_cands, srs_report* report) {
+}  // namespace
+
+srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype, const double* mc,
+                            int32_t n_templates, const srs_params* params, float* stat_map, srs_candidate* cands,
+                            int32_t* n_cands, srs_report* report) {
   srs_status s = check_common(ctx, strain, dtype, params);
   if (s != SRS_OK) return s;
   if (!cands || !n_cands) return set_err(ctx, SRS_ERR_ARG, "cands and n_cands are required");
@@ -396,6 +350,8 @@ srs_status search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
   }
   return SRS_OK;
 }
+
+namespace {
 
 srs_status spectra_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype, const double* mc,
                         int32_t n_templates, int32_t seg_begin, int32_t seg_end, const srs_params* params,
@@ -570,10 +526,7 @@ void srs_destroy(srs_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
-  for (DevBuf* b : {&c->items, &c->anchors, &c->partial, &c->betas, &c->nseg, &c->item_off, &c->corr, &c->tw,
-                    &c->keys, &c->topk_a, &c->topk_b, &c->cands, &c->queue, &c->strain, &c->strain32,
-                    &c->errflag, &c->map, &c->S, &c->F, &c->psi, &c->th, &c->im, &c->ii})
-    b->release();
+  for (DevBuf* b : c->all_buffers()) b->release();
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->ev2) cudaEventDestroy(c->ev2);

@@ -1,0 +1,89 @@
+// srs_ctx.h -- the context object behind srs_ctx* and the helpers every C ABI
+// source of libsrs uses (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "srs_internal.h"
+
+namespace srs {
+
+// A device buffer that only grows.
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t b = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e == cudaSuccess) cap = b;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+}  // namespace srs
+
+struct srs_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int n_sm = 0;
+  std::string err;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+  // last plan whose tables are on the device (key: call kind, sizes, params, templates)
+  bool have_plan = false;
+  std::vector<unsigned char> plan_key;
+  srs::Plan plan;
+  srs::DevBuf items, anchors, partial, betas, nseg, item_off, corr, tw, keys, topk_a, topk_b, cands, queue, strain,
+      strain32, errflag, map, S, F, psi, th, im, ii;
+  // learned proposal
+  srs::DevBuf xb, yb, z1, logits, dz, lossv, grad, wts, adam_m, adam_v, w1h, w2h, idx, patches, cells_m, cells_b,
+      sp_items, sp_bins, sp_partial, sp_cells, sp_out, cmap, ccands, inj;
+  std::vector<srs::DevBuf*> all_buffers() {
+    return {&items, &anchors, &partial, &betas, &nseg, &item_off, &corr, &tw, &keys, &topk_a, &topk_b, &cands,
+            &queue, &strain, &strain32, &errflag, &map, &S, &F, &psi, &th, &im, &ii, &xb, &yb, &z1, &logits, &dz,
+            &lossv, &grad, &wts, &adam_m, &adam_v, &w1h, &w2h, &idx, &patches, &cells_m, &cells_b, &sp_items,
+            &sp_bins, &sp_partial, &sp_cells, &sp_out, &cmap, &ccands, &inj};
+  }
+};
+
+namespace srs {
+
+inline srs_status set_err(srs_ctx* c, srs_status s, const std::string& m) {
+  if (c) c->err = m;
+  return s;
+}
+
+inline srs_status cuda_err(srs_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();  // clear a non-sticky error so the context stays usable
+  return set_err(c, e == cudaErrorMemoryAllocation ? SRS_ERR_OOM : SRS_ERR_CUDA, m);
+}
+
+// Search entry used by the proposal pipeline (srs_capi.cpp).
+srs_status search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype, const double* mc,
+                       int32_t n_templates, const srs_params* params, float* stat_map, srs_candidate* cands,
+                       int32_t* n_cands, srs_report* report);
+srs_status strain_f32(srs_ctx* ctx, const void* dstrain, int32_t dtype, int64_t samples, int64_t n_s,
+                      const float** out, int* use_tma);
+
+}  // namespace srs
+
+#define SRS_CK(call, where)                                  \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return srs::cuda_err(ctx, e_, where); \
+  } while (0)

@@ -67,6 +67,9 @@ struct Plan {
   std::vector<double> tw_re, tw_im;                      // [n_fine] exp(-2 pi i m / n_fine)
 };
 
+// Sec. II Eq. (beta) for chirp mass mc (Msun) at frequency f (Hz), in 1/s.
+double chirp_beta(double mc, double f);
+
 // Host planner (srs_plan.cpp).  Returns SRS_OK or an error with `msg` set.
 srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
                      int64_t n_samples, bool need_segments_all, int32_t seg_begin,

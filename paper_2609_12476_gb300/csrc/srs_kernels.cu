@@ -18,6 +18,7 @@
 
 #include "srs_internal.h"
 #include "srs_kernels.h"
+#include "srs_device.cuh"
 
 namespace srs {
 
@@ -189,57 +190,6 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // K1: FP64 anchors of the resampled time (Eq. new_t), one thread per
 // (segment, anchor).  Segment g belongs to the item with the largest g0 <= g.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t frac_to_u32(double f) {  // f in [0, 1)
-  long long v = __double2ll_rn(f * 4294967296.0);
-  return (uint32_t)(v & 0xffffffffLL);
-}
-
-// Anchor ai of segment i of a template with chirp parameter b (Eq. new_t
-// expanded around the anchor sample l_a = ai * span): the segment-local
-// resampled time delta(s) = tau(t_i0 + s) - tau(t_i0) at s0 = l_a / fs, written
-// without cancellation, its derivative A^(-3/8) (= f / f0, Eq. f), and the
-// Taylor coefficients of delta in the sample index.
-__device__ __forceinline__ Anchor compute_anchor(double b, int i, int ai, const AnchorArgs& aa) {
-  const double t_i0 = (double)i * (double)aa.n_s / aa.fs;
-  const double a = 1.0 - (8.0 / 3.0) * b * t_i0;
-  const double a58 = exp(0.625 * log(a));                       // a^(5/8)
-  const double s0 = (double)ai * (double)aa.span / aa.fs;
-  const double x = (8.0 / 3.0) * b * s0 / a;
-  const double L = log1p(-x);                                     // log(A / a)
-  const double d0 = 3.0 * a58 / (5.0 * b) * (-expm1(0.625 * L)); // delta(s0)
-  const double e1 = (a58 / a) * exp(-0.375 * L);                  // A^(-3/8) = d delta / ds
-  const double A = a * (1.0 - x);                                 // 1 - 8/3 beta (t_i0 + s0)
-  Anchor an;
-  double psi = d0 / aa.t_coh;
-  an.psi0 = frac_to_u32(psi - floor(psi));
-  double P1 = e1 / (aa.fs * aa.t_coh);
-  double P1f = P1 - floor(P1);
-  double N1 = rint(P1f * 4294967296.0);
-  an.n1 = (uint32_t)((long long)N1 & 0xffffffffLL);
-  an.p1lo = (float)(P1f - N1 * 2.3283064365386962890625e-10);
-  double th = aa.f_c * d0;
-  an.th0 = frac_to_u32(th - floor(th));
-  double M1 = aa.f_c * e1 / aa.fs;
-  double M1f = M1 - floor(M1);
-  double Mr = rint(M1f * 4294967296.0);
-  an.m1 = (uint32_t)((long long)Mr & 0xffffffffLL);
-  an.m1lo = (float)(M1f - Mr * 2.3283064365386962890625e-10);
-  // E_{k+1} = E_k * (8/3)(3/8 + k - 1) beta / (A fs (k + 1)), per sample, in periods
-  const double r = b / (A * aa.fs);
-  const double E1 = e1 / aa.fs;
-  const double E2 = E1 * r * 0.5;
-  const double E3 = E2 * r * (11.0 / 9.0);
-  const double E4 = E3 * r * (19.0 / 12.0);
-  const double E5 = E4 * r * (9.0 / 5.0);
-  an.p2 = (float)(E2 / aa.t_coh);
-  an.p3 = (float)(E3 / aa.t_coh);
-  an.p4 = (float)(E4 / aa.t_coh);
-  an.p5 = (float)(E5 / aa.t_coh);
-  an.pad0 = 0.f;
-  an.pad1 = 0.f;
-  return an;
-}
-
 __global__ void k_anchors(const Item* __restrict__ items, int n_items, const double* __restrict__ betas,
                           AnchorArgs aa, Anchor* __restrict__ out, long long total) {
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -254,19 +204,6 @@ __global__ void k_anchors(const Item* __restrict__ items, int n_items, const dou
     const Item it = items[lo];
     out[idx] = compute_anchor(betas[it.m], it.i0 + (int)(g - it.g0), ai, aa);
   }
-}
-
-// Phase of sample l (0 <= l < span) of an anchor's span: the fine-grid phase
-// Psi (unsigned 32-bit fixed point, periods of t_coh) and the demodulation
-// phase th = f_c delta mod 1 in [-0.5, 0.5] (cycles).
-__device__ __forceinline__ void mixed_phase(const Anchor& A, int l, float kc, uint32_t& Psi, float& th) {
-  const float lf = (float)l;
-  const float cq = fmaf(fmaf(fmaf(A.p5, lf, A.p4), lf, A.p3), lf, A.p2) * (lf * lf);
-  const float cpsi = fmaf(A.p1lo, lf, cq);
-  Psi = A.psi0 + (uint32_t)l * A.n1 + (uint32_t)__float2int_rn(cpsi * 4294967296.0f);
-  const float cth = fmaf(A.m1lo, lf, kc * cq);
-  float t = (float)(int32_t)(A.th0 + (uint32_t)l * A.m1) * 2.3283064365386963e-10f + cth;
-  th = t - rintf(t);
 }
 
 // ---------------------------------------------------------------------------

@@ -19,11 +19,6 @@ constexpr double kPi = 3.14159265358979323846;
 // G * Msun / c^3 [s] from the IAU nominal G*Msun and the defined speed of light.
 constexpr double kGMsunC3 = 1.32712440018e20 / (299792458.0 * 299792458.0 * 299792458.0);
 
-// Eq. (beta): beta = (96/5) pi^(8/3) (G Mc / c^3)^(5/3) f^(8/3)  [1/s].
-double chirp_beta(double mc, double f) {
-  return 96.0 / 5.0 * std::pow(kPi, 8.0 / 3.0) * std::pow(kGMsunC3 * mc, 5.0 / 3.0) *
-         std::pow(f, 8.0 / 3.0);
-}
 
 // Smallest 2^a 3^b 5^c >= n.
 int32_t next_smooth(int32_t n) {
@@ -101,6 +96,12 @@ double es_hat(double beta, double xi, const std::vector<double>& gx, const std::
 bool is_int(double v, double tol) { return std::fabs(v - std::round(v)) <= tol * std::max(1.0, std::fabs(v)); }
 
 }  // namespace
+
+// Eq. (beta): beta = (96/5) pi^(8/3) (G Mc / c^3)^(5/3) f^(8/3)  [1/s].
+double chirp_beta(double mc, double f) {
+  return 96.0 / 5.0 * std::pow(kPi, 8.0 / 3.0) * std::pow(kGMsunC3 * mc, 5.0 / 3.0) *
+         std::pow(f, 8.0 / 3.0);
+}
 
 srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates, int64_t n_samples,
                      bool spectra_mode, int32_t seg_begin, int32_t seg_end, Plan& pl, std::string& msg) {

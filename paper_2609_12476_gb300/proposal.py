@@ -1,0 +1,222 @@
+"""Learned proposal: training data, training, calibration and the recall judge.
+
+Host orchestration of the library's kernels (every computation runs in
+libsrs: strain synthesis, searches, patches, the network, refinement):
+
+  training_set  seeded strain realisations with 0PN chirps injected on a
+                grid of well-separated coarse cells (amplitudes uniform in a
+                range) -> the coarse search -> 9 x 33 patches centred (with
+                +-1 jitter) on injection cells (label 1) and on cells far from
+                any injection (label 0), in equal shares
+  init_params   a seeded Kaiming-uniform start for the 297-64-1 network
+  train         Adam on the device set
+  calibrate     score threshold that proposes a fraction `far` of the cells of
+                noise-only coarse maps (and the same for coarse n_sigma, the
+                proposal without a network)
+  evaluate      recall of injections: full fine-template search vs the
+                proposal search vs the n_sigma-threshold proposal, at a per-cell
+                false-alarm probability from the exact chi^2 null of the
+                equal-weight statistic (Sec. III.C: n_sigma is an affine map of
+                chi^2 with 2 N_seg degrees of freedom)
+"""
+import math
+
+import numpy as np
+
+from . import _capi
+from ._capi import Params, SRS_F32
+
+GMSUN_C3 = 1.32712440018e20 / 299792458.0 ** 3
+
+
+def beta_of(mc, f):
+    """Sec. II Eq. (beta)."""
+    return (96.0 / 5.0) * math.pi ** (8.0 / 3.0) * (GMSUN_C3 * mc) ** (5.0 / 3.0) * f ** (8.0 / 3.0)
+
+
+def log_bank(lo, hi, n):
+    return np.exp(np.linspace(np.log(lo), np.log(hi), n))
+
+
+def nearest_template(bank, mc):
+    return int(np.argmin(np.abs(np.log(bank) - np.log(mc))))
+
+
+def injections_on_grid(rng, coarse_mc, params, count, amp_range, t_rows=9, b_cols=33):
+    """`count` injections on distinct cells of a (t_rows x b_cols)-spaced grid
+    of the coarse map, so their patches do not overlap.  Each injection's
+    chirp parameter at its f0 equals a template chirp parameter at f_ref
+    somewhere inside its cell (label mass log-uniform within the cell, f0
+    uniform within the bin).  Returns (injections, cells)."""
+    n_bins = int(round((params.f_hi - params.f_lo) * params.t_coh))
+    M = len(coarse_mc)
+    rows = list(range(t_rows // 2, M - t_rows // 2, t_rows))
+    cols = list(range(b_cols // 2, n_bins - b_cols // 2, b_cols))
+    slots = [(r, c) for r in rows for c in cols]
+    pick = rng.choice(len(slots), size=min(count, len(slots)), replace=False)
+    dlog = np.log(coarse_mc[1] / coarse_mc[0]) if M > 1 else 0.1
+    inj, cells = [], []
+    for k in pick:
+        m, b = slots[k]
+        label = coarse_mc[m] * math.exp(rng.uniform(-0.5, 0.5) * dlog)
+        f0 = params.f_lo + (b + rng.uniform(-0.5, 0.5)) / params.t_coh
+        # beta(f0, mc_inj) = beta(f_ref, label)  =>  mc_inj = label (f_ref / f0)^(8/5)
+        mc_inj = label * (params.f_ref / f0) ** 1.6
+        amp = rng.uniform(*amp_range)
+        inj.append({"mc": mc_inj, "f0": f0, "amp": amp, "phi0": rng.uniform(0, 2 * math.pi), "label": label})
+        cells.append((m, b))
+    return inj, cells
+
+
+def coarse_map(ctx, strain, coarse_mc, params):
+    out = {"map": None, "cands": None}
+    import torch
+    M = len(coarse_mc)
+    n_bins = int(round((params.f_hi - params.f_lo) * params.t_coh))
+    out["map"] = torch.empty((M, n_bins), dtype=torch.float32, device=strain.device)
+    out["cands"] = torch.empty((params.top_k, 3), dtype=torch.int32, device=strain.device)
+    res, rep = ctx.search(strain, coarse_mc, params, out=out)
+    return res["map"], rep
+
+
+def training_set(ctx, coarse_mc, params, t_obs, n_real, per_real, seed, amp_range=(0.01, 0.1)):
+    """Device tensors X [N, 297], y [N] from n_real realisations."""
+    import torch
+    rng = np.random.default_rng(seed)
+    n = int(round(t_obs * params.fs))
+    n_bins = int(round((params.f_hi - params.f_lo) * params.t_coh))
+    M = len(coarse_mc)
+    Xs, ys = [], []
+    for r in range(n_real):
+        inj, cells = injections_on_grid(rng, coarse_mc, params, per_real, amp_range)
+        x = ctx.make_strain(n, params.fs, seed * 1000003 + r, inj, f_hi=params.f_hi)
+        smap, _ = coarse_map(ctx, x, coarse_mc, params)
+        pos = [(min(M - 1, max(0, m + rng.integers(-1, 2))), min(n_bins - 1, max(0, b + rng.integers(-1, 2))))
+               for m, b in cells]
+        taken = np.zeros((M, n_bins), dtype=bool)
+        for m, b in cells:
+            taken[max(0, m - 6):m + 7, max(0, b - 20):b + 21] = True
+        free = np.argwhere(~taken)
+        neg = [tuple(free[k]) for k in rng.choice(len(free), size=len(pos), replace=False)]
+        X = ctx.patches(smap, pos + neg)
+        Xs.append(X)
+        ys.append(torch.tensor([1.0] * len(pos) + [0.0] * len(neg), dtype=torch.float32, device=X.device))
+    return torch.cat(Xs), torch.cat(ys)
+
+
+def init_params(seed):
+    """Kaiming-uniform weights (fan-in), zero biases."""
+    r = np.random.default_rng(seed)
+    D, H = _capi.MLP_INPUTS, _capi.MLP_HIDDEN
+    p = np.zeros(_capi.MLP_PARAMS, dtype=np.float32)
+    p[:H * D] = r.uniform(-1, 1, H * D) * math.sqrt(6.0 / D)
+    p[H * D + H:H * D + 2 * H] = r.uniform(-1, 1, H) * math.sqrt(6.0 / H)
+    return p
+
+
+def noise_maps(ctx, coarse_mc, params, t_obs, n_maps, seed):
+    n = int(round(t_obs * params.fs))
+    for r in range(n_maps):
+        x = ctx.make_strain(n, params.fs, seed * 7919 + r, [], f_hi=params.f_hi)
+        yield coarse_map(ctx, x, coarse_mc, params)[0]
+
+
+def calibrate(ctx, mlp_params, coarse_mc, params, t_obs, n_maps, seed, far):
+    """Thresholds proposing a fraction `far` of noise-only coarse cells: one on
+    the network score, one on the coarse n_sigma (the proposal without the
+    network)."""
+    import torch
+    sc, ns = [], []
+    for smap in noise_maps(ctx, coarse_mc, params, t_obs, n_maps, seed):
+        sc.append(ctx.score_map(smap, mlp_params).flatten())
+        ns.append(smap.flatten())
+    sc = torch.cat(sc).double().cpu().numpy()
+    ns = torch.cat(ns).double().cpu().numpy()
+    return float(np.quantile(sc, 1.0 - far)), float(np.quantile(ns, 1.0 - far))
+
+
+def detection_threshold(nseg, p_fa):
+    """n_sigma threshold at per-cell false-alarm probability p_fa:
+    n_sigma = (S - 2N) / (2 sqrt N) with S ~ chi^2_{2N} under noise."""
+    from scipy.stats import chi2
+    nseg = np.asarray(nseg, dtype=np.float64)
+    return (chi2.isf(p_fa, 2 * nseg) - 2 * nseg) / (2 * np.sqrt(nseg))
+
+
+def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t_obs, n_real, per_real, seed,
+             p_fa=1e-6, amp_range=(0.01, 0.1)):
+    """Recall of injections in three searches over the same realisations.
+    An injection counts as recovered when a cell within +-2 fine templates and
+    +-1 bin of its own (label) cell exceeds the detection threshold; in the
+    proposal searches that cell must also have been evaluated."""
+    import torch
+    rng = np.random.default_rng(seed)
+    n = int(round(t_obs * params.fs))
+    n_bins = int(round((params.f_hi - params.f_lo) * params.t_coh))
+    Mf = len(fine_mc)
+    info, _, nseg_f = _capi.srs_plan(params, fine_mc, n)
+    th_f = detection_threshold(nseg_f, p_fa)
+    out = {"injections": 0, "full": 0, "proposal": 0, "nsigma_proposal": 0, "full_ms": 0.0, "proposal_ms": 0.0,
+           "nsigma_cells": 0, "proposal_cells": 0, "full_spectra": int(info["n_spectra"]),
+           "proposal_coarse_spectra": 0, "proposal_segment_bins": 0}
+    for r in range(n_real):
+        inj, _cells = injections_on_grid(rng, coarse_mc, params, per_real, amp_range)
+        x = ctx.make_strain(n, params.fs, seed * 1000003 + 7 + r, inj, f_hi=params.f_hi)
+        # full fine search (the judge)
+        fmap = torch.empty((Mf, n_bins), dtype=torch.float32, device=x.device)
+        res, rep = ctx.search(x, fine_mc, params, out={"map": fmap, "cands": torch.empty((params.top_k, 3),
+                              dtype=torch.int32, device=x.device)})
+        out["full_ms"] += rep["device_ms"]
+        fm = fmap.cpu().numpy()
+        # proposal search with the network
+        pr = ctx.search_proposed(x, coarse_mc, fine_mc, params, mlp_params, score_th)
+        out["proposal_ms"] += pr["report"]["device_ms"]
+        out["proposal_cells"] += pr["n_cells"]
+        out["proposal_coarse_spectra"] += pr["report"]["coarse_spectra"]
+        out["proposal_segment_bins"] += pr["report"]["fine_segment_bins"]
+        got = {}
+        for (m, b), v in zip(pr["cells"], pr["nsigma"]):
+            got[(int(m), int(b))] = float(v)
+        # proposal by coarse n_sigma alone (same refinement)
+        cmap, _ = coarse_map(ctx, x, coarse_mc, params)
+        cm = cmap.cpu().numpy()
+        prop = np.argwhere(cm > nsigma_th)
+        fine_cells = fine_cells_of(prop, coarse_mc, fine_mc, n_bins)
+        out["nsigma_cells"] += len(fine_cells)
+        base = {}
+        if len(fine_cells):
+            nsb, _ = ctx.refine(x, fine_mc, params, fine_cells)
+            for (m, b), v in zip(fine_cells, nsb):
+                base[(int(m), int(b))] = float(v)
+        for I in inj:
+            out["injections"] += 1
+            mf = nearest_template(fine_mc, I["label"])
+            bf = int(round((I["f0"] - params.f_lo) * params.t_coh))
+            nb = [(m, b) for m in range(max(0, mf - 2), min(Mf, mf + 3))
+                  for b in range(max(0, bf - 1), min(n_bins, bf + 2))]
+            if any(fm[m, b] > th_f[m] for m, b in nb):
+                out["full"] += 1
+            if any(got.get((m, b), -np.inf) > th_f[m] for m, b in nb):
+                out["proposal"] += 1
+            if any(base.get((m, b), -np.inf) > th_f[m] for m, b in nb):
+                out["nsigma_proposal"] += 1
+    out["recall_full"] = out["full"] / max(1, out["injections"])
+    out["recall_proposal"] = out["proposal"] / max(1, out["injections"])
+    out["recall_nsigma_proposal"] = out["nsigma_proposal"] / max(1, out["injections"])
+    return out
+
+
+def fine_cells_of(coarse_cells, coarse_mc, fine_mc, n_bins):
+    """Fine (template, bin) cells proposed by coarse cells: fine templates whose
+    nearest coarse template is within one of the cell's, bins within one."""
+    parent = np.array([nearest_template(coarse_mc, m) for m in fine_mc])
+    children = {}
+    for f, c in enumerate(parent):
+        children.setdefault(int(c), []).append(f)
+    cells = set()
+    for m, b in coarse_cells:
+        for c in range(int(m) - 1, int(m) + 2):
+            for f in children.get(c, []):
+                for bb in range(max(0, int(b) - 1), min(n_bins, int(b) + 2)):
+                    cells.add((f, bb))
+    return sorted(cells)
