@@ -113,6 +113,74 @@ srs_status refine_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
       return set_err(ctx, SRS_ERR_ARG, "refine: cell outside the map");
   if (n_cells == 0) return SRS_OK;
 
+  // Templates with many requested bins are cheaper through the NUFFT (all
+  // bins of a spectrum at once) than through direct sums (one pass over the
+  // samples per bin): take those through the mixed search on that template
+  // subset and read the requested cells off its map.
+  {
+    std::vector<int32_t> per_t(n_templates, 0);
+    std::vector<long long> ks(n_cells);
+    for (int32_t c = 0; c < n_cells; ++c) ks[c] = (long long)cell_m[c] * pl.n_bins + cell_b[c];
+    std::vector<long long> u(ks);
+    std::sort(u.begin(), u.end());
+    u.erase(std::unique(u.begin(), u.end()), u.end());
+    for (long long key : u) ++per_t[(int32_t)(key / pl.n_bins)];
+    std::vector<int32_t> dense;
+    for (int32_t m = 0; m < n_templates; ++m)
+      if (per_t[m] > kDirectMaxBins) dense.push_back(m);
+    if (!dense.empty()) {
+      std::vector<int32_t> slot(n_templates, -1);
+      std::vector<double> dmc(dense.size());
+      for (size_t k = 0; k < dense.size(); ++k) { slot[dense[k]] = (int32_t)k; dmc[k] = mc[dense[k]]; }
+      std::vector<int32_t> rest_m, rest_b, rest_idx;
+      for (int32_t c = 0; c < n_cells; ++c)
+        if (slot[cell_m[c]] < 0) { rest_m.push_back(cell_m[c]); rest_b.push_back(cell_b[c]); rest_idx.push_back(c); }
+      // dense templates: mixed search with a device map
+      srs_params ps = pc;
+      ps.io_on_device = 1;
+      ps.top_k = 1;
+      ps.chunk = 0;
+      const void* dstrain_all = strain;
+      if (!params->io_on_device) {
+        const size_t bytes = (size_t)n_samples * (dtype == SRS_F64 ? 8 : 4);
+        SRS_CK(ctx->F.ensure(bytes), "alloc strain");
+        SRS_CK(cudaMemcpyAsync(ctx->F.p, strain, bytes, cudaMemcpyHostToDevice, ctx->stream), "copy strain");
+        dstrain_all = ctx->F.p;
+      }
+      SRS_CK(ctx->S.ensure(dense.size() * (size_t)pl.n_bins * 4), "alloc dense map");
+      SRS_CK(ctx->ccands.ensure(sizeof(srs_candidate)), "alloc cands");
+      int32_t nc = 0;
+      srs_report rs;
+      std::memset(&rs, 0, sizeof rs);
+      s = search_impl(ctx, dstrain_all, n_samples, dtype, dmc.data(), (int32_t)dense.size(), &ps,
+                      ctx->S.as<float>(), ctx->ccands.as<srs_candidate>(), &nc, &rs);
+      if (s != SRS_OK) return s;
+      std::vector<float> dmap(dense.size() * (size_t)pl.n_bins);
+      SRS_CK(cudaMemcpy(dmap.data(), ctx->S.p, dmap.size() * 4, cudaMemcpyDeviceToHost), "copy dense map");
+      int64_t sb_rest = 0;
+      int32_t t_rest = 0;
+      std::vector<float> ns_rest(rest_idx.size());
+      if (!rest_idx.empty()) {
+        s = refine_impl(ctx, dstrain_all, n_samples, dtype, mc, n_templates, &ps, rest_m.data(), rest_b.data(),
+                        (int32_t)rest_idx.size(), ns_rest.data(), nullptr, &sb_rest, &t_rest);
+        if (s != SRS_OK) return s;
+      }
+      for (int32_t c = 0; c < n_cells; ++c)
+        if (slot[cell_m[c]] >= 0) nsigma[c] = dmap[(size_t)slot[cell_m[c]] * pl.n_bins + cell_b[c]];
+      for (size_t k = 0; k < rest_idx.size(); ++k) nsigma[rest_idx[k]] = ns_rest[k];
+      int64_t dense_segs = 0;
+      for (int32_t m : dense) dense_segs += pl.nseg[m];
+      if (seg_bins_out) *seg_bins_out = sb_rest + dense_segs * (int64_t)pl.n_bins;
+      if (templates_out) *templates_out = t_rest + (int32_t)dense.size();
+      if (report) {
+        std::memset(report, 0, sizeof *report);
+        report->n_spectra = dense_segs;
+        report->device_ms = rs.device_ms;
+      }
+      return SRS_OK;
+    }
+  }
+
   // unique (template, bin) pairs, grouped by template, up to kSparseMaxBins per group
   std::vector<long long> keys(n_cells);
   for (int32_t c = 0; c < n_cells; ++c) keys[c] = (long long)cell_m[c] * pl.n_bins + cell_b[c];

@@ -80,7 +80,11 @@ def coarse_map(ctx, strain, coarse_mc, params):
 
 
 def training_set(ctx, coarse_mc, params, t_obs, n_real, per_real, seed, amp_range=(0.01, 0.1)):
-    """Device tensors X [N, 297], y [N] from n_real realisations."""
+    """Device tensors X [N, 297], y [N] from n_real realisations.  Per
+    injection: its cell with the centre jittered by up to one template and one
+    bin (label 1) and a near miss two to four templates or two to twelve bins
+    away (label 0); plus twice as many patches of cells far from every injection
+    (label 0) -- half the patches from injection regions, half pure noise."""
     import torch
     rng = np.random.default_rng(seed)
     n = int(round(t_obs * params.fs))
@@ -93,15 +97,67 @@ def training_set(ctx, coarse_mc, params, t_obs, n_real, per_real, seed, amp_rang
         smap, _ = coarse_map(ctx, x, coarse_mc, params)
         pos = [(min(M - 1, max(0, m + rng.integers(-1, 2))), min(n_bins - 1, max(0, b + rng.integers(-1, 2))))
                for m, b in cells]
+        near = []
+        for m, b in cells:
+            if rng.random() < 0.5:
+                dm, db = int(rng.choice([-1, 1]) * rng.integers(2, 5)), int(rng.integers(-1, 2))
+            else:
+                dm, db = int(rng.integers(-1, 2)), int(rng.choice([-1, 1]) * rng.integers(2, 13))
+            near.append((min(M - 1, max(0, m + dm)), min(n_bins - 1, max(0, b + db))))
         taken = np.zeros((M, n_bins), dtype=bool)
         for m, b in cells:
             taken[max(0, m - 6):m + 7, max(0, b - 20):b + 21] = True
         free = np.argwhere(~taken)
-        neg = [tuple(free[k]) for k in rng.choice(len(free), size=len(pos), replace=False)]
-        X = ctx.patches(smap, pos + neg)
+        neg = [tuple(free[k]) for k in rng.choice(len(free), size=2 * len(pos), replace=False)]
+        X = ctx.patches(smap, pos + near + neg)
         Xs.append(X)
-        ys.append(torch.tensor([1.0] * len(pos) + [0.0] * len(neg), dtype=torch.float32, device=X.device))
+        ys.append(torch.tensor([1.0] * len(pos) + [0.0] * (len(near) + len(neg)), dtype=torch.float32,
+                               device=X.device))
     return torch.cat(Xs), torch.cat(ys)
+
+
+def hard_negatives(ctx, mlp_params, coarse_mc, params, t_obs, n_maps, per_map, seed):
+    """The highest-scoring cells of pure-noise coarse maps, as label-0 patches."""
+    import torch
+    Xs = []
+    for smap in noise_maps(ctx, coarse_mc, params, t_obs, n_maps, seed):
+        sc = ctx.score_map(smap, mlp_params).flatten()
+        top = torch.topk(sc, per_map).indices.cpu().numpy()
+        nb = smap.shape[1]
+        Xs.append(ctx.patches(smap, [(int(c) // nb, int(c) % nb) for c in top]))
+    X = torch.cat(Xs)
+    return X, torch.zeros(X.shape[0], dtype=torch.float32, device=X.device)
+
+
+def train_proposal(ctx, coarse_mc, params, t_obs, n_patches=20000, per_real=64, seed=1, hard_frac=0.25,
+                   epochs=(30, 20, 10), lrs=(1e-3, 3e-4, 1e-4), batch=256):
+    """The full training recipe: n_patches patches, half injections (amplitude
+    uniform in [0.01, 0.1]) and half pure noise, of which hard_frac come from
+    the top scores of pure-noise maps after a first round.  Returns
+    (parameters, per-epoch losses, held-out (X, y))."""
+    import torch
+    n_neg_hard = int(n_patches * 0.5 * hard_frac)
+    n_real = int(math.ceil((n_patches - n_neg_hard) / (4.0 * per_real)))
+    X, y = training_set(ctx, coarse_mc, params, t_obs, n_real, per_real, seed)
+    g = torch.Generator().manual_seed(seed)
+    perm = torch.randperm(X.shape[0], generator=g).to(X.device)
+    n_hold = max(1, X.shape[0] // 10)
+    Xh, yh = X[perm[:n_hold]].contiguous(), y[perm[:n_hold]].contiguous()
+    Xt, yt = X[perm[n_hold:]].contiguous(), y[perm[n_hold:]].contiguous()
+    torch.cuda.synchronize()
+    p = init_params(seed)
+    losses = []
+    p, l = ctx.mlp_train(Xt, yt, p, epochs=epochs[0], batch=batch, lr=lrs[0], seed=seed)
+    losses += list(l)
+    if n_neg_hard > 0:
+        per_map = 512
+        Xn, yn = hard_negatives(ctx, p, coarse_mc, params, t_obs, max(1, n_neg_hard // per_map), per_map, seed + 17)
+        Xt, yt = torch.cat([Xt, Xn]).contiguous(), torch.cat([yt, yn]).contiguous()
+        torch.cuda.synchronize()
+    for e, lr in zip(epochs[1:], lrs[1:]):
+        p, l = ctx.mlp_train(Xt, yt, p, epochs=e, batch=batch, lr=lr, seed=seed + e)
+        losses += list(l)
+    return p, np.array(losses), (Xh, yh), int(Xt.shape[0])
 
 
 def init_params(seed):
@@ -145,10 +201,18 @@ def detection_threshold(nseg, p_fa):
 
 def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t_obs, n_real, per_real, seed,
              p_fa=1e-6, amp_range=(0.01, 0.1)):
-    """Recall of injections in three searches over the same realisations.
+    """Recall of injections over the same realisations in four searches:
+      full            every fine template (the judge)
+      proposal        the network's proposal at its noise-calibrated threshold
+                      (the library's srs_search_proposed)
+      nsigma_equal    the proposal without the network at equal cost: the same
+                      number of coarse cells, the highest coarse n_sigma first
+      nsigma_far      the proposal without the network at the same noise false-
+                      alarm rate: coarse cells above the calibrated n_sigma threshold
     An injection counts as recovered when a cell within +-2 fine templates and
-    +-1 bin of its own (label) cell exceeds the detection threshold; in the
-    proposal searches that cell must also have been evaluated."""
+    +-1 bin of its own (label) cell exceeds the detection threshold at
+    per-cell false-alarm probability p_fa; in the proposal searches that cell
+    must also have been evaluated."""
     import torch
     rng = np.random.default_rng(seed)
     n = int(round(t_obs * params.fs))
@@ -156,9 +220,12 @@ def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t
     Mf = len(fine_mc)
     info, _, nseg_f = _capi.srs_plan(params, fine_mc, n)
     th_f = detection_threshold(nseg_f, p_fa)
-    out = {"injections": 0, "full": 0, "proposal": 0, "nsigma_proposal": 0, "full_ms": 0.0, "proposal_ms": 0.0,
-           "nsigma_cells": 0, "proposal_cells": 0, "full_spectra": int(info["n_spectra"]),
-           "proposal_coarse_spectra": 0, "proposal_segment_bins": 0}
+    keys = ("full", "proposal", "nsigma_equal", "nsigma_far")
+    out = {"injections": 0, "full_ms": 0.0, "proposal_ms": 0.0, "full_spectra": 0, "proposal_coarse_spectra": 0,
+           "proposal_segment_bins": 0, "proposed_coarse": 0}
+    for k in keys:
+        out[k] = 0
+        out[k + "_cells"] = 0
     for r in range(n_real):
         inj, _cells = injections_on_grid(rng, coarse_mc, params, per_real, amp_range)
         x = ctx.make_strain(n, params.fs, seed * 1000003 + 7 + r, inj, f_hi=params.f_hi)
@@ -167,42 +234,42 @@ def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t
         res, rep = ctx.search(x, fine_mc, params, out={"map": fmap, "cands": torch.empty((params.top_k, 3),
                               dtype=torch.int32, device=x.device)})
         out["full_ms"] += rep["device_ms"]
+        out["full_spectra"] += rep["n_spectra"]
         fm = fmap.cpu().numpy()
-        # proposal search with the network
+        found = {"full": {(m, b): float(fm[m, b]) for m, b in np.argwhere(fm > th_f[:, None])}}
+        out["full_cells"] += fm.size
+        # the network's proposal search
         pr = ctx.search_proposed(x, coarse_mc, fine_mc, params, mlp_params, score_th)
         out["proposal_ms"] += pr["report"]["device_ms"]
-        out["proposal_cells"] += pr["n_cells"]
         out["proposal_coarse_spectra"] += pr["report"]["coarse_spectra"]
         out["proposal_segment_bins"] += pr["report"]["fine_segment_bins"]
-        got = {}
-        for (m, b), v in zip(pr["cells"], pr["nsigma"]):
-            got[(int(m), int(b))] = float(v)
-        # proposal by coarse n_sigma alone (same refinement)
+        out["proposed_coarse"] += pr["report"]["proposed_coarse"]
+        out["proposal_cells"] += pr["n_cells"]
+        found["proposal"] = {(int(m), int(b)): float(v) for (m, b), v in zip(pr["cells"], pr["nsigma"])}
+        # proposals without the network
         cmap, _ = coarse_map(ctx, x, coarse_mc, params)
         cm = cmap.cpu().numpy()
-        prop = np.argwhere(cm > nsigma_th)
-        fine_cells = fine_cells_of(prop, coarse_mc, fine_mc, n_bins)
-        out["nsigma_cells"] += len(fine_cells)
-        base = {}
-        if len(fine_cells):
-            nsb, _ = ctx.refine(x, fine_mc, params, fine_cells)
-            for (m, b), v in zip(fine_cells, nsb):
-                base[(int(m), int(b))] = float(v)
+        K = pr["report"]["proposed_coarse"]
+        order = np.argsort(-cm, axis=None)[:K]
+        for key, prop in (("nsigma_equal", np.stack(np.unravel_index(order, cm.shape), axis=1)),
+                          ("nsigma_far", np.argwhere(cm > nsigma_th))):
+            fc = fine_cells_of(prop, coarse_mc, fine_mc, n_bins)
+            out[key + "_cells"] += len(fc)
+            found[key] = {}
+            if len(fc):
+                nsb, _ = ctx.refine(x, fine_mc, params, fc)
+                found[key] = {(int(m), int(b)): float(v) for (m, b), v in zip(fc, nsb)}
         for I in inj:
             out["injections"] += 1
             mf = nearest_template(fine_mc, I["label"])
             bf = int(round((I["f0"] - params.f_lo) * params.t_coh))
             nb = [(m, b) for m in range(max(0, mf - 2), min(Mf, mf + 3))
                   for b in range(max(0, bf - 1), min(n_bins, bf + 2))]
-            if any(fm[m, b] > th_f[m] for m, b in nb):
-                out["full"] += 1
-            if any(got.get((m, b), -np.inf) > th_f[m] for m, b in nb):
-                out["proposal"] += 1
-            if any(base.get((m, b), -np.inf) > th_f[m] for m, b in nb):
-                out["nsigma_proposal"] += 1
-    out["recall_full"] = out["full"] / max(1, out["injections"])
-    out["recall_proposal"] = out["proposal"] / max(1, out["injections"])
-    out["recall_nsigma_proposal"] = out["nsigma_proposal"] / max(1, out["injections"])
+            for key in keys:
+                if any(found[key].get((m, b), -np.inf) > th_f[m] for m, b in nb):
+                    out[key] += 1
+    for key in keys:
+        out["recall_" + key] = out[key] / max(1, out["injections"])
     return out
 
 
