@@ -52,6 +52,7 @@ MixedArgs mixed_args(const Plan& pl, const srs_ctx* ctx, int seg_begin, int seg_
   a.aa.n_anchor = pl.n_anchor;
   a.fft_fixed = (pl.n_fine == 1200 && pl.radices == std::vector<int32_t>{4, 4, 3, 5, 5}) ? 1200 : 0;
   a.kc = (float)pl.k_c;
+  a.kc_int = (pl.k_c >= 1.0 && pl.k_c < 1073741824.0 && pl.k_c == std::floor(pl.k_c)) ? (int)pl.k_c : 0;
   a.inv_ns = (float)(1.0 / (double)pl.n_s);
   a.es_beta_log2e = (float)(pl.beta_es * 1.4426950408889634074);
   a.two_over_w = (float)(2.0 / pl.w);
@@ -145,6 +146,11 @@ srs_status stage_strain(srs_ctx* ctx, const void* strain, int64_t samples, int32
 
 srs_status check_common(srs_ctx* ctx, const void* strain, int32_t dtype, const srs_params* params) {
   if (!ctx) return SRS_ERR_ARG;
+  {
+    // an error left by an earlier unchecked runtime call must not be blamed on this call
+    const cudaError_t stale = cudaGetLastError();
+    if (stale != cudaSuccess) std::fprintf(stderr, "srs: cleared stale CUDA error: %s\n", cudaGetErrorString(stale));
+  }
   if (!strain) return set_err(ctx, SRS_ERR_ARG, "strain is NULL");
   if (!params) return set_err(ctx, SRS_ERR_ARG, "params is NULL");
   if (dtype != SRS_F32 && dtype != SRS_F64) return set_err(ctx, SRS_ERR_ARG, "dtype must be SRS_F32 or SRS_F64");
@@ -183,6 +189,12 @@ srs_status get_plan(srs_ctx* ctx, int kind, const srs_params* params, const doub
     return SRS_OK;
   }
   ctx->have_plan = false;
+  // a new plan means new tables: a captured graph may point at the old ones
+  if (ctx->graph_exec) {
+    cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = nullptr;
+    ctx->graph_key.clear();
+  }
   std::string msg;
   srs_status s = make_plan(*params, mc, n_templates, n_samples, spectra_mode, a, b, ctx->plan, msg);
   if (s != SRS_OK) return set_err(ctx, s, msg);
@@ -200,11 +212,15 @@ namespace srs {
 
 // The mixed form reads FP32 samples: convert FP64 strain once per call, and
 // use FP32 strain in place when TMA can read it (16-byte aligned, n_s % 4 == 0).
+bool tma_disabled() {
+  const char* no_tma = std::getenv("SRS_NO_TMA");
+  return no_tma && no_tma[0] == '1';
+}
+
 srs_status strain_f32(srs_ctx* ctx, const void* dstrain, int32_t dtype, int64_t samples, int64_t n_s,
                       const float** out, int* use_tma) {
   // SRS_NO_TMA=1 in the environment selects plain shared-memory staging.
-  const char* no_tma = std::getenv("SRS_NO_TMA");
-  const bool tma_ok_len = (n_s % 4) == 0 && !(no_tma && no_tma[0] == '1');
+  const bool tma_ok_len = (n_s % 4) == 0 && !tma_disabled();
   if (dtype == SRS_F64) {
     SRS_CK(ctx->strain32.ensure((size_t)samples * 4), "alloc strain32");
     SRS_CK(launch_to_f32(static_cast<const double*>(dstrain), ctx->strain32.as<float>(), samples, ctx->n_sm,
@@ -222,6 +238,80 @@ srs_status strain_f32(srs_ctx* ctx, const void* dstrain, int32_t dtype, int64_t 
 }  // namespace srs
 
 namespace {
+
+// Autotuner of the mixed spreader: segments per work item and resident CTAs
+// per SM, timed with CUDA events on the whole search's spreader launch for
+// searches of up to kTuneMaxSpectra spectra; the choice is kept per shape
+// (segment length, band, fine grid, kernel width, templates, spectra).
+constexpr long long kTuneMaxSpectra = 2000000;
+
+srs_status autotune_mixed(srs_ctx* ctx, Plan& pl, const float* s32, int use_tma, int* ctas_out) {
+  std::vector<unsigned char> key;
+  auto put = [&](const void* d, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(d);
+    key.insert(key.end(), c, c + n);
+  };
+  put(&pl.n_s, sizeof pl.n_s);
+  put(&pl.n_bins, sizeof pl.n_bins);
+  put(&pl.n_fine, sizeof pl.n_fine);
+  put(&pl.w, sizeof pl.w);
+  put(&pl.n_templates, sizeof pl.n_templates);
+  put(&pl.n_spectra, sizeof pl.n_spectra);
+  for (const auto& t : ctx->tuned)
+    if (t.key == key) {
+      if (t.chunk != pl.chunk) {
+        make_items(pl, t.chunk, false, 0, 0);
+        SRS_CK(ctx->items.ensure(pl.items.size() * sizeof(Item)), "alloc items");
+        SRS_CK(ctx->item_off.ensure(pl.item_off.size() * 4), "alloc item_off");
+        SRS_CK(cudaMemcpyAsync(ctx->items.p, pl.items.data(), pl.items.size() * sizeof(Item), cudaMemcpyHostToDevice, ctx->stream), "copy items");
+        SRS_CK(cudaMemcpyAsync(ctx->item_off.p, pl.item_off.data(), pl.item_off.size() * 4, cudaMemcpyHostToDevice, ctx->stream), "copy item_off");
+      }
+      *ctas_out = t.ctas;
+      return SRS_OK;
+    }
+  if (pl.n_spectra > kTuneMaxSpectra) {
+    ctx->tuned.push_back({key, pl.chunk, 0, 0.0});
+    *ctas_out = 0;
+    return SRS_OK;
+  }
+  const int chunks[] = {1, 2, 4, 8, 16};
+  const int ctas[] = {0, 3};
+  int best_chunk = pl.chunk, best_ctas = 0;
+  double best = 1e30;
+  for (int ch : chunks) {
+    make_items(pl, ch, false, 0, 0);
+    const size_t n_items = pl.items.size();
+    SRS_CK(ctx->items.ensure(n_items * sizeof(Item)), "alloc items");
+    SRS_CK(ctx->item_off.ensure(pl.item_off.size() * 4), "alloc item_off");
+    SRS_CK(ctx->partial.ensure(n_items * (size_t)pl.n_bins * 4), "alloc partial");
+    SRS_CK(cudaMemcpyAsync(ctx->items.p, pl.items.data(), n_items * sizeof(Item), cudaMemcpyHostToDevice, ctx->stream), "copy items");
+    MixedArgs a = mixed_args(pl, ctx, 0, 0);
+    a.use_tma = use_tma;
+    for (int ct : ctas) {
+      float best_ms = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
+        SRS_CK(cudaEventRecord(ctx->ev2, ctx->stream), "event");
+        SRS_CK(launch_mixed(false, pl.w, s32, ctx->items.as<Item>(), (int)n_items, ctx->betas.as<double>(),
+                            ctx->queue.as<int>(), a, ctx->partial.as<float>(), nullptr, ctx->errflag.as<int>(),
+                            ctx->n_sm, ct, ctx->stream), "k_mixed (tuning)");
+        SRS_CK(cudaEventRecord(ctx->ev3, ctx->stream), "event");
+        SRS_CK(cudaEventSynchronize(ctx->ev3), "tuning");
+        best_ms = std::min(best_ms, elapsed_ms(ctx->ev2, ctx->ev3));
+      }
+      if (best_ms < best) { best = best_ms; best_chunk = ch; best_ctas = ct; }
+    }
+  }
+  make_items(pl, best_chunk, false, 0, 0);
+  SRS_CK(ctx->items.ensure(pl.items.size() * sizeof(Item)), "alloc items");
+  SRS_CK(ctx->item_off.ensure(pl.item_off.size() * 4), "alloc item_off");
+  SRS_CK(cudaMemcpyAsync(ctx->items.p, pl.items.data(), pl.items.size() * sizeof(Item), cudaMemcpyHostToDevice, ctx->stream), "copy items");
+  SRS_CK(cudaMemcpyAsync(ctx->item_off.p, pl.item_off.data(), pl.item_off.size() * 4, cudaMemcpyHostToDevice, ctx->stream), "copy item_off");
+  SRS_CK(cudaStreamSynchronize(ctx->stream), "tuning");
+  ctx->tuned.push_back({key, best_chunk, best_ctas, best});
+  *ctas_out = best_ctas;
+  return SRS_OK;
+}
 
 srs_status check_err_flag(srs_ctx* ctx) {
   int flag[5] = {0, 0, 0, 0, 0};
@@ -246,7 +336,7 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
   const Plan* plp = nullptr;
   s = get_plan(ctx, 1, params, mc, n_templates, n_samples, dtype, false, 0, 0, &plp);
   if (s != SRS_OK) return s;
-  const Plan& pl = *plp;
+  Plan& pl = ctx->plan;
   const bool mixed = pl.precision == SRS_MIXED;
   const bool f64 = dtype == SRS_F64;
   const int on_dev = params->io_on_device;
@@ -276,7 +366,7 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
     dc = ctx->cands.as<srs_candidate>();
   }
   int launches = 0;
-  const long long n_items = (long long)pl.items.size();
+  long long n_items = (long long)pl.items.size();
   if (mixed) {
     SRS_CK(ctx->partial.ensure(n_items * pl.n_bins * 4), "alloc partial");
     SRS_CK(ctx->queue.ensure(64), "alloc queue");
@@ -285,55 +375,141 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
     SRS_CK(ctx->S.ensure(n_map * 8), "alloc S");
   }
 
-  SRS_CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
+  // FP32 strain buffer before any capture (the conversion itself is part of the sequence)
+  const float* s32 = nullptr;
+  int use_tma = 0;
   if (mixed) {
-    MixedArgs a = mixed_args(pl, ctx, 0, 0);
-    const float* s32 = nullptr;
-    s = strain_f32(ctx, dstrain, dtype, (int64_t)max_seg * pl.n_s, pl.n_s, &s32, &a.use_tma);
-    if (s != SRS_OK) return s;
-    if (f64) ++launches;
-    SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
-    SRS_CK(cudaMemsetAsync(ctx->errflag.p, 0, 64, ctx->stream), "memset error flag");
-    SRS_CK(cudaEventRecord(ctx->ev2, ctx->stream), "event");
-    SRS_CK(launch_mixed(false, pl.w, s32, ctx->items.as<Item>(), (int)n_items, ctx->betas.as<double>(),
-                        ctx->queue.as<int>(), a, ctx->partial.as<float>(), nullptr, ctx->errflag.as<int>(), ctx->n_sm,
-                        0, ctx->stream), "k_mixed");
-    SRS_CK(cudaEventRecord(ctx->ev3, ctx->stream), "event");
-    ++launches;
-    SRS_CK(launch_reduce_mixed(ctx->partial.as<float>(), ctx->item_off.as<int>(), ctx->nseg.as<int>(), n_templates,
-                               pl.n_bins, dmap, ctx->keys.as<unsigned long long>(), ctx->n_sm, ctx->stream), "k_reduce_mixed");
-    ++launches;
-  } else {
-    PlainArgs p = plain_args(pl, ctx, 0, 0);
-    SRS_CK(cudaMemsetAsync(ctx->S.p, 0, n_map * 8, ctx->stream), "memset S");
-    SRS_CK(cudaEventRecord(ctx->ev2, ctx->stream), "event");
-    SRS_CK(launch_plain(f64, false, dstrain, ctx->betas.as<double>(), ctx->nseg.as<int>(), p, max_seg, n_templates,
-                        ctx->S.as<double>(), nullptr, ctx->stream), "k_plain");
-    SRS_CK(cudaEventRecord(ctx->ev3, ctx->stream), "event");
-    ++launches;
-    SRS_CK(launch_finish_plain(ctx->S.as<double>(), ctx->nseg.as<int>(), n_templates, pl.n_bins, dmap,
-                               ctx->keys.as<unsigned long long>(), ctx->n_sm, ctx->stream), "k_finish_plain");
-    ++launches;
+    const bool tma_len = (pl.n_s % 4) == 0 && !tma_disabled();
+    if (f64) {
+      SRS_CK(ctx->strain32.ensure((size_t)max_seg * pl.n_s * 4), "alloc strain32");
+      s32 = ctx->strain32.as<float>();
+      use_tma = tma_len ? 1 : 0;
+    } else {
+      s32 = static_cast<const float*>(dstrain);
+      use_tma = (tma_len && ((uintptr_t)dstrain % 16) == 0) ? 1 : 0;
+    }
   }
-  const unsigned long long* top = nullptr;
-  SRS_CK(launch_topk(ctx->keys.as<unsigned long long>(), n_map, k, ctx->topk_a.as<unsigned long long>(),
-                     ctx->topk_b.as<unsigned long long>(), &top, &launches, ctx->stream), "k_topk_tile");
-  SRS_CK(launch_keys_to_cands(top, k, pl.n_bins, dc, ctx->stream), "k_keys_to_cands");
-  ++launches;
+  if (mixed && params->chunk == 0) {
+    // the tuner needs the FP32 strain and the tables on the device
+    if (f64) SRS_CK(launch_to_f32(static_cast<const double*>(dstrain), ctx->strain32.as<float>(),
+                                  (int64_t)max_seg * pl.n_s, ctx->n_sm, ctx->stream), "k_to_f32 (before tuning)");
+    int ct = 0;
+    const int chunk_before = pl.chunk;
+    s = autotune_mixed(ctx, pl, s32, use_tma, &ct);
+    if (s != SRS_OK) return s;
+    ctx->ctas_per_sm = ct;
+    if (pl.chunk != chunk_before) {
+      n_items = (long long)pl.items.size();
+      SRS_CK(ctx->partial.ensure(n_items * pl.n_bins * 4), "alloc partial");
+    }
+  } else {
+    ctx->ctas_per_sm = 0;
+  }
+  // The device part of a search: one stream-ordered sequence, replayed from a
+  // CUDA graph when the plan and the buffers are the same as last time.
+  auto enqueue = [&]() -> srs_status {
+    launches = 0;
+    if (mixed) {
+      MixedArgs a = mixed_args(pl, ctx, 0, 0);
+      a.use_tma = use_tma;
+      if (f64) {
+        SRS_CK(launch_to_f32(static_cast<const double*>(dstrain), ctx->strain32.as<float>(), (int64_t)max_seg * pl.n_s,
+                             ctx->n_sm, ctx->stream), "k_to_f32");
+        ++launches;
+      }
+      SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
+      SRS_CK(cudaMemsetAsync(ctx->errflag.p, 0, 64, ctx->stream), "memset error flag");
+      SRS_CK(cudaEventRecordWithFlags(ctx->ev2, ctx->stream, cudaEventRecordExternal), "event");
+      SRS_CK(launch_mixed(false, pl.w, s32, ctx->items.as<Item>(), (int)n_items, ctx->betas.as<double>(),
+                          ctx->queue.as<int>(), a, ctx->partial.as<float>(), nullptr, ctx->errflag.as<int>(),
+                          ctx->n_sm, ctx->ctas_per_sm, ctx->stream), "k_mixed");
+      SRS_CK(cudaEventRecordWithFlags(ctx->ev3, ctx->stream, cudaEventRecordExternal), "event");
+      ++launches;
+      SRS_CK(launch_reduce_mixed(ctx->partial.as<float>(), ctx->item_off.as<int>(), ctx->nseg.as<int>(), n_templates,
+                                 pl.n_bins, dmap, ctx->keys.as<unsigned long long>(), ctx->n_sm, ctx->stream),
+             "k_reduce_mixed");
+      ++launches;
+    } else {
+      PlainArgs p = plain_args(pl, ctx, 0, 0);
+      SRS_CK(cudaMemsetAsync(ctx->S.p, 0, n_map * 8, ctx->stream), "memset S");
+      SRS_CK(cudaEventRecordWithFlags(ctx->ev2, ctx->stream, cudaEventRecordExternal), "event");
+      SRS_CK(launch_plain(f64, false, dstrain, ctx->betas.as<double>(), ctx->nseg.as<int>(), p, max_seg, n_templates,
+                          ctx->S.as<double>(), nullptr, ctx->stream), "k_plain");
+      SRS_CK(cudaEventRecordWithFlags(ctx->ev3, ctx->stream, cudaEventRecordExternal), "event");
+      ++launches;
+      SRS_CK(launch_finish_plain(ctx->S.as<double>(), ctx->nseg.as<int>(), n_templates, pl.n_bins, dmap,
+                                 ctx->keys.as<unsigned long long>(), ctx->n_sm, ctx->stream), "k_finish_plain");
+      ++launches;
+    }
+    const unsigned long long* top = nullptr;
+    SRS_CK(launch_topk(ctx->keys.as<unsigned long long>(), n_map, k, ctx->topk_a.as<unsigned long long>(),
+                       ctx->topk_b.as<unsigned long long>(), &top, &launches, ctx->stream), "k_topk_tile");
+    SRS_CK(launch_keys_to_cands(top, k, pl.n_bins, dc, ctx->stream), "k_keys_to_cands");
+    ++launches;
+    if (mixed)
+      SRS_CK(cudaMemcpyAsync(ctx->hflag, ctx->errflag.p, 32, cudaMemcpyDeviceToHost, ctx->stream), "read error flag");
+    return SRS_OK;
+  };
+  std::vector<unsigned char> gkey = ctx->plan_key;
+  for (const void* ptr : {dstrain, (const void*)s32, (const void*)dmap, (const void*)dc, (const void*)ctx->partial.p,
+                          (const void*)ctx->keys.p, (const void*)ctx->strain32.p, (const void*)ctx->items.p,
+                          (const void*)ctx->betas.p, (const void*)ctx->nseg.p, (const void*)ctx->item_off.p,
+                          (const void*)ctx->corr.p, (const void*)ctx->tw.p, (const void*)ctx->queue.p,
+                          (const void*)ctx->errflag.p, (const void*)ctx->topk_a.p, (const void*)ctx->topk_b.p,
+                          (const void*)ctx->S.p})
+    gkey.insert(gkey.end(), (const unsigned char*)&ptr, (const unsigned char*)&ptr + sizeof ptr);
+  gkey.push_back((unsigned char)ctx->ctas_per_sm);
+  SRS_CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
+  bool ran = false;
+  if (ctx->use_graphs) {
+    if (!(ctx->graph_exec && gkey == ctx->graph_key)) {
+      if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
+      cudaGraph_t g = nullptr;
+      const cudaError_t be = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed);
+      if (be == cudaSuccess) {
+        const srs_status es = enqueue();
+        const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+        cudaError_t ie = cudaErrorUnknown;
+        if (es == SRS_OK && ce == cudaSuccess && g) ie = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+        if (ie == cudaSuccess) {
+          ctx->graph_key = gkey;
+          ctx->graph_launches = launches;
+        } else {
+          std::fprintf(stderr, "srs: graph capture not used (enqueue %d: %s; end %s; instantiate %s)\n", (int)es,
+                       ctx->err.c_str(), cudaGetErrorString(ce), cudaGetErrorString(ie));
+          ctx->graph_exec = nullptr;
+        }
+        if (g) cudaGraphDestroy(g);
+      } else {
+        std::fprintf(stderr, "srs: begin capture failed: %s\n", cudaGetErrorString(be));
+      }
+      cudaGetLastError();
+    }
+    if (ctx->graph_exec) {
+      SRS_CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream), "graph launch");
+      launches = ctx->graph_launches;
+      ran = true;
+    }
+  }
+  if (!ran) {
+    s = enqueue();
+    if (s != SRS_OK) return s;
+  }
   SRS_CK(cudaEventRecord(ctx->ev1, ctx->stream), "event");
   if (!on_dev) {
     SRS_CK(cudaMemcpyAsync(cands, dc, (size_t)k * sizeof(srs_candidate), cudaMemcpyDeviceToHost, ctx->stream), "copy cands");
     if (stat_map) SRS_CK(cudaMemcpyAsync(stat_map, dmap, n_map * 4, cudaMemcpyDeviceToHost, ctx->stream), "copy map");
   }
   SRS_CK(cudaStreamSynchronize(ctx->stream), "search");
-  if (mixed) {
-    s = check_err_flag(ctx);
-    if (s != SRS_OK) return s;
+  if (mixed && ctx->hflag[0]) {
+    char b[200];
+    std::snprintf(b, sizeof b, "a device wait gave up (TMA copy did not complete in time): item %d segment %d parity %d block %d",
+                  ctx->hflag[1], ctx->hflag[2], ctx->hflag[3], ctx->hflag[4]);
+    return set_err(ctx, SRS_ERR_TIMEOUT, b);
   }
   *n_cands = k;
   if (report) {
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    const float ms = elapsed_ms(ctx->ev0, ctx->ev1);
     report->device_ms = ms;
     report->n_spectra = pl.n_spectra;
     report->spectra_per_s = ms > 0 ? pl.n_spectra / (ms * 1e-3) : 0.0;
@@ -344,9 +520,7 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
     report->chunk = mixed ? pl.chunk : 1;
     report->n_items = mixed ? (int32_t)n_items : (int32_t)pl.n_spectra;
     report->kernel_launches = launches;
-    float sms = 0.f;
-    cudaEventElapsedTime(&sms, ctx->ev2, ctx->ev3);
-    report->spread_ms = sms;
+    report->spread_ms = elapsed_ms(ctx->ev2, ctx->ev3);
   }
   return SRS_OK;
 }
@@ -407,8 +581,7 @@ srs_status spectra_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int
     if (s != SRS_OK) return s;
   }
   if (report) {
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    const float ms = elapsed_ms(ctx->ev0, ctx->ev1);
     std::memset(report, 0, sizeof *report);
     report->device_ms = ms;
     report->n_spectra = pl.n_spectra;
@@ -512,7 +685,8 @@ srs_status srs_create(srs_ctx** out, int device, void* cuda_stream) {
     c->own_stream = true;
   }
   if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
-      cudaEventCreate(&c->ev2) != cudaSuccess || cudaEventCreate(&c->ev3) != cudaSuccess) {
+      cudaEventCreate(&c->ev2) != cudaSuccess || cudaEventCreate(&c->ev3) != cudaSuccess ||
+      cudaMallocHost(&c->hflag, 64) != cudaSuccess) {
     cudaGetLastError();
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -526,6 +700,8 @@ void srs_destroy(srs_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->hflag) cudaFreeHost(c->hflag);
   for (DevBuf* b : c->all_buffers()) b->release();
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);

@@ -47,6 +47,20 @@ struct srs_ctx {
   bool have_plan = false;
   std::vector<unsigned char> plan_key;
   srs::Plan plan;
+  // the search's device sequence as a CUDA graph, and what it was captured for
+  bool use_graphs = true;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<unsigned char> graph_key;
+  int graph_launches = 0;
+  int ctas_per_sm = 0;      // 0: as many as fit
+  // autotuned (segments per item, CTAs per SM) of the mixed spreader per shape
+  struct Tuned {
+    std::vector<unsigned char> key;
+    int chunk, ctas;
+    double ms;
+  };
+  std::vector<Tuned> tuned;
+  int* hflag = nullptr;     // pinned copy of the device error flag
   srs::DevBuf items, anchors, partial, betas, nseg, item_off, corr, tw, keys, topk_a, topk_b, cands, queue, strain,
       strain32, errflag, map, S, F, psi, th, im, ii;
   // learned proposal
@@ -73,12 +87,24 @@ inline srs_status cuda_err(srs_ctx* c, cudaError_t e, const char* where) {
   return set_err(c, e == cudaErrorMemoryAllocation ? SRS_ERR_OOM : SRS_ERR_CUDA, m);
 }
 
+// Milliseconds between two recorded events; 0 (and the runtime's error state
+// cleared) when they cannot be compared.
+inline float elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.f;
+  }
+  return ms;
+}
+
 // Search entry used by the proposal pipeline (srs_capi.cpp).
 srs_status search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype, const double* mc,
                        int32_t n_templates, const srs_params* params, float* stat_map, srs_candidate* cands,
                        int32_t* n_cands, srs_report* report);
 srs_status strain_f32(srs_ctx* ctx, const void* dstrain, int32_t dtype, int64_t samples, int64_t n_s,
                       const float** out, int* use_tma);
+bool tma_disabled();
 
 }  // namespace srs
 

@@ -74,4 +74,12 @@ __device__ __forceinline__ void mixed_phase(const Anchor& A, int l, float kc, ui
   th = t - rintf(t);
 }
 
+// The fine-grid phase alone (periods, 32-bit fixed point) of sample l.
+__device__ __forceinline__ uint32_t mixed_psi(const Anchor& A, int l) {
+  const float lf = (float)l;
+  const float cq = fmaf(fmaf(fmaf(A.p5, lf, A.p4), lf, A.p3), lf, A.p2) * (lf * lf);
+  const float cpsi = fmaf(A.p1lo, lf, cq);
+  return A.psi0 + (uint32_t)l * A.n1 + (uint32_t)__float2int_rn(cpsi * 4294967296.0f);
+}
+
 }  // namespace srs

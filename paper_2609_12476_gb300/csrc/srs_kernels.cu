@@ -242,16 +242,24 @@ struct TapIn {
   float z0, cre, cim;
 };
 
+template <bool INT_KC>
 __device__ __forceinline__ TapIn tap_inputs(const Anchor& A, const float* __restrict__ xs, int j, int l_base,
                                             int W, const MixedArgs& a) {
   uint32_t Psi;
-  float th;
-  mixed_phase(A, j - l_base, a.kc, Psi, th);
+  float sn, cs;
+  if (INT_KC) {
+    // f_c t_coh = k_c is a whole number: f_c delta = k_c (delta / t_coh), so the
+    // demodulation phase is k_c * Psi modulo one cycle, exactly
+    Psi = mixed_psi(A, j - l_base);
+    __sincosf((float)(int32_t)(Psi * (uint32_t)a.kc_int) * 1.4629180792671596e-09f, &sn, &cs);  // 2 pi / 2^32
+  } else {
+    float th;
+    mixed_phase(A, j - l_base, a.kc, Psi, th);
+    __sincosf(6.28318530717958647692f * th, &sn, &cs);
+  }
   const int n = a.n_fine;
   const int cell = (int)__umulhi(Psi, (uint32_t)n);
   const float fr = (float)(Psi * (uint32_t)n) * 2.3283064365386963e-10f;
-  float sn, cs;
-  __sincosf(6.28318530717958647692f * th, &sn, &cs);
   const float xv = xs[j];
   const float off = ceilf(fr - 0.5f * (float)W);
   TapIn t;
@@ -269,7 +277,7 @@ __device__ __forceinline__ TapIn tap_inputs(const Anchor& A, const float* __rest
 // walks cell by cell: each lane adds all of its samples whose first cell is
 // Bm, then every lane moves its window one cell on (flushing acc[0] with a
 // shared-memory atomic), so the shift is warp-uniform.
-template <int W>
+template <int W, bool INT_KC>
 __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2* __restrict__ grid,
                                            const Anchor& A, int j_begin, int j_end, int l_base,
                                            const MixedArgs& a) {
@@ -283,7 +291,7 @@ __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2*
   int j = j_begin;
   bool live = j < j_end;
   TapIn p = {0, 0.f, 0.f, 0.f};
-  if (live) p = tap_inputs(A, xs, j, l_base, W, a);
+  if (live) p = tap_inputs<INT_KC>(A, xs, j, l_base, W, a);
   int Bm = p.l0;  // fine-grid cell of acc[0]
   while (__any_sync(mask, live)) {
     while (live && p.l0 == Bm) {
@@ -297,7 +305,7 @@ __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2*
       }
       ++j;
       live = j < j_end;
-      if (live) p = tap_inputs(A, xs, j, l_base, W, a);
+      if (live) p = tap_inputs<INT_KC>(A, xs, j, l_base, W, a);
     }
     // cell Bm is complete for this lane
     if (acc_re[0] != 0.f || acc_im[0] != 0.f) {
@@ -326,7 +334,7 @@ __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2*
 // shared memory by a TMA bulk copy (the next segment's copy overlaps this
 // segment's FFT), spread, FFT, deconvolve, then either write F (SPECTRA) or
 // add (P - 2) / 2 into the item's running sum Z.
-template <int W, bool SPECTRA>
+template <int W, bool SPECTRA, bool INT_KC>
 __global__ void __launch_bounds__(kSpreadThreads, 4)
 k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_items,
         const double* __restrict__ betas, int* __restrict__ queue, MixedArgs a,
@@ -386,7 +394,7 @@ k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_
       {
         const int j0 = (warp * 32 + lane) * a.run;
         const int j1 = min(j0 + a.run, a.n_s);
-        if (j0 < a.n_s) spread_run<W>(xs, g0, anc[(i - it.i0) * a.n_anchor + warp], j0, j1, warp * a.span, a);
+        if (j0 < a.n_s) spread_run<W, INT_KC>(xs, g0, anc[(i - it.i0) * a.n_anchor + warp], j0, j1, warp * a.span, a);
       }
       __syncthreads();
       if (tid == 0 && a.use_tma && i + 1 < it.i1) bulk_load(xs, strain + (long long)(i + 1) * a.n_s, seg_bytes, &s_bar);
@@ -650,7 +658,7 @@ static cudaError_t launch_mixed_t(const float* strain, const Item* items, int n_
                                   int* queue, const MixedArgs& a, float* partial, double2* Fout, int* err, int n_sm,
                                   int ctas_per_sm, cudaStream_t st) {
   const size_t smem = mixed_smem_bytes(a);
-  auto kern = k_mixed<W, SP>;
+  auto kern = a.kc_int > 0 ? k_mixed<W, SP, true> : k_mixed<W, SP, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;

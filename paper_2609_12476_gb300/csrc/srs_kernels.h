@@ -26,6 +26,7 @@ struct MixedArgs {
   int seg_begin, seg_range;       // spectra output: first segment, segments per template
   AnchorArgs aa;                  // FP64 anchor inputs
   float kc;                       // f_c * t_coh
+  int kc_int;                     // f_c * t_coh when it is a whole number in [1, 2^30), else 0
   float inv_ns;                   // 1 / n_s
   float es_beta_log2e;            // ES shape parameter * log2(e)
   float two_over_w;

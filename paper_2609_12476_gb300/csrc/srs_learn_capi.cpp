@@ -42,6 +42,7 @@ void shuffle(std::vector<int32_t>& v, uint64_t& state) {
 
 srs_status begin(srs_ctx* ctx) {
   if (!ctx) return SRS_ERR_ARG;
+  cudaGetLastError();  // an earlier unchecked call's error is not this call's
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_err(ctx, cudaGetLastError(), "cudaSetDevice");
   return SRS_OK;
 }
@@ -287,8 +288,7 @@ srs_status refine_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
   SRS_CK(cudaMemcpyAsync(nsigma, ctx->sp_out.p, (size_t)n_cells * 4, cudaMemcpyDeviceToHost, ctx->stream), "copy n_sigma");
   SRS_CK(cudaStreamSynchronize(ctx->stream), "refine");
   if (report) {
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    const float ms = elapsed_ms(ctx->ev0, ctx->ev1);
     std::memset(report, 0, sizeof *report);
     report->device_ms = ms;
     report->spread_ms = ms;
@@ -619,8 +619,7 @@ srs_status srs_search_proposed(srs_ctx* ctx, const void* strain, int64_t n_sampl
     }
     *n_cands = k;
     if (report) {
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ctx->ev2, ctx->ev3);
+      const float ms = elapsed_ms(ctx->ev2, ctx->ev3);
       report->device_ms = ms;
       report->coarse_spectra = rep.n_spectra;
       report->proposed_coarse = proposed;

@@ -14,6 +14,7 @@
 // the process exits.  The caller owns the strain and the output.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -175,6 +176,7 @@ srs_status run(void* stream_v, const void* strain, int64_t n_samples, int32_t dt
   a.aa.n_anchor = pl.n_anchor;
   a.fft_fixed = (pl.n_fine == 1200 && pl.radices == std::vector<int32_t>{4, 4, 3, 5, 5}) ? 1200 : 0;
   a.kc = (float)pl.k_c;
+  a.kc_int = (pl.k_c >= 1.0 && pl.k_c < 1073741824.0 && pl.k_c == std::floor(pl.k_c)) ? (int)pl.k_c : 0;
   a.inv_ns = (float)(1.0 / (double)pl.n_s);
   a.es_beta_log2e = (float)(pl.beta_es * 1.4426950408889634074);
   a.two_over_w = (float)(2.0 / pl.w);

@@ -250,3 +250,23 @@ def test_topk_is_exact_on_the_returned_map(ctx, two_hours, k):
     v, m, b = oracle.topk(smap, k)
     assert np.array_equal(cands["template_idx"], m) and np.array_equal(cands["bin"], b)
     assert np.array_equal(cands["value"], v.astype(np.float32))
+
+
+def test_graph_replay_and_interleaved_calls(ctx, two_hours):
+    """Repeated searches replay a captured CUDA graph; calls of another kind in
+    between (which regrow the device tables) must not leave a stale graph."""
+    w = two_hours
+    p = Params(eps=1e-6, top_k=16)
+    c0, m0, r0 = ctx.search(w["strain"], w["mc"], p)
+    c1, m1, r1 = ctx.search(w["strain"], w["mc"], p)
+    assert r1["kernel_launches"] == r0["kernel_launches"]
+    # a spectra call with a wider band and more templates regrows corr / tw / items
+    wide = Params(fs=256.0, f_lo=20.0, f_hi=100.0, eps=1e-6)
+    ctx.segment_spectra(w["strain"], srs_synth.log_templates(2e-2, 5e-2, 80), 0, 3, wide)
+    ctx.time_map(w["mc"], [(0, 0), (5, 3)], p, w["n_samples"])
+    c2, m2, r2 = ctx.search(w["strain"], w["mc"], p)
+    for m in (m1, m2):
+        assert np.max(np.abs(m - m0)) < 1e-4
+    assert (c2["template_idx"][0], c2["bin"][0]) == (c0["template_idx"][0], c0["bin"][0])
+    # autotuned chunk stays fixed for this shape
+    assert r2["chunk"] == r0["chunk"]
