@@ -112,7 +112,7 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_oracle_rate(w, budget_s=12.0, seed=1234):
+def cpu_oracle_rate(w, budget_s=12.0, seed=1234, ctx=None, n_parity=64):
     """Oracle spectra/s on the host cores, on a seeded random sample of the
     workload's (template, segment) items sized to about budget_s seconds."""
     import oracle
@@ -137,9 +137,20 @@ def cpu_oracle_rate(w, budget_s=12.0, seed=1234):
     for k, (m, _i) in enumerate(sample):
         S[m] += P[k]
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d random (template, segment) spectra of %d (seed %d): direct FP64 NDFT + power + sum"
-                      % (n, len(all_items), seed), "seconds": dt}
+    out = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "%d random (template, segment) spectra of %d (seed %d): direct FP64 NDFT + power + sum"
+                     % (n, len(all_items), seed), "seconds": dt}
+    if ctx is not None:
+        # parity of the same sample's first spectra: the GPU's mixed form vs the oracle
+        from paper_2609_12476_gb300 import SRS_MIXED
+        pm = params_for(w, SRS_MIXED)
+        errs = []
+        for k, (m, i) in enumerate(sample[:n_parity]):
+            G, _ = ctx.segment_spectra(w["strain"], w["mc"][[m]], i, i + 1, pm)
+            errs.append(float(np.linalg.norm(G[0, 0] - F[k]) / np.linalg.norm(F[k])))
+        out.update({"parity_items": len(errs), "parity_rel_l2_max": max(errs),
+                    "parity_rel_l2_median": float(np.median(errs)), "parity_bar": 10 * w["eps"]})
+    return out
 
 
 def run_reference(args):
@@ -242,23 +253,34 @@ def run_ours(args):
     line = None
     if rank == 0:
         pk = peaks()
-        elem = hnp.itemsize
-        # algorithmic bytes of the transform kernel per launch: the segment's
-        # strain samples read once per spectrum, the FP64 anchors, the partial sums
-        alg_bytes = n_spec * (int(info["n_s"]) * elem + 8 * 48) + int(info["n_items"]) * n_bins * 4
+        n_s, n_fine, w_taps = int(info["n_s"]), int(info["n_fine"]), int(info["w"])
         spread_avg = float(np.mean(spread_ms))
+        # k_mixed's algorithmic FP32 operations per spectrum (the ES-spread
+        # type-1 NUFFT): per sample w taps x (z, 1-z^2, sqrt, scale, exp, and a
+        # complex-by-real multiply-add = 4) + demodulation (sin, cos, 2 mul)
+        # + grid position (2); FFT 5 n log2 n; deconvolution + power 8 per bin
+        flops = n_spec * (n_s * (9 * w_taps + 6) + 5 * n_fine * np.log2(n_fine) + 8 * n_bins)
+        achieved_tf = flops / (spread_avg * 1e-3) / 1e12
+        sm_mhz = (ck or {}).get("sm_mhz") or (pk or {}).get("sm_max_mhz", 2070.0)
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_tf = 2.0 * 128 * n_sm * sm_mhz * 1e6 / 1e12      # FP32 FMA lanes x 2 x SMs x clock
+        traffic = profile_traffic("k_mixed_semicoherent_2h.md") if args.workload == "semicoherent_2h" else None
+        roof = {"kernel": "k_mixed", "bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved_tf / peak_tf, "traffic": traffic,
+                "peak_source": "128 FP32 lanes x %d SMs x 2 flop x %.0f MHz (median SM clock in the timed region)"
+                               % (n_sm, sm_mhz)}
+        # the HBM view the metric asks for: FP32 samples the kernel reads per
+        # spectrum (the working copy) + partial sums it writes
+        alg_bytes = n_spec * n_s * 4 + int(info["n_items"]) * n_bins * 4
         ach = alg_bytes / (spread_avg * 1e-3) / 1e9
         hbm_peak = pk["hbm_gbs"] if pk else 6800.0
-        roof = {"kernel": "k_mixed", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback 6.8 TB/s",
-                "note": "the kernel is issue-bound (FP32 + MUFU), not HBM-bound; see alu"}
-        # FP32 issue roofline: lanes x SMs x measured median SM clock
-        sm_mhz = (ck or {}).get("sm_mhz") or (pk or {}).get("sm_max_mhz", 2070.0)
+        roof_hbm = {"kernel": "k_mixed", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": ach / hbm_peak, "traffic": traffic,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback 6.8 TB/s"}
         plain = None
         if not args.no_plain:
             plain = time_plain(ctx, xd, w, stream, flush, n_spec, n_bins, info, pk)
-        cpu = None if (args.no_cpu or world > 1) else cpu_oracle_rate(w)
+        cpu = None if (args.no_cpu or world > 1) else cpu_oracle_rate(w, ctx=ctx)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -268,12 +290,31 @@ def run_ours(args):
                            "eps": w["eps"], "w": info["w"], "n_fine": info["n_fine"], "chunk": info["chunk"],
                            "precision": "mixed: FP64 time-map anchors, FP32 spread/FFT/power",
                            "l2": "flushed (256 MB write) before every timed step"},
-                "roofline": roof, "clocks": ck, "gpu_launches": launches,
+                "roofline": roof, "roofline_hbm": roof_hbm, "clocks": ck, "gpu_launches": launches,
                 "e2e": e2e, "cpu_baseline": cpu, "plain_fp64": plain,
                 "spread_ms_avg": spread_avg}
         print(json.dumps(line), flush=True)
     barrier(world)
     ctx.close()
+
+
+def profile_traffic(name):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the kernel source that is built now (hash of srs_kernels.cu + srs_device.cuh)."""
+    import hashlib
+    try:
+        txt = open(os.path.join(ROOT, "profiles", name)).read()
+        csrc = os.path.join(ROOT, "paper_2609_12476_gb300", "csrc")
+        h = hashlib.sha256(open(os.path.join(csrc, "srs_kernels.cu"), "rb").read() +
+                           open(os.path.join(csrc, "srs_device.cuh"), "rb").read()).hexdigest()[:16]
+        if h not in txt:
+            return None
+        for line in txt.splitlines():
+            if line.startswith("traffic_bytes_per_launch:"):
+                return int(line.split(":")[1])
+    except Exception:
+        return None
+    return None
 
 
 def ctx_stream(stream):
