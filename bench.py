@@ -394,7 +394,7 @@ def run_learned(args):
     info, _, _ = __import__("paper_2609_12476_gb300").srs_plan(p, fine, n)
     full_spec = int(info["n_spectra"])
     for k in range(args.warmup):
-        ctx.search_proposed(strains[k], coarse, fine, p, mlp, sth)
+        ctx.search_proposed(strains[k], coarse, fine, p, mlp, sth, nms=proposal.NMS)
     torch.cuda.synchronize()
     clocks = Clocks(0)
     ev = []
@@ -402,7 +402,7 @@ def run_learned(args):
     for k in range(args.warmup, args.warmup + args.steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        r = ctx.search_proposed(strains[k], coarse, fine, p, mlp, sth)
+        r = ctx.search_proposed(strains[k], coarse, fine, p, mlp, sth, nms=proposal.NMS)
         b.record(stream)
         ev.append((a, b))
         reps.append(r["report"])

@@ -287,19 +287,28 @@ srs_status srs_refine(srs_ctx* ctx, const void* strain, int64_t n_samples, int32
                       int32_t n_templates, const srs_params* params, const int32_t* cell_m,
                       const int32_t* cell_b, int32_t n_cells, float* nsigma, srs_report* report);
 
+/* How proposed coarse cells become fine cells. */
+typedef struct {
+  float score_threshold;   /* a coarse cell is proposed when its logit exceeds this */
+  int32_t nms_templates;   /* non-maximum suppression half-window in coarse templates (0: off) */
+  int32_t nms_bins;        /* ... and in bins (0: off) */
+  int32_t fine_rows;       /* fine templates of coarse rows within this many of the cell (0: its own) */
+} srs_proposal_params;
+
 /* The proposal search: the coarse search over coarse_mc, network scores of
- * all its cells, every cell scoring above score_threshold proposes the fine
- * templates whose nearest coarse template (in log Mc) is within one of it and
- * bins within one of its bin; those fine cells are evaluated with
- * srs_refine.  Outputs (host): up to max_cells evaluated cells (cell_m,
- * cell_b, cell_nsigma; *n_cells_out = how many were evaluated, possibly more
- * than max_cells), the top-k of them in cands, and a report. */
+ * all its cells; a cell scoring above the threshold (and, with suppression
+ * on, highest within its window) proposes the fine templates whose nearest
+ * coarse template (in log Mc) is within fine_rows of it, at bins within one of
+ * its bin; those fine cells are evaluated with srs_refine.  Outputs (host):
+ * up to max_cells evaluated cells (cell_m, cell_b, cell_nsigma; *n_cells_out
+ * = how many were evaluated, possibly more than max_cells), the top-k of them
+ * in cands, and a report. */
 srs_status srs_search_proposed(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype,
                                const double* coarse_mc, int32_t n_coarse, const double* fine_mc,
                                int32_t n_fine, const srs_params* params, const float* mlp_params,
-                               float score_threshold, int32_t max_cells, int32_t* cell_m, int32_t* cell_b,
-                               float* cell_nsigma, int32_t* n_cells_out, srs_candidate* cands,
-                               int32_t* n_cands, srs_proposal_report* report);
+                               const srs_proposal_params* prop, int32_t max_cells, int32_t* cell_m,
+                               int32_t* cell_b, float* cell_nsigma, int32_t* n_cells_out,
+                               srs_candidate* cands, int32_t* n_cands, srs_proposal_report* report);
 
 /* Size of the fixed device scratch used by srs_segment_spectra_static(). */
 #define SRS_STATIC_SCRATCH_BYTES (16u << 20)

@@ -71,6 +71,11 @@ class _TrainCfg(ctypes.Structure):
                 ("seed", ctypes.c_uint64)]
 
 
+class _ProposalParams(ctypes.Structure):
+    _fields_ = [("score_threshold", ctypes.c_float), ("nms_templates", ctypes.c_int32),
+                ("nms_bins", ctypes.c_int32), ("fine_rows", ctypes.c_int32)]
+
+
 class _ProposalReport(ctypes.Structure):
     _fields_ = [("device_ms", ctypes.c_double), ("coarse_spectra", ctypes.c_int64),
                 ("proposed_coarse", ctypes.c_int32), ("fine_cells", ctypes.c_int32),
@@ -148,8 +153,8 @@ def lib():
                                  ctypes.POINTER(_Report)]
         L.srs_search_proposed.restype = i32
         L.srs_search_proposed.argtypes = [vp, vp, i64, i32, vp, i32, vp, i32, ctypes.POINTER(_Params), vp,
-                                          ctypes.c_float, i32, vp, vp, vp, ctypes.POINTER(i32), vp,
-                                          ctypes.POINTER(i32), ctypes.POINTER(_ProposalReport)]
+                                          ctypes.POINTER(_ProposalParams), i32, vp, vp, vp, ctypes.POINTER(i32),
+                                          vp, ctypes.POINTER(i32), ctypes.POINTER(_ProposalReport)]
         L.srs_segment_spectra_static.restype = i32
         L.srs_segment_spectra_static.argtypes = [vp, vp, i64, i32, vp, i32, i32, i32, ctypes.POINTER(_Params),
                                                  vp, ctypes.c_char_p, ctypes.c_size_t]
@@ -393,9 +398,12 @@ class Context:
         self._check(st)
         return ns, _report_dict(rep)
 
-    def search_proposed(self, strain, coarse_mc, fine_mc, params, mlp_params, threshold, max_cells=1 << 20):
+    def search_proposed(self, strain, coarse_mc, fine_mc, params, mlp_params, threshold, max_cells=1 << 20,
+                        nms=(0, 0), fine_rows=1):
         """srs_search_proposed: returns dict(cells [n, 2], nsigma [n], cands,
-        report)."""
+        report).  nms = (templates, bins) half-window of the non-maximum
+        suppression ((0, 0): off); fine_rows = coarse rows either side whose
+        fine templates a proposal covers."""
         cmc = np.ascontiguousarray(coarse_mc, dtype=np.float64)
         fmc = np.ascontiguousarray(fine_mc, dtype=np.float64)
         mp = np.ascontiguousarray(mlp_params, dtype=np.float32)
@@ -412,9 +420,10 @@ class Context:
             strain = np.ascontiguousarray(strain)
             p.io_on_device = 0
             ptr, n = strain.ctypes.data, strain.size
+        pp = _ProposalParams(float(threshold), int(nms[0]), int(nms[1]), int(fine_rows))
         st = self._lib.srs_search_proposed(self._h, ptr, n, _dtype_code(strain), cmc.ctypes.data, cmc.size,
                                            fmc.ctypes.data, fmc.size, ctypes.byref(p), mp.ctypes.data,
-                                           float(threshold), max_cells, cm.ctypes.data, cb.ctypes.data,
+                                           ctypes.byref(pp), max_cells, cm.ctypes.data, cb.ctypes.data,
                                            ns.ctypes.data, ctypes.byref(nout), cands.ctypes.data,
                                            ctypes.byref(nc), ctypes.byref(rep))
         self._check(st)

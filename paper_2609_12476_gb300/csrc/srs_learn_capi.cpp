@@ -140,7 +140,7 @@ srs_status refine_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
       srs_params ps = pc;
       ps.io_on_device = 1;
       ps.top_k = 1;
-      ps.chunk = 0;
+      ps.chunk = 16;   // no autotuning of a one-off template subset
       const void* dstrain_all = strain;
       if (!params->io_on_device) {
         const size_t bytes = (size_t)n_samples * (dtype == SRS_F64 ? 8 : 4);
@@ -517,11 +517,14 @@ srs_status srs_refine(srs_ctx* ctx, const void* strain, int64_t n_samples, int32
 
 srs_status srs_search_proposed(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype,
                                const double* coarse_mc, int32_t n_coarse, const double* fine_mc, int32_t n_fine,
-                               const srs_params* params, const float* mlp_params, float score_threshold,
-                               int32_t max_cells, int32_t* cell_m, int32_t* cell_b, float* cell_nsigma,
-                               int32_t* n_cells_out, srs_candidate* cands, int32_t* n_cands,
-                               srs_proposal_report* report) {
+                               const srs_params* params, const float* mlp_params,
+                               const srs_proposal_params* prop, int32_t max_cells, int32_t* cell_m,
+                               int32_t* cell_b, float* cell_nsigma, int32_t* n_cells_out, srs_candidate* cands,
+                               int32_t* n_cands, srs_proposal_report* report) {
   try {
+    if (!prop) return set_err(ctx, SRS_ERR_ARG, "search_proposed: prop is NULL");
+    const srs_proposal_params params_prop = *prop;
+    const float score_threshold = prop->score_threshold;
     srs_status s = begin(ctx);
     if (s != SRS_OK) return s;
     if (!strain || !params || !coarse_mc || !fine_mc || !mlp_params || n_coarse <= 0 || n_fine <= 0 || !n_cells_out ||
@@ -561,22 +564,49 @@ srs_status srs_search_proposed(srs_ctx* ctx, const void* strain, int64_t n_sampl
     SRS_CK(cudaStreamSynchronize(ctx->stream), "score");
     // 3. proposed coarse cells -> fine cells (nearest coarse template in log Mc)
     std::vector<int32_t> parent(n_fine);
-    for (int32_t f = 0; f < n_fine; ++f) {
-      double best = 1e300;
+    {
+      std::vector<double> lc(n_coarse);
+      bool sorted = true;
       for (int32_t c = 0; c < n_coarse; ++c) {
-        const double d = std::fabs(std::log(fine_mc[f]) - std::log(coarse_mc[c]));
-        if (d < best) { best = d; parent[f] = c; }
+        lc[c] = std::log(coarse_mc[c]);
+        if (c > 0 && !(lc[c] > lc[c - 1])) sorted = false;
+      }
+      for (int32_t f = 0; f < n_fine; ++f) {
+        const double lf = std::log(fine_mc[f]);
+        if (sorted) {
+          const int32_t hi = (int32_t)(std::lower_bound(lc.begin(), lc.end(), lf) - lc.begin());
+          int32_t best = std::min(hi, n_coarse - 1);
+          if (hi > 0 && (hi == n_coarse || std::fabs(lf - lc[hi - 1]) <= std::fabs(lf - lc[hi]))) best = hi - 1;
+          parent[f] = best;
+        } else {
+          double bd = 1e300;
+          for (int32_t c = 0; c < n_coarse; ++c)
+            if (std::fabs(lf - lc[c]) < bd) { bd = std::fabs(lf - lc[c]); parent[f] = c; }
+        }
       }
     }
     std::vector<std::vector<int32_t>> children(n_coarse);
     for (int32_t f = 0; f < n_fine; ++f) children[parent[f]].push_back(f);
     std::vector<long long> fk;
     int32_t proposed = 0;
+    const int32_t rt = std::max(0, params_prop.nms_templates), rb = std::max(0, params_prop.nms_bins);
+    const int32_t rows = std::max(0, params_prop.fine_rows);
     for (long long cell = 0; cell < ncells; ++cell) {
       if (!(scores[cell] > score_threshold)) continue;
-      ++proposed;
       const int32_t cm = (int32_t)(cell / n_bins), cb = (int32_t)(cell % n_bins);
-      for (int32_t c = std::max(0, cm - 1); c <= std::min(n_coarse - 1, cm + 1); ++c)
+      if (rt > 0 || rb > 0) {
+        // non-maximum suppression: keep a cell only if no cell within
+        // (+-rt templates, +-rb bins) scores higher (ties: the first in row-major order)
+        bool peak = true;
+        for (int32_t m = std::max(0, cm - rt); m <= std::min(n_coarse - 1, cm + rt) && peak; ++m)
+          for (int32_t b = std::max(0, cb - rb); b <= std::min(n_bins - 1, cb + rb); ++b) {
+            const long long o = (long long)m * n_bins + b;
+            if (scores[o] > scores[cell] || (scores[o] == scores[cell] && o < cell)) { peak = false; break; }
+          }
+        if (!peak) continue;
+      }
+      ++proposed;
+      for (int32_t c = std::max(0, cm - rows); c <= std::min(n_coarse - 1, cm + rows); ++c)
         for (int32_t f : children[c])
           for (int32_t b = std::max(0, cb - 1); b <= std::min(n_bins - 1, cb + 1); ++b)
             fk.push_back((long long)f * n_bins + b);

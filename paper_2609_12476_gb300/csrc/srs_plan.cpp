@@ -248,7 +248,7 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
   // alpha = w h / 2, sum_l psi(l h - x) exp(-i k l h) ~= exp(-i k x) alpha phihat(k alpha) / h,
   // so F_k = G_k * (2 / w) / phihat(k pi w / n).
   std::vector<double> gx, gw;
-  gauss_legendre(256, gx, gw);
+  gauss_legendre(128, gx, gw);
   pl.corr.resize(pl.n_bins);
   for (int32_t b = 0; b < pl.n_bins; ++b) {
     double k = (double)(b - pl.half_bins);

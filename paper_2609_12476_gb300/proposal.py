@@ -177,18 +177,35 @@ def noise_maps(ctx, coarse_mc, params, t_obs, n_maps, seed):
         yield coarse_map(ctx, x, coarse_mc, params)[0]
 
 
-def calibrate(ctx, mlp_params, coarse_mc, params, t_obs, n_maps, seed, far):
-    """Thresholds proposing a fraction `far` of noise-only coarse cells: one on
-    the network score, one on the coarse n_sigma (the proposal without the
-    network)."""
-    import torch
-    sc, ns = [], []
+NMS = (4, 16)        # suppression half-window: the patch's half-size (templates, bins)
+
+
+def peaks(values, nms):
+    """Mask of the cells that are the maximum of their (+-nms[0], +-nms[1])
+    window (ties: the first in row-major order keeps it)."""
+    from scipy.ndimage import maximum_filter
+    v = np.asarray(values, dtype=np.float64)
+    if nms[0] <= 0 and nms[1] <= 0:
+        return np.ones(v.shape, dtype=bool)
+    mx = maximum_filter(v, size=(2 * nms[0] + 1, 2 * nms[1] + 1), mode="constant", cval=-np.inf)
+    return v >= mx
+
+
+def calibrate(ctx, mlp_params, coarse_mc, params, t_obs, n_maps, seed, far, nms=NMS):
+    """Thresholds that propose a fraction `far` of the cells of pure-noise coarse
+    maps after non-maximum suppression: one on the network's score, one on the
+    coarse n_sigma (the proposal without a network)."""
+    sc_peaks, ns_peaks, total = [], [], 0
     for smap in noise_maps(ctx, coarse_mc, params, t_obs, n_maps, seed):
-        sc.append(ctx.score_map(smap, mlp_params).flatten())
-        ns.append(smap.flatten())
-    sc = torch.cat(sc).double().cpu().numpy()
-    ns = torch.cat(ns).double().cpu().numpy()
-    return float(np.quantile(sc, 1.0 - far)), float(np.quantile(ns, 1.0 - far))
+        sc = ctx.score_map(smap, mlp_params).double().cpu().numpy()
+        ns = smap.double().cpu().numpy()
+        total += sc.size
+        sc_peaks.append(sc[peaks(sc, nms)])
+        ns_peaks.append(ns[peaks(ns, nms)])
+    k = max(1, int(round(far * total)))
+    sp = np.sort(np.concatenate(sc_peaks))[::-1]
+    npk = np.sort(np.concatenate(ns_peaks))[::-1]
+    return float(sp[min(k, len(sp) - 1)]), float(npk[min(k, len(npk) - 1)])
 
 
 def detection_threshold(nseg, p_fa):
@@ -200,7 +217,7 @@ def detection_threshold(nseg, p_fa):
 
 
 def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t_obs, n_real, per_real, seed,
-             p_fa=1e-6, amp_range=(0.01, 0.1)):
+             p_fa=1e-6, amp_range=(0.01, 0.1), nms=NMS, fine_rows=1):
     """Recall of injections over the same realisations in four searches:
       full            every fine template (the judge)
       proposal        the network's proposal at its noise-calibrated threshold
@@ -239,7 +256,7 @@ def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t
         found = {"full": {(m, b): float(fm[m, b]) for m, b in np.argwhere(fm > th_f[:, None])}}
         out["full_cells"] += fm.size
         # the network's proposal search
-        pr = ctx.search_proposed(x, coarse_mc, fine_mc, params, mlp_params, score_th)
+        pr = ctx.search_proposed(x, coarse_mc, fine_mc, params, mlp_params, score_th, nms=nms, fine_rows=fine_rows)
         out["proposal_ms"] += pr["report"]["device_ms"]
         out["proposal_coarse_spectra"] += pr["report"]["coarse_spectra"]
         out["proposal_segment_bins"] += pr["report"]["fine_segment_bins"]
@@ -250,10 +267,12 @@ def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t
         cmap, _ = coarse_map(ctx, x, coarse_mc, params)
         cm = cmap.cpu().numpy()
         K = pr["report"]["proposed_coarse"]
-        order = np.argsort(-cm, axis=None)[:K]
-        for key, prop in (("nsigma_equal", np.stack(np.unravel_index(order, cm.shape), axis=1)),
-                          ("nsigma_far", np.argwhere(cm > nsigma_th))):
-            fc = fine_cells_of(prop, coarse_mc, fine_mc, n_bins)
+        pk = peaks(cm, nms)
+        cand = np.argwhere(pk)
+        order = np.argsort(-cm[pk])[:K]
+        for key, prop in (("nsigma_equal", cand[order]),
+                          ("nsigma_far", np.argwhere(pk & (cm > nsigma_th)))):
+            fc = fine_cells_of(prop, coarse_mc, fine_mc, n_bins, fine_rows)
             out[key + "_cells"] += len(fc)
             found[key] = {}
             if len(fc):
@@ -273,16 +292,16 @@ def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t
     return out
 
 
-def fine_cells_of(coarse_cells, coarse_mc, fine_mc, n_bins):
+def fine_cells_of(coarse_cells, coarse_mc, fine_mc, n_bins, fine_rows=1):
     """Fine (template, bin) cells proposed by coarse cells: fine templates whose
-    nearest coarse template is within one of the cell's, bins within one."""
+    nearest coarse template is within fine_rows of the cell's, bins within one."""
     parent = np.array([nearest_template(coarse_mc, m) for m in fine_mc])
     children = {}
     for f, c in enumerate(parent):
         children.setdefault(int(c), []).append(f)
     cells = set()
     for m, b in coarse_cells:
-        for c in range(int(m) - 1, int(m) + 2):
+        for c in range(int(m) - fine_rows, int(m) + fine_rows + 1):
             for f in children.get(c, []):
                 for bb in range(max(0, int(b) - 1), min(n_bins, int(b) + 2)):
                     cells.add((f, bb))

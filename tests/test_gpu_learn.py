@@ -142,9 +142,9 @@ def test_proposal_search_extremes(ctx):
     x = srs_synth.strain_with_chirps(nseg * 7680, fs, 4, [{"mc": 6e-2, "f0": 50.0, "amp": 0.08}])
     p = Params(eps=1e-6, top_k=8)
     params = proposal.init_params(0)
-    none = ctx.search_proposed(x, coarse, fine, p, params, threshold=np.inf)
+    none = ctx.search_proposed(x, coarse, fine, p, params, threshold=np.inf, nms=(0, 0))
     assert none["n_cells"] == 0 and none["report"]["proposed_coarse"] == 0
-    allc = ctx.search_proposed(x, coarse, fine, p, params, threshold=-np.inf)
+    allc = ctx.search_proposed(x, coarse, fine, p, params, threshold=-np.inf, nms=(0, 0))
     assert allc["report"]["proposed_coarse"] == 6 * 600
     assert allc["n_cells"] == 24 * 600
     _, fmap, _ = ctx.search(x, fine, p)
@@ -153,3 +153,19 @@ def test_proposal_search_extremes(ctx):
     assert np.max(np.abs(got - fmap)) < 2e-3
     c = allc["cands"][0]
     assert c["value"] == pytest.approx(float(fmap.max()), abs=2e-3)
+
+
+def test_proposal_suppression_keeps_local_maxima(ctx):
+    fs, nseg = 256.0, 24
+    coarse = srs_synth.log_templates(3e-2, 1e-1, 6)
+    fine = srs_synth.log_templates(3e-2, 1e-1, 24)
+    x = srs_synth.strain_with_chirps(nseg * 7680, fs, 4, [{"mc": 6e-2, "f0": 50.0, "amp": 0.08}])
+    p = Params(eps=1e-6, top_k=8)
+    params = proposal.init_params(0)
+    r = ctx.search_proposed(x, coarse, fine, p, params, threshold=-np.inf, nms=(4, 16), fine_rows=0)
+    smap = torch.from_numpy(ctx.search(x, coarse, p)[1]).cuda()
+    sc = ctx.score_map(smap, params).cpu().numpy()
+    assert r["report"]["proposed_coarse"] == int(proposal.peaks(sc, (4, 16)).sum())
+    parent = [proposal.nearest_template(coarse, m) for m in fine]
+    max_children = max(parent.count(c) for c in range(len(coarse)))
+    assert 0 < r["n_cells"] <= r["report"]["proposed_coarse"] * max_children * 3
