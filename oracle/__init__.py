@@ -25,12 +25,11 @@ from . import build as _build
 _LIB = None
 
 
-def lib():
-    global _LIB
-    if _LIB is None:
-        path = _build.build()
-        L = ctypes.CDLL(path)
-        d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
+def load(path):
+    """Load an oracle library built from srs_oracle.c and declare its functions."""
+    L = ctypes.CDLL(path)
+    d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
+    if True:
         P = ctypes.c_void_p
         L.orc_beta.restype = d; L.orc_beta.argtypes = [d, d]
         L.orc_duration.restype = d; L.orc_duration.argtypes = [d, d, d]
@@ -40,7 +39,13 @@ def lib():
         L.orc_nseg.restype = i32; L.orc_nseg.argtypes = [d, d, d, d, i32, ctypes.c_int]
         L.orc_spectra.restype = ctypes.c_int
         L.orc_spectra.argtypes = [P, i64, d, d, d, i32, P, P, P, i32, ctypes.c_int, P, P]
-        _LIB = L
+    return L
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = load(_build.build())
     return _LIB
 
 

@@ -1,0 +1,61 @@
+"""The oracle's pins must catch plausible mistakes.  Each case compiles a copy
+of the C oracle with one mistake planted (a flipped sign, a wrong exponent, an
+off-by-one bin, a wrong rounding rule), points the oracle at it, and checks
+that the pin meant to catch it fails.  CPU only."""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "srs_oracle.c")
+
+MUTANTS = [
+    # (name, original text, mistake, pins that must fail)
+    ("spectrum sign", "im[b] -= x[j] * sin(ang);", "im[b] += x[j] * sin(ang);",
+     ["test_tone_in_tau_gives_exactly_n", "test_uniform_limit_is_the_fft"]),
+    ("resampled-time exponent", "(-expm1((5.0 / 8.0) * log1p(-x)))", "(-expm1((3.0 / 8.0) * log1p(-x)))",
+     ["test_delta_matches_high_precision_eq_new_t", "test_tone_in_tau_gives_exactly_n",
+      "test_delta_derivative_is_frequency_ratio"]),
+    ("bin frequency off by one", "double fb = f_lo + (double)b / t_coh;", "double fb = f_lo + (double)(b + 1) / t_coh;",
+     ["test_uniform_limit_is_the_fft", "test_noiseless_exact_template_chirp_concentrates_power"]),
+    ("beta frequency power", "pow(f0, 8.0 / 3.0);\n}", "pow(f0, 5.0 / 3.0);\n}",
+     ["test_beta_range_matches_paper", "test_band_crossing_times_match_paper"]),
+    ("whole-segment rounding", "double k = floor(t / t_coh);", "double k = ceil(t / t_coh);",
+     ["test_injection_segment_count_matches_paper"]),
+    ("duration exponent", "(1.0 - pow(f0 / f_end, 8.0 / 3.0))", "(1.0 - pow(f0 / f_end, 5.0 / 3.0))",
+     ["test_injection_segment_count_matches_paper", "test_frequency_reaches_f_end_after_duration"]),
+]
+
+
+@pytest.mark.parametrize("name,orig,bad,catchers", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(tmp_path, monkeypatch, name, orig, bad, catchers):
+    src = open(SRC).read()
+    assert src.count(orig) == 1, name
+    mutant = tmp_path / "mutant.c"
+    mutant.write_text(src.replace(orig, bad))
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(so), str(mutant), "-lm", "-lpthread"])
+    monkeypatch.setattr(oracle, "_LIB", oracle.load(str(so)))
+    for pin in catchers:
+        fn = getattr(pins, pin)
+        with pytest.raises(AssertionError):
+            fn()
+
+
+def test_pins_pass_on_the_unmodified_oracle(tmp_path, monkeypatch):
+    so = tmp_path / "libsame.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(so), SRC, "-lm", "-lpthread"])
+    monkeypatch.setattr(oracle, "_LIB", oracle.load(str(so)))
+    for _, _, _, catchers in MUTANTS:
+        for pin in catchers:
+            getattr(pins, pin)()
+
+
+def test_power_normalisation_pin(monkeypatch):
+    """P = 2|F|^2/n_s (Sec. III.C); dropping the factor 2 breaks the noise pin."""
+    monkeypatch.setattr(oracle, "power", lambda F, n_s: abs(F) ** 2 / n_s)
+    with pytest.raises(AssertionError):
+        pins.test_noise_power_moments_and_n_sigma_null()
