@@ -287,7 +287,8 @@ def run_ours(args):
                 "data": "synthetic (seeded N(0,1) noise + 0PN chirps)",
                 "config": {"workload": args.workload, "templates": int(len(w["mc"])), "spectra_per_step": n_spec,
                            "strain": "%d samples %s at %g Hz" % (w["n_samples"], w["dtype"], w["fs"]),
-                           "eps": w["eps"], "w": info["w"], "n_fine": info["n_fine"], "chunk": info["chunk"],
+                           "eps": w["eps"], "w": info["w"], "n_fine": info["n_fine"], "chunk": rep["chunk"],
+                           "cta_threads": rep["cta_threads"], "staging": "tma" if rep["staging"] else "global loads",
                            "precision": "mixed: FP64 time-map anchors, FP32 spread/FFT/power",
                            "l2": "flushed (256 MB write) before every timed step"},
                 "roofline": roof, "roofline_hbm": roof_hbm, "clocks": ck, "gpu_launches": launches,
@@ -394,7 +395,7 @@ def run_learned(args):
     info, _, _ = __import__("paper_2609_12476_gb300").srs_plan(p, fine, n)
     full_spec = int(info["n_spectra"])
     for k in range(args.warmup):
-        ctx.search_proposed(strains[k], coarse, fine, p, mlp, sth, nms=proposal.NMS)
+        ctx.search_proposed(strains[k], coarse, fine, p, mlp, sth)
     torch.cuda.synchronize()
     clocks = Clocks(0)
     ev = []
@@ -402,7 +403,7 @@ def run_learned(args):
     for k in range(args.warmup, args.warmup + args.steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        r = ctx.search_proposed(strains[k], coarse, fine, p, mlp, sth, nms=proposal.NMS)
+        r = ctx.search_proposed(strains[k], coarse, fine, p, mlp, sth)
         b.record(stream)
         ev.append((a, b))
         reps.append(r["report"])

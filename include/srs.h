@@ -140,6 +140,8 @@ typedef struct {
   int32_t n_items;
   int32_t kernel_launches;/* kernels this call launched */
   double spread_ms;       /* device time of the transform kernel alone (k_mixed / k_plain) */
+  int32_t cta_threads;    /* threads per CTA of the transform kernel */
+  int32_t staging;        /* mixed form: 1 = samples staged by TMA bulk copies, 0 = read from global memory */
 } srs_report;
 
 /* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t

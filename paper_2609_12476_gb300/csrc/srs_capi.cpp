@@ -37,6 +37,7 @@ MixedArgs mixed_args(const Plan& pl, const srs_ctx* ctx, int seg_begin, int seg_
   a.run = pl.run;
   a.span = pl.span;
   a.n_anchor = pl.n_anchor;
+  a.threads = pl.threads;
   a.n_pass = (int)pl.radices.size();
   a.seg_begin = seg_begin;
   a.seg_range = seg_range;
@@ -239,11 +240,22 @@ srs_status strain_f32(srs_ctx* ctx, const void* dstrain, int32_t dtype, int64_t 
 
 namespace {
 
-// Autotuner of the mixed spreader: segments per work item and resident CTAs
+// Autotuner of the mixed spreader: segments per work item, threads per CTA
+// (256, or 128 where the anchor expansion stays accurate over the longer warp
+// span), TMA staging or direct global reads of the samples, and resident CTAs
 // per SM, timed with CUDA events on the whole search's spreader launch for
 // searches of up to kTuneMaxSpectra spectra; the choice is kept per shape
 // (segment length, band, fine grid, kernel width, templates, spectra).
 constexpr long long kTuneMaxSpectra = 2000000;
+
+srs_status upload_items(srs_ctx* ctx, Plan& pl) {
+  SRS_CK(ctx->items.ensure(pl.items.size() * sizeof(Item)), "alloc items");
+  SRS_CK(ctx->item_off.ensure(pl.item_off.size() * 4), "alloc item_off");
+  SRS_CK(ctx->partial.ensure(pl.items.size() * (size_t)pl.n_bins * 4), "alloc partial");
+  SRS_CK(cudaMemcpyAsync(ctx->items.p, pl.items.data(), pl.items.size() * sizeof(Item), cudaMemcpyHostToDevice, ctx->stream), "copy items");
+  SRS_CK(cudaMemcpyAsync(ctx->item_off.p, pl.item_off.data(), pl.item_off.size() * 4, cudaMemcpyHostToDevice, ctx->stream), "copy item_off");
+  return SRS_OK;
+}
 
 srs_status autotune_mixed(srs_ctx* ctx, Plan& pl, const float* s32, int use_tma, int* ctas_out) {
   std::vector<unsigned char> key;
@@ -257,59 +269,78 @@ srs_status autotune_mixed(srs_ctx* ctx, Plan& pl, const float* s32, int use_tma,
   put(&pl.w, sizeof pl.w);
   put(&pl.n_templates, sizeof pl.n_templates);
   put(&pl.n_spectra, sizeof pl.n_spectra);
+  key.push_back((unsigned char)use_tma);
+  key.push_back((unsigned char)pl.allow_128);
+  // SRS_MIXED_LAYOUT=<threads>:<tma|global> restricts the search to one layout
+  // (used to check every layout against the same reference).
+  int only_threads = 0, only_gx = -1;
+  if (const char* lay = std::getenv("SRS_MIXED_LAYOUT")) {
+    const std::string l(lay);
+    key.insert(key.end(), l.begin(), l.end());
+    if (l.rfind("128", 0) == 0) only_threads = 128;
+    if (l.rfind("256", 0) == 0) only_threads = 256;
+    if (l.find(":global") != std::string::npos) only_gx = 1;
+    if (l.find(":tma") != std::string::npos) only_gx = 0;
+  }
   for (const auto& t : ctx->tuned)
     if (t.key == key) {
+      set_cta(pl, t.threads);
+      pl.global_x = t.global_x != 0;
       if (t.chunk != pl.chunk) {
         make_items(pl, t.chunk, false, 0, 0);
-        SRS_CK(ctx->items.ensure(pl.items.size() * sizeof(Item)), "alloc items");
-        SRS_CK(ctx->item_off.ensure(pl.item_off.size() * 4), "alloc item_off");
-        SRS_CK(cudaMemcpyAsync(ctx->items.p, pl.items.data(), pl.items.size() * sizeof(Item), cudaMemcpyHostToDevice, ctx->stream), "copy items");
-        SRS_CK(cudaMemcpyAsync(ctx->item_off.p, pl.item_off.data(), pl.item_off.size() * 4, cudaMemcpyHostToDevice, ctx->stream), "copy item_off");
+        { srs_status us = upload_items(ctx, pl); if (us != SRS_OK) return us; }
       }
       *ctas_out = t.ctas;
       return SRS_OK;
     }
   if (pl.n_spectra > kTuneMaxSpectra) {
-    ctx->tuned.push_back({key, pl.chunk, 0, 0.0});
+    ctx->tuned.push_back({key, pl.chunk, 0, pl.threads, 0, 0.0});
     *ctas_out = 0;
     return SRS_OK;
   }
-  const int chunks[] = {1, 2, 4, 8, 16};
-  const int ctas[] = {0, 3};
-  int best_chunk = pl.chunk, best_ctas = 0;
+  struct Choice { int chunk, ctas, threads, global_x; };
+  Choice best_c{pl.chunk, 0, kSpreadThreads, 0};
   double best = 1e30;
-  for (int ch : chunks) {
-    make_items(pl, ch, false, 0, 0);
-    const size_t n_items = pl.items.size();
-    SRS_CK(ctx->items.ensure(n_items * sizeof(Item)), "alloc items");
-    SRS_CK(ctx->item_off.ensure(pl.item_off.size() * 4), "alloc item_off");
-    SRS_CK(ctx->partial.ensure(n_items * (size_t)pl.n_bins * 4), "alloc partial");
-    SRS_CK(cudaMemcpyAsync(ctx->items.p, pl.items.data(), n_items * sizeof(Item), cudaMemcpyHostToDevice, ctx->stream), "copy items");
-    MixedArgs a = mixed_args(pl, ctx, 0, 0);
-    a.use_tma = use_tma;
-    for (int ct : ctas) {
-      float best_ms = 1e30f;
-      for (int rep = 0; rep < 2; ++rep) {
-        SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
-        SRS_CK(cudaEventRecord(ctx->ev2, ctx->stream), "event");
-        SRS_CK(launch_mixed(false, pl.w, s32, ctx->items.as<Item>(), (int)n_items, ctx->betas.as<double>(),
-                            ctx->queue.as<int>(), a, ctx->partial.as<float>(), nullptr, ctx->errflag.as<int>(),
-                            ctx->n_sm, ct, ctx->stream), "k_mixed (tuning)");
-        SRS_CK(cudaEventRecord(ctx->ev3, ctx->stream), "event");
-        SRS_CK(cudaEventSynchronize(ctx->ev3), "tuning");
-        best_ms = std::min(best_ms, elapsed_ms(ctx->ev2, ctx->ev3));
+  for (int threads : {256, 128}) {
+    if (threads == 128 && !pl.allow_128) continue;
+    if (only_threads && threads != only_threads) continue;
+    set_cta(pl, threads);
+    for (int gx : {0, 1}) {
+      if (gx == 0 && !use_tma) continue;
+      if (only_gx >= 0 && gx != only_gx) continue;
+      for (int ch : {1, 2, 4, 8, 16}) {
+        make_items(pl, ch, false, 0, 0);
+        srs_status us = upload_items(ctx, pl);
+        if (us != SRS_OK) return us;
+        MixedArgs a = mixed_args(pl, ctx, 0, 0);
+        a.use_tma = gx ? 0 : 1;
+        const int n_items = (int)pl.items.size();
+        for (int ct : {0, threads == 256 ? 3 : 6}) {
+          float best_ms = 1e30f;
+          for (int rep = 0; rep < 2; ++rep) {
+            SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
+            SRS_CK(cudaEventRecord(ctx->ev2, ctx->stream), "event");
+            SRS_CK(launch_mixed(false, pl.w, s32, ctx->items.as<Item>(), n_items, ctx->betas.as<double>(),
+                                ctx->queue.as<int>(), a, ctx->partial.as<float>(), nullptr, ctx->errflag.as<int>(),
+                                ctx->n_sm, ct, ctx->stream), "k_mixed (tuning)");
+            SRS_CK(cudaEventRecord(ctx->ev3, ctx->stream), "event");
+            SRS_CK(cudaEventSynchronize(ctx->ev3), "tuning");
+            const float ms = elapsed_ms(ctx->ev2, ctx->ev3);
+            best_ms = std::min(best_ms, ms);
+            if (ms > 20.f) break;  // long launches: one timing is enough
+          }
+          if (best_ms < best) { best = best_ms; best_c = {ch, ct, threads, gx}; }
+        }
       }
-      if (best_ms < best) { best = best_ms; best_chunk = ch; best_ctas = ct; }
     }
   }
-  make_items(pl, best_chunk, false, 0, 0);
-  SRS_CK(ctx->items.ensure(pl.items.size() * sizeof(Item)), "alloc items");
-  SRS_CK(ctx->item_off.ensure(pl.item_off.size() * 4), "alloc item_off");
-  SRS_CK(cudaMemcpyAsync(ctx->items.p, pl.items.data(), pl.items.size() * sizeof(Item), cudaMemcpyHostToDevice, ctx->stream), "copy items");
-  SRS_CK(cudaMemcpyAsync(ctx->item_off.p, pl.item_off.data(), pl.item_off.size() * 4, cudaMemcpyHostToDevice, ctx->stream), "copy item_off");
+  set_cta(pl, best_c.threads);
+  pl.global_x = best_c.global_x != 0;
+  make_items(pl, best_c.chunk, false, 0, 0);
+  { srs_status us = upload_items(ctx, pl); if (us != SRS_OK) return us; }
   SRS_CK(cudaStreamSynchronize(ctx->stream), "tuning");
-  ctx->tuned.push_back({key, best_chunk, best_ctas, best});
-  *ctas_out = best_ctas;
+  ctx->tuned.push_back({key, best_c.chunk, best_c.ctas, best_c.threads, best_c.global_x, best});
+  *ctas_out = best_c.ctas;
   return SRS_OK;
 }
 
@@ -394,16 +425,19 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
     if (f64) SRS_CK(launch_to_f32(static_cast<const double*>(dstrain), ctx->strain32.as<float>(),
                                   (int64_t)max_seg * pl.n_s, ctx->n_sm, ctx->stream), "k_to_f32 (before tuning)");
     int ct = 0;
-    const int chunk_before = pl.chunk;
     s = autotune_mixed(ctx, pl, s32, use_tma, &ct);
     if (s != SRS_OK) return s;
     ctx->ctas_per_sm = ct;
-    if (pl.chunk != chunk_before) {
-      n_items = (long long)pl.items.size();
-      SRS_CK(ctx->partial.ensure(n_items * pl.n_bins * 4), "alloc partial");
-    }
+    n_items = (long long)pl.items.size();
+    SRS_CK(ctx->partial.ensure(n_items * pl.n_bins * 4), "alloc partial");
+    if (pl.global_x) use_tma = 0;
   } else {
     ctx->ctas_per_sm = 0;
+    if (mixed && (pl.threads != kSpreadThreads || pl.global_x)) {
+      // an explicit chunk runs the default layout: 256 threads, TMA staging where possible
+      set_cta(pl, kSpreadThreads);
+      pl.global_x = false;
+    }
   }
   // The device part of a search: one stream-ordered sequence, replayed from a
   // CUDA graph when the plan and the buffers are the same as last time.
@@ -459,6 +493,8 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
                           (const void*)ctx->S.p})
     gkey.insert(gkey.end(), (const unsigned char*)&ptr, (const unsigned char*)&ptr + sizeof ptr);
   gkey.push_back((unsigned char)ctx->ctas_per_sm);
+  gkey.push_back((unsigned char)(pl.threads >> 4));
+  gkey.push_back((unsigned char)use_tma);
   SRS_CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
   bool ran = false;
   if (ctx->use_graphs) {
@@ -518,6 +554,8 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
     report->sigma = pl.sigma;
     report->beta_es = pl.beta_es;
     report->chunk = mixed ? pl.chunk : 1;
+    report->cta_threads = mixed ? pl.threads : 256;
+    report->staging = (mixed && use_tma) ? 1 : 0;
     report->n_items = mixed ? (int32_t)n_items : (int32_t)pl.n_spectra;
     report->kernel_launches = launches;
     report->spread_ms = elapsed_ms(ctx->ev2, ctx->ev3);
@@ -550,7 +588,7 @@ srs_status spectra_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int
     SRS_CK(ctx->F.ensure(fbytes), "alloc F");
     dF = ctx->F.as<double2>();
   }
-  int launches = 0;
+  int launches = 0, staged = 0;
   SRS_CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
   if (mixed) {
     const long long n_items = (long long)pl.items.size();
@@ -560,6 +598,7 @@ srs_status spectra_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int
     const float* s32 = nullptr;
     s = strain_f32(ctx, dstrain, dtype, (int64_t)seg_end * pl.n_s, pl.n_s, &s32, &a.use_tma);
     if (s != SRS_OK) return s;
+    staged = a.use_tma;
     if (f64) ++launches;
     SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
     SRS_CK(cudaMemsetAsync(ctx->errflag.p, 0, 64, ctx->stream), "memset error flag");
@@ -592,6 +631,8 @@ srs_status spectra_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int
     report->beta_es = pl.beta_es;
     report->chunk = pl.chunk;
     report->n_items = (int32_t)pl.items.size();
+    report->cta_threads = mixed ? pl.threads : 256;
+    report->staging = staged;
     report->kernel_launches = launches;
   }
   return SRS_OK;

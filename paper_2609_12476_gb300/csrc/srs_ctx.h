@@ -56,7 +56,7 @@ struct srs_ctx {
   // autotuned (segments per item, CTAs per SM) of the mixed spreader per shape
   struct Tuned {
     std::vector<unsigned char> key;
-    int chunk, ctas;
+    int chunk, ctas, threads, global_x;
     double ms;
   };
   std::vector<Tuned> tuned;

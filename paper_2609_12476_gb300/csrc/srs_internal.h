@@ -58,7 +58,10 @@ struct Plan {
   std::vector<int32_t> nseg;                             // per template
   int64_t n_spectra = 0;
   // mixed form work decomposition
+  int32_t threads = 256;                                 // threads per CTA of the mixed spreader
   int32_t run = 0, span = 0, n_anchor = 0;               // samples per thread / per warp / anchors per segment
+  bool allow_128 = false;                                // 128-thread CTAs keep the anchor expansion accurate
+  bool global_x = false;                                 // spreader reads samples from global memory (no TMA staging)
   int32_t chunk = 0;
   std::vector<Item> items;
   std::vector<int32_t> item_off;                         // [n_templates+1] first item of template m
@@ -75,6 +78,8 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
                      int64_t n_samples, bool need_segments_all, int32_t seg_begin,
                      int32_t seg_end, Plan& out, std::string& msg);
 void fill_info(const Plan& pl, srs_plan_info* info);
+// Threads per CTA of the mixed spreader and the run / span / anchor layout that follows.
+void set_cta(Plan& pl, int32_t threads);
 // Work items of the mixed form for a given chunk size (search: each template's
 // first nseg_m segments; spectra: [seg_begin, seg_end) of every template).
 void make_items(Plan& pl, int32_t chunk, bool spectra_mode, int32_t seg_begin, int32_t seg_end);

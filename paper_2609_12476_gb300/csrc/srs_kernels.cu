@@ -236,15 +236,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Tap inputs of one sample: first fine-grid cell l0 (wrapped into [0, n)),
-// the kernel argument of tap 0, and the demodulated sample c = x exp(-2 pi i th).
+// a0 = E (1 - z0) and b0 = E (1 + z0) for the kernel argument z0 of tap 0
+// (E = beta log2 e, so that tap t's exponent is sqrt((a0 - t H)(b0 + t H))
+// in base 2 with H = 2 E / W), and the demodulated sample
+// c = 2^-E x exp(-2 pi i th) (the 2^-E of the ES kernel folded in).
 struct TapIn {
   int l0;
-  float z0, cre, cim;
+  float a0, b0, cre, cim;
+};
+
+// Per-lane constants of the tap inputs.
+struct TapConst {
+  float es_scale;  // 2^-E
+  float eh32;      // E (2 / W) 2^-32: kernel argument per 2^-32 cell
+  float two_e;     // 2 E
 };
 
 template <bool INT_KC>
 __device__ __forceinline__ TapIn tap_inputs(const Anchor& A, const float* __restrict__ xs, int j, int l_base,
-                                            int W, const MixedArgs& a) {
+                                            int W, const TapConst& k, const MixedArgs& a) {
   uint32_t Psi;
   float sn, cs;
   if (INT_KC) {
@@ -258,15 +268,19 @@ __device__ __forceinline__ TapIn tap_inputs(const Anchor& A, const float* __rest
     __sincosf(6.28318530717958647692f * th, &sn, &cs);
   }
   const int n = a.n_fine;
-  const int cell = (int)__umulhi(Psi, (uint32_t)n);
-  const float fr = (float)(Psi * (uint32_t)n) * 2.3283064365386963e-10f;
-  const float xv = xs[j];
-  const float off = ceilf(fr - 0.5f * (float)W);
-  TapIn t;
-  int l0 = cell + (int)off;
+  // s = Psi n - W/2 cells in 32.32 fixed point; the first tap sits at cell
+  // l0 = ceil(s), and e = (l0 - s) 2^32 gives its kernel argument
+  // z0 = (e 2^-32 - W/2) (2/W)
+  const long long s = (long long)((unsigned long long)Psi * (uint32_t)n) - ((long long)W << 31);
+  const uint32_t e = 0u - (uint32_t)s;
+  int l0 = (int)(s >> 32) + (e != 0u ? 1 : 0);
   if (l0 < 0) l0 += n; else if (l0 >= n) l0 -= n;
+  const float ef = (float)e;
+  const float xv = xs[j] * k.es_scale;
+  TapIn t;
   t.l0 = l0;
-  t.z0 = fmaxf((off - fr) * a.two_over_w, -1.0f);
+  t.b0 = k.eh32 * ef;                  // E (1 + z0)
+  t.a0 = fmaf(-k.eh32, ef, k.two_e);   // E (1 - z0)
   t.cre = xv * cs;
   t.cim = -xv * sn;
   return t;
@@ -279,52 +293,67 @@ __device__ __forceinline__ TapIn tap_inputs(const Anchor& A, const float* __rest
 // shared-memory atomic), so the shift is warp-uniform.
 template <int W, bool INT_KC>
 __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2* __restrict__ grid,
-                                           const Anchor& A, int j_begin, int j_end, int l_base,
+                                           const Anchor A, int j_begin, int j_end, int l_base,
                                            const MixedArgs& a) {
-  float acc_re[W], acc_im[W];
+  float2 acc[W];
 #pragma unroll
-  for (int t = 0; t < W; ++t) { acc_re[t] = 0.f; acc_im[t] = 0.f; }
+  for (int t = 0; t < W; ++t) acc[t] = make_float2(0.f, 0.f);
   const int n = a.n_fine;
-  const float h = a.two_over_w;
-  const float esb = a.es_beta_log2e;
+  // ES kernel in base 2: phi(z) = 2^(E sqrt(1 - z^2) - E); with Z = E z,
+  // E sqrt(1 - z^2) = sqrt((E - Z)(E + Z)), and tap t has Z = Z0 + t H.
+  const float E = a.es_beta_log2e;
+  const float H = E * a.two_over_w;
+  TapConst kc;
+  kc.es_scale = exp2f(-E);
+  kc.eh32 = H * 2.3283064365386963e-10f;
+  kc.two_e = 2.0f * E;
+  const float2 HH = make_float2(H, H), mHH = make_float2(-H, -H);
   const unsigned mask = __activemask();
   int j = j_begin;
   bool live = j < j_end;
-  TapIn p = {0, 0.f, 0.f, 0.f};
-  if (live) p = tap_inputs<INT_KC>(A, xs, j, l_base, W, a);
+  TapIn p = {0, 0.f, 0.f, 0.f, 0.f};
+  if (live) p = tap_inputs<INT_KC>(A, xs, j, l_base, W, kc, a);
   int Bm = p.l0;  // fine-grid cell of acc[0]
   while (__any_sync(mask, live)) {
     while (live && p.l0 == Bm) {
+      const float2 cv = make_float2(p.cre, p.cim);
+      const float2 aa = make_float2(p.a0, p.a0), bb = make_float2(p.b0, p.b0);
+      // taps in pairs on the packed FP32x2 pipe; |.| guards a rounding just below zero at the footprint's edge
 #pragma unroll
-      for (int t = 0; t < W; ++t) {
-        const float z = fmaf((float)t, h, p.z0);
-        const float q = fmaf(-z, z, 1.0f);
-        const float ph = ex2_approx(fmaf(esb, sqrt_approx(q), -esb));
-        acc_re[t] = fmaf(ph, p.cre, acc_re[t]);
-        acc_im[t] = fmaf(ph, p.cim, acc_im[t]);
+      for (int t = 0; t + 1 < W; t += 2) {
+        const float2 tt = make_float2((float)t, (float)(t + 1));
+        const float2 q = __fmul2_rn(__ffma2_rn(tt, mHH, aa), __ffma2_rn(tt, HH, bb));
+        const float p0 = ex2_approx(sqrt_approx(fabsf(q.x)));
+        const float p1 = ex2_approx(sqrt_approx(fabsf(q.y)));
+        acc[t] = __ffma2_rn(make_float2(p0, p0), cv, acc[t]);
+        acc[t + 1] = __ffma2_rn(make_float2(p1, p1), cv, acc[t + 1]);
+      }
+      if (W & 1) {
+        const float tl = (float)(W - 1);
+        const float pl = ex2_approx(sqrt_approx(fabsf(fmaf(tl, -H, p.a0) * fmaf(tl, H, p.b0))));
+        acc[W - 1] = __ffma2_rn(make_float2(pl, pl), cv, acc[W - 1]);
       }
       ++j;
       live = j < j_end;
-      if (live) p = tap_inputs<INT_KC>(A, xs, j, l_base, W, a);
+      if (live) p = tap_inputs<INT_KC>(A, xs, j, l_base, W, kc, a);
     }
     // cell Bm is complete for this lane
-    if (acc_re[0] != 0.f || acc_im[0] != 0.f) {
-      atomicAdd(&grid[Bm].x, acc_re[0]);
-      atomicAdd(&grid[Bm].y, acc_im[0]);
+    if (acc[0].x != 0.f || acc[0].y != 0.f) {
+      atomicAdd(&grid[Bm].x, acc[0].x);
+      atomicAdd(&grid[Bm].y, acc[0].y);
     }
 #pragma unroll
-    for (int t = 0; t < W - 1; ++t) { acc_re[t] = acc_re[t + 1]; acc_im[t] = acc_im[t + 1]; }
-    acc_re[W - 1] = 0.f;
-    acc_im[W - 1] = 0.f;
+    for (int t = 0; t < W - 1; ++t) acc[t] = acc[t + 1];
+    acc[W - 1] = make_float2(0.f, 0.f);
     Bm = (Bm + 1 == n) ? 0 : Bm + 1;
   }
 #pragma unroll
   for (int t = 0; t < W - 1; ++t) {
     int c = Bm + t;
     if (c >= n) c -= n;
-    if (acc_re[t] != 0.f || acc_im[t] != 0.f) {
-      atomicAdd(&grid[c].x, acc_re[t]);
-      atomicAdd(&grid[c].y, acc_im[t]);
+    if (acc[t].x != 0.f || acc[t].y != 0.f) {
+      atomicAdd(&grid[c].x, acc[t].x);
+      atomicAdd(&grid[c].y, acc[t].y);
     }
   }
 }
@@ -334,14 +363,16 @@ __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2*
 // shared memory by a TMA bulk copy (the next segment's copy overlaps this
 // segment's FFT), spread, FFT, deconvolve, then either write F (SPECTRA) or
 // add (P - 2) / 2 into the item's running sum Z.
-template <int W, bool SPECTRA, bool INT_KC>
+template <int W, bool SPECTRA, bool INT_KC, bool GLOBAL_X>
 __global__ void __launch_bounds__(kSpreadThreads, 4)
 k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_items,
         const double* __restrict__ betas, int* __restrict__ queue, MixedArgs a,
         float* __restrict__ partial, double2* __restrict__ Fout, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
-  float* xs = reinterpret_cast<float*>(smem);                       // [ns4]
-  float2* g0 = reinterpret_cast<float2*>(xs + a.ns4);               // [n_fine]
+  // GLOBAL_X: samples are read straight from the (L2-resident) strain;
+  // otherwise a TMA bulk copy stages each segment in shared memory
+  float* xs = reinterpret_cast<float*>(smem);                       // [ns4] unless GLOBAL_X
+  float2* g0 = reinterpret_cast<float2*>(xs + (GLOBAL_X ? 0 : a.ns4));  // [n_fine]
   float2* g1 = g0 + a.n_fine;                                       // [n_fine]
   float* Z = reinterpret_cast<float*>(g1 + a.n_fine);               // [nb4]
   Anchor* anc = reinterpret_cast<Anchor*>(Z + a.nb4);               // [chunk * n_anchor]
@@ -362,7 +393,7 @@ k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_
     const int q = s_item;
     if (q >= n_items) break;
     const Item it = items[q];
-    if (tid == 0 && a.use_tma) bulk_load(xs, strain + (long long)it.i0 * a.n_s, seg_bytes, &s_bar);
+    if (!GLOBAL_X && tid == 0) bulk_load(xs, strain + (long long)it.i0 * a.n_s, seg_bytes, &s_bar);
     {
       const int na = (it.i1 - it.i0) * a.n_anchor;
       const double b = betas[it.m];
@@ -373,16 +404,13 @@ k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_
       for (int b = tid; b < a.n_bins; b += blockDim.x) Z[b] = 0.f;
     for (int i = it.i0; i < it.i1; ++i) {
       for (int j = tid; j < a.n_fine; j += blockDim.x) g0[j] = make_float2(0.f, 0.f);
-      if (a.use_tma) {
+      if (!GLOBAL_X) {
         if (tid == 0 && !mbar_wait(&s_bar, parity)) {
           // record where the wait gave up: flag, item, segment, parity, block
           s_abort = 1;
           if (atomicExch(err, 1) == 0) { err[1] = q; err[2] = i; err[3] = (int)parity; err[4] = blockIdx.x; }
         }
         parity ^= 1u;
-      } else {
-        const float* src = strain + (long long)i * a.n_s;
-        for (int j = tid; j < a.n_s; j += blockDim.x) xs[j] = src[j];
       }
       __syncthreads();
       if (s_abort) {
@@ -394,10 +422,11 @@ k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_
       {
         const int j0 = (warp * 32 + lane) * a.run;
         const int j1 = min(j0 + a.run, a.n_s);
-        if (j0 < a.n_s) spread_run<W, INT_KC>(xs, g0, anc[(i - it.i0) * a.n_anchor + warp], j0, j1, warp * a.span, a);
+        const float* xsrc = GLOBAL_X ? strain + (long long)i * a.n_s : xs;
+        if (j0 < a.n_s) spread_run<W, INT_KC>(xsrc, g0, anc[(i - it.i0) * a.n_anchor + warp], j0, j1, warp * a.span, a);
       }
       __syncthreads();
-      if (tid == 0 && a.use_tma && i + 1 < it.i1) bulk_load(xs, strain + (long long)(i + 1) * a.n_s, seg_bytes, &s_bar);
+      if (!GLOBAL_X && tid == 0 && i + 1 < it.i1) bulk_load(xs, strain + (long long)(i + 1) * a.n_s, seg_bytes, &s_bar);
       float2* res = a.fft_fixed == 1200 ? fft_1200<float2>(g0, g1, tw)
                                         : fft_smem<float2>(g0, g1, a.n_fine, s_rad, a.n_pass, tw);
       for (int b = tid; b < a.n_bins; b += blockDim.x) {
@@ -630,7 +659,7 @@ __global__ void k_time_map_plain(const int* __restrict__ item_m, const int* __re
 // Launchers
 // ---------------------------------------------------------------------------
 size_t mixed_smem_bytes(const MixedArgs& a) {
-  size_t s = (size_t)a.ns4 * sizeof(float);
+  size_t s = a.use_tma ? (size_t)a.ns4 * sizeof(float) : 0;
   s += (size_t)a.n_fine * 2 * sizeof(float2);
   s += (size_t)a.nb4 * sizeof(float);
   s += (size_t)a.chunk * a.n_anchor * sizeof(Anchor);
@@ -658,18 +687,20 @@ static cudaError_t launch_mixed_t(const float* strain, const Item* items, int n_
                                   int* queue, const MixedArgs& a, float* partial, double2* Fout, int* err, int n_sm,
                                   int ctas_per_sm, cudaStream_t st) {
   const size_t smem = mixed_smem_bytes(a);
-  auto kern = a.kc_int > 0 ? k_mixed<W, SP, true> : k_mixed<W, SP, false>;
+  auto kern = a.kc_int > 0 ? (a.use_tma ? k_mixed<W, SP, true, false> : k_mixed<W, SP, true, true>)
+                           : (a.use_tma ? k_mixed<W, SP, false, false> : k_mixed<W, SP, false, true>);
+  const int threads = a.threads > 0 ? a.threads : kSpreadThreads;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kSpreadThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
   long long grid = (long long)n_sm * occ;
   if (grid > n_items) grid = n_items;
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, kSpreadThreads, smem, st>>>(strain, items, n_items, betas, queue, a, partial, Fout, err);
+  kern<<<(unsigned)grid, threads, smem, st>>>(strain, items, n_items, betas, queue, a, partial, Fout, err);
   return cudaGetLastError();
 }
 

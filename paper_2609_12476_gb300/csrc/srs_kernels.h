@@ -21,7 +21,9 @@ struct MixedArgs {
   int run, span, n_anchor, n_pass;
   int ns4, nb4;                   // n_s, n_bins rounded up to multiples of 4 (shared-memory layout)
   int chunk;                      // most segments in one item
-  int use_tma;                    // 1: samples staged by TMA bulk copies (n_s % 4 == 0, 16-byte aligned strain)
+  int use_tma;                    // 1: samples staged by TMA bulk copies (n_s % 4 == 0, 16-byte aligned strain);
+                                  // 0: samples read straight from the strain in global memory
+  int threads;                    // threads per CTA (128 or 256); run, span and n_anchor follow it
   int fft_fixed;                  // 1200: the compile-time 4-4-3-5-5 plan applies; 0: generic passes
   int seg_begin, seg_range;       // spectra output: first segment, segments per template
   AnchorArgs aa;                  // FP64 anchor inputs

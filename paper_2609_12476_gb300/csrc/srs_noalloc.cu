@@ -161,6 +161,7 @@ srs_status run(void* stream_v, const void* strain, int64_t n_samples, int32_t dt
   a.run = pl.run;
   a.span = pl.span;
   a.n_anchor = pl.n_anchor;
+  a.threads = pl.threads;
   a.n_pass = (int)pl.radices.size();
   a.ns4 = (int)((pl.n_s + 3) & ~3LL);
   a.nb4 = (pl.n_bins + 3) & ~3;

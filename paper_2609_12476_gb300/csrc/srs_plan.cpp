@@ -220,14 +220,24 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
   pl.radices = radix_plan(pl.n_fine);
 
   // Mixed form: run of samples per thread, one FP64 anchor per warp span.
-  pl.run = (int32_t)((pl.n_s + kSpreadThreads - 1) / kSpreadThreads);
-  pl.span = 32 * pl.run;
-  pl.n_anchor = (int32_t)((pl.n_s + pl.span - 1) / pl.span);
+  set_cta(pl, kSpreadThreads);
   if (p.precision == SRS_MIXED) {
     // Local degree-5 expansion over one span must be accurate to 1e-9 cycles at
     // the band edge: bound the first omitted term, coef_6 beta^5 A^(-43/8) / 6!
     // (d^6 delta / ds^6 / 6!), at the smallest A = 1 - 8/3 beta t of any segment.
+    // Checked for 256-thread CTAs (required) and 128-thread CTAs (twice the span; allowed if it holds).
     double fmax = std::max(std::fabs(p.f_lo), std::fabs(p.f_hi));
+    const double ds_half = 32.0 * (double)((pl.n_s + 127) / 128) / p.fs;
+    pl.allow_128 = true;
+    for (int32_t m = 0; m < n_templates; ++m) {
+      int32_t last_seg = spectra_mode ? seg_end : pl.nseg[m];
+      double A = 1.0 - 8.0 / 3.0 * pl.beta[m] * (((double)last_seg * pl.n_s) / p.fs);
+      A = std::max(A, 1e-300);
+      double b = pl.beta[m];
+      double e6 = 2438.3333333333333 * std::pow(b, 5) * std::pow(A, -43.0 / 8.0) / 720.0;
+      double e2 = 0.5 * b * std::pow(A, -11.0 / 8.0);
+      if (e6 * std::pow(ds_half, 6) * fmax > 1e-9 || e2 * ds_half * ds_half / p.t_coh > 0.25) pl.allow_128 = false;
+    }
     double ds = pl.span / p.fs;
     for (int32_t m = 0; m < n_templates; ++m) {
       int32_t last_seg = spectra_mode ? seg_end : pl.nseg[m];
@@ -294,6 +304,13 @@ void make_items(Plan& pl, int32_t chunk, bool spectra_mode, int32_t seg_begin, i
     }
   }
   pl.item_off[pl.n_templates] = (int32_t)pl.items.size();
+}
+
+void set_cta(Plan& pl, int32_t threads) {
+  pl.threads = threads;
+  pl.run = (int32_t)((pl.n_s + threads - 1) / threads);
+  pl.span = 32 * pl.run;
+  pl.n_anchor = (int32_t)((pl.n_s + pl.span - 1) / pl.span);
 }
 
 void fill_info(const Plan& pl, srs_plan_info* info) {

@@ -178,6 +178,8 @@ def noise_maps(ctx, coarse_mc, params, t_obs, n_maps, seed):
 
 
 NMS = (4, 16)        # suppression half-window: the patch's half-size (templates, bins)
+NO_NMS = (0, 0)      # default: every cell above threshold is proposed (suppression costs recall
+                     # when injections crowd a map: a loud ridge hides its neighbours' peaks)
 
 
 def peaks(values, nms):
@@ -191,7 +193,7 @@ def peaks(values, nms):
     return v >= mx
 
 
-def calibrate(ctx, mlp_params, coarse_mc, params, t_obs, n_maps, seed, far, nms=NMS):
+def calibrate(ctx, mlp_params, coarse_mc, params, t_obs, n_maps, seed, far, nms=NO_NMS):
     """Thresholds that propose a fraction `far` of the cells of pure-noise coarse
     maps after non-maximum suppression: one on the network's score, one on the
     coarse n_sigma (the proposal without a network)."""
@@ -217,7 +219,7 @@ def detection_threshold(nseg, p_fa):
 
 
 def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t_obs, n_real, per_real, seed,
-             p_fa=1e-6, amp_range=(0.01, 0.1), nms=NMS, fine_rows=1):
+             p_fa=1e-6, amp_range=(0.01, 0.1), nms=NO_NMS, fine_rows=1):
     """Recall of injections over the same realisations in four searches:
       full            every fine template (the judge)
       proposal        the network's proposal at its noise-calibrated threshold

@@ -270,3 +270,38 @@ def test_graph_replay_and_interleaved_calls(ctx, two_hours):
     assert (c2["template_idx"][0], c2["bin"][0]) == (c0["template_idx"][0], c0["bin"][0])
     # autotuned chunk stays fixed for this shape
     assert r2["chunk"] == r0["chunk"]
+
+
+@pytest.mark.parametrize("layout", ["256:tma", "256:global", "128:tma", "128:global"])
+def test_every_spreader_layout_against_oracle(monkeypatch, layout):
+    """Each CTA size / sample-staging layout the tuner may pick gives the same
+    map as the FP64 oracle within the spectrum-error bound."""
+    monkeypatch.setenv("SRS_MIXED_LAYOUT", layout)
+    # lighter templates than _search_case, so that the degree-5 anchor expansion
+    # also holds over the 128-thread layout's doubled warp span
+    fs, T, nseg_tot = 256.0, 30.0, 40
+    mc = srs_synth.log_templates(2e-2, 5e-2, 6)
+    b3 = srs_synth.chirp_beta(mc[3], 40.0)
+    inj = [{"mc": srs_synth.mc_for_beta(b3, 44.0), "f0": 44.0, "amp": 0.05}]
+    x = srs_synth.strain_with_chirps(nseg_tot * 7680, fs, 23, inj)
+    eps = 1e-6
+    c = Context(0)
+    try:
+        cands, smap, rep = c.search(x.astype(np.float32), mc, Params(precision=SRS_MIXED, eps=eps, top_k=8))
+    finally:
+        c.close()
+    threads, staging = layout.split(":")
+    assert rep["cta_threads"] == int(threads)
+    assert rep["staging"] == (1 if staging == "tma" else 0)
+    betas = [oracle.beta(m, 40.0) for m in mc]
+    nsegs = [oracle.nseg(b, 40.0, 60.0, 30.0, 40) for b in betas]
+    items = [(m, i) for m in range(len(mc)) for i in range(nsegs[m])]
+    F = oracle.spectra(x.astype(np.float32).astype(np.float64), 256.0, 30.0, 40.0, 600, betas, items)
+    P = oracle.power(F, 7680)
+    S = np.zeros((len(mc), 600))
+    for k, (m, _i) in enumerate(items):
+        S[m] += P[k]
+    ns = oracle.n_sigma(S, nsegs)
+    tol = _map_tolerance(P, items, nsegs, eps, 7680, ns.shape) + 1e-5 * np.abs(ns) + 1e-6
+    assert np.all(np.abs(smap - ns) <= tol), np.max(np.abs(smap - ns) / tol)
+    assert (int(cands[0]["template_idx"]), int(cands[0]["bin"])) == (3, 120)
