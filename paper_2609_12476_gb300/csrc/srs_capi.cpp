@@ -317,7 +317,7 @@ srs_status autotune_mixed(srs_ctx* ctx, Plan& pl, const float* s32, int use_tma,
         const int n_items = (int)pl.items.size();
         for (int ct : {0, threads == 256 ? 3 : 6}) {
           float best_ms = 1e30f;
-          for (int rep = 0; rep < 2; ++rep) {
+          for (int rep = 0; rep < 3; ++rep) {
             SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
             SRS_CK(cudaEventRecord(ctx->ev2, ctx->stream), "event");
             SRS_CK(launch_mixed(false, pl.w, s32, ctx->items.as<Item>(), n_items, ctx->betas.as<double>(),

@@ -80,6 +80,8 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
 void fill_info(const Plan& pl, srs_plan_info* info);
 // Threads per CTA of the mixed spreader and the run / span / anchor layout that follows.
 void set_cta(Plan& pl, int32_t threads);
+// Samples per thread of the mixed spreader for CTAs of `threads` threads (odd).
+int32_t run_for(int64_t n_s, int32_t threads);
 // Work items of the mixed form for a given chunk size (search: each template's
 // first nseg_m segments; spectra: [seg_begin, seg_end) of every template).
 void make_items(Plan& pl, int32_t chunk, bool spectra_mode, int32_t seg_begin, int32_t seg_end);

@@ -227,7 +227,7 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
     // (d^6 delta / ds^6 / 6!), at the smallest A = 1 - 8/3 beta t of any segment.
     // Checked for 256-thread CTAs (required) and 128-thread CTAs (twice the span; allowed if it holds).
     double fmax = std::max(std::fabs(p.f_lo), std::fabs(p.f_hi));
-    const double ds_half = 32.0 * (double)((pl.n_s + 127) / 128) / p.fs;
+    const double ds_half = 32.0 * (double)run_for(pl.n_s, 128) / p.fs;
     pl.allow_128 = true;
     for (int32_t m = 0; m < n_templates; ++m) {
       int32_t last_seg = spectra_mode ? seg_end : pl.nseg[m];
@@ -306,9 +306,16 @@ void make_items(Plan& pl, int32_t chunk, bool spectra_mode, int32_t seg_begin, i
   pl.item_off[pl.n_templates] = (int32_t)pl.items.size();
 }
 
+int32_t run_for(int64_t n_s, int32_t threads) {
+  // samples per thread, odd: lane l reads xs[l run + m], so an odd run puts
+  // the 32 lanes of a warp on 32 different shared-memory banks
+  int32_t run = (int32_t)((n_s + threads - 1) / threads);
+  return run | 1;
+}
+
 void set_cta(Plan& pl, int32_t threads) {
   pl.threads = threads;
-  pl.run = (int32_t)((pl.n_s + threads - 1) / threads);
+  pl.run = run_for(pl.n_s, threads);
   pl.span = 32 * pl.run;
   pl.n_anchor = (int32_t)((pl.n_s + pl.span - 1) / pl.span);
 }
