@@ -288,7 +288,8 @@ def run_ours(args):
                 "config": {"workload": args.workload, "templates": int(len(w["mc"])), "spectra_per_step": n_spec,
                            "strain": "%d samples %s at %g Hz" % (w["n_samples"], w["dtype"], w["fs"]),
                            "eps": w["eps"], "w": info["w"], "n_fine": info["n_fine"], "chunk": rep["chunk"],
-                           "cta_threads": rep["cta_threads"], "staging": "tma" if rep["staging"] else "global loads",
+                           "cta_threads": rep["cta_threads"], "ctas_per_sm": rep["ctas_per_sm"],
+                           "staging": "tma" if rep["staging"] else "global loads",
                            "precision": "mixed: FP64 time-map anchors, FP32 spread/FFT/power",
                            "l2": "flushed (256 MB write) before every timed step"},
                 "roofline": roof, "roofline_hbm": roof_hbm, "clocks": ck, "gpu_launches": launches,

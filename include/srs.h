@@ -142,6 +142,7 @@ typedef struct {
   double spread_ms;       /* device time of the transform kernel alone (k_mixed / k_plain) */
   int32_t cta_threads;    /* threads per CTA of the transform kernel */
   int32_t staging;        /* mixed form: 1 = samples staged by TMA bulk copies, 0 = read from global memory */
+  int32_t ctas_per_sm;    /* mixed form: resident CTAs per SM the search asked for (0 = as many as fit) */
 } srs_report;
 
 /* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t

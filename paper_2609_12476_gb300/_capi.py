@@ -58,7 +58,7 @@ class _Report(ctypes.Structure):
                 ("n_spectra", ctypes.c_int64), ("w", ctypes.c_int32), ("n_fine", ctypes.c_int32),
                 ("sigma", ctypes.c_double), ("beta_es", ctypes.c_double), ("chunk", ctypes.c_int32),
                 ("n_items", ctypes.c_int32), ("kernel_launches", ctypes.c_int32), ("spread_ms", ctypes.c_double),
-                ("cta_threads", ctypes.c_int32), ("staging", ctypes.c_int32)]
+                ("cta_threads", ctypes.c_int32), ("staging", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
 
 
 class _Injection(ctypes.Structure):

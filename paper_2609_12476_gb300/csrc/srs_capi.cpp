@@ -243,10 +243,12 @@ namespace {
 // Autotuner of the mixed spreader: segments per work item, threads per CTA
 // (256, or 128 where the anchor expansion stays accurate over the longer warp
 // span), TMA staging or direct global reads of the samples, and resident CTAs
-// per SM, timed with CUDA events on the whole search's spreader launch for
-// searches of up to kTuneMaxSpectra spectra; the choice is kept per shape
-// (segment length, band, fine grid, kernel width, templates, spectra).
-constexpr long long kTuneMaxSpectra = 2000000;
+// per SM.  Each candidate runs the spreader over the items of the first
+// templates (at most kTuneSpectra spectra; all of a smaller search), timed
+// with CUDA events, and is scored by spectra per second; the choice is kept
+// per shape (segment length, band, fine grid, kernel width, templates,
+// spectra).  Large searches skip the small chunks and the smallest CTA caps.
+constexpr long long kTuneSpectra = 150000;
 
 srs_status upload_items(srs_ctx* ctx, Plan& pl) {
   SRS_CK(ctx->items.ensure(pl.items.size() * sizeof(Item)), "alloc items");
@@ -293,14 +295,14 @@ srs_status autotune_mixed(srs_ctx* ctx, Plan& pl, const float* s32, int use_tma,
       *ctas_out = t.ctas;
       return SRS_OK;
     }
-  if (pl.n_spectra > kTuneMaxSpectra) {
-    ctx->tuned.push_back({key, pl.chunk, 0, pl.threads, 0, 0.0});
-    *ctas_out = 0;
-    return SRS_OK;
-  }
+  // templates [0, n_tune) carry at least kTuneSpectra spectra (or all of them)
+  int32_t n_tune = 0;
+  long long tune_spectra = 0;
+  while (n_tune < pl.n_templates && tune_spectra < kTuneSpectra) tune_spectra += pl.nseg[n_tune++];
+  const bool large = pl.n_spectra > kTuneSpectra;
   struct Choice { int chunk, ctas, threads, global_x; };
   Choice best_c{pl.chunk, 0, kSpreadThreads, 0};
-  double best = 1e30;
+  double best = 1e30;  // ms per spectrum
   for (int threads : {256, 128}) {
     if (threads == 128 && !pl.allow_128) continue;
     if (only_threads && threads != only_threads) continue;
@@ -309,13 +311,18 @@ srs_status autotune_mixed(srs_ctx* ctx, Plan& pl, const float* s32, int use_tma,
       if (gx == 0 && !use_tma) continue;
       if (only_gx >= 0 && gx != only_gx) continue;
       for (int ch : {1, 2, 4, 8, 16}) {
+        if (large && ch < 4) continue;
         make_items(pl, ch, false, 0, 0);
         srs_status us = upload_items(ctx, pl);
         if (us != SRS_OK) return us;
         MixedArgs a = mixed_args(pl, ctx, 0, 0);
         a.use_tma = gx ? 0 : 1;
-        const int n_items = (int)pl.items.size();
-        for (int ct : {0, threads == 256 ? 3 : 6}) {
+        const int n_items = pl.item_off[n_tune];
+        const int cands_256[] = {0, 3, 2}, cands_128[] = {0, 7, 6, 5, 4};
+        const int* ctl = threads == 256 ? cands_256 : cands_128;
+        const int n_ct = large ? (threads == 256 ? 2 : 3) : (threads == 256 ? 3 : 5);
+        for (int ci = 0; ci < n_ct; ++ci) {
+          const int ct = ctl[ci];
           float best_ms = 1e30f;
           for (int rep = 0; rep < 3; ++rep) {
             SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
@@ -329,7 +336,8 @@ srs_status autotune_mixed(srs_ctx* ctx, Plan& pl, const float* s32, int use_tma,
             best_ms = std::min(best_ms, ms);
             if (ms > 20.f) break;  // long launches: one timing is enough
           }
-          if (best_ms < best) { best = best_ms; best_c = {ch, ct, threads, gx}; }
+          const double per = best_ms / (double)tune_spectra;
+          if (per < best) { best = per; best_c = {ch, ct, threads, gx}; }
         }
       }
     }
@@ -556,6 +564,7 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
     report->chunk = mixed ? pl.chunk : 1;
     report->cta_threads = mixed ? pl.threads : 256;
     report->staging = (mixed && use_tma) ? 1 : 0;
+    report->ctas_per_sm = mixed ? ctx->ctas_per_sm : 0;
     report->n_items = mixed ? (int32_t)n_items : (int32_t)pl.n_spectra;
     report->kernel_launches = launches;
     report->spread_ms = elapsed_ms(ctx->ev2, ctx->ev3);

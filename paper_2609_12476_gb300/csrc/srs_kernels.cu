@@ -696,12 +696,30 @@ static cudaError_t launch_mixed_t(const float* strain, const Item* items, int n_
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
-  if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
+  // With fewer resident CTAs than shared memory allows, hand the rest of the
+  // SM's 256 KB to L1 (global-load sample reads live there); a launch
+  // attribute, so that a captured graph keeps it.
+  cudaLaunchAttribute attr[1];
+  int n_attr = 0;
+  if (ctas_per_sm > 0 && ctas_per_sm < occ) {
+    occ = ctas_per_sm;
+    const size_t need = (size_t)occ * (smem + 1024);
+    unsigned carveout = (unsigned)((100 * need + 228 * 1024 - 1) / (228 * 1024));
+    attr[0].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
+    attr[0].val.sharedMemCarveout = carveout > 100 ? 100u : carveout;
+    n_attr = 1;
+  }
   long long grid = (long long)n_sm * occ;
   if (grid > n_items) grid = n_items;
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, threads, smem, st>>>(strain, items, n_items, betas, queue, a, partial, Fout, err);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = n_attr ? attr : nullptr;
+  cfg.numAttrs = (unsigned)n_attr;
+  return cudaLaunchKernelEx(&cfg, kern, strain, items, n_items, betas, queue, a, partial, Fout, err);
 }
 
 cudaError_t launch_mixed(bool spectra, int w, const float* strain, const Item* items, int n_items,
