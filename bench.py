@@ -41,7 +41,7 @@ UNIT = "spectra/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="semicoherent_2h", choices=sorted(srs_synth.WORKLOADS) + ["learned_6h"])
@@ -82,7 +82,7 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -159,7 +159,7 @@ def run_reference(args):
         return
     w = workload(args.workload, 0)
     steps, warm = args.steps, args.warmup
-    budget = min(20.0, max(2.0, 150.0 / max(1, steps + warm)))
+    budget = min(20.0, max(0.2, 150.0 / max(1, steps + warm)))
     for _ in range(warm):
         cpu_oracle_rate(w, budget_s=budget * 0.25)
     vals, secs = [], []
@@ -255,23 +255,23 @@ def run_ours(args):
         pk = peaks()
         n_s, n_fine, w_taps = int(info["n_s"]), int(info["n_fine"]), int(info["w"])
         spread_avg = float(np.mean(spread_ms))
-        # k_mixed's algorithmic FP32 operations per spectrum (the ES-spread
-        # type-1 NUFFT): per sample w taps x (z, 1-z^2, sqrt, scale, exp, and a
-        # complex-by-real multiply-add = 4) + demodulation (sin, cos, 2 mul)
-        # + grid position (2); FFT 5 n log2 n; deconvolution + power 8 per bin
-        flops = n_spec * (n_s * (9 * w_taps + 6) + 5 * n_fine * np.log2(n_fine) + 8 * n_bins)
-        achieved_tf = flops / (spread_avg * 1e-3) / 1e12
         sm_mhz = (ck or {}).get("sm_mhz") or (pk or {}).get("sm_max_mhz", 2070.0)
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak_tf = 2.0 * 128 * n_sm * sm_mhz * 1e6 / 1e12      # FP32 FMA lanes x 2 x SMs x clock
         traffic = profile_traffic("k_mixed_semicoherent_2h.md") if args.workload == "semicoherent_2h" else None
-        roof = {"kernel": "k_mixed", "bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": achieved_tf / peak_tf, "traffic": traffic,
-                "peak_source": "128 FP32 lanes x %d SMs x 2 flop x %.0f MHz (median SM clock in the timed region)"
-                               % (n_sm, sm_mhz)}
+        roof = xu_roofline(n_spec, n_s, w_taps, spread_avg, n_sm, sm_mhz, traffic)
+        # FP32-FMA view: the NUFFT's algorithmic FP32 operations per spectrum
+        # against the FMA pipes (per sample w taps x 9 + 6; FFT 5 n log2 n;
+        # deconvolution + power 8 per bin)
+        flops = n_spec * (n_s * (9 * w_taps + 6) + 5 * n_fine * np.log2(n_fine) + 8 * n_bins)
+        achieved_tf = flops / (spread_avg * 1e-3) / 1e12
+        peak_tf = 2.0 * 128 * n_sm * sm_mhz * 1e6 / 1e12      # FP32 FMA lanes x 2 x SMs x clock
+        roof_fma = {"kernel": "k_mixed", "bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                    "frac": achieved_tf / peak_tf, "traffic": traffic,
+                    "peak_source": "128 FP32 lanes x %d SMs x 2 flop x %.0f MHz (median SM clock in the timed region)"
+                                   % (n_sm, sm_mhz)}
         # the HBM view the metric asks for: FP32 samples the kernel reads per
         # spectrum (the working copy) + partial sums it writes
-        alg_bytes = n_spec * n_s * 4 + int(info["n_items"]) * n_bins * 4
+        alg_bytes = n_spec * n_s * 4 + int(rep["n_items"]) * n_bins * 4
         ach = alg_bytes / (spread_avg * 1e-3) / 1e9
         hbm_peak = pk["hbm_gbs"] if pk else 6800.0
         roof_hbm = {"kernel": "k_mixed", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
@@ -292,12 +292,36 @@ def run_ours(args):
                            "staging": "tma" if rep["staging"] else "global loads",
                            "precision": "mixed: FP64 time-map anchors, FP32 spread/FFT/power",
                            "l2": "flushed (256 MB write) before every timed step"},
-                "roofline": roof, "roofline_hbm": roof_hbm, "clocks": ck, "gpu_launches": launches,
+                "roofline": roof, "roofline_fma": roof_fma, "roofline_hbm": roof_hbm, "clocks": ck,
+                "gpu_launches": launches,
                 "e2e": e2e, "cpu_baseline": cpu, "plain_fp64": plain,
                 "spread_ms_avg": spread_avg}
         print(json.dumps(line), flush=True)
     barrier(world)
     ctx.close()
+
+
+# Special-function (XU) unit: sqrt.approx, sin.approx and cos.approx issue at
+# 16 per clock per SM on GB300 and ex2.approx at 32, so an ex2 costs half a
+# slot (measured by tests/test_gpu_unit_rates.py with tests/probes/xu_rates.cu).
+XU_SLOTS_PER_CLK_SM = 16
+XU_EX2_SLOT = 0.5
+
+
+def xu_roofline(n_spec, n_s, w_taps, kernel_ms, n_sm, sm_mhz, traffic):
+    """k_mixed against its binding unit: per sample the ES spreader needs w
+    square roots and w base-2 exponentials (one tap each) and one sine and one
+    cosine (the demodulation), i.e. w (1 + XU_EX2_SLOT) + 2 XU slots; the peak
+    is XU_SLOTS_PER_CLK_SM x SMs x the median SM clock of the timed region."""
+    slots = n_spec * n_s * (w_taps * (1 + XU_EX2_SLOT) + 2)
+    achieved = slots / (kernel_ms * 1e-3) / 1e12
+    peak = XU_SLOTS_PER_CLK_SM * n_sm * sm_mhz * 1e6 / 1e12
+    return {"kernel": "k_mixed", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tslot/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_source": "special-function unit: %d slots/clk/SM (sqrt, sin, cos 1 slot; ex2 %.1f) x %d SMs x "
+                           "%.0f MHz (median SM clock in the timed region)"
+                           % (XU_SLOTS_PER_CLK_SM, XU_EX2_SLOT, n_sm, sm_mhz),
+            "slots_per_sample": w_taps * (1 + XU_EX2_SLOT) + 2}
 
 
 def profile_traffic(name):
@@ -386,25 +410,27 @@ def run_learned(args):
     mlp, losses, _, n_tr = proposal.train_proposal(ctx, coarse, p, t_obs, n_patches=20000, seed=1)
     sth, nth = proposal.calibrate(ctx, mlp, coarse, p, t_obs, 10, seed=5, far=1e-3)
     train_s = time.time() - t0
-    rng = np.random.default_rng(123)
     n = int(round(t_obs * p.fs))
-    strains = []
-    for k in range(args.steps + args.warmup):
-        inj, _ = proposal.injections_on_grid(rng, coarse, p, 8, (0.01, 0.1))
-        strains.append(ctx.make_strain(n, p.fs, 50000 + k, inj, f_hi=p.f_hi))
+
+    def strain_for(k):
+        # a new realisation per step, made on the device outside the timed events
+        inj, _ = proposal.injections_on_grid(np.random.default_rng(123 + k), coarse, p, 8, (0.01, 0.1))
+        return ctx.make_strain(n, p.fs, 50000 + k, inj, f_hi=p.f_hi)
+
     torch.cuda.synchronize()
     info, _, _ = __import__("paper_2609_12476_gb300").srs_plan(p, fine, n)
     full_spec = int(info["n_spectra"])
     for k in range(args.warmup):
-        ctx.search_proposed(strains[k], coarse, fine, p, mlp, sth)
+        ctx.search_proposed(strain_for(k), coarse, fine, p, mlp, sth)
     torch.cuda.synchronize()
     clocks = Clocks(0)
     ev = []
     reps = []
     for k in range(args.warmup, args.warmup + args.steps):
+        x = strain_for(k)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        r = ctx.search_proposed(strains[k], coarse, fine, p, mlp, sth)
+        r = ctx.search_proposed(x, coarse, fine, p, mlp, sth)
         b.record(stream)
         ev.append((a, b))
         reps.append(r["report"])
@@ -416,9 +442,10 @@ def run_learned(args):
     cands = torch.empty((p.top_k, 3), dtype=torch.int32, device="cuda")
     full_ms = 0.0
     for k in range(args.warmup, args.warmup + args.steps):
+        x = strain_for(k)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        ctx.search(strains[k], fine, p, out={"map": fmap, "cands": cands})
+        ctx.search(x, fine, p, out={"map": fmap, "cands": cands})
         b.record(stream)
         torch.cuda.synchronize()
         full_ms += a.elapsed_time(b)

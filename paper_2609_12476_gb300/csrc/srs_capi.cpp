@@ -273,9 +273,10 @@ srs_status autotune_mixed(srs_ctx* ctx, Plan& pl, const float* s32, int use_tma,
   put(&pl.n_spectra, sizeof pl.n_spectra);
   key.push_back((unsigned char)use_tma);
   key.push_back((unsigned char)pl.allow_128);
-  // SRS_MIXED_LAYOUT=<threads>:<tma|global> restricts the search to one layout
-  // (used to check every layout against the same reference).
-  int only_threads = 0, only_gx = -1;
+  // SRS_MIXED_LAYOUT=<threads>:<tma|global>[:<chunk>:<ctas>] restricts the
+  // search to one layout (used to check every layout against the same
+  // reference, and to profile one fixed configuration).
+  int only_threads = 0, only_gx = -1, only_chunk = 0, only_ctas = -1;
   if (const char* lay = std::getenv("SRS_MIXED_LAYOUT")) {
     const std::string l(lay);
     key.insert(key.end(), l.begin(), l.end());
@@ -283,6 +284,12 @@ srs_status autotune_mixed(srs_ctx* ctx, Plan& pl, const float* s32, int use_tma,
     if (l.rfind("256", 0) == 0) only_threads = 256;
     if (l.find(":global") != std::string::npos) only_gx = 1;
     if (l.find(":tma") != std::string::npos) only_gx = 0;
+    int t = 0, c = 0, k = -1;
+    char st[16] = {0};
+    if (std::sscanf(lay, "%d:%15[a-z]:%d:%d", &t, st, &c, &k) == 4 && c >= 1 && c <= 16 && k >= 0) {
+      only_chunk = c;
+      only_ctas = k;
+    }
   }
   for (const auto& t : ctx->tuned)
     if (t.key == key) {
@@ -311,7 +318,8 @@ srs_status autotune_mixed(srs_ctx* ctx, Plan& pl, const float* s32, int use_tma,
       if (gx == 0 && !use_tma) continue;
       if (only_gx >= 0 && gx != only_gx) continue;
       for (int ch : {1, 2, 4, 8, 16}) {
-        if (large && ch < 4) continue;
+        if (large && ch < 4 && only_chunk == 0) continue;
+        if (only_chunk && ch != only_chunk) continue;
         make_items(pl, ch, false, 0, 0);
         srs_status us = upload_items(ctx, pl);
         if (us != SRS_OK) return us;
@@ -321,8 +329,8 @@ srs_status autotune_mixed(srs_ctx* ctx, Plan& pl, const float* s32, int use_tma,
         const int cands_256[] = {0, 3, 2}, cands_128[] = {0, 7, 6, 5, 4};
         const int* ctl = threads == 256 ? cands_256 : cands_128;
         const int n_ct = large ? (threads == 256 ? 2 : 3) : (threads == 256 ? 3 : 5);
-        for (int ci = 0; ci < n_ct; ++ci) {
-          const int ct = ctl[ci];
+        for (int ci = 0; ci < (only_ctas >= 0 ? 1 : n_ct); ++ci) {
+          const int ct = only_ctas >= 0 ? only_ctas : ctl[ci];
           float best_ms = 1e30f;
           for (int rep = 0; rep < 3; ++rep) {
             SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");

@@ -96,3 +96,18 @@ def test_plan_items_cover_every_segment_once():
         info, _, nseg = srs_plan(Params(chunk=chunk), mc, 720 * 7680)
         assert info["chunk"] == chunk
         assert info["n_items"] == sum((int(n) + chunk - 1) // chunk for n in nseg)
+
+
+def test_xu_roofline_arithmetic():
+    """bench.py's XU model: w sqrt + w ex2 (half a slot) + sin + cos per sample."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "bench", os.path.join(os.path.dirname(os.path.abspath(__file__)), "..", "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    r = bench.xu_roofline(n_spec=1000, n_s=7680, w_taps=7, kernel_ms=1.0, n_sm=152, sm_mhz=2000.0, traffic=None)
+    assert r["slots_per_sample"] == 12.5
+    assert abs(r["achieved"] - 1000 * 7680 * 12.5 / 1e-3 / 1e12) < 1e-12
+    assert abs(r["peak"] - 16 * 152 * 2000e6 / 1e12) < 1e-12
+    assert r["bound"] == "alu" and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-15
