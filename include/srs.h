@@ -178,6 +178,26 @@ srs_status srs_search(srs_ctx* ctx, const void* strain, int64_t n_samples, int32
                       float* stat_map, srs_candidate* cands, int32_t* n_cands,
                       srs_report* report);
 
+/* Stream-ordered form of srs_search for device-resident data (params->io_on_device
+ * must be 1; strain, stat_map and cands are device pointers).  Enqueues the
+ * same device sequence on the context's stream and returns without waiting;
+ * *n_cands is set at once.  Outputs are valid, and a device-side failure (a
+ * staging wait that gave up) is reported, only after srs_sync; keep the
+ * buffers alive until then.  Calls may be queued back to back; a new shape's
+ * first call still plans and tunes synchronously.  Errors found on the host
+ * (arguments, planning) return at once. */
+srs_status srs_search_async(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype,
+                            const double* mc, int32_t n_templates, const srs_params* params,
+                            float* stat_map, srs_candidate* cands, int32_t* n_cands);
+
+/* Wait for the context's stream and settle every srs_search_async since the
+ * last srs_sync: SRS_ERR_TIMEOUT if any of them failed on the device.  With
+ * report != NULL: the last call's sizes, and device_ms / spread_ms averaged
+ * over the settled calls (CUDA events around each call's sequence and its
+ * transform kernel).  More than 256 unsettled calls settle the oldest 256
+ * internally; a failure among them is returned here. */
+srs_status srs_sync(srs_ctx* ctx, srs_report* report);
+
 /* Segment spectra F_b for templates [0, n_templates) and segments
  * [seg_begin, seg_end) (Sec. III.B), through the same time map, spreader,
  * FFT and deconvolution as srs_search.

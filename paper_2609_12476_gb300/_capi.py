@@ -21,7 +21,7 @@ SRS_F32, SRS_F64 = 0, 1
 SRS_PLAIN_FP64, SRS_MIXED = 0, 1
 
 # Entry points declared in include/srs.h (checked by the tests).
-EXPORTS = ("srs_create", "srs_destroy", "srs_last_error", "srs_plan", "srs_search",
+EXPORTS = ("srs_create", "srs_destroy", "srs_last_error", "srs_plan", "srs_search", "srs_search_async", "srs_sync",
            "srs_segment_spectra", "srs_time_map", "srs_segment_spectra_static", "srs_make_strain",
            "srs_patches", "srs_mlp_forward", "srs_mlp_grad", "srs_mlp_train", "srs_score_map", "srs_refine",
            "srs_search_proposed")
@@ -131,6 +131,11 @@ def lib():
         L.srs_search.restype = i32
         L.srs_search.argtypes = [vp, vp, i64, i32, vp, i32, ctypes.POINTER(_Params), vp, vp,
                                  ctypes.POINTER(i32), ctypes.POINTER(_Report)]
+        L.srs_search_async.restype = i32
+        L.srs_search_async.argtypes = [vp, vp, i64, i32, vp, i32, ctypes.POINTER(_Params), vp, vp,
+                                       ctypes.POINTER(i32)]
+        L.srs_sync.restype = i32
+        L.srs_sync.argtypes = [vp, ctypes.POINTER(_Report)]
         L.srs_segment_spectra.restype = i32
         L.srs_segment_spectra.argtypes = [vp, vp, i64, i32, vp, i32, i32, i32, ctypes.POINTER(_Params), vp,
                                           ctypes.POINTER(_Report)]
@@ -260,6 +265,31 @@ class Context:
                                   ctypes.byref(n_cands), ctypes.byref(rep))
         self._check(st)
         return c[:n_cands.value], m, _report_dict(rep)
+
+    def search_async(self, strain, mc, params, out):
+        """srs_search_async: enqueue a search over a torch CUDA strain into the
+        device tensors of `out` ({"map": float32 [templates, n_bins] or None,
+        "cands": int32 [top_k, 3]}) and return at once; results and device
+        status become final at sync()."""
+        if not _is_torch_cuda(strain):
+            raise ValueError("search_async needs a torch CUDA strain")
+        mc = np.ascontiguousarray(mc, dtype=np.float64)
+        p = params.c()
+        p.io_on_device = 1
+        n_cands = ctypes.c_int32(0)
+        mp = out["map"].data_ptr() if out.get("map") is not None else None
+        st = self._lib.srs_search_async(self._h, strain.data_ptr(), strain.numel(), _dtype_code(strain),
+                                        mc.ctypes.data, mc.size, ctypes.byref(p), mp, out["cands"].data_ptr(),
+                                        ctypes.byref(n_cands))
+        self._check(st)
+        return int(n_cands.value)
+
+    def sync(self):
+        """srs_sync: wait for the queued asynchronous searches; their averaged
+        timing and the last one's sizes as a report dict."""
+        rep = _Report()
+        self._check(self._lib.srs_sync(self._h, ctypes.byref(rep)))
+        return _report_dict(rep)
 
     def segment_spectra(self, strain, mc, seg_begin, seg_end, params):
         """srs_segment_spectra: complex128 [templates, seg_end - seg_begin, n_bins]

@@ -180,6 +180,45 @@ std::vector<unsigned char> make_key(int kind, const srs_params* p, int64_t n_sam
 
 // Plan for this call, reusing the context's last plan (and its device tables)
 // when the call kind, sizes, parameters and templates are the same.
+// Pinned error-flag copies: slot 0 for synchronous calls, one slot of eight
+// ints per asynchronous call since the last srs_sync.
+constexpr size_t kHostFlagBytes = (size_t)8 * (1 + srs_ctx::kAsyncSlots) * sizeof(int);
+
+// Drop the captured search graph (an in-flight launch finishes on its own).
+void destroy_graph(srs_ctx* ctx) {
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  ctx->graph_exec = nullptr;
+  ctx->graph = nullptr;
+  ctx->graph_ev_node[0] = ctx->graph_ev_node[1] = nullptr;
+  ctx->graph_key.clear();
+}
+
+// The captured graph's event-record nodes for the context's transform-kernel
+// events (ev2, ev3), so that each launch can point them at its own events.
+void find_event_nodes(srs_ctx* ctx) {
+  ctx->graph_ev_node[0] = ctx->graph_ev_node[1] = nullptr;
+  size_t n = 0;
+  if (cudaGraphGetNodes(ctx->graph, nullptr, &n) != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return;
+  }
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(ctx->graph, nodes.data(), &n) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeEventRecord) continue;
+    cudaEvent_t ev = nullptr;
+    if (cudaGraphEventRecordNodeGetEvent(nd, &ev) != cudaSuccess) continue;
+    if (ev == ctx->ev2) ctx->graph_ev_node[0] = nd;
+    if (ev == ctx->ev3) ctx->graph_ev_node[1] = nd;
+  }
+  cudaGetLastError();
+}
+
 srs_status get_plan(srs_ctx* ctx, int kind, const srs_params* params, const double* mc, int32_t n_templates,
                     int64_t n_samples, int32_t dtype, bool spectra_mode, int32_t a, int32_t b, const Plan** out) {
   srs_params key_p = *params;
@@ -191,11 +230,7 @@ srs_status get_plan(srs_ctx* ctx, int kind, const srs_params* params, const doub
   }
   ctx->have_plan = false;
   // a new plan means new tables: a captured graph may point at the old ones
-  if (ctx->graph_exec) {
-    cudaGraphExecDestroy(ctx->graph_exec);
-    ctx->graph_exec = nullptr;
-    ctx->graph_key.clear();
-  }
+  destroy_graph(ctx);
   std::string msg;
   srs_status s = make_plan(*params, mc, n_templates, n_samples, spectra_mode, a, b, ctx->plan, msg);
   if (s != SRS_OK) return set_err(ctx, s, msg);
@@ -376,10 +411,32 @@ srs_status check_err_flag(srs_ctx* ctx) {
 
 srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype, const double* mc,
                             int32_t n_templates, const srs_params* params, float* stat_map, srs_candidate* cands,
-                            int32_t* n_cands, srs_report* report) {
+                            int32_t* n_cands, srs_report* report, bool async_mode) {
   srs_status s = check_common(ctx, strain, dtype, params);
   if (s != SRS_OK) return s;
   if (!cands || !n_cands) return set_err(ctx, SRS_ERR_ARG, "cands and n_cands are required");
+  if (async_mode && params->io_on_device != 1)
+    return set_err(ctx, SRS_ERR_ARG, "srs_search_async needs device buffers (params.io_on_device = 1)");
+  // events of this call: the context's own, or the next asynchronous slot
+  int slot = -1;
+  cudaEvent_t e0 = ctx->ev0, e1 = ctx->ev1, e2 = ctx->ev2, e3 = ctx->ev3;
+  if (async_mode) {
+    if (ctx->async_n == srs_ctx::kAsyncSlots) {
+      // every slot is in use: settle them (a failure is kept for the next srs_sync)
+      const srs_status ss = sync_impl(ctx, nullptr);
+      if (ss != SRS_OK && ctx->async_status == SRS_OK) {
+        ctx->async_status = ss;
+        ctx->async_err = ctx->err;
+      }
+    }
+    slot = ctx->async_n;
+    for (int q = 0; q < 4; ++q)
+      if (!ctx->aev[slot][q]) SRS_CK(cudaEventCreate(&ctx->aev[slot][q]), "event");
+    e0 = ctx->aev[slot][0];
+    e1 = ctx->aev[slot][1];
+    e2 = ctx->aev[slot][2];
+    e3 = ctx->aev[slot][3];
+  }
   const Plan* plp = nullptr;
   s = get_plan(ctx, 1, params, mc, n_templates, n_samples, dtype, false, 0, 0, &plp);
   if (s != SRS_OK) return s;
@@ -457,6 +514,9 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
   }
   // The device part of a search: one stream-ordered sequence, replayed from a
   // CUDA graph when the plan and the buffers are the same as last time.
+  // events around the transform kernel inside the sequence (a captured graph
+  // holds the context's own pair and is re-pointed per launch)
+  cudaEvent_t k_ev2 = e2, k_ev3 = e3;
   auto enqueue = [&]() -> srs_status {
     launches = 0;
     if (mixed) {
@@ -469,11 +529,11 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
       }
       SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
       SRS_CK(cudaMemsetAsync(ctx->errflag.p, 0, 64, ctx->stream), "memset error flag");
-      SRS_CK(cudaEventRecordWithFlags(ctx->ev2, ctx->stream, cudaEventRecordExternal), "event");
+      SRS_CK(cudaEventRecordWithFlags(k_ev2, ctx->stream, cudaEventRecordExternal), "event");
       SRS_CK(launch_mixed(false, pl.w, s32, ctx->items.as<Item>(), (int)n_items, ctx->betas.as<double>(),
                           ctx->queue.as<int>(), a, ctx->partial.as<float>(), nullptr, ctx->errflag.as<int>(),
                           ctx->n_sm, ctx->ctas_per_sm, ctx->stream), "k_mixed");
-      SRS_CK(cudaEventRecordWithFlags(ctx->ev3, ctx->stream, cudaEventRecordExternal), "event");
+      SRS_CK(cudaEventRecordWithFlags(k_ev3, ctx->stream, cudaEventRecordExternal), "event");
       ++launches;
       SRS_CK(launch_reduce_mixed(ctx->partial.as<float>(), ctx->item_off.as<int>(), ctx->nseg.as<int>(), n_templates,
                                  pl.n_bins, dmap, ctx->keys.as<unsigned long long>(), ctx->n_sm, ctx->stream),
@@ -482,10 +542,10 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
     } else {
       PlainArgs p = plain_args(pl, ctx, 0, 0);
       SRS_CK(cudaMemsetAsync(ctx->S.p, 0, n_map * 8, ctx->stream), "memset S");
-      SRS_CK(cudaEventRecordWithFlags(ctx->ev2, ctx->stream, cudaEventRecordExternal), "event");
+      SRS_CK(cudaEventRecordWithFlags(k_ev2, ctx->stream, cudaEventRecordExternal), "event");
       SRS_CK(launch_plain(f64, false, dstrain, ctx->betas.as<double>(), ctx->nseg.as<int>(), p, max_seg, n_templates,
                           ctx->S.as<double>(), nullptr, ctx->stream), "k_plain");
-      SRS_CK(cudaEventRecordWithFlags(ctx->ev3, ctx->stream, cudaEventRecordExternal), "event");
+      SRS_CK(cudaEventRecordWithFlags(k_ev3, ctx->stream, cudaEventRecordExternal), "event");
       ++launches;
       SRS_CK(launch_finish_plain(ctx->S.as<double>(), ctx->nseg.as<int>(), n_templates, pl.n_bins, dmap,
                                  ctx->keys.as<unsigned long long>(), ctx->n_sm, ctx->stream), "k_finish_plain");
@@ -511,12 +571,14 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
   gkey.push_back((unsigned char)ctx->ctas_per_sm);
   gkey.push_back((unsigned char)(pl.threads >> 4));
   gkey.push_back((unsigned char)use_tma);
-  SRS_CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
+  SRS_CK(cudaEventRecord(e0, ctx->stream), "event");
   bool ran = false;
   if (ctx->use_graphs) {
     if (!(ctx->graph_exec && gkey == ctx->graph_key)) {
-      if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
+      destroy_graph(ctx);
       cudaGraph_t g = nullptr;
+      k_ev2 = ctx->ev2;
+      k_ev3 = ctx->ev3;
       const cudaError_t be = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed);
       if (be == cudaSuccess) {
         const srs_status es = enqueue();
@@ -526,6 +588,9 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
         if (ie == cudaSuccess) {
           ctx->graph_key = gkey;
           ctx->graph_launches = launches;
+          ctx->graph = g;
+          g = nullptr;
+          find_event_nodes(ctx);
         } else {
           std::fprintf(stderr, "srs: graph capture not used (enqueue %d: %s; end %s; instantiate %s)\n", (int)es,
                        ctx->err.c_str(), cudaGetErrorString(ce), cudaGetErrorString(ie));
@@ -536,6 +601,17 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
         std::fprintf(stderr, "srs: begin capture failed: %s\n", cudaGetErrorString(be));
       }
       cudaGetLastError();
+      k_ev2 = e2;
+      k_ev3 = e3;
+    }
+    if (ctx->graph_exec) {
+      if (ctx->graph_ev_node[0] && ctx->graph_ev_node[1]) {
+        SRS_CK(cudaGraphExecEventRecordNodeSetEvent(ctx->graph_exec, ctx->graph_ev_node[0], e2), "graph event");
+        SRS_CK(cudaGraphExecEventRecordNodeSetEvent(ctx->graph_exec, ctx->graph_ev_node[1], e3), "graph event");
+      } else if (async_mode) {
+        // no re-pointable timing nodes: time this call's transform kernel without the graph
+        destroy_graph(ctx);
+      }
     }
     if (ctx->graph_exec) {
       SRS_CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream), "graph launch");
@@ -547,7 +623,28 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
     s = enqueue();
     if (s != SRS_OK) return s;
   }
-  SRS_CK(cudaEventRecord(ctx->ev1, ctx->stream), "event");
+  SRS_CK(cudaEventRecord(e1, ctx->stream), "event");
+  if (async_mode) {
+    if (mixed)
+      SRS_CK(cudaMemcpyAsync(ctx->hflag + 8 * (1 + slot), ctx->errflag.p, 5 * sizeof(int), cudaMemcpyDeviceToHost,
+                             ctx->stream), "read error flag");
+    ctx->async_n = slot + 1;
+    srs_report& r = ctx->async_rep;
+    std::memset(&r, 0, sizeof r);
+    r.n_spectra = pl.n_spectra;
+    r.w = pl.w;
+    r.n_fine = pl.n_fine;
+    r.sigma = pl.sigma;
+    r.beta_es = pl.beta_es;
+    r.chunk = mixed ? pl.chunk : 1;
+    r.n_items = mixed ? (int32_t)n_items : (int32_t)pl.n_spectra;
+    r.kernel_launches = launches;
+    r.cta_threads = mixed ? pl.threads : 256;
+    r.staging = (mixed && use_tma) ? 1 : 0;
+    r.ctas_per_sm = mixed ? ctx->ctas_per_sm : 0;
+    *n_cands = k;
+    return SRS_OK;
+  }
   if (!on_dev) {
     SRS_CK(cudaMemcpyAsync(cands, dc, (size_t)k * sizeof(srs_candidate), cudaMemcpyDeviceToHost, ctx->stream), "copy cands");
     if (stat_map) SRS_CK(cudaMemcpyAsync(stat_map, dmap, n_map * 4, cudaMemcpyDeviceToHost, ctx->stream), "copy map");
@@ -561,7 +658,7 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
   }
   *n_cands = k;
   if (report) {
-    const float ms = elapsed_ms(ctx->ev0, ctx->ev1);
+    const float ms = elapsed_ms(e0, e1);
     report->device_ms = ms;
     report->n_spectra = pl.n_spectra;
     report->spectra_per_s = ms > 0 ? pl.n_spectra / (ms * 1e-3) : 0.0;
@@ -575,8 +672,43 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
     report->ctas_per_sm = mixed ? ctx->ctas_per_sm : 0;
     report->n_items = mixed ? (int32_t)n_items : (int32_t)pl.n_spectra;
     report->kernel_launches = launches;
-    report->spread_ms = elapsed_ms(ctx->ev2, ctx->ev3);
+    report->spread_ms = elapsed_ms(e2, e3);
   }
+  return SRS_OK;
+}
+
+srs_status srs::sync_impl(srs_ctx* ctx, srs_report* report) {
+  SRS_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  srs_status st = ctx->async_status;
+  std::string msg = ctx->async_err;
+  double dev = 0.0, spr = 0.0;
+  const int n = ctx->async_n;
+  for (int k = 0; k < n; ++k) {
+    int* f = ctx->hflag + 8 * (1 + k);
+    if (f[0] && st == SRS_OK) {
+      char b[220];
+      std::snprintf(b, sizeof b,
+                    "asynchronous search %d: a device wait gave up (TMA copy did not complete in time): item %d "
+                    "segment %d parity %d block %d", k, f[1], f[2], f[3], f[4]);
+      st = SRS_ERR_TIMEOUT;
+      msg = b;
+    }
+    f[0] = 0;
+    dev += elapsed_ms(ctx->aev[k][0], ctx->aev[k][1]);
+    spr += elapsed_ms(ctx->aev[k][2], ctx->aev[k][3]);
+  }
+  if (report) {
+    *report = ctx->async_rep;
+    if (n > 0) {
+      report->device_ms = dev / n;
+      report->spread_ms = spr / n;
+      report->spectra_per_s = report->device_ms > 0 ? report->n_spectra / (report->device_ms * 1e-3) : 0.0;
+    }
+  }
+  ctx->async_n = 0;
+  ctx->async_status = SRS_OK;
+  ctx->async_err.clear();
+  if (st != SRS_OK) return set_err(ctx, st, msg);
   return SRS_OK;
 }
 
@@ -744,12 +876,13 @@ srs_status srs_create(srs_ctx** out, int device, void* cuda_stream) {
   }
   if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
       cudaEventCreate(&c->ev2) != cudaSuccess || cudaEventCreate(&c->ev3) != cudaSuccess ||
-      cudaMallocHost(&c->hflag, 64) != cudaSuccess) {
+      cudaMallocHost(&c->hflag, kHostFlagBytes) != cudaSuccess) {
     cudaGetLastError();
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return SRS_ERR_CUDA;
   }
+  std::memset(c->hflag, 0, kHostFlagBytes);
   *out = c;
   return SRS_OK;
 }
@@ -758,7 +891,10 @@ void srs_destroy(srs_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
-  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  destroy_graph(c);
+  for (auto& slot : c->aev)
+    for (cudaEvent_t& e : slot)
+      if (e) cudaEventDestroy(e);
   if (c->hflag) cudaFreeHost(c->hflag);
   for (DevBuf* b : c->all_buffers()) b->release();
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -800,6 +936,28 @@ srs_status srs_search(srs_ctx* ctx, const void* strain, int64_t n_samples, int32
     return search_impl(ctx, strain, n_samples, dtype, mc, n_templates, params, stat_map, cands, n_cands, report);
   } catch (const std::bad_alloc&) {
     return set_err(ctx, SRS_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return set_err(ctx, SRS_ERR_ARG, "unexpected host error");
+  }
+}
+
+srs_status srs_search_async(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype, const double* mc,
+                            int32_t n_templates, const srs_params* params, float* stat_map, srs_candidate* cands,
+                            int32_t* n_cands) {
+  try {
+    return search_impl(ctx, strain, n_samples, dtype, mc, n_templates, params, stat_map, cands, n_cands, nullptr,
+                       true);
+  } catch (const std::bad_alloc&) {
+    return set_err(ctx, SRS_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return set_err(ctx, SRS_ERR_ARG, "unexpected host error");
+  }
+}
+
+srs_status srs_sync(srs_ctx* ctx, srs_report* report) {
+  if (!ctx) return SRS_ERR_ARG;
+  try {
+    return sync_impl(ctx, report);
   } catch (...) {
     return set_err(ctx, SRS_ERR_ARG, "unexpected host error");
   }

@@ -60,7 +60,19 @@ struct srs_ctx {
     double ms;
   };
   std::vector<Tuned> tuned;
-  int* hflag = nullptr;     // pinned copy of the device error flag
+  int* hflag = nullptr;     // pinned copies of the device error flag: [0] synchronous calls,
+                            // [8 (1 + k)] the k-th srs_search_async since the last srs_sync
+  // stream-ordered searches (srs_search_async) since the last srs_sync: per call
+  // the events around the whole sequence (0, 1) and around the transform kernel (2, 3)
+  static constexpr int kAsyncSlots = 256;
+  cudaEvent_t aev[kAsyncSlots][4] = {};
+  int async_n = 0;
+  srs_status async_status = SRS_OK;   // a failure found when the slots ran out and were synced
+  std::string async_err;
+  srs_report async_rep = {};          // sizes of the last asynchronous call
+  // the captured graph (kept for its event-record nodes, re-pointed per launch)
+  cudaGraph_t graph = nullptr;
+  cudaGraphNode_t graph_ev_node[2] = {nullptr, nullptr};
   srs::DevBuf items, anchors, partial, betas, nseg, item_off, corr, tw, keys, topk_a, topk_b, cands, queue, strain,
       strain32, errflag, map, S, F, psi, th, im, ii;
   // learned proposal
@@ -101,7 +113,9 @@ inline float elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
 // Search entry used by the proposal pipeline (srs_capi.cpp).
 srs_status search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype, const double* mc,
                        int32_t n_templates, const srs_params* params, float* stat_map, srs_candidate* cands,
-                       int32_t* n_cands, srs_report* report);
+                       int32_t* n_cands, srs_report* report, bool async_mode = false);
+// Wait for the stream and settle every srs_search_async since the last sync.
+srs_status sync_impl(srs_ctx* ctx, srs_report* report);
 srs_status strain_f32(srs_ctx* ctx, const void* dstrain, int32_t dtype, int64_t samples, int64_t n_s,
                       const float** out, int* use_tma);
 bool tma_disabled();

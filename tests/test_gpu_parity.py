@@ -305,3 +305,35 @@ def test_every_spreader_layout_against_oracle(monkeypatch, layout):
     tol = _map_tolerance(P, items, nsegs, eps, 7680, ns.shape) + 1e-5 * np.abs(ns) + 1e-6
     assert np.all(np.abs(smap - ns) <= tol), np.max(np.abs(smap - ns) / tol)
     assert (int(cands[0]["template_idx"]), int(cands[0]["bin"])) == (3, 120)
+
+
+def test_async_searches_match_synchronous(ctx):
+    """srs_search_async queued back to back on different strains (and past the
+    256 event slots) equals srs_search on each, within the map tolerance of
+    run-to-run float summation order; srs_sync reports averaged timing."""
+    torch = pytest.importorskip("torch")
+    fs, nseg_tot = 256.0, 12
+    mc = srs_synth.log_templates(2e-2, 5e-2, 4)
+    p = Params(eps=1e-6, top_k=8)
+    xs = [torch.from_numpy(srs_synth.white_noise(nseg_tot * 7680, 100 + k)).cuda() for k in range(3)]
+    ref = [ctx.search(x, mc, p)[0]["map"].clone() for x in xs]
+    outs = [{"map": torch.empty_like(ref[0]), "cands": torch.empty((8, 3), dtype=torch.int32, device="cuda")}
+            for _ in xs]
+    for rep in range(2):
+        for x, o in zip(xs, outs):
+            assert ctx.search_async(x, mc, p, o) == 8
+    r = ctx.sync()
+    from paper_2609_12476_gb300 import srs_plan
+    info, _, _ = srs_plan(p, mc, nseg_tot * 7680)
+    assert r["device_ms"] > 0 and r["spread_ms"] > 0 and r["n_spectra"] == info["n_spectra"]
+    for a, b in zip(outs, ref):
+        assert torch.allclose(a["map"], b, rtol=1e-5, atol=1e-5)
+    # more calls than event slots: the oldest are settled inside, the rest at sync
+    for k in range(300):
+        ctx.search_async(xs[k % 3], mc, p, outs[k % 3])
+    ctx.sync()
+    for a, b in zip(outs, ref):
+        assert torch.allclose(a["map"], b, rtol=1e-5, atol=1e-5)
+    # host buffers are refused
+    with pytest.raises(ValueError):
+        ctx.search_async(xs[0].cpu().numpy(), mc, p, outs[0])
