@@ -316,11 +316,16 @@ typedef struct {
   int32_t nms_templates;   /* non-maximum suppression half-window in coarse templates (0: off) */
   int32_t nms_bins;        /* ... and in bins (0: off) */
   int32_t fine_rows;       /* fine templates of coarse rows within this many of the cell (0: its own) */
+  int32_t component_top;   /* > 0: of each 8-connected group of cells above the threshold, propose only
+                              the component_top cells with the highest coarse n_sigma (suppression off) */
+  int32_t nms_by_nsigma;   /* 1: the suppression window compares coarse n_sigma instead of scores */
 } srs_proposal_params;
 
 /* The proposal search: the coarse search over coarse_mc, network scores of
  * all its cells; a cell scoring above the threshold (and, with suppression
- * on, highest within its window) proposes the fine templates whose nearest
+ * on, highest within its window; with component_top > 0, among the
+ * component_top highest coarse n_sigma of its group of adjacent
+ * above-threshold cells) proposes the fine templates whose nearest
  * coarse template (in log Mc) is within fine_rows of it, at bins within one of
  * its bin; those fine cells are evaluated with srs_refine.  Outputs (host):
  * up to max_cells evaluated cells (cell_m, cell_b, cell_nsigma; *n_cells_out

@@ -895,6 +895,8 @@ void srs_destroy(srs_ctx* c) {
   for (auto& slot : c->aev)
     for (cudaEvent_t& e : slot)
       if (e) cudaEventDestroy(e);
+  for (cudaEvent_t& e : c->pev)
+    if (e) cudaEventDestroy(e);
   if (c->hflag) cudaFreeHost(c->hflag);
   for (DevBuf* b : c->all_buffers()) b->release();
   if (c->ev0) cudaEventDestroy(c->ev0);

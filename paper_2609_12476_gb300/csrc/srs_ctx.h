@@ -70,6 +70,8 @@ struct srs_ctx {
   srs_status async_status = SRS_OK;   // a failure found when the slots ran out and were synced
   std::string async_err;
   srs_report async_rep = {};          // sizes of the last asynchronous call
+  // events around a whole proposal search (it runs searches that use the others)
+  cudaEvent_t pev[2] = {nullptr, nullptr};
   // the captured graph (kept for its event-record nodes, re-pointed per launch)
   cudaGraph_t graph = nullptr;
   cudaGraphNode_t graph_ev_node[2] = {nullptr, nullptr};

@@ -533,7 +533,9 @@ srs_status srs_search_proposed(srs_ctx* ctx, const void* strain, int64_t n_sampl
     if (dtype != SRS_F32 && dtype != SRS_F64) return set_err(ctx, SRS_ERR_ARG, "dtype must be SRS_F32 or SRS_F64");
     const int n_bins = (int)std::llround((params->f_hi - params->f_lo) * params->t_coh);
     if (n_bins <= 0) return set_err(ctx, SRS_ERR_ARG, "search_proposed: empty band");
-    SRS_CK(cudaEventRecord(ctx->ev2, ctx->stream), "event");
+    for (cudaEvent_t& e : ctx->pev)
+      if (!e) SRS_CK(cudaEventCreate(&e), "event");
+    SRS_CK(cudaEventRecord(ctx->pev[0], ctx->stream), "event");
     // 1. strain on the device once, then the coarse search with a device map
     const void* dstrain = strain;
     srs_params pc = *params;
@@ -559,9 +561,49 @@ srs_status srs_search_proposed(srs_ctx* ctx, const void* strain, int64_t n_sampl
     SRS_CK(ctx->sp_out.ensure((size_t)ncells * 4), "alloc scores");
     s = score_map_impl(ctx, ctx->cmap.as<float>(), n_coarse, n_bins, ctx->sp_out.as<float>());
     if (s != SRS_OK) return s;
-    std::vector<float> scores(ncells);
+    std::vector<float> scores(ncells), cmap;
     SRS_CK(cudaMemcpyAsync(scores.data(), ctx->sp_out.p, (size_t)ncells * 4, cudaMemcpyDeviceToHost, ctx->stream), "copy scores");
+    if (params_prop.component_top > 0 || params_prop.nms_by_nsigma) {
+      cmap.resize(ncells);
+      SRS_CK(cudaMemcpyAsync(cmap.data(), ctx->cmap.p, (size_t)ncells * 4, cudaMemcpyDeviceToHost, ctx->stream),
+             "copy coarse map");
+    }
     SRS_CK(cudaStreamSynchronize(ctx->stream), "score");
+    // component rule: of each 8-connected group of above-threshold cells, the
+    // component_top cells of highest coarse n_sigma (ties: lower index first)
+    std::vector<unsigned char> keep;
+    if (params_prop.component_top > 0) {
+      keep.assign(ncells, 0);
+      std::vector<int32_t> comp_of(ncells, -1), stack, members;
+      for (long long c0 = 0; c0 < ncells; ++c0) {
+        if (!(scores[c0] > score_threshold) || comp_of[c0] >= 0) continue;
+        members.clear();
+        stack.assign(1, (int32_t)c0);
+        comp_of[c0] = (int32_t)c0;
+        while (!stack.empty()) {
+          const int32_t c = stack.back();
+          stack.pop_back();
+          members.push_back(c);
+          const int32_t cm = c / n_bins, cb = c % n_bins;
+          for (int32_t dm = -1; dm <= 1; ++dm)
+            for (int32_t db = -1; db <= 1; ++db) {
+              const int32_t m = cm + dm, b = cb + db;
+              if (m < 0 || m >= n_coarse || b < 0 || b >= n_bins) continue;
+              const int32_t o = m * n_bins + b;
+              if (comp_of[o] < 0 && scores[o] > score_threshold) {
+                comp_of[o] = (int32_t)c0;
+                stack.push_back(o);
+              }
+            }
+        }
+        const size_t top = std::min<size_t>(members.size(), (size_t)params_prop.component_top);
+        std::partial_sort(members.begin(), members.begin() + top, members.end(), [&](int32_t a, int32_t b) {
+          if (cmap[a] != cmap[b]) return cmap[a] > cmap[b];
+          return a < b;
+        });
+        for (size_t u = 0; u < top; ++u) keep[members[u]] = 1;
+      }
+    }
     // 3. proposed coarse cells -> fine cells (nearest coarse template in log Mc)
     std::vector<int32_t> parent(n_fine);
     {
@@ -593,15 +635,18 @@ srs_status srs_search_proposed(srs_ctx* ctx, const void* strain, int64_t n_sampl
     const int32_t rows = std::max(0, params_prop.fine_rows);
     for (long long cell = 0; cell < ncells; ++cell) {
       if (!(scores[cell] > score_threshold)) continue;
+      if (!keep.empty() && !keep[cell]) continue;
       const int32_t cm = (int32_t)(cell / n_bins), cb = (int32_t)(cell % n_bins);
-      if (rt > 0 || rb > 0) {
+      if (keep.empty() && (rt > 0 || rb > 0)) {
         // non-maximum suppression: keep a cell only if no cell within
-        // (+-rt templates, +-rb bins) scores higher (ties: the first in row-major order)
+        // (+-rt templates, +-rb bins) has a higher key -- the score, or the
+        // coarse n_sigma with nms_by_nsigma (ties: the first in row-major order)
+        const std::vector<float>& key = params_prop.nms_by_nsigma ? cmap : scores;
         bool peak = true;
         for (int32_t m = std::max(0, cm - rt); m <= std::min(n_coarse - 1, cm + rt) && peak; ++m)
           for (int32_t b = std::max(0, cb - rb); b <= std::min(n_bins - 1, cb + rb); ++b) {
             const long long o = (long long)m * n_bins + b;
-            if (scores[o] > scores[cell] || (scores[o] == scores[cell] && o < cell)) { peak = false; break; }
+            if (key[o] > key[cell] || (key[o] == key[cell] && o < cell)) { peak = false; break; }
           }
         if (!peak) continue;
       }
@@ -625,7 +670,7 @@ srs_status srs_search_proposed(srs_ctx* ctx, const void* strain, int64_t n_sampl
                       nullptr, &seg_bins, &templ);
       if (s != SRS_OK) return s;
     }
-    SRS_CK(cudaEventRecord(ctx->ev3, ctx->stream), "event");
+    SRS_CK(cudaEventRecord(ctx->pev[1], ctx->stream), "event");
     SRS_CK(cudaStreamSynchronize(ctx->stream), "search_proposed");
     for (int32_t k = 0; k < std::min(nf, max_cells); ++k) {
       cell_m[k] = fm[k];
@@ -649,7 +694,7 @@ srs_status srs_search_proposed(srs_ctx* ctx, const void* strain, int64_t n_sampl
     }
     *n_cands = k;
     if (report) {
-      const float ms = elapsed_ms(ctx->ev2, ctx->ev3);
+      const float ms = elapsed_ms(ctx->pev[0], ctx->pev[1]);
       report->device_ms = ms;
       report->coarse_spectra = rep.n_spectra;
       report->proposed_coarse = proposed;

@@ -193,18 +193,66 @@ def peaks(values, nms):
     return v >= mx
 
 
-def calibrate(ctx, mlp_params, coarse_mc, params, t_obs, n_maps, seed, far, nms=NO_NMS):
+def component_cells(score, threshold, nsigma, top):
+    """Mask of the cells the component rule proposes (the library's
+    srs_search_proposed with component_top = top): of each 8-connected group of
+    cells whose score exceeds the threshold, the `top` cells of highest coarse
+    n_sigma (ties: lower row-major index first)."""
+    from scipy.ndimage import label
+    score = np.asarray(score)
+    mask = score > threshold
+    lab, n = label(mask, structure=np.ones((3, 3), dtype=int))
+    keep = np.zeros(score.shape, dtype=bool)
+    if n == 0:
+        return keep
+    idx = np.flatnonzero(mask)
+    grp = lab.ravel()[idx]
+    ns = np.asarray(nsigma, dtype=np.float32).ravel()[idx]
+    order = np.lexsort((idx, -ns, grp))
+    g = grp[order]
+    start = np.r_[0, np.flatnonzero(np.diff(g)) + 1]
+    rank = np.arange(len(g)) - np.repeat(start, np.diff(np.r_[start, len(g)]))
+    keep.ravel()[idx[order[rank < top]]] = True
+    return keep
+
+
+def _threshold_for_count(maps, k, component_top):
+    """Score threshold whose component-rule proposals over `maps` ((score,
+    n_sigma) pairs) number about k: the first threshold, scanning scores
+    downwards by bisection, at which at least k cells are proposed."""
+    vals = np.sort(np.concatenate([s.ravel() for s, _ in maps]))[::-1]
+    count = lambda t: sum(int(component_cells(s, t, n, component_top).sum()) for s, n in maps)
+    lo, hi = 0, len(vals) - 1
+    while lo < hi:
+        mid = (lo + hi) // 2
+        if count(vals[mid]) >= k:
+            hi = mid
+        else:
+            lo = mid + 1
+    return float(vals[lo])
+
+
+def calibrate(ctx, mlp_params, coarse_mc, params, t_obs, n_maps, seed, far, nms=NO_NMS, component_top=0,
+              nms_by_nsigma=False):
     """Thresholds that propose a fraction `far` of the cells of pure-noise coarse
-    maps after non-maximum suppression: one on the network's score, one on the
-    coarse n_sigma (the proposal without a network)."""
-    sc_peaks, ns_peaks, total = [], [], 0
+    maps (after non-maximum suppression -- on the score, or on the coarse
+    n_sigma with nms_by_nsigma -- or under the component rule): one on the
+    network's score, one on the coarse n_sigma (the proposal without a
+    network)."""
+    sc_peaks, ns_peaks, total, maps = [], [], 0, []
     for smap in noise_maps(ctx, coarse_mc, params, t_obs, n_maps, seed):
         sc = ctx.score_map(smap, mlp_params).double().cpu().numpy()
         ns = smap.double().cpu().numpy()
         total += sc.size
-        sc_peaks.append(sc[peaks(sc, nms)])
-        ns_peaks.append(ns[peaks(ns, nms)])
+        if component_top > 0:
+            maps.append((sc.astype(np.float32), ns.astype(np.float32)))
+        else:
+            sc_peaks.append(sc[peaks(ns if nms_by_nsigma else sc, nms)])
+            ns_peaks.append(ns[peaks(ns, nms)])
     k = max(1, int(round(far * total)))
+    if component_top > 0:
+        return (_threshold_for_count(maps, k, component_top),
+                _threshold_for_count([(n, n) for _, n in maps], k, component_top))
     sp = np.sort(np.concatenate(sc_peaks))[::-1]
     npk = np.sort(np.concatenate(ns_peaks))[::-1]
     return float(sp[min(k, len(sp) - 1)]), float(npk[min(k, len(npk) - 1)])
@@ -219,7 +267,7 @@ def detection_threshold(nseg, p_fa):
 
 
 def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t_obs, n_real, per_real, seed,
-             p_fa=1e-6, amp_range=(0.01, 0.1), nms=NO_NMS, fine_rows=1):
+             p_fa=1e-6, amp_range=(0.01, 0.1), nms=NO_NMS, fine_rows=1, component_top=0, nms_by_nsigma=False):
     """Recall of injections over the same realisations in four searches:
       full            every fine template (the judge)
       proposal        the network's proposal at its noise-calibrated threshold
@@ -258,7 +306,8 @@ def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t
         found = {"full": {(m, b): float(fm[m, b]) for m, b in np.argwhere(fm > th_f[:, None])}}
         out["full_cells"] += fm.size
         # the network's proposal search
-        pr = ctx.search_proposed(x, coarse_mc, fine_mc, params, mlp_params, score_th, nms=nms, fine_rows=fine_rows)
+        pr = ctx.search_proposed(x, coarse_mc, fine_mc, params, mlp_params, score_th, nms=nms, fine_rows=fine_rows,
+                                 component_top=component_top, nms_by_nsigma=nms_by_nsigma)
         out["proposal_ms"] += pr["report"]["device_ms"]
         out["proposal_coarse_spectra"] += pr["report"]["coarse_spectra"]
         out["proposal_segment_bins"] += pr["report"]["fine_segment_bins"]
@@ -269,11 +318,19 @@ def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t
         cmap, _ = coarse_map(ctx, x, coarse_mc, params)
         cm = cmap.cpu().numpy()
         K = pr["report"]["proposed_coarse"]
-        pk = peaks(cm, nms)
-        cand = np.argwhere(pk)
-        order = np.argsort(-cm[pk])[:K]
-        for key, prop in (("nsigma_equal", cand[order]),
-                          ("nsigma_far", np.argwhere(pk & (cm > nsigma_th)))):
+        if component_top > 0:
+            # the same rule on the n_sigma map: K cells at the threshold that
+            # first proposes K, and the cells above the calibrated threshold
+            t_eq = _threshold_for_count([(cm, cm)], K, component_top) if K > 0 else np.inf
+            eq = np.argwhere(component_cells(cm, t_eq, cm, component_top))
+            eq = eq[np.argsort(-cm[eq[:, 0], eq[:, 1]], kind="stable")[:K]]
+            far_cells = np.argwhere(component_cells(cm, nsigma_th, cm, component_top))
+        else:
+            pk = peaks(cm, nms)
+            cand = np.argwhere(pk)
+            eq = cand[np.argsort(-cm[pk])[:K]]
+            far_cells = np.argwhere(pk & (cm > nsigma_th))
+        for key, prop in (("nsigma_equal", eq), ("nsigma_far", far_cells)):
             fc = fine_cells_of(prop, coarse_mc, fine_mc, n_bins, fine_rows)
             out[key + "_cells"] += len(fc)
             found[key] = {}

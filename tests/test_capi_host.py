@@ -111,3 +111,35 @@ def test_xu_roofline_arithmetic():
     assert abs(r["achieved"] - 1000 * 7680 * 12.5 / 1e-3 / 1e12) < 1e-12
     assert abs(r["peak"] - 16 * 152 * 2000e6 / 1e12) < 1e-12
     assert r["bound"] == "alu" and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-15
+
+
+def test_component_rule_against_breadth_first_search():
+    """proposal.component_cells vs a plain BFS over 8-neighbours on random masks."""
+    import numpy as np
+    from paper_2609_12476_gb300.proposal import component_cells
+    rng = np.random.default_rng(5)
+    for trial in range(20):
+        score = rng.random((17, 23))
+        ns = rng.standard_normal((17, 23)).astype(np.float32)
+        th, top = 0.7, int(rng.integers(1, 4))
+        mask = score > th
+        seen = np.zeros(mask.shape, bool)
+        expect = np.zeros(mask.shape, bool)
+        for i0, j0 in zip(*np.nonzero(mask)):
+            if seen[i0, j0]:
+                continue
+            comp, stack = [], [(i0, j0)]
+            seen[i0, j0] = True
+            while stack:
+                i, j = stack.pop()
+                comp.append((i, j))
+                for di in (-1, 0, 1):
+                    for dj in (-1, 0, 1):
+                        a, b = i + di, j + dj
+                        if 0 <= a < 17 and 0 <= b < 23 and mask[a, b] and not seen[a, b]:
+                            seen[a, b] = True
+                            stack.append((a, b))
+            comp.sort(key=lambda c: (-ns[c], c[0] * 23 + c[1]))
+            for c in comp[:top]:
+                expect[c] = True
+        assert (component_cells(score, th, ns, top) == expect).all(), trial

@@ -169,3 +169,25 @@ def test_proposal_suppression_keeps_local_maxima(ctx):
     parent = [proposal.nearest_template(coarse, m) for m in fine]
     max_children = max(parent.count(c) for c in range(len(coarse)))
     assert 0 < r["n_cells"] <= r["report"]["proposed_coarse"] * max_children * 3
+
+
+@pytest.mark.parametrize("top", [1, 3])
+def test_proposal_component_rule_matches_host_rule(ctx, top):
+    """component_top: the library proposes, per connected group of
+    above-threshold cells, the `top` cells of highest coarse n_sigma -- the
+    same cells as proposal.component_cells on the same maps."""
+    fs, nseg = 256.0, 24
+    coarse = srs_synth.log_templates(3e-2, 1e-1, 6)
+    fine = srs_synth.log_templates(3e-2, 1e-1, 24)
+    x = srs_synth.strain_with_chirps(nseg * 7680, fs, 4, [{"mc": 6e-2, "f0": 50.0, "amp": 0.08}])
+    p = Params(eps=1e-6, top_k=8)
+    params = proposal.init_params(0)
+    smap = torch.from_numpy(ctx.search(x, coarse, p)[1]).cuda()
+    sc = ctx.score_map(smap, params).cpu().numpy()
+    th = float(np.float32(np.quantile(sc, 0.97)))
+    keep = proposal.component_cells(sc, th, smap.cpu().numpy(), top)
+    r = ctx.search_proposed(x, coarse, fine, p, params, threshold=th, fine_rows=0, component_top=top)
+    assert r["report"]["proposed_coarse"] == int(keep.sum())
+    expect = proposal.fine_cells_of(np.argwhere(keep), coarse, fine, 600, fine_rows=0)
+    got = sorted(map(tuple, r["cells"].tolist()))
+    assert got == [tuple(c) for c in expect]
