@@ -59,6 +59,7 @@ MixedArgs mixed_args(const Plan& pl, const srs_ctx* ctx, int seg_begin, int seg_
   a.two_over_w = (float)(2.0 / pl.w);
   a.corr = ctx->corr.as<float>();
   a.tw = ctx->tw.as<float>();
+  a.order = pl.order.empty() ? nullptr : ctx->order.as<int>();
   fill_radices(pl, a.radices);
   return a;
 }
@@ -285,7 +286,16 @@ namespace {
 // spectra).  Large searches skip the small chunks and the smallest CTA caps.
 constexpr long long kTuneSpectra = 150000;
 
+// One-segment items queued last by the tuned search: about two per resident
+// CTA of the largest configuration, so that the last wave is fine-grained.
+int32_t tail_singles(const srs_ctx* ctx) { return 2 * 8 * ctx->n_sm; }
+
 srs_status upload_items(srs_ctx* ctx, Plan& pl) {
+  if (!pl.order.empty()) {
+    SRS_CK(ctx->order.ensure(pl.order.size() * 4), "alloc order");
+    SRS_CK(cudaMemcpyAsync(ctx->order.p, pl.order.data(), pl.order.size() * 4, cudaMemcpyHostToDevice, ctx->stream),
+           "copy order");
+  }
   SRS_CK(ctx->items.ensure(pl.items.size() * sizeof(Item)), "alloc items");
   SRS_CK(ctx->item_off.ensure(pl.item_off.size() * 4), "alloc item_off");
   SRS_CK(ctx->partial.ensure(pl.items.size() * (size_t)pl.n_bins * 4), "alloc partial");
@@ -330,9 +340,10 @@ srs_status autotune_mixed(srs_ctx* ctx, Plan& pl, const float* s32, int use_tma,
     if (t.key == key) {
       set_cta(pl, t.threads);
       pl.global_x = t.global_x != 0;
-      if (t.chunk != pl.chunk) {
-        make_items(pl, t.chunk, false, 0, 0);
+      if (!pl.tuned_items || t.chunk != pl.chunk) {
+        make_items(pl, t.chunk, false, 0, 0, tail_singles(ctx));
         { srs_status us = upload_items(ctx, pl); if (us != SRS_OK) return us; }
+        pl.tuned_items = true;
       }
       *ctas_out = t.ctas;
       return SRS_OK;
@@ -355,7 +366,7 @@ srs_status autotune_mixed(srs_ctx* ctx, Plan& pl, const float* s32, int use_tma,
       for (int ch : {1, 2, 4, 8, 16}) {
         if (large && ch < 4 && only_chunk == 0) continue;
         if (only_chunk && ch != only_chunk) continue;
-        make_items(pl, ch, false, 0, 0);
+        make_items(pl, ch, false, 0, 0);   // no tail while timing a prefix of the items
         srs_status us = upload_items(ctx, pl);
         if (us != SRS_OK) return us;
         MixedArgs a = mixed_args(pl, ctx, 0, 0);
@@ -387,7 +398,8 @@ srs_status autotune_mixed(srs_ctx* ctx, Plan& pl, const float* s32, int use_tma,
   }
   set_cta(pl, best_c.threads);
   pl.global_x = best_c.global_x != 0;
-  make_items(pl, best_c.chunk, false, 0, 0);
+  make_items(pl, best_c.chunk, false, 0, 0, tail_singles(ctx));
+  pl.tuned_items = true;
   { srs_status us = upload_items(ctx, pl); if (us != SRS_OK) return us; }
   SRS_CK(cudaStreamSynchronize(ctx->stream), "tuning");
   ctx->tuned.push_back({key, best_c.chunk, best_c.ctas, best_c.threads, best_c.global_x, best});
@@ -566,6 +578,7 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
                           (const void*)ctx->betas.p, (const void*)ctx->nseg.p, (const void*)ctx->item_off.p,
                           (const void*)ctx->corr.p, (const void*)ctx->tw.p, (const void*)ctx->queue.p,
                           (const void*)ctx->errflag.p, (const void*)ctx->topk_a.p, (const void*)ctx->topk_b.p,
+                          (const void*)(pl.order.empty() ? nullptr : ctx->order.p),
                           (const void*)ctx->S.p})
     gkey.insert(gkey.end(), (const unsigned char*)&ptr, (const unsigned char*)&ptr + sizeof ptr);
   gkey.push_back((unsigned char)ctx->ctas_per_sm);

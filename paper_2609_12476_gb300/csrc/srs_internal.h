@@ -64,6 +64,8 @@ struct Plan {
   bool global_x = false;                                 // spreader reads samples from global memory (no TMA staging)
   int32_t chunk = 0;
   std::vector<Item> items;
+  std::vector<int32_t> order;                            // queue position -> item (empty: in item order)
+  bool tuned_items = false;                              // items and order are the tuner's choice
   std::vector<int32_t> item_off;                         // [n_templates+1] first item of template m
   // tables (FP64, converted by the launcher)
   std::vector<double> corr;                              // [n_bins] deconvolution factor
@@ -84,6 +86,10 @@ void set_cta(Plan& pl, int32_t threads);
 int32_t run_for(int64_t n_s, int32_t threads);
 // Work items of the mixed form for a given chunk size (search: each template's
 // first nseg_m segments; spectra: [seg_begin, seg_end) of every template).
-void make_items(Plan& pl, int32_t chunk, bool spectra_mode, int32_t seg_begin, int32_t seg_end);
+// With tail_singles > 0 (search mode, chunk > 1) the last segments of every
+// template, about tail_singles in all, become one-segment items queued after
+// all the others, so that the persistent kernel's last wave is fine-grained.
+void make_items(Plan& pl, int32_t chunk, bool spectra_mode, int32_t seg_begin, int32_t seg_end,
+                int32_t tail_singles = 0);
 
 }  // namespace srs

@@ -392,7 +392,8 @@ k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_
     __syncthreads();
     const int q = s_item;
     if (q >= n_items) break;
-    const Item it = items[q];
+    const int qi = a.order ? a.order[q] : q;   // the item this queue position runs
+    const Item it = items[qi];
     if (!GLOBAL_X && tid == 0) bulk_load(xs, strain + (long long)it.i0 * a.n_s, seg_bytes, &s_bar);
     {
       const int na = (it.i1 - it.i0) * a.n_anchor;
@@ -445,7 +446,7 @@ k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_
       __syncthreads();
     }
     if (!SPECTRA)
-      for (int b = tid; b < a.n_bins; b += blockDim.x) partial[(long long)q * a.n_bins + b] = Z[b];
+      for (int b = tid; b < a.n_bins; b += blockDim.x) partial[(long long)qi * a.n_bins + b] = Z[b];
   }
 }
 

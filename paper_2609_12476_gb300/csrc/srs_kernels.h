@@ -34,6 +34,7 @@ struct MixedArgs {
   float two_over_w;
   const float* corr;              // [n_bins] deconvolution factors
   const float* tw;                // [2 n_fine] interleaved exp(-2 pi i m / n_fine)
+  const int* order;               // [n_items] queue position -> item, or NULL (item order)
   int8_t radices[16];
 };
 

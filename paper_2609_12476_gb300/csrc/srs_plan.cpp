@@ -284,26 +284,39 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
   return SRS_OK;
 }
 
-void make_items(Plan& pl, int32_t chunk, bool spectra_mode, int32_t seg_begin, int32_t seg_end) {
+void make_items(Plan& pl, int32_t chunk, bool spectra_mode, int32_t seg_begin, int32_t seg_end,
+                int32_t tail_singles) {
   pl.chunk = chunk;
   pl.items.clear();
+  pl.order.clear();
   pl.item_off.assign(pl.n_templates + 1, 0);
+  const bool tail = !spectra_mode && chunk > 1 && tail_singles > 0 && pl.n_spectra > 0;
+  std::vector<int32_t> singles;
   int64_t g = 0;
   for (int32_t m = 0; m < pl.n_templates; ++m) {
     pl.item_off[m] = (int32_t)pl.items.size();
     int32_t a = spectra_mode ? seg_begin : 0;
     int32_t e = spectra_mode ? seg_end : pl.nseg[m];
-    for (int32_t i = a; i < e; i += chunk) {
+    int32_t e_multi = e;
+    if (tail) {
+      const int64_t s_m = ((int64_t)(e - a) * tail_singles + pl.n_spectra - 1) / pl.n_spectra;
+      e_multi = e - (int32_t)std::min<int64_t>(s_m, e - a);
+    }
+    for (int32_t i = a; i < e; ) {
       Item it;
       it.m = m;
       it.i0 = i;
-      it.i1 = std::min(e, i + chunk);
+      it.i1 = i < e_multi ? std::min(e_multi, i + chunk) : i + 1;
       it.g0 = (int32_t)g;
       g += it.i1 - it.i0;
+      if (tail && i >= e_multi) singles.push_back((int32_t)pl.items.size());
+      else if (tail) pl.order.push_back((int32_t)pl.items.size());
       pl.items.push_back(it);
+      i = it.i1;
     }
   }
   pl.item_off[pl.n_templates] = (int32_t)pl.items.size();
+  if (tail) pl.order.insert(pl.order.end(), singles.begin(), singles.end());
 }
 
 int32_t run_for(int64_t n_s, int32_t threads) {
