@@ -473,7 +473,9 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
     }
   }
   SRS_CK(ctx->keys.ensure(n_map * 8), "alloc keys");
-  const long long scratch = topk_scratch_keys(n_map, k);
+  // k <= 32 (mixed form): the reduction selects the top k itself
+  const bool top32 = mixed && k <= 32;
+  const long long scratch = std::max(topk_scratch_keys(n_map, k), 4LL * ctx->n_sm * 32);
   SRS_CK(ctx->topk_a.ensure(scratch * 8), "alloc topk");
   SRS_CK(ctx->topk_b.ensure(scratch * 8), "alloc topk");
   srs_candidate* dc = on_dev ? cands : nullptr;
@@ -547,6 +549,15 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
                           ctx->n_sm, ctx->ctas_per_sm, ctx->stream), "k_mixed");
       SRS_CK(cudaEventRecordWithFlags(k_ev3, ctx->stream, cudaEventRecordExternal), "event");
       ++launches;
+      if (top32) {
+        SRS_CK(launch_reduce_mixed_top32(ctx->partial.as<float>(), ctx->item_off.as<int>(), ctx->nseg.as<int>(),
+                                         n_templates, pl.n_bins, dmap, k, ctx->topk_a.as<unsigned long long>(),
+                                         ctx->queue.as<int>() + 4, dc, ctx->n_sm, ctx->stream),
+               "k_reduce_mixed_top32");
+        ++launches;
+        SRS_CK(cudaMemcpyAsync(ctx->hflag, ctx->errflag.p, 32, cudaMemcpyDeviceToHost, ctx->stream), "read error flag");
+        return SRS_OK;
+      }
       SRS_CK(launch_reduce_mixed(ctx->partial.as<float>(), ctx->item_off.as<int>(), ctx->nseg.as<int>(), n_templates,
                                  pl.n_bins, dmap, ctx->keys.as<unsigned long long>(), ctx->n_sm, ctx->stream),
              "k_reduce_mixed");

@@ -562,6 +562,98 @@ __global__ void k_reduce_mixed(const float* __restrict__ partial, const int* __r
   }
 }
 
+// Warp-level top-32 lists: one key per lane, sorted descending across the
+// lanes (lane 0 holds the largest); missing keys are 0.
+__device__ __forceinline__ unsigned long long warp_sort32_desc(unsigned long long v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, stride);
+      const bool keep_max = ((lane & stride) == 0) == ((lane & size) == 0);
+      v = keep_max ? (v > o ? v : o) : (v < o ? v : o);
+    }
+  }
+  return v;
+}
+// The 32 largest of two descending lists: max against the other list
+// reversed gives a bitonic sequence holding them, which a half-cleaner sorts.
+__device__ __forceinline__ unsigned long long warp_merge32_desc(unsigned long long a, unsigned long long b) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long br = __shfl_sync(0xffffffffu, b, 31 - lane);
+  unsigned long long v = a > br ? a : br;
+#pragma unroll
+  for (int stride = 16; stride > 0; stride >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, stride);
+    v = ((lane & stride) == 0) ? (v > o ? v : o) : (v < o ? v : o);
+  }
+  return v;
+}
+
+// Mixed form with k <= 32: k_reduce_mixed's cells, and the top k on the way.
+// Each warp keeps the top 32 keys of the cells it has reduced; each block
+// merges its warps' lists into scratch; the last block to finish (a ticket
+// taken after a fence; no block waits for another) merges the blocks' lists
+// and writes the candidates.
+__global__ void __launch_bounds__(256)
+k_reduce_mixed_top32(const float* __restrict__ partial, const int* __restrict__ item_off,
+                     const int* __restrict__ nseg, int n_templates, int n_bins, float* __restrict__ map, int k,
+                     unsigned long long* __restrict__ scratch, int* __restrict__ ticket,
+                     srs_candidate* __restrict__ cands) {
+  __shared__ unsigned long long s_top[8][32];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long total = (long long)n_templates * n_bins;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  unsigned long long top = 0ull;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
+    const long long f = base + threadIdx.x;
+    unsigned long long key = 0ull;
+    if (f < total) {
+      const int m = (int)(f / n_bins);
+      const int b = (int)(f - (long long)m * n_bins);
+      const int q0 = item_off[m], q1 = item_off[m + 1];
+      double z = 0.0;
+      for (int q = q0; q < q1; ++q) z += (double)partial[(long long)q * n_bins + b];
+      const float v = (float)(z / sqrt((double)nseg[m]));
+      if (map) map[f] = v;
+      key = make_key(v, (uint32_t)f);
+    }
+    top = warp_merge32_desc(top, warp_sort32_desc(key));
+  }
+  s_top[warp][lane] = top;
+  __syncthreads();
+  if (warp == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) top = warp_merge32_desc(top, s_top[w][lane]);
+    scratch[(long long)blockIdx.x * 32 + lane] = top;
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // the last block: merge every block's list (each already sorted)
+  top = 0ull;
+  for (int blk = warp; blk < (int)gridDim.x; blk += (int)(blockDim.x >> 5))
+    top = warp_merge32_desc(top, __ldcg(&scratch[(long long)blk * 32 + lane]));
+  s_top[warp][lane] = top;
+  __syncthreads();
+  if (warp == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) top = warp_merge32_desc(top, s_top[w][lane]);
+    if (lane < k) {
+      const uint32_t flat = ~(uint32_t)(top & 0xffffffffull);
+      srs_candidate c;
+      c.value = key_value(top);
+      c.template_idx = (int32_t)(flat / (uint32_t)n_bins);
+      c.bin = (int32_t)(flat % (uint32_t)n_bins);
+      cands[lane] = c;
+    }
+    if (lane == 0) *ticket = 0;
+  }
+}
+
 // Plain form: n_sigma = (S - 2 N) / (2 sqrt(N)) in FP64.
 __global__ void k_finish_plain(const double* __restrict__ S, const int* __restrict__ nseg, int n_templates,
                                int n_bins, float* __restrict__ map, unsigned long long* __restrict__ keys) {
@@ -767,6 +859,18 @@ cudaError_t launch_reduce_mixed(const float* partial, const int* item_off, const
   long long blocks = (total + 255) / 256;
   if (blocks > (long long)n_sm * 16) blocks = (long long)n_sm * 16;
   k_reduce_mixed<<<(unsigned)blocks, 256, 0, st>>>(partial, item_off, nseg, n_templates, n_bins, map, keys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_mixed_top32(const float* partial, const int* item_off, const int* nseg, int n_templates,
+                                      int n_bins, float* map, int k, unsigned long long* scratch, int* ticket,
+                                      srs_candidate* cands, int n_sm, cudaStream_t st) {
+  if (k < 1 || k > 32) return cudaErrorInvalidValue;
+  long long total = (long long)n_templates * n_bins;
+  long long blocks = (total + 255) / 256;
+  if (blocks > (long long)n_sm * 4) blocks = (long long)n_sm * 4;
+  k_reduce_mixed_top32<<<(unsigned)blocks, 256, 0, st>>>(partial, item_off, nseg, n_templates, n_bins, map, k,
+                                                          scratch, ticket, cands);
   return cudaGetLastError();
 }
 

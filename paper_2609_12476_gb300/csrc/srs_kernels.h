@@ -60,6 +60,12 @@ cudaError_t launch_plain(bool f64_in, bool spectra, const void* strain, const do
                          cudaStream_t st);
 cudaError_t launch_reduce_mixed(const float* partial, const int* item_off, const int* nseg, int n_templates,
                                 int n_bins, float* map, unsigned long long* keys, int n_sm, cudaStream_t st);
+// k <= 32: the same reduction with the top k selected on the way (warp lists,
+// block lists in scratch[blocks * 32], the last block writes cands); *ticket
+// starts at zero and is left at zero.  Blocks: at most 4 per SM.
+cudaError_t launch_reduce_mixed_top32(const float* partial, const int* item_off, const int* nseg, int n_templates,
+                                      int n_bins, float* map, int k, unsigned long long* scratch, int* ticket,
+                                      srs_candidate* cands, int n_sm, cudaStream_t st);
 cudaError_t launch_finish_plain(const double* S, const int* nseg, int n_templates, int n_bins, float* map,
                                 unsigned long long* keys, int n_sm, cudaStream_t st);
 long long topk_scratch_keys(long long n, int k);
