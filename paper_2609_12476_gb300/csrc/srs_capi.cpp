@@ -179,11 +179,15 @@ std::vector<unsigned char> make_key(int kind, const srs_params* p, int64_t n_sam
   return k;
 }
 
-// Plan for this call, reusing the context's last plan (and its device tables)
-// when the call kind, sizes, parameters and templates are the same.
 // Pinned error-flag copies: slot 0 for synchronous calls, one slot of eight
 // ints per asynchronous call since the last srs_sync.
 constexpr size_t kHostFlagBytes = (size_t)8 * (1 + srs_ctx::kAsyncSlots) * sizeof(int);
+
+// An event around the transform kernel: inside a stream capture it must become
+// an event-record node (external), outside one it is an ordinary record.
+cudaError_t record_kernel_event(cudaEvent_t ev, cudaStream_t st, bool capturing) {
+  return capturing ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal) : cudaEventRecord(ev, st);
+}
 
 // Drop the captured search graph (an in-flight launch finishes on its own).
 void destroy_graph(srs_ctx* ctx) {
@@ -220,6 +224,8 @@ void find_event_nodes(srs_ctx* ctx) {
   cudaGetLastError();
 }
 
+// Plan for this call, reusing the context's last plan (and its device tables)
+// when the call kind, sizes, parameters and templates are the same.
 srs_status get_plan(srs_ctx* ctx, int kind, const srs_params* params, const double* mc, int32_t n_templates,
                     int64_t n_samples, int32_t dtype, bool spectra_mode, int32_t a, int32_t b, const Plan** out) {
   srs_params key_p = *params;
@@ -531,6 +537,7 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
   // events around the transform kernel inside the sequence (a captured graph
   // holds the context's own pair and is re-pointed per launch)
   cudaEvent_t k_ev2 = e2, k_ev3 = e3;
+  bool capturing = false;
   auto enqueue = [&]() -> srs_status {
     launches = 0;
     if (mixed) {
@@ -543,11 +550,11 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
       }
       SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
       SRS_CK(cudaMemsetAsync(ctx->errflag.p, 0, 64, ctx->stream), "memset error flag");
-      SRS_CK(cudaEventRecordWithFlags(k_ev2, ctx->stream, cudaEventRecordExternal), "event");
+      SRS_CK(record_kernel_event(k_ev2, ctx->stream, capturing), "event");
       SRS_CK(launch_mixed(false, pl.w, s32, ctx->items.as<Item>(), (int)n_items, ctx->betas.as<double>(),
                           ctx->queue.as<int>(), a, ctx->partial.as<float>(), nullptr, ctx->errflag.as<int>(),
                           ctx->n_sm, ctx->ctas_per_sm, ctx->stream), "k_mixed");
-      SRS_CK(cudaEventRecordWithFlags(k_ev3, ctx->stream, cudaEventRecordExternal), "event");
+      SRS_CK(record_kernel_event(k_ev3, ctx->stream, capturing), "event");
       ++launches;
       if (top32) {
         SRS_CK(launch_reduce_mixed_top32(ctx->partial.as<float>(), ctx->item_off.as<int>(), ctx->nseg.as<int>(),
@@ -565,10 +572,10 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
     } else {
       PlainArgs p = plain_args(pl, ctx, 0, 0);
       SRS_CK(cudaMemsetAsync(ctx->S.p, 0, n_map * 8, ctx->stream), "memset S");
-      SRS_CK(cudaEventRecordWithFlags(k_ev2, ctx->stream, cudaEventRecordExternal), "event");
+      SRS_CK(record_kernel_event(k_ev2, ctx->stream, capturing), "event");
       SRS_CK(launch_plain(f64, false, dstrain, ctx->betas.as<double>(), ctx->nseg.as<int>(), p, max_seg, n_templates,
                           ctx->S.as<double>(), nullptr, ctx->stream), "k_plain");
-      SRS_CK(cudaEventRecordWithFlags(k_ev3, ctx->stream, cudaEventRecordExternal), "event");
+      SRS_CK(record_kernel_event(k_ev3, ctx->stream, capturing), "event");
       ++launches;
       SRS_CK(launch_finish_plain(ctx->S.as<double>(), ctx->nseg.as<int>(), n_templates, pl.n_bins, dmap,
                                  ctx->keys.as<unsigned long long>(), ctx->n_sm, ctx->stream), "k_finish_plain");
@@ -605,7 +612,9 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
       k_ev3 = ctx->ev3;
       const cudaError_t be = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed);
       if (be == cudaSuccess) {
+        capturing = true;
         const srs_status es = enqueue();
+        capturing = false;
         const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
         cudaError_t ie = cudaErrorUnknown;
         if (es == SRS_OK && ce == cudaSuccess && g) ie = cudaGraphInstantiate(&ctx->graph_exec, g, 0);

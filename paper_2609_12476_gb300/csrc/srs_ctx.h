@@ -79,12 +79,12 @@ struct srs_ctx {
       strain32, errflag, map, S, F, psi, th, im, ii;
   // learned proposal
   srs::DevBuf xb, yb, z1, logits, dz, lossv, grad, wts, adam_m, adam_v, w1h, w2h, idx, patches, cells_m, cells_b,
-      sp_items, sp_bins, sp_partial, sp_cells, sp_out, cmap, ccands, inj;
+      sp_items, sp_bins, sp_partial, sp_cells, sp_out, sp_betas, cmap, ccands, inj;
   std::vector<srs::DevBuf*> all_buffers() {
     return {&items, &order, &anchors, &partial, &betas, &nseg, &item_off, &corr, &tw, &keys, &topk_a, &topk_b, &cands,
             &queue, &strain, &strain32, &errflag, &map, &S, &F, &psi, &th, &im, &ii, &xb, &yb, &z1, &logits, &dz,
             &lossv, &grad, &wts, &adam_m, &adam_v, &w1h, &w2h, &idx, &patches, &cells_m, &cells_b, &sp_items,
-            &sp_bins, &sp_partial, &sp_cells, &sp_out, &cmap, &ccands, &inj};
+            &sp_bins, &sp_partial, &sp_cells, &sp_out, &sp_betas, &cmap, &ccands, &inj};
   }
 };
 

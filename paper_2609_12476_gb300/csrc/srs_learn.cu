@@ -245,22 +245,26 @@ __global__ void __launch_bounds__(256)
 k_sparse_bins(const float* __restrict__ strain, const SparseItem* __restrict__ items, int n_items,
               const double* __restrict__ betas, const int* __restrict__ bins, SparseArgs a,
               float* __restrict__ partial) {
-  __shared__ Anchor anc[kSpreadWarps];
+  __shared__ Anchor anc[kSparseChunk][kSpreadWarps];   // every anchor of the item, computed up front
   __shared__ float red[kSparseMaxBins][2][kSpreadWarps];
   __shared__ float sZ[kSparseMaxBins];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int q = blockIdx.x; q < n_items; q += gridDim.x) {
     const SparseItem it = items[q];
+    const int nb = it.nb;
     int kk[kSparseMaxBins];
 #pragma unroll
-    for (int u = 0; u < kSparseMaxBins; ++u) kk[u] = u < it.nb ? bins[it.b0 + u] - a.half_bins : 0;
-    __syncthreads();
+    for (int u = 0; u < kSparseMaxBins; ++u) kk[u] = u < nb ? bins[it.b0 + u] - a.half_bins : 0;
+    __syncthreads();   // the previous item is done with anc and sZ
+    {
+      const double b = betas[it.m];
+      const int na = (it.i1 - it.i0) * a.aa.n_anchor;
+      for (int t = tid; t < na; t += blockDim.x)
+        anc[t / a.aa.n_anchor][t % a.aa.n_anchor] = compute_anchor(b, it.i0 + t / a.aa.n_anchor, t % a.aa.n_anchor, a.aa);
+    }
     if (tid < kSparseMaxBins) sZ[tid] = 0.f;
-    const double b = betas[it.m];
     for (int i = it.i0; i < it.i1; ++i) {
-      __syncthreads();
-      if (tid < a.aa.n_anchor) anc[tid] = compute_anchor(b, i, tid, a.aa);
-      __syncthreads();
+      __syncthreads();   // anchors ready; red free again
       float re[kSparseMaxBins], im[kSparseMaxBins];
 #pragma unroll
       for (int u = 0; u < kSparseMaxBins; ++u) { re[u] = 0.f; im[u] = 0.f; }
@@ -269,7 +273,7 @@ k_sparse_bins(const float* __restrict__ strain, const SparseItem* __restrict__ i
       const int j_lo = warp * a.span;
       const int j_hi = min(j_lo + a.span, a.n_s);
       if (j_lo < a.n_s) {
-        const Anchor A = anc[warp];
+        const Anchor A = anc[i - it.i0][warp];
         for (int j = j_lo + lane; j < j_hi; j += 32) {
           uint32_t Psi;
           float th;
@@ -279,7 +283,7 @@ k_sparse_bins(const float* __restrict__ strain, const SparseItem* __restrict__ i
           const float xv = x[j];
 #pragma unroll
           for (int u = 0; u < kSparseMaxBins; ++u) {
-            if (u < it.nb) {
+            if (u < nb) {
               const uint32_t Tb = T0 + (uint32_t)kk[u] * Psi;
               float sn, cs;
               __sincosf((float)(int32_t)Tb * 1.4629180792671596e-09f, &sn, &cs);  // 2 pi / 2^32
@@ -291,15 +295,17 @@ k_sparse_bins(const float* __restrict__ strain, const SparseItem* __restrict__ i
       }
 #pragma unroll
       for (int u = 0; u < kSparseMaxBins; ++u) {
-        float r = re[u], m_ = im[u];
-        for (int o = 16; o > 0; o >>= 1) {
-          r += __shfl_down_sync(0xffffffffu, r, o);
-          m_ += __shfl_down_sync(0xffffffffu, m_, o);
+        if (u < nb) {   // uniform across the block
+          float r = re[u], m_ = im[u];
+          for (int o = 16; o > 0; o >>= 1) {
+            r += __shfl_down_sync(0xffffffffu, r, o);
+            m_ += __shfl_down_sync(0xffffffffu, m_, o);
+          }
+          if (lane == 0) { red[u][0][warp] = r; red[u][1][warp] = m_; }
         }
-        if (lane == 0) { red[u][0][warp] = r; red[u][1][warp] = m_; }
       }
       __syncthreads();
-      if (tid < it.nb) {
+      if (tid < nb) {
         float r = 0.f, m_ = 0.f;
         for (int w = 0; w < kSpreadWarps; ++w) { r += red[tid][0][w]; m_ += red[tid][1][w]; }
         sZ[tid] += fmaf(r, r, m_ * m_) * a.inv_ns - 1.0f;   // (P - 2) / 2

@@ -18,6 +18,7 @@ constexpr int kParams = SRS_MLP_PARAMS;             // W1, b1, w2, b2
 static_assert(kPatchSize == kPatchTemplates * kPatchBins, "patch size");
 static_assert(kParams == kHidden * kPatchSize + 2 * kHidden + 1, "parameter count");
 constexpr int kSparseMaxBins = 8;                   // bins per refinement work item
+constexpr int kSparseChunk = 16;                    // segments per refinement work item
 // Above this many requested bins a template is refined through the NUFFT
 // (one spectrum gives every bin) instead of direct sums (one pass per bin).
 constexpr int kDirectMaxBins = 24;

@@ -97,18 +97,22 @@ srs_status score_map_impl(srs_ctx* ctx, const float* map, int32_t n_templates, i
 srs_status refine_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype, const double* mc,
                        int32_t n_templates, const srs_params* params, const int32_t* cell_m, const int32_t* cell_b,
                        int32_t n_cells, float* nsigma, srs_report* report, int64_t* seg_bins_out,
-                       int32_t* templates_out) {
+                       int32_t* templates_out, const Plan* planned = nullptr) {
   if (!params || !mc || !nsigma || (n_cells > 0 && (!cell_m || !cell_b)) || n_cells < 0)
     return set_err(ctx, SRS_ERR_ARG, "refine: NULL argument");
   if (dtype != SRS_F32 && dtype != SRS_F64) return set_err(ctx, SRS_ERR_ARG, "dtype must be SRS_F32 or SRS_F64");
   srs_params pc = *params;
   pc.precision = SRS_MIXED;
   if (pc.eps < 1e-7) pc.eps = 1e-7;   // direct sums: eps only sizes a NUFFT that is not used here
-  pc.chunk = 16;
-  Plan pl;
-  std::string msg;
-  srs_status s = make_plan(pc, mc, n_templates, n_samples, false, 0, 0, pl, msg);
-  if (s != SRS_OK) return set_err(ctx, s, msg);
+  pc.chunk = kSparseChunk;
+  Plan own;
+  if (!planned) {
+    std::string msg;
+    srs_status s0 = make_plan(pc, mc, n_templates, n_samples, false, 0, 0, own, msg);
+    if (s0 != SRS_OK) return set_err(ctx, s0, msg);
+  }
+  const Plan& pl = planned ? *planned : own;
+  srs_status s = SRS_OK;
   for (int32_t c = 0; c < n_cells; ++c)
     if (cell_m[c] < 0 || cell_m[c] >= n_templates || cell_b[c] < 0 || cell_b[c] >= pl.n_bins)
       return set_err(ctx, SRS_ERR_ARG, "refine: cell outside the map");
@@ -153,8 +157,12 @@ srs_status refine_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
       int32_t nc = 0;
       srs_report rs;
       std::memset(&rs, 0, sizeof rs);
+      // a one-off template subset: launched directly, not captured as a graph
+      const bool graphs = ctx->use_graphs;
+      ctx->use_graphs = false;
       s = search_impl(ctx, dstrain_all, n_samples, dtype, dmc.data(), (int32_t)dense.size(), &ps,
                       ctx->S.as<float>(), ctx->ccands.as<srs_candidate>(), &nc, &rs);
+      ctx->use_graphs = graphs;
       if (s != SRS_OK) return s;
       std::vector<float> dmap(dense.size() * (size_t)pl.n_bins);
       SRS_CK(cudaMemcpy(dmap.data(), ctx->S.p, dmap.size() * 4, cudaMemcpyDeviceToHost), "copy dense map");
@@ -163,7 +171,7 @@ srs_status refine_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
       std::vector<float> ns_rest(rest_idx.size());
       if (!rest_idx.empty()) {
         s = refine_impl(ctx, dstrain_all, n_samples, dtype, mc, n_templates, &ps, rest_m.data(), rest_b.data(),
-                        (int32_t)rest_idx.size(), ns_rest.data(), nullptr, &sb_rest, &t_rest);
+                        (int32_t)rest_idx.size(), ns_rest.data(), nullptr, &sb_rest, &t_rest, &pl);
         if (s != SRS_OK) return s;
       }
       for (int32_t c = 0; c < n_cells; ++c)
@@ -191,7 +199,7 @@ srs_status refine_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
   std::vector<int32_t> bins;
   std::vector<SparseItem> items;
   std::vector<int32_t> key_item0(uk.size()), key_nitems(uk.size()), key_slot(uk.size()), key_nseg(uk.size());
-  const int chunk = 16;
+  const int chunk = kSparseChunk;
   int32_t n_templ_touched = 0;
   int64_t seg_bins = 0;
   size_t k = 0;
@@ -248,14 +256,14 @@ srs_status refine_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
   int use_tma = 0;
   s = strain_f32(ctx, dstrain, dtype, samples, pl.n_s, &s32, &use_tma);
   if (s != SRS_OK) return s;
-  SRS_CK(ctx->betas.ensure(pl.beta.size() * 8), "alloc betas");
+  SRS_CK(ctx->sp_betas.ensure(pl.beta.size() * 8), "alloc betas");
   SRS_CK(ctx->sp_items.ensure(items.size() * sizeof(SparseItem)), "alloc items");
   SRS_CK(ctx->sp_bins.ensure(bins.size() * 4), "alloc bins");
   SRS_CK(ctx->sp_partial.ensure(items.size() * kSparseMaxBins * 4), "alloc partial");
   SRS_CK(ctx->sp_cells.ensure((size_t)n_cells * 16), "alloc cells");
   SRS_CK(ctx->sp_out.ensure((size_t)n_cells * 4), "alloc out");
-  ctx->have_plan = false;  // the template table is overwritten below
-  SRS_CK(cudaMemcpyAsync(ctx->betas.p, pl.beta.data(), pl.beta.size() * 8, cudaMemcpyHostToDevice, ctx->stream), "copy betas");
+  SRS_CK(cudaMemcpyAsync(ctx->sp_betas.p, pl.beta.data(), pl.beta.size() * 8, cudaMemcpyHostToDevice, ctx->stream),
+         "copy betas");
   SRS_CK(cudaMemcpyAsync(ctx->sp_items.p, items.data(), items.size() * sizeof(SparseItem), cudaMemcpyHostToDevice,
                          ctx->stream), "copy items");
   SRS_CK(cudaMemcpyAsync(ctx->sp_bins.p, bins.data(), bins.size() * 4, cudaMemcpyHostToDevice, ctx->stream), "copy bins");
@@ -278,7 +286,7 @@ srs_status refine_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
   a.aa.span = pl.span;
   a.aa.n_anchor = pl.n_anchor;
   SRS_CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
-  SRS_CK(launch_sparse_bins(s32, ctx->sp_items.as<SparseItem>(), (int)items.size(), ctx->betas.as<double>(),
+  SRS_CK(launch_sparse_bins(s32, ctx->sp_items.as<SparseItem>(), (int)items.size(), ctx->sp_betas.as<double>(),
                             ctx->sp_bins.as<int>(), a, ctx->sp_partial.as<float>(), ctx->n_sm, ctx->stream),
          "k_sparse_bins");
   SRS_CK(launch_sparse_reduce(ctx->sp_partial.as<float>(), dc, dc + n_cells, dc + 2 * (size_t)n_cells,

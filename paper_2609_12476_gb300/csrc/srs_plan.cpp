@@ -8,6 +8,7 @@
 // paper uses (its reference for FINUFFT).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 
 #include "srs_internal.h"
@@ -149,13 +150,16 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
   pl.beta.resize(n_templates);
   pl.nseg.resize(n_templates);
   pl.n_spectra = 0;
+  // Eq. (beta) with its Mc-independent factor taken once
+  const double beta_scale = 96.0 / 5.0 * std::pow(kPi, 8.0 / 3.0) * std::pow(p.f_ref, 8.0 / 3.0);
+  const double exit_frac = 1.0 - std::pow(p.f_ref / p.f_hi, 8.0 / 3.0);
   for (int32_t m = 0; m < n_templates; ++m) {
     if (!(mc[m] > 0) || !std::isfinite(mc[m])) return fail(SRS_ERR_ARG, "chirp masses must be positive and finite");
-    double b = chirp_beta(mc[m], p.f_ref);
+    double b = beta_scale * std::pow(kGMsunC3 * mc[m], 5.0 / 3.0);
     pl.beta[m] = b;
     int32_t ns = pl.n_seg_total;
     if (pl.cut) {
-      double t_exit = 3.0 / (8.0 * b) * (1.0 - std::pow(p.f_ref / p.f_hi, 8.0 / 3.0));
+      double t_exit = 3.0 / (8.0 * b) * exit_frac;
       double k = std::floor(t_exit / p.t_coh);
       ns = (int32_t)std::max(1.0, std::min(k, (double)pl.n_seg_total));
     }
@@ -228,25 +232,22 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
     // Checked for 256-thread CTAs (required) and 128-thread CTAs (twice the span; allowed if it holds).
     double fmax = std::max(std::fabs(p.f_lo), std::fabs(p.f_hi));
     const double ds_half = 32.0 * (double)run_for(pl.n_s, 128) / p.fs;
+    const double ds = pl.span / p.fs;
+    // d^6 delta / ds^6 / 6! = coef_6 beta^5 A^(-43/8) / 720 and d^2 delta / ds^2 / 2 = beta A^(-11/8) / 2,
+    // through logarithms (one log of beta and of A per template)
+    const double c6 = 2438.3333333333333 / 720.0;
+    const double lim6_half = 1e-9 / (std::pow(ds_half, 6) * fmax), lim2_half = 0.25 * p.t_coh / (ds_half * ds_half);
+    const double lim6 = 1e-9 / (std::pow(ds, 6) * fmax), lim2 = 0.25 * p.t_coh / (ds * ds);
     pl.allow_128 = true;
     for (int32_t m = 0; m < n_templates; ++m) {
       int32_t last_seg = spectra_mode ? seg_end : pl.nseg[m];
       double A = 1.0 - 8.0 / 3.0 * pl.beta[m] * (((double)last_seg * pl.n_s) / p.fs);
       A = std::max(A, 1e-300);
-      double b = pl.beta[m];
-      double e6 = 2438.3333333333333 * std::pow(b, 5) * std::pow(A, -43.0 / 8.0) / 720.0;
-      double e2 = 0.5 * b * std::pow(A, -11.0 / 8.0);
-      if (e6 * std::pow(ds_half, 6) * fmax > 1e-9 || e2 * ds_half * ds_half / p.t_coh > 0.25) pl.allow_128 = false;
-    }
-    double ds = pl.span / p.fs;
-    for (int32_t m = 0; m < n_templates; ++m) {
-      int32_t last_seg = spectra_mode ? seg_end : pl.nseg[m];
-      double A = 1.0 - 8.0 / 3.0 * pl.beta[m] * (((double)last_seg * pl.n_s) / p.fs);
-      A = std::max(A, 1e-300);
-      double b = pl.beta[m];
-      double e6 = 2438.3333333333333 * std::pow(b, 5) * std::pow(A, -43.0 / 8.0) / 720.0;
-      double e2 = 0.5 * b * std::pow(A, -11.0 / 8.0);
-      if (e6 * std::pow(ds, 6) * fmax > 1e-9 || e2 * ds * ds / p.t_coh > 0.25) {
+      const double lb = std::log(pl.beta[m]), la = std::log(A);
+      const double e6 = c6 * std::exp(5.0 * lb - 43.0 / 8.0 * la);
+      const double e2 = 0.5 * std::exp(lb - 11.0 / 8.0 * la);
+      if (e6 > lim6_half || e2 > lim2_half) pl.allow_128 = false;
+      if (e6 > lim6 || e2 > lim2) {
         std::snprintf(buf, sizeof buf, "template %d chirps too fast for the mixed form's anchor spacing; use SRS_PLAIN_FP64", m);
         msg = buf;
         return SRS_ERR_UNSUPPORTED;
@@ -257,20 +258,48 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
   // Deconvolution: with fine grid spacing h = 2 pi / n and kernel half-width
   // alpha = w h / 2, sum_l psi(l h - x) exp(-i k l h) ~= exp(-i k x) alpha phihat(k alpha) / h,
   // so F_k = G_k * (2 / w) / phihat(k pi w / n).
-  std::vector<double> gx, gw;
-  gauss_legendre(128, gx, gw);
-  pl.corr.resize(pl.n_bins);
-  for (int32_t b = 0; b < pl.n_bins; ++b) {
-    double k = (double)(b - pl.half_bins);
-    double ph = es_hat(pl.beta_es, k * kPi * pl.w / pl.n_fine, gx, gw);
-    pl.corr[b] = (2.0 / pl.w) / ph;
-  }
-  pl.tw_re.resize(pl.n_fine);
-  pl.tw_im.resize(pl.n_fine);
-  for (int32_t m = 0; m < pl.n_fine; ++m) {
-    double a = -2.0 * kPi * (double)m / pl.n_fine;
-    pl.tw_re[m] = std::cos(a);
-    pl.tw_im[m] = std::sin(a);
+  // The tables depend on (beta_ES, w, n_fine, n_bins) only; the last few are
+  // kept, so that re-planning a template list costs no quadrature.
+  {
+    struct Tables {
+      double beta_es;
+      int32_t w, n_fine, n_bins;
+      std::vector<double> corr, tw_re, tw_im;
+    };
+    static std::mutex mu;
+    static std::vector<Tables> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    const Tables* hit = nullptr;
+    for (const Tables& t : cache)
+      if (t.beta_es == pl.beta_es && t.w == pl.w && t.n_fine == pl.n_fine && t.n_bins == pl.n_bins) hit = &t;
+    if (!hit) {
+      Tables t;
+      t.beta_es = pl.beta_es;
+      t.w = pl.w;
+      t.n_fine = pl.n_fine;
+      t.n_bins = pl.n_bins;
+      std::vector<double> gx, gw;
+      gauss_legendre(128, gx, gw);
+      t.corr.resize(pl.n_bins);
+      for (int32_t b = 0; b < pl.n_bins; ++b) {
+        double k = (double)(b - pl.half_bins);
+        double ph = es_hat(pl.beta_es, k * kPi * pl.w / pl.n_fine, gx, gw);
+        t.corr[b] = (2.0 / pl.w) / ph;
+      }
+      t.tw_re.resize(pl.n_fine);
+      t.tw_im.resize(pl.n_fine);
+      for (int32_t m = 0; m < pl.n_fine; ++m) {
+        double a = -2.0 * kPi * (double)m / pl.n_fine;
+        t.tw_re[m] = std::cos(a);
+        t.tw_im[m] = std::sin(a);
+      }
+      if (cache.size() >= 8) cache.erase(cache.begin());
+      cache.push_back(std::move(t));
+      hit = &cache.back();
+    }
+    pl.corr = hit->corr;
+    pl.tw_re = hit->tw_re;
+    pl.tw_im = hit->tw_im;
   }
 
   // Default chunk: enough items to keep ~8 per resident CTA of a 152-SM part.
