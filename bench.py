@@ -297,7 +297,7 @@ def run_ours(args):
                 "roofline": roof, "roofline_fma": roof_fma, "roofline_hbm": roof_hbm, "clocks": ck,
                 "gpu_launches": launches,
                 "e2e": e2e, "cpu_baseline": cpu, "plain_fp64": plain,
-                "spread_ms_avg": spread_avg}
+                "spread_ms_avg": spread_avg, "search_device_ms_avg": rep["device_ms"]}
         print(json.dumps(line), flush=True)
     barrier(world)
     ctx.close()

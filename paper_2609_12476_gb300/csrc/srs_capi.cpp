@@ -179,6 +179,11 @@ std::vector<unsigned char> make_key(int kind, const srs_params* p, int64_t n_sam
   return k;
 }
 
+// The search's small device words share one buffer (one memset per search):
+// [0] work-queue counter, [4] top-k ticket, [16..20] error flag and where.
+constexpr size_t kQueueBytes = 128;
+int* search_errflag(srs_ctx* ctx) { return ctx->queue.as<int>() + 16; }
+
 // Pinned error-flag copies: slot 0 for synchronous calls, one slot of eight
 // ints per asynchronous call since the last srs_sync.
 constexpr size_t kHostFlagBytes = (size_t)8 * (1 + srs_ctx::kAsyncSlots) * sizeof(int);
@@ -385,10 +390,10 @@ srs_status autotune_mixed(srs_ctx* ctx, Plan& pl, const float* s32, int use_tma,
           const int ct = only_ctas >= 0 ? only_ctas : ctl[ci];
           float best_ms = 1e30f;
           for (int rep = 0; rep < 3; ++rep) {
-            SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
+            SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, kQueueBytes, ctx->stream), "memset queue");
             SRS_CK(cudaEventRecord(ctx->ev2, ctx->stream), "event");
             SRS_CK(launch_mixed(false, pl.w, s32, ctx->items.as<Item>(), n_items, ctx->betas.as<double>(),
-                                ctx->queue.as<int>(), a, ctx->partial.as<float>(), nullptr, ctx->errflag.as<int>(),
+                                ctx->queue.as<int>(), a, ctx->partial.as<float>(), nullptr, search_errflag(ctx),
                                 ctx->n_sm, ct, ctx->stream), "k_mixed (tuning)");
             SRS_CK(cudaEventRecord(ctx->ev3, ctx->stream), "event");
             SRS_CK(cudaEventSynchronize(ctx->ev3), "tuning");
@@ -493,8 +498,7 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
   long long n_items = (long long)pl.items.size();
   if (mixed) {
     SRS_CK(ctx->partial.ensure(n_items * pl.n_bins * 4), "alloc partial");
-    SRS_CK(ctx->queue.ensure(64), "alloc queue");
-    SRS_CK(ctx->errflag.ensure(64), "alloc error flag");
+    SRS_CK(ctx->queue.ensure(kQueueBytes), "alloc queue");
   } else {
     SRS_CK(ctx->S.ensure(n_map * 8), "alloc S");
   }
@@ -548,11 +552,11 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
                              ctx->n_sm, ctx->stream), "k_to_f32");
         ++launches;
       }
-      SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
-      SRS_CK(cudaMemsetAsync(ctx->errflag.p, 0, 64, ctx->stream), "memset error flag");
+      // one memset clears the work queue, the top-k ticket and the error flag
+      SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, kQueueBytes, ctx->stream), "memset queue");
       SRS_CK(record_kernel_event(k_ev2, ctx->stream, capturing), "event");
       SRS_CK(launch_mixed(false, pl.w, s32, ctx->items.as<Item>(), (int)n_items, ctx->betas.as<double>(),
-                          ctx->queue.as<int>(), a, ctx->partial.as<float>(), nullptr, ctx->errflag.as<int>(),
+                          ctx->queue.as<int>(), a, ctx->partial.as<float>(), nullptr, search_errflag(ctx),
                           ctx->n_sm, ctx->ctas_per_sm, ctx->stream), "k_mixed");
       SRS_CK(record_kernel_event(k_ev3, ctx->stream, capturing), "event");
       ++launches;
@@ -562,7 +566,6 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
                                          ctx->queue.as<int>() + 4, dc, ctx->n_sm, ctx->stream),
                "k_reduce_mixed_top32");
         ++launches;
-        SRS_CK(cudaMemcpyAsync(ctx->hflag, ctx->errflag.p, 32, cudaMemcpyDeviceToHost, ctx->stream), "read error flag");
         return SRS_OK;
       }
       SRS_CK(launch_reduce_mixed(ctx->partial.as<float>(), ctx->item_off.as<int>(), ctx->nseg.as<int>(), n_templates,
@@ -586,8 +589,6 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
                        ctx->topk_b.as<unsigned long long>(), &top, &launches, ctx->stream), "k_topk_tile");
     SRS_CK(launch_keys_to_cands(top, k, pl.n_bins, dc, ctx->stream), "k_keys_to_cands");
     ++launches;
-    if (mixed)
-      SRS_CK(cudaMemcpyAsync(ctx->hflag, ctx->errflag.p, 32, cudaMemcpyDeviceToHost, ctx->stream), "read error flag");
     return SRS_OK;
   };
   std::vector<unsigned char> gkey = ctx->plan_key;
@@ -595,7 +596,7 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
                           (const void*)ctx->keys.p, (const void*)ctx->strain32.p, (const void*)ctx->items.p,
                           (const void*)ctx->betas.p, (const void*)ctx->nseg.p, (const void*)ctx->item_off.p,
                           (const void*)ctx->corr.p, (const void*)ctx->tw.p, (const void*)ctx->queue.p,
-                          (const void*)ctx->errflag.p, (const void*)ctx->topk_a.p, (const void*)ctx->topk_b.p,
+                          (const void*)ctx->topk_a.p, (const void*)ctx->topk_b.p,
                           (const void*)(pl.order.empty() ? nullptr : ctx->order.p),
                           (const void*)ctx->S.p})
     gkey.insert(gkey.end(), (const unsigned char*)&ptr, (const unsigned char*)&ptr + sizeof ptr);
@@ -657,10 +658,11 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
     if (s != SRS_OK) return s;
   }
   SRS_CK(cudaEventRecord(e1, ctx->stream), "event");
+  // the device error flag, to this call's pinned slot (read at return, or at srs_sync)
+  if (mixed)
+    SRS_CK(cudaMemcpyAsync(ctx->hflag + (async_mode ? 8 * (1 + slot) : 0), search_errflag(ctx), 5 * sizeof(int),
+                           cudaMemcpyDeviceToHost, ctx->stream), "read error flag");
   if (async_mode) {
-    if (mixed)
-      SRS_CK(cudaMemcpyAsync(ctx->hflag + 8 * (1 + slot), ctx->errflag.p, 5 * sizeof(int), cudaMemcpyDeviceToHost,
-                             ctx->stream), "read error flag");
     ctx->async_n = slot + 1;
     srs_report& r = ctx->async_rep;
     std::memset(&r, 0, sizeof r);
