@@ -918,6 +918,9 @@ srs_status srs_create(srs_ctx** out, int device, void* cuda_stream) {
     return SRS_ERR_CUDA;
   }
   std::memset(c->hflag, 0, kHostFlagBytes);
+  // SRS_NO_GRAPHS=1: launch the search's kernels directly, not from a captured
+  // graph (profilers replay a direct launch with all of its launch attributes)
+  if (const char* ng = std::getenv("SRS_NO_GRAPHS")) c->use_graphs = !(ng[0] == '1');
   *out = c;
   return SRS_OK;
 }
