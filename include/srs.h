@@ -145,6 +145,14 @@ typedef struct {
   int32_t ctas_per_sm;    /* mixed form: resident CTAs per SM the search asked for (0 = as many as fit) */
 } srs_report;
 
+/* Environment variables read by the library (diagnostics and profiling):
+ *   SRS_NO_TMA=1          never stage samples with TMA bulk copies;
+ *   SRS_MIXED_LAYOUT=T:S[:C:K]  restrict the autotuner to T threads per CTA
+ *                         (128 or 256) and staging S (tma or global), and with
+ *                         C:K to C segments per item and K CTAs per SM;
+ *   SRS_NO_GRAPHS=1       launch a search's kernels directly instead of
+ *                         replaying a captured CUDA graph (read at srs_create). */
+
 /* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
  * the context will use (NULL: the context creates its own non-blocking
  * stream).  *out receives the context.  Errors: SRS_ERR_ARG, SRS_ERR_CUDA. */

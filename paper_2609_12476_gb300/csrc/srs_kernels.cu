@@ -8,11 +8,13 @@
 // (Eqs. weights, semicoherent_statistic), then top-k.
 //
 // Two forms:
-//   mixed  -- k_anchors (FP64, a few samples per segment) + k_mixed (FP32
-//             spreading, shared-memory Stockham FFT, FP32 power/sum) as a
-//             persistent kernel over (template, segment-chunk) items, then an
-//             ordered reduction and top-k;
+//   mixed  -- k_mixed: a persistent kernel over (template, segment-chunk)
+//             items with FP64 anchors of the time map (a few per segment),
+//             FP32 spreading, shared-memory Stockham FFT and FP32 power/sum;
+//             then an ordered FP64 reduction with the top-k
+//             (k_reduce_mixed_top32, or k_reduce_mixed + k_topk_tile);
 //   plain  -- k_plain: one CTA per spectrum, every step in FP64.
+// k_anchors and k_time_map_* expose the time map itself.
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -358,11 +360,12 @@ __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2*
   }
 }
 
-// Persistent CTAs take (template, segment-chunk) items from `queue`.  Per
-// item: FP64 anchors of all its segments; per segment: samples staged in
-// shared memory by a TMA bulk copy (the next segment's copy overlaps this
-// segment's FFT), spread, FFT, deconvolve, then either write F (SPECTRA) or
-// add (P - 2) / 2 into the item's running sum Z.
+// Persistent CTAs take (template, segment-chunk) items from `queue` (in the
+// order `a.order` gives, if any).  Per item: FP64 anchors of all its
+// segments; per segment: samples staged in shared memory by a TMA bulk copy
+// (the next segment's copy overlaps this segment's FFT) or read from global
+// memory (GLOBAL_X), spread, FFT, deconvolve, then either write F (SPECTRA)
+// or add (P - 2) / 2 into the item's running sum Z.
 template <int W, bool SPECTRA, bool INT_KC, bool GLOBAL_X>
 __global__ void __launch_bounds__(kSpreadThreads, 4)
 k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_items,
