@@ -103,7 +103,7 @@ srs_status refine_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
   if (dtype != SRS_F32 && dtype != SRS_F64) return set_err(ctx, SRS_ERR_ARG, "dtype must be SRS_F32 or SRS_F64");
   srs_params pc = *params;
   pc.precision = SRS_MIXED;
-  if (pc.eps < 1e-7) pc.eps = 1e-7;   // direct sums: eps only sizes a NUFFT that is not used here
+  if (pc.eps < kMixedMinEps) pc.eps = kMixedMinEps;   // direct sums: eps only sizes a NUFFT not used here
   pc.chunk = kSparseChunk;
   Plan own;
   if (!planned) {

@@ -190,7 +190,10 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
   };
   const size_t smem_cap = 200 * 1024;
   if (p.precision == SRS_MIXED) {
-    if (p.eps < 1e-7) return fail(SRS_ERR_UNSUPPORTED, "the mixed (FP32) form needs eps >= 1e-7; use SRS_PLAIN_FP64");
+    // FP32 samples, phases and grid leave a floor of about 1.2e-6 relative L2
+    // error per spectrum, so 10 eps must stay above it
+    if (p.eps < kMixedMinEps)
+      return fail(SRS_ERR_UNSUPPORTED, "the mixed (FP32) form needs eps >= 2e-7; use SRS_PLAIN_FP64");
     pl.sigma = p.sigma > 0 ? p.sigma : 2.0;
     es_params(pl.sigma, pl.w, pl.beta_es);
     if (pl.w > kMixedMaxW) return fail(SRS_ERR_UNSUPPORTED, "kernel width above the mixed form's maximum (raise eps or sigma)");

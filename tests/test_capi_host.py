@@ -85,9 +85,14 @@ def test_plan_domain_error_past_coalescence():
 
 
 def test_plan_mixed_form_floor():
-    with pytest.raises(SrsError) as e:
-        srs_plan(Params(eps=1e-9, precision=SRS_MIXED), [1e-2], 7680)
-    assert e.value.status == -5
+    """The mixed form accepts eps down to 2e-7 (its FP32 floor of about 1.2e-6
+    relative error must stay under 10 eps) and refuses anything tighter."""
+    for eps in (1e-9, 1.5e-7):
+        with pytest.raises(SrsError) as e:
+            srs_plan(Params(eps=eps, precision=SRS_MIXED), [1e-2], 7680)
+        assert e.value.status == -5
+    info, _, _ = srs_plan(Params(eps=2e-7, precision=SRS_MIXED), [1e-2], 7680)
+    assert info["w"] == 8
 
 
 def test_plan_items_cover_every_segment_once():

@@ -95,8 +95,8 @@ def test_spectra_two_hours_subset(ctx, two_hours, precision):
 
 
 @pytest.mark.parametrize("precision,eps", [(SRS_MIXED, 1e-2), (SRS_MIXED, 1e-3), (SRS_MIXED, 1e-4),
-                                           (SRS_MIXED, 1e-5), (SRS_PLAIN_FP64, 1e-3), (SRS_PLAIN_FP64, 1e-7),
-                                           (SRS_PLAIN_FP64, 1e-10)])
+                                           (SRS_MIXED, 1e-5), (SRS_MIXED, 2e-7), (SRS_PLAIN_FP64, 1e-3),
+                                           (SRS_PLAIN_FP64, 1e-7), (SRS_PLAIN_FP64, 1e-10)])
 def test_eps_sweep(ctx, two_hours, precision, eps):
     w = two_hours
     mc = w["mc"][[5, 60]]
@@ -337,3 +337,36 @@ def test_async_searches_match_synchronous(ctx):
     # host buffers are refused
     with pytest.raises(ValueError):
         ctx.search_async(xs[0].cpu().numpy(), mc, p, outs[0])
+
+
+def test_search_degenerate_sizes(ctx):
+    """One segment of data; a template that leaves the band inside its first
+    segment (N_seg = 1, FP64 form: the mixed form refuses chirps that fast);
+    top_k at its maximum, 1024."""
+    fs = 256.0
+    x1 = srs_synth.strain_with_chirps(7680, fs, 31, [{"mc": 3e-2, "f0": 50.0, "amp": 0.1}])
+    c, m, rep = ctx.search(x1, [3e-2], Params(eps=1e-6, top_k=4))
+    assert rep["n_spectra"] == 1
+    F = oracle.spectra(x1, fs, 30.0, 40.0, 600, [oracle.beta(3e-2, 40.0)], [(0, 0)])
+    ref = oracle.n_sigma(oracle.power(F, 7680), [1])
+    assert np.max(np.abs(m - ref)) < 1e-3
+    # N_seg = 1 next to a light template, FP64 form
+    x = srs_synth.strain_with_chirps(8 * 7680, fs, 32, [])
+    mc = np.array([0.62, 3e-2])
+    betas = [oracle.beta(v, 40.0) for v in mc]
+    nsegs = [oracle.nseg(b, 40.0, 60.0, 30.0, 8) for b in betas]
+    assert nsegs[0] == 1
+    c, m, rep = ctx.search(x, mc, Params(eps=1e-9, precision=SRS_PLAIN_FP64, top_k=8))
+    assert rep["n_spectra"] == sum(nsegs)
+    items = [(k, i) for k in range(2) for i in range(nsegs[k])]
+    P = oracle.power(oracle.spectra(x, fs, 30.0, 40.0, 600, betas, items), 7680)
+    S = np.zeros((2, 600))
+    for q, (k, _i) in enumerate(items):
+        S[k] += P[q]
+    assert np.max(np.abs(m - oracle.n_sigma(S, nsegs))) < 1e-4
+    # the largest top-k
+    w = srs_synth.make_workload("semicoherent_2h")
+    cands, smap, _ = ctx.search(w["strain"], w["mc"], Params(eps=1e-6, top_k=1024))
+    v, mm, bb = oracle.topk(smap, 1024)
+    assert len(cands) == 1024
+    assert np.array_equal(cands["template_idx"], mm) and np.array_equal(cands["bin"], bb)
