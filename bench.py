@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="semicoherent_2h", choices=sorted(srs_synth.WORKLOADS) + ["learned_6h"])
-    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 and cuFFT comparisons")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
 
@@ -282,6 +282,9 @@ def run_ours(args):
         plain = None
         if not args.no_plain:
             plain = time_plain(ctx, xd, w, stream, flush, n_spec, n_bins, info, pk)
+        fftcmp = None
+        if not args.no_plain and args.workload == "semicoherent_2h":
+            fftcmp = time_fft_comparison(ctx, xd, w, flush)
         cpu = None if (args.no_cpu or world > 1) else cpu_oracle_rate(w, ctx=ctx)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -296,7 +299,7 @@ def run_ours(args):
                            "l2": "flushed (256 MB write) before every timed step"},
                 "roofline": roof, "roofline_fma": roof_fma, "roofline_hbm": roof_hbm, "clocks": ck,
                 "gpu_launches": launches,
-                "e2e": e2e, "cpu_baseline": cpu, "plain_fp64": plain,
+                "e2e": e2e, "cpu_baseline": cpu, "plain_fp64": plain, "cufft_comparison": fftcmp,
                 "spread_ms_avg": spread_avg, "search_device_ms_avg": rep["device_ms"]}
         print(json.dumps(line), flush=True)
     barrier(world)
@@ -371,6 +374,36 @@ def time_plain(ctx, xd, w, stream, flush, n_spec, n_bins, info, pk, steps=3):
     hbm_peak = pk["hbm_gbs"] if pk else 6800.0
     return {"value": n_spec * steps / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / steps,
             "kernel": "k_plain", "hbm_achieved_gbs": ach, "hbm_frac": ach / hbm_peak, "steps": steps}
+
+
+def time_fft_comparison(ctx, xd, w, flush, steps=3, seg_end=112):
+    """The transform stage fused (k_mixed: spread, shared-memory FFT and
+    deconvolution in one kernel) against the unfused comparison (k_mixed
+    writes the spread grids to HBM, cuFFT's batched C2C transforms them,
+    k_grid_deconv deconvolves): segment spectra of every template for
+    segments [0, seg_end), device times from the library's CUDA events."""
+    import torch
+    from paper_2609_12476_gb300 import SRS_MIXED
+    p = params_for(w, SRS_MIXED)
+    res = {}
+    for via in (False, True):
+        ctx.segment_spectra(xd, w["mc"], 0, seg_end, p, via_cufft=via)
+        torch.cuda.synchronize()
+        dev, sp, ff = [], [], []
+        for _ in range(steps):
+            flush.zero_()
+            _, rep = ctx.segment_spectra(xd, w["mc"], 0, seg_end, p, via_cufft=via)
+            torch.cuda.synchronize()
+            dev.append(rep["device_ms"])
+            sp.append(rep["spread_ms"])
+            ff.append(rep["fft_ms"])
+        res[via] = (float(np.mean(dev)), float(np.mean(sp)), float(np.mean(ff)), int(rep["n_fine"]))
+    n_spec = len(w["mc"]) * seg_end
+    fu, un = res[False], res[True]
+    return {"spectra": n_spec, "segments": [0, seg_end], "fused_ms": fu[0],
+            "unfused_ms": un[0], "unfused_spread_ms": un[1], "unfused_cufft_ms": un[2],
+            "unfused_deconv_ms": un[0] - un[1] - un[2], "grid_bytes": n_spec * un[3] * 8,
+            "fused_speedup": un[0] / fu[0] if fu[0] > 0 else None, "steps": steps}
 
 
 def barrier(world):

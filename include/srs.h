@@ -143,6 +143,7 @@ typedef struct {
   int32_t cta_threads;    /* threads per CTA of the transform kernel */
   int32_t staging;        /* mixed form: 1 = samples staged by TMA bulk copies, 0 = read from global memory */
   int32_t ctas_per_sm;    /* mixed form: resident CTAs per SM the search asked for (0 = as many as fit) */
+  double fft_ms;          /* srs_segment_spectra_cufft only: device time of the cuFFT transforms */
 } srs_report;
 
 /* Environment variables read by the library (diagnostics and profiling):
@@ -217,6 +218,23 @@ srs_status srs_segment_spectra(srs_ctx* ctx, const void* strain, int64_t n_sampl
                                int32_t dtype, const double* mc, int32_t n_templates,
                                int32_t seg_begin, int32_t seg_end, const srs_params* params,
                                double* F, srs_report* report);
+
+/* Timed comparison only: the same segment spectra as srs_segment_spectra()
+ * in the mixed form, computed unfused.  k_mixed writes each segment's spread
+ * grid (n_fine complex float, Sec. III.B spreading step) to device memory,
+ * cuFFT's batched single-precision C2C forward transform runs on it, and a
+ * third kernel deconvolves and selects the band.  Arguments, layout and
+ * ownership as srs_segment_spectra(); params->precision must be SRS_MIXED.
+ * The grid scratch (n_templates * (seg_end-seg_begin) * n_fine * 8 bytes) and
+ * the cuFFT plan belong to the context.  report->spread_ms is the spreading
+ * kernel (after the FP32 strain copy, for float64 strain), report->fft_ms the
+ * transforms, report->device_ms everything.
+ * SRS_ERR_UNSUPPORTED when libcufft cannot be loaded at run time (the rest of
+ * the library does not depend on it); SRS_ERR_ARG for another precision. */
+srs_status srs_segment_spectra_cufft(srs_ctx* ctx, const void* strain, int64_t n_samples,
+                                     int32_t dtype, const double* mc, int32_t n_templates,
+                                     int32_t seg_begin, int32_t seg_end, const srs_params* params,
+                                     double* F, srs_report* report);
 
 /* The time map alone (Sec. III.B Eq. new_t), as the chosen precision form
  * evaluates it inside the spreader, for n_items (template, segment) pairs:

@@ -22,7 +22,7 @@ SRS_PLAIN_FP64, SRS_MIXED = 0, 1
 
 # Entry points declared in include/srs.h (checked by the tests).
 EXPORTS = ("srs_create", "srs_destroy", "srs_last_error", "srs_plan", "srs_search", "srs_search_async", "srs_sync",
-           "srs_segment_spectra", "srs_time_map", "srs_segment_spectra_static", "srs_make_strain",
+           "srs_segment_spectra", "srs_segment_spectra_cufft", "srs_time_map", "srs_segment_spectra_static", "srs_make_strain",
            "srs_patches", "srs_mlp_forward", "srs_mlp_grad", "srs_mlp_train", "srs_score_map", "srs_refine",
            "srs_search_proposed")
 MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 297, 64, 19137
@@ -58,7 +58,8 @@ class _Report(ctypes.Structure):
                 ("n_spectra", ctypes.c_int64), ("w", ctypes.c_int32), ("n_fine", ctypes.c_int32),
                 ("sigma", ctypes.c_double), ("beta_es", ctypes.c_double), ("chunk", ctypes.c_int32),
                 ("n_items", ctypes.c_int32), ("kernel_launches", ctypes.c_int32), ("spread_ms", ctypes.c_double),
-                ("cta_threads", ctypes.c_int32), ("staging", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("cta_threads", ctypes.c_int32), ("staging", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("fft_ms", ctypes.c_double)]
 
 
 class _Injection(ctypes.Structure):
@@ -137,9 +138,10 @@ def lib():
                                        ctypes.POINTER(i32)]
         L.srs_sync.restype = i32
         L.srs_sync.argtypes = [vp, ctypes.POINTER(_Report)]
-        L.srs_segment_spectra.restype = i32
-        L.srs_segment_spectra.argtypes = [vp, vp, i64, i32, vp, i32, i32, i32, ctypes.POINTER(_Params), vp,
-                                          ctypes.POINTER(_Report)]
+        for fn in (L.srs_segment_spectra, L.srs_segment_spectra_cufft):
+            fn.restype = i32
+            fn.argtypes = [vp, vp, i64, i32, vp, i32, i32, i32, ctypes.POINTER(_Params), vp,
+                           ctypes.POINTER(_Report)]
         L.srs_time_map.restype = i32
         L.srs_time_map.argtypes = [vp, vp, i32, vp, vp, i32, ctypes.POINTER(_Params), i64, vp, vp]
         f32p = ctypes.POINTER(ctypes.c_float)
@@ -292,9 +294,12 @@ class Context:
         self._check(self._lib.srs_sync(self._h, ctypes.byref(rep)))
         return _report_dict(rep)
 
-    def segment_spectra(self, strain, mc, seg_begin, seg_end, params):
+    def segment_spectra(self, strain, mc, seg_begin, seg_end, params, via_cufft=False):
         """srs_segment_spectra: complex128 [templates, seg_end - seg_begin, n_bins]
-        (numpy for host strain, torch for a CUDA tensor)."""
+        (numpy for host strain, torch for a CUDA tensor).  via_cufft=True calls
+        srs_segment_spectra_cufft, the unfused comparison (spread grids in HBM,
+        cuFFT transforms, deconvolution)."""
+        fn = self._lib.srs_segment_spectra_cufft if via_cufft else self._lib.srs_segment_spectra
         mc = np.ascontiguousarray(mc, dtype=np.float64)
         dt = _dtype_code(strain)
         p = params.c()
@@ -305,17 +310,15 @@ class Context:
             import torch
             p.io_on_device = 1
             F = torch.empty(shape, dtype=torch.complex128, device=strain.device)
-            st = self._lib.srs_segment_spectra(self._h, strain.data_ptr(), strain.numel(), dt, mc.ctypes.data,
-                                               mc.size, int(seg_begin), int(seg_end), ctypes.byref(p),
-                                               F.data_ptr(), ctypes.byref(rep))
+            st = fn(self._h, strain.data_ptr(), strain.numel(), dt, mc.ctypes.data, mc.size, int(seg_begin),
+                    int(seg_end), ctypes.byref(p), F.data_ptr(), ctypes.byref(rep))
             self._check(st)
             return F, _report_dict(rep)
         strain = np.ascontiguousarray(strain)
         p.io_on_device = 0
         F = np.empty(shape, dtype=np.complex128)
-        st = self._lib.srs_segment_spectra(self._h, strain.ctypes.data, strain.size, dt, mc.ctypes.data, mc.size,
-                                           int(seg_begin), int(seg_end), ctypes.byref(p), F.ctypes.data,
-                                           ctypes.byref(rep))
+        st = fn(self._h, strain.ctypes.data, strain.size, dt, mc.ctypes.data, mc.size, int(seg_begin),
+                int(seg_end), ctypes.byref(p), F.ctypes.data, ctypes.byref(rep))
         self._check(st)
         return F, _report_dict(rep)
 

@@ -4,12 +4,15 @@
 // (srs_plan.cpp) into kernel launches (srs_kernels.cu), and copies results to
 // the caller's buffers.  No exception crosses the ABI.
 #include <cuda_runtime.h>
+#include <cufft.h>
+#include <dlfcn.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -749,9 +752,41 @@ srs_status srs::sync_impl(srs_ctx* ctx, srs_report* report) {
 
 namespace {
 
+// cuFFT, loaded when the comparison path first runs (the rest of the library
+// does not depend on it).
+struct CufftApi {
+  bool tried = false, ok = false;
+  decltype(&cufftPlanMany) plan_many = nullptr;
+  decltype(&cufftSetStream) set_stream = nullptr;
+  decltype(&cufftExecC2C) exec_c2c = nullptr;
+  decltype(&cufftDestroy) destroy = nullptr;
+};
+CufftApi& cufft_api() {
+  static CufftApi api;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!api.tried) {
+    api.tried = true;
+    std::vector<std::string> names = {"libcufft.so.12", "libcufft.so"};
+    if (const char* home = std::getenv("CUDA_HOME")) names.push_back(std::string(home) + "/lib64/libcufft.so.12");
+    names.push_back("/usr/local/cuda/lib64/libcufft.so.12");
+    void* h = nullptr;
+    for (const std::string& n : names)
+      if (!h) h = dlopen(n.c_str(), RTLD_NOW | RTLD_LOCAL);
+    if (h) {
+      api.plan_many = reinterpret_cast<decltype(&cufftPlanMany)>(dlsym(h, "cufftPlanMany"));
+      api.set_stream = reinterpret_cast<decltype(&cufftSetStream)>(dlsym(h, "cufftSetStream"));
+      api.exec_c2c = reinterpret_cast<decltype(&cufftExecC2C)>(dlsym(h, "cufftExecC2C"));
+      api.destroy = reinterpret_cast<decltype(&cufftDestroy)>(dlsym(h, "cufftDestroy"));
+      api.ok = api.plan_many && api.set_stream && api.exec_c2c && api.destroy;
+    }
+  }
+  return api;
+}
+
 srs_status spectra_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype, const double* mc,
                         int32_t n_templates, int32_t seg_begin, int32_t seg_end, const srs_params* params,
-                        double* F, srs_report* report) {
+                        double* F, srs_report* report, bool via_cufft = false) {
   srs_status s = check_common(ctx, strain, dtype, params);
   if (s != SRS_OK) return s;
   if (!F) return set_err(ctx, SRS_ERR_ARG, "F is NULL");
@@ -760,6 +795,8 @@ srs_status spectra_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int
   if (s != SRS_OK) return s;
   const Plan& pl = *plp;
   const bool mixed = pl.precision == SRS_MIXED;
+  if (via_cufft && !mixed) return set_err(ctx, SRS_ERR_ARG, "the cuFFT comparison runs the mixed form only");
+  if (via_cufft && !cufft_api().ok) return set_err(ctx, SRS_ERR_UNSUPPORTED, "libcufft could not be loaded");
   const bool f64 = dtype == SRS_F64;
   const int on_dev = params->io_on_device;
   const void* dstrain = nullptr;
@@ -784,12 +821,43 @@ srs_status spectra_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int
     if (s != SRS_OK) return s;
     staged = a.use_tma;
     if (f64) ++launches;
+    const long long n_spec = (long long)n_templates * range;
+    if (via_cufft) {
+      SRS_CK(ctx->grid.ensure((size_t)n_spec * pl.n_fine * sizeof(float2)), "alloc grid");
+      a.grid_out = ctx->grid.as<float2>();
+    }
     SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
     SRS_CK(cudaMemsetAsync(ctx->errflag.p, 0, 64, ctx->stream), "memset error flag");
     SRS_CK(launch_mixed(true, pl.w, s32, ctx->items.as<Item>(), (int)n_items, ctx->betas.as<double>(),
                         ctx->queue.as<int>(), a, nullptr, dF, ctx->errflag.as<int>(), ctx->n_sm, 0, ctx->stream),
            "k_mixed");
     launches += 1;
+    if (via_cufft) {
+      // unfused comparison: batched single-precision C2C transforms of the
+      // spread grids in HBM, then deconvolution and band selection
+      CufftApi& api = cufft_api();
+      SRS_CK(cudaEventRecord(ctx->ev2, ctx->stream), "event");
+      if (!ctx->fft_plan_ok || ctx->fft_n != pl.n_fine || ctx->fft_batch != n_spec) {
+        if (ctx->fft_plan_ok) api.destroy(ctx->fft_plan);
+        ctx->fft_plan_ok = false;
+        int n = pl.n_fine;
+        cufftHandle h;
+        if (api.plan_many(&h, 1, &n, nullptr, 1, n, nullptr, 1, n, CUFFT_C2C, (int)n_spec) != CUFFT_SUCCESS)
+          return set_err(ctx, SRS_ERR_CUDA, "cufftPlanMany failed");
+        ctx->fft_plan = h;
+        ctx->fft_plan_ok = true;
+        ctx->fft_n = pl.n_fine;
+        ctx->fft_batch = n_spec;
+      }
+      if (api.set_stream(ctx->fft_plan, ctx->stream) != CUFFT_SUCCESS ||
+          api.exec_c2c(ctx->fft_plan, reinterpret_cast<cufftComplex*>(ctx->grid.p),
+                       reinterpret_cast<cufftComplex*>(ctx->grid.p), CUFFT_FORWARD) != CUFFT_SUCCESS)
+        return set_err(ctx, SRS_ERR_CUDA, "cufftExecC2C failed");
+      SRS_CK(cudaEventRecord(ctx->ev3, ctx->stream), "event");
+      SRS_CK(launch_grid_deconv(ctx->grid.as<float2>(), n_spec, pl.n_fine, pl.n_bins, pl.half_bins,
+                                ctx->corr.as<float>(), dF, ctx->n_sm, ctx->stream), "k_grid_deconv");
+      launches += 2;
+    }
   } else {
     PlainArgs p = plain_args(pl, ctx, seg_begin, range);
     SRS_CK(launch_plain(f64, true, dstrain, ctx->betas.as<double>(), ctx->nseg.as<int>(), p, range, n_templates,
@@ -818,6 +886,10 @@ srs_status spectra_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int
     report->cta_threads = mixed ? pl.threads : 256;
     report->staging = staged;
     report->kernel_launches = launches;
+    if (via_cufft) {
+      report->spread_ms = elapsed_ms(ctx->ev0, ctx->ev2);
+      report->fft_ms = elapsed_ms(ctx->ev2, ctx->ev3);
+    }
   }
   return SRS_OK;
 }
@@ -935,6 +1007,7 @@ void srs_destroy(srs_ctx* c) {
       if (e) cudaEventDestroy(e);
   for (cudaEvent_t& e : c->pev)
     if (e) cudaEventDestroy(e);
+  if (c->fft_plan_ok) cufft_api().destroy(c->fft_plan);
   if (c->hflag) cudaFreeHost(c->hflag);
   for (DevBuf* b : c->all_buffers()) b->release();
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -974,6 +1047,18 @@ srs_status srs_search(srs_ctx* ctx, const void* strain, int64_t n_samples, int32
                       int32_t* n_cands, srs_report* report) {
   try {
     return search_impl(ctx, strain, n_samples, dtype, mc, n_templates, params, stat_map, cands, n_cands, report);
+  } catch (const std::bad_alloc&) {
+    return set_err(ctx, SRS_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return set_err(ctx, SRS_ERR_ARG, "unexpected host error");
+  }
+}
+
+srs_status srs_segment_spectra_cufft(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype,
+                                     const double* mc, int32_t n_templates, int32_t seg_begin, int32_t seg_end,
+                                     const srs_params* params, double* F, srs_report* report) {
+  try {
+    return spectra_impl(ctx, strain, n_samples, dtype, mc, n_templates, seg_begin, seg_end, params, F, report, true);
   } catch (const std::bad_alloc&) {
     return set_err(ctx, SRS_ERR_OOM, "host allocation failed");
   } catch (...) {

@@ -70,18 +70,23 @@ struct srs_ctx {
   srs_status async_status = SRS_OK;   // a failure found when the slots ran out and were synced
   std::string async_err;
   srs_report async_rep = {};          // sizes of the last asynchronous call
+  // cuFFT plan of the unfused comparison path (handle valid when fft_plan_ok)
+  int fft_plan = 0;
+  bool fft_plan_ok = false;
+  int fft_n = 0;
+  long long fft_batch = 0;
   // events around a whole proposal search (it runs searches that use the others)
   cudaEvent_t pev[2] = {nullptr, nullptr};
   // the captured graph (kept for its event-record nodes, re-pointed per launch)
   cudaGraph_t graph = nullptr;
   cudaGraphNode_t graph_ev_node[2] = {nullptr, nullptr};
-  srs::DevBuf items, order, anchors, partial, betas, nseg, item_off, corr, tw, keys, topk_a, topk_b, cands, queue, strain,
+  srs::DevBuf items, order, grid, anchors, partial, betas, nseg, item_off, corr, tw, keys, topk_a, topk_b, cands, queue, strain,
       strain32, errflag, map, S, F, psi, th, im, ii;
   // learned proposal
   srs::DevBuf xb, yb, z1, logits, dz, lossv, grad, wts, adam_m, adam_v, w1h, w2h, idx, patches, cells_m, cells_b,
       sp_items, sp_bins, sp_partial, sp_cells, sp_out, sp_betas, cmap, ccands, inj;
   std::vector<srs::DevBuf*> all_buffers() {
-    return {&items, &order, &anchors, &partial, &betas, &nseg, &item_off, &corr, &tw, &keys, &topk_a, &topk_b, &cands,
+    return {&items, &order, &grid, &anchors, &partial, &betas, &nseg, &item_off, &corr, &tw, &keys, &topk_a, &topk_b, &cands,
             &queue, &strain, &strain32, &errflag, &map, &S, &F, &psi, &th, &im, &ii, &xb, &yb, &z1, &logits, &dz,
             &lossv, &grad, &wts, &adam_m, &adam_v, &w1h, &w2h, &idx, &patches, &cells_m, &cells_b, &sp_items,
             &sp_bins, &sp_partial, &sp_cells, &sp_out, &sp_betas, &cmap, &ccands, &inj};

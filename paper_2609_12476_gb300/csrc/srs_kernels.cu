@@ -431,6 +431,13 @@ k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_
       }
       __syncthreads();
       if (!GLOBAL_X && tid == 0 && i + 1 < it.i1) bulk_load(xs, strain + (long long)(i + 1) * a.n_s, seg_bytes, &s_bar);
+      if (SPECTRA && a.grid_out) {
+        // the spread grid alone, for an FFT outside this kernel
+        float2* go = a.grid_out + ((long long)it.m * a.seg_range + (i - a.seg_begin)) * a.n_fine;
+        for (int j = tid; j < a.n_fine; j += blockDim.x) go[j] = g0[j];
+        __syncthreads();
+        continue;
+      }
       float2* res = a.fft_fixed == 1200 ? fft_1200<float2>(g0, g1, tw)
                                         : fft_smem<float2>(g0, g1, a.n_fine, s_rad, a.n_pass, tw);
       for (int b = tid; b < a.n_bins; b += blockDim.x) {
@@ -450,6 +457,21 @@ k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_
     }
     if (!SPECTRA)
       for (int b = tid; b < a.n_bins; b += blockDim.x) partial[(long long)qi * a.n_bins + b] = Z[b];
+  }
+}
+
+// Deconvolution and band selection of externally transformed grids.
+__global__ void k_grid_deconv(const float2* __restrict__ grid, long long n_spec, int n_fine, int n_bins,
+                              int half_bins, const float* __restrict__ corr, double2* __restrict__ F) {
+  const long long total = n_spec * n_bins;
+  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < total;
+       f += (long long)gridDim.x * blockDim.x) {
+    const long long sp = f / n_bins;
+    const int b = (int)(f - sp * n_bins);
+    const int k = b - half_bins;
+    const float2 G = grid[sp * n_fine + (k < 0 ? k + n_fine : k)];
+    const float c = corr[b];
+    F[f] = make_double2(G.x * c, G.y * c);
   }
 }
 
@@ -874,6 +896,16 @@ cudaError_t launch_reduce_mixed_top32(const float* partial, const int* item_off,
   if (blocks > (long long)n_sm * 4) blocks = (long long)n_sm * 4;
   k_reduce_mixed_top32<<<(unsigned)blocks, 256, 0, st>>>(partial, item_off, nseg, n_templates, n_bins, map, k,
                                                           scratch, ticket, cands);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grid_deconv(const float2* grid, long long n_spec, int n_fine, int n_bins, int half_bins,
+                               const float* corr, double2* F, int n_sm, cudaStream_t st) {
+  const long long total = n_spec * n_bins;
+  if (total <= 0) return cudaSuccess;
+  long long blocks = (total + 255) / 256;
+  if (blocks > (long long)n_sm * 16) blocks = (long long)n_sm * 16;
+  k_grid_deconv<<<(unsigned)blocks, 256, 0, st>>>(grid, n_spec, n_fine, n_bins, half_bins, corr, F);
   return cudaGetLastError();
 }
 

@@ -35,6 +35,8 @@ struct MixedArgs {
   const float* corr;              // [n_bins] deconvolution factors
   const float* tw;                // [2 n_fine] interleaved exp(-2 pi i m / n_fine)
   const int* order;               // [n_items] queue position -> item, or NULL (item order)
+  float2* grid_out;               // spectra mode: write the spread grid [template][segment][n_fine]
+                                  // here and skip FFT / deconvolution (the cuFFT comparison), or NULL
   int8_t radices[16];
 };
 
@@ -66,6 +68,10 @@ cudaError_t launch_reduce_mixed(const float* partial, const int* item_off, const
 cudaError_t launch_reduce_mixed_top32(const float* partial, const int* item_off, const int* nseg, int n_templates,
                                       int n_bins, float* map, int k, unsigned long long* scratch, int* ticket,
                                       srs_candidate* cands, int n_sm, cudaStream_t st);
+// F[s][b] = G[s][k(b)] * corr[b] for the grids G of n_spec spectra (after an
+// external FFT), k(b) = b - half_bins wrapped into [0, n_fine).
+cudaError_t launch_grid_deconv(const float2* grid, long long n_spec, int n_fine, int n_bins, int half_bins,
+                               const float* corr, double2* F, int n_sm, cudaStream_t st);
 cudaError_t launch_finish_plain(const double* S, const int* nseg, int n_templates, int n_bins, float* map,
                                 unsigned long long* keys, int n_sm, cudaStream_t st);
 long long topk_scratch_keys(long long n, int k);

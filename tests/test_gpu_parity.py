@@ -370,3 +370,32 @@ def test_search_degenerate_sizes(ctx):
     v, mm, bb = oracle.topk(smap, 1024)
     assert len(cands) == 1024
     assert np.array_equal(cands["template_idx"], mm) and np.array_equal(cands["bin"], bb)
+
+
+def test_cufft_comparison_path_matches_oracle_and_fused(ctx, two_hours):
+    """srs_segment_spectra_cufft (spread grids in HBM, cuFFT C2C, separate
+    deconvolution) computes the same spectra as the fused kernel: both within
+    10 eps of the oracle, and within FP32 rounding of each other."""
+    w = two_hours
+    p = Params(precision=SRS_MIXED, eps=1e-6)
+    mc = w["mc"][[0, 31, 63]]
+    F, _ = ctx.segment_spectra(w["strain"], mc, 0, 3, p)
+    Fc, rep = ctx.segment_spectra(w["strain"], mc, 0, 3, p, via_cufft=True)
+    betas = [oracle.beta(m, 40.0) for m in mc]
+    items = [(m, i) for m in range(3) for i in range(3)]
+    R = oracle.spectra(w["strain"], 256.0, 30.0, 40.0, 600, betas, items).reshape(3, 3, 600)
+    assert rel_l2(Fc, R).max() <= 1e-5
+    assert rel_l2(Fc, F).max() <= 2e-6
+    assert rep["kernel_launches"] >= 3 and rep["fft_ms"] > 0 and rep["spread_ms"] > 0
+    # device-resident strain, a larger batch that re-plans cuFFT, then the first size again
+    torch = pytest.importorskip("torch")
+    xd = torch.from_numpy(np.ascontiguousarray(w["strain"])).cuda()
+    mcb = w["mc"][:16]
+    Fd, _ = ctx.segment_spectra(xd, mcb, 10, 30, p)
+    Fdc, _ = ctx.segment_spectra(xd, mcb, 10, 30, p, via_cufft=True)
+    assert rel_l2(Fdc.cpu().numpy(), Fd.cpu().numpy()).max() <= 2e-6
+    Fc2, _ = ctx.segment_spectra(w["strain"], mc, 0, 3, p, via_cufft=True)
+    # shared-memory atomics in the spreader sum in no fixed order: equal up to FP32 rounding
+    assert rel_l2(Fc2, Fc).max() <= 1e-6
+    with pytest.raises(SrsError):
+        ctx.segment_spectra(w["strain"], mc, 0, 1, Params(precision=SRS_PLAIN_FP64, eps=1e-6), via_cufft=True)
