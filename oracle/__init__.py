@@ -39,6 +39,8 @@ def load(path):
         L.orc_nseg.restype = i32; L.orc_nseg.argtypes = [d, d, d, d, i32, ctypes.c_int]
         L.orc_spectra.restype = ctypes.c_int
         L.orc_spectra.argtypes = [P, i64, d, d, d, i32, P, P, P, i32, ctypes.c_int, P, P]
+        L.orc_spectra_ex.restype = ctypes.c_int
+        L.orc_spectra_ex.argtypes = [P, i64, d, d, d, i32, P, P, P, i32, ctypes.c_int, ctypes.c_int, P, P]
     return L
 
 
@@ -83,10 +85,12 @@ def nseg(beta_, f_ref, f_hi, t_coh, n_total, cut=True):
                               int(n_total), 1 if cut else 0))
 
 
-def spectra(strain, fs, t_coh, f_lo, n_b, betas, items, n_threads=None):
+def spectra(strain, fs, t_coh, f_lo, n_b, betas, items, n_threads=None, local=False):
     """Direct non-uniform DFT F(f_b) = sum_j x_j exp(-2 pi i f_b delta_j) for each
     (template m, segment i) in `items`; f_b = f_lo + b / t_coh.  Returns complex
-    array [len(items), n_b]."""
+    array [len(items), n_b].  local=True resamples every segment with a 0PN
+    template that starts at the segment's first sample (delta_j = tau(s_j) -
+    tau(0) with beta_m), the per-segment form of Sec. III.C's stack-slide."""
     strain = np.ascontiguousarray(strain, dtype=np.float64)
     betas = np.ascontiguousarray(betas, dtype=np.float64)
     items = np.asarray(items, dtype=np.int32).reshape(-1, 2)
@@ -95,9 +99,9 @@ def spectra(strain, fs, t_coh, f_lo, n_b, betas, items, n_threads=None):
     re = np.zeros((n, n_b)); im = np.zeros((n, n_b))
     if n_threads is None:
         n_threads = os.cpu_count() or 1
-    rc = lib().orc_spectra(strain.ctypes.data, strain.size, float(fs), float(t_coh), float(f_lo),
-                           int(n_b), betas.ctypes.data, im_.ctypes.data, ii_.ctypes.data, n,
-                           int(n_threads), re.ctypes.data, im.ctypes.data)
+    rc = lib().orc_spectra_ex(strain.ctypes.data, strain.size, float(fs), float(t_coh), float(f_lo),
+                              int(n_b), betas.ctypes.data, im_.ctypes.data, ii_.ctypes.data, n,
+                              int(n_threads), 1 if local else 0, re.ctypes.data, im.ctypes.data)
     if rc != 0:
         raise ValueError("oracle: bad arguments to spectra")
     return re + 1j * im

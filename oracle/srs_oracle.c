@@ -106,7 +106,7 @@ static void spectrum(const double* x, int64_t n_s, double fs, double beta, doubl
 typedef struct {
   const double* strain; int64_t n_s; double fs; double t_coh; double f_lo; int32_t n_b;
   const double* betas; const int32_t* item_m; const int32_t* item_i; int32_t n_items;
-  double* out_re; double* out_im; int32_t next; pthread_mutex_t mu;
+  double* out_re; double* out_im; int32_t next; pthread_mutex_t mu; int local;
 } orc_job;
 
 static void* worker(void* arg) {
@@ -117,7 +117,9 @@ static void* worker(void* arg) {
     pthread_mutex_unlock(&J->mu);
     if (k >= J->n_items) break;
     int32_t m = J->item_m[k], i = J->item_i[k];
-    double t_i0 = (double)i * (double)J->n_s / J->fs;
+    /* local: the 0PN template starts at the segment's own first sample (the
+     * per-segment resampling of Sec. III.C's stack-slide), so t_i0 = 0 */
+    double t_i0 = J->local ? 0.0 : (double)i * (double)J->n_s / J->fs;
     spectrum(J->strain + (int64_t)i * J->n_s, J->n_s, J->fs, J->betas[m], t_i0, J->f_lo,
              J->t_coh, J->n_b, J->out_re + (int64_t)k * J->n_b, J->out_im + (int64_t)k * J->n_b);
   }
@@ -125,18 +127,20 @@ static void* worker(void* arg) {
 }
 
 /* Spectra for a list of (template m, segment i) items; segment i covers samples
- * [i n_s, (i+1) n_s) of `strain`.  Each item is computed by one thread start to
- * finish, so the result does not depend on n_threads.  Returns 0, or -1 on a
- * bad argument. */
-int orc_spectra(const double* strain, int64_t n_samples, double fs, double t_coh, double f_lo,
-                int32_t n_b, const double* betas, const int32_t* item_m, const int32_t* item_i,
-                int32_t n_items, int n_threads, double* out_re, double* out_im) {
+ * [i n_s, (i+1) n_s) of `strain`.  With local = 0 the template's track starts at
+ * t = 0 (delta referenced to t_i0 = i T); with local = 1 each segment is
+ * resampled with a 0PN template that starts at the segment's first sample.
+ * Each item is computed by one thread start to finish, so the result does not
+ * depend on n_threads.  Returns 0, or -1 on a bad argument. */
+int orc_spectra_ex(const double* strain, int64_t n_samples, double fs, double t_coh, double f_lo,
+                   int32_t n_b, const double* betas, const int32_t* item_m, const int32_t* item_i,
+                   int32_t n_items, int n_threads, int local, double* out_re, double* out_im) {
   int64_t n_s = (int64_t)llround(t_coh * fs);
   if (n_s <= 0 || n_b <= 0 || n_items < 0 || n_threads <= 0) return -1;
   for (int32_t k = 0; k < n_items; ++k)
     if (item_i[k] < 0 || (int64_t)(item_i[k] + 1) * n_s > n_samples) return -1;
   orc_job J = {strain, n_s, fs, t_coh, f_lo, n_b, betas, item_m, item_i, n_items,
-               out_re, out_im, 0, PTHREAD_MUTEX_INITIALIZER};
+               out_re, out_im, 0, PTHREAD_MUTEX_INITIALIZER, local ? 1 : 0};
   if (n_threads > 256) n_threads = 256;
   pthread_t th[256];
   int started = 0;
@@ -145,4 +149,11 @@ int orc_spectra(const double* strain, int64_t n_samples, double fs, double t_coh
   if (started == 0) worker(&J);
   for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
   return 0;
+}
+
+int orc_spectra(const double* strain, int64_t n_samples, double fs, double t_coh, double f_lo,
+                int32_t n_b, const double* betas, const int32_t* item_m, const int32_t* item_i,
+                int32_t n_items, int n_threads, double* out_re, double* out_im) {
+  return orc_spectra_ex(strain, n_samples, fs, t_coh, f_lo, n_b, betas, item_m, item_i, n_items,
+                        n_threads, 0, out_re, out_im);
 }

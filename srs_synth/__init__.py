@@ -105,6 +105,85 @@ WORKLOADS = {
 }
 
 
+def slide_rows(mc_list, f_hi, t_coh, bin_step=1.0):
+    """Rows of a stack-slide template grid theta = {Mc, t0}: for each chirp mass,
+    t0 fractions c = q / Q (q < Q) of a segment, with Q chosen so that moving t0
+    by T / Q moves the band-edge frequency f_hi by at most bin_step bins:
+    Q = max(1, ceil(fdot(f_hi) T^2 / bin_step)), fdot(f) = f beta(Mc, f).
+    Returns (mc [R], c [R]) float arrays."""
+    mcs, cs = [], []
+    for mc in np.asarray(mc_list, dtype=np.float64):
+        fdot = f_hi * chirp_beta(float(mc), f_hi)
+        q_n = max(1, int(math.ceil(fdot * t_coh * t_coh / bin_step)))
+        for q in range(q_n):
+            mcs.append(float(mc))
+            cs.append(q / q_n)
+    return np.asarray(mcs), np.asarray(cs)
+
+
+def random_cube(n_beta, n_bins, n_seg, seed):
+    """A power cube [n_beta][n_bins][n_seg] float32 of independent chi-square
+    (2 degrees of freedom) draws, the distribution of P = 2 |F|^2 / n_s for
+    white unit-variance noise (mean 2), from numpy's PCG64 stream `seed`."""
+    r = np.random.default_rng(seed)
+    return r.exponential(2.0, size=(n_beta, n_bins, n_seg)).astype(np.float32)
+
+
+# Two-stage (cube + stack-slide) workloads: the local resampling bank of the
+# paper (69 templates uniform in beta over 3e-8..7e-4 1/s), tracks entering
+# the band at f0 = 40 Hz at t0.
+SLIDE_WORKLOADS = {
+    # 6 h float64, 48 chirp masses 5e-4..1e-1, 4 chirps entering the band after t = 0
+    "stackslide_6h": dict(fs=256.0, t_obs=21600.0, t_coh=30.0, f_lo=40.0, f_hi=60.0, eps=1e-6,
+                          seed=0, dtype="f64", top_k=32, bank=(3e-8, 7e-4, 69),
+                          mc=("log", 5e-4, 1e-1, 48), bin_step=1.0,
+                          injections=[{"mc": 2e-2, "t_start": 3000.0, "amp": 0.06},
+                                      {"mc": 6e-2, "t_start": 9015.0, "amp": 0.06},
+                                      {"mc": 3e-3, "t_start": 600.0, "amp": 0.03},
+                                      {"mc": 9e-2, "t_start": 15012.0, "amp": 0.08}]),
+    # 24 h float32, 256 chirp masses 5e-4..1e-1, 16 chirps entering at random times
+    "stackslide_24h": dict(fs=256.0, t_obs=86400.0, t_coh=30.0, f_lo=40.0, f_hi=60.0, eps=1e-6,
+                           seed=0, dtype="f32", top_k=32, bank=(3e-8, 7e-4, 69),
+                           mc=("log", 5e-4, 1e-1, 256), bin_step=1.0,
+                           injections=("entering", 16, 2, (0.04, 0.08))),
+}
+
+
+def entering_injections(count, seed, mc_lo, mc_hi, t_obs, amp, f0=40.0):
+    """count chirps that enter the band at f0 at a time t_start uniform over the
+    first 90% of the data; chirp mass log-uniform, phi0 uniform, amp a number or
+    a (lo, hi) pair."""
+    r = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        a = amp if np.isscalar(amp) else r.uniform(amp[0], amp[1])
+        out.append({"mc": float(np.exp(r.uniform(np.log(mc_lo), np.log(mc_hi)))), "f0": f0,
+                    "t_start": float(r.uniform(0.0, 0.9 * t_obs)), "amp": float(a),
+                    "phi0": float(r.uniform(0, 2 * np.pi))})
+    return out
+
+
+def make_slide_workload(name, **over):
+    """Materialise a two-stage workload: strain, bank bounds, stack-slide rows
+    (mc, c) and the search parameters."""
+    w = dict(SLIDE_WORKLOADS[name]); w.update(over)
+    n = int(round(w["t_obs"] * w["fs"]))
+    mc = w["mc"]
+    if isinstance(mc, tuple) and mc[0] == "log":
+        mc = log_templates(mc[1], mc[2], mc[3])
+    mc = np.asarray(mc, dtype=np.float64)
+    inj = w["injections"]
+    if isinstance(inj, tuple) and inj[0] == "entering":
+        inj = entering_injections(inj[1], inj[2], 5e-4, 1e-1, w["t_obs"], inj[3], w["f_lo"])
+    inj = [dict(i, f0=i.get("f0", w["f_lo"])) for i in inj]
+    dtype = np.float32 if w["dtype"] == "f32" else np.float64
+    x = strain_with_chirps(n, w["fs"], w["seed"], inj, dtype=dtype)
+    rows_mc, rows_c = slide_rows(mc, w["f_hi"], w["t_coh"], w["bin_step"])
+    w.update(strain=x, mc=mc, injections=inj, n_samples=n, rows_mc=rows_mc, rows_c=rows_c,
+             n_total=n // int(round(w["t_coh"] * w["fs"])))
+    return w
+
+
 def make_workload(name, **over):
     """Materialise a named workload: returns dict with strain (numpy), mc list
     and the search parameters."""

@@ -59,3 +59,45 @@ def test_power_normalisation_pin(monkeypatch):
     monkeypatch.setattr(oracle, "power", lambda F, n_s: abs(F) ** 2 / n_s)
     with pytest.raises(AssertionError):
         pins.test_noise_power_moments_and_n_sigma_null()
+
+
+# Mistakes planted in the two-stage oracle (oracle/slide.py), caught by the
+# pins in test_oracle_slide.py.
+SLIDE_MUTANTS = [
+    ("t0 fraction sign", "off = (1.0 if c > 0 else 0.0) - c", "off = (1.0 if c > 0 else 0.0) + c",
+     ["test_track_frequency_is_the_phase_derivative", "test_track_length_matches_band_time"]),
+    ("bin rounded down", "j = int(np.rint((f - f_lo) * t_coh))", "j = int(np.floor((f - f_lo) * t_coh))",
+     ["test_track_frequency_is_the_phase_derivative"]),
+    ("bank entry for beta at f0", "bl = beta(mc, f)", "bl = beta(mc, f0)",
+     ["test_track_bank_index_is_nearest_local_beta"]),
+    ("power not centred", "np.sum((P_track - 2.0) / 2.0)", "np.sum(P_track / 2.0)",
+     ["test_stack_slide_closed_forms"]),
+    ("segment containing t0 kept", "return n + (1 if c > 0 else 0)", "return n",
+     ["test_stack_slide_brute_force_on_a_random_cube"]),
+    ("local map referenced to t = 0", "items, n_threads=n_threads, local=True)", "items, n_threads=n_threads, local=False)",
+     ["test_power_cube_concentrates_an_entering_chirp"]),
+]
+
+
+@pytest.mark.parametrize("name,orig,bad,catchers", SLIDE_MUTANTS, ids=[m[0] for m in SLIDE_MUTANTS])
+def test_slide_pins_catch_planted_mistake(monkeypatch, name, orig, bad, catchers):
+    import types
+    import test_oracle_slide as spins
+    from oracle import slide
+    src = open(slide.__file__).read()
+    assert src.count(orig) == 1, name
+    mod = types.ModuleType("oracle.slide_mutant")
+    mod.__package__ = "oracle"
+    exec(compile(src.replace(orig, bad), "slide_mutant.py", "exec"), mod.__dict__)
+    for fn in ("local_bank", "power_cube", "first_segment", "track", "n_sigma_track", "stack_slide"):
+        monkeypatch.setattr(slide, fn, getattr(mod, fn))
+    for pin in catchers:
+        fn = getattr(spins, pin)
+        args = {"test_track_frequency_is_the_phase_derivative": [(6e-2, 0.25), (1e-2, 0.0)],
+                "test_track_length_matches_band_time": [(1e-1, 0.5)]}.get(pin)
+        with pytest.raises(AssertionError):
+            if args:
+                for a in args:
+                    fn(*a)
+            else:
+                fn()
