@@ -144,6 +144,7 @@ typedef struct {
   int32_t staging;        /* mixed form: 1 = samples staged by TMA bulk copies, 0 = read from global memory */
   int32_t ctas_per_sm;    /* mixed form: resident CTAs per SM the search asked for (0 = as many as fit) */
   double fft_ms;          /* srs_segment_spectra_cufft only: device time of the cuFFT transforms */
+  double slide_ms;        /* two-stage calls: device time of the stack-slide kernels */
 } srs_report;
 
 /* Environment variables read by the library (diagnostics and profiling):
@@ -245,6 +246,78 @@ srs_status srs_time_map(srs_ctx* ctx, const double* mc, int32_t n_templates,
                         const int32_t* item_m, const int32_t* item_i, int32_t n_items,
                         const srs_params* params, int64_t n_samples, double* psi_out,
                         double* theta_out);
+
+/* ------------------------------------------------------------------------
+ * Two-stage search (Sec. III.B local bank, Sec. III.C stack-slide, Sec. VI).
+ * Stage one resamples every segment with each entry of a bank of 0PN
+ * templates that start at the segment's first sample and stores the powers
+ * P = 2|F|^2/n_s (Eq. normalized_power, white unit-variance noise) as a cube.
+ * Stage two sums, for each template theta = {Mc, t0} whose frequency passes
+ * f0 at t0, the powers along its track: in every segment that starts at or
+ * after t0, the bin nearest the 0PN frequency at the segment's first sample
+ * (Eq. f) and the bank entry nearest the local chirp parameter beta(Mc, f)
+ * (Eq. beta); the track ends where that bin leaves the band, at coalescence,
+ * or at the end of the data.  n_sigma = sum (P - 2)/2 / sqrt(N_seg(theta))
+ * (Eq. semicoherent_statistic, equal weights, mu = sigma = 2); 0 when the
+ * track has no segment in the data.
+ * ------------------------------------------------------------------------ */
+
+/* The local resampling bank: n_beta chirp parameters uniform over
+ * [beta_min, beta_max] (1/s); the paper's search uses 69 over 3e-8 .. 7e-4. */
+typedef struct {
+  double beta_min, beta_max;
+  int32_t n_beta;
+} srs_bank;
+
+/* Stack-slide templates theta = {Mc, t0}.  Row r has chirp mass mc[r] (Msun)
+ * and t0 fraction c[r] in [0, 1); column n has t0 = (n + c[r]) t_coh, so the
+ * map is [n_rows][n_t0].  mc and c are host arrays.  f0 in [f_lo, f_hi) is
+ * the frequency at t0 (the paper: the band's lower edge). */
+typedef struct {
+  double f0;
+  const double* mc;
+  const double* c;
+  int32_t n_rows;
+  int32_t n_t0;
+} srs_slide_grid;
+
+/* Flags of srs_stack_slide. */
+enum { SRS_SLIDE_FIRST = 1, SRS_SLIDE_LAST = 2 };
+
+/* Stage one for segments [seg_begin, seg_end):
+ *   cube [n_beta][n_bins][seg_end - seg_begin] float, segment innermost,
+ * host or device per params->io_on_device (caller-owned).  Mixed form only
+ * (SRS_ERR_UNSUPPORTED otherwise); params->f_ref is not used (the bank gives
+ * beta directly).  SRS_ERR_DOMAIN if a bank entry coalesces within one
+ * segment.  report: device_ms, spread_ms (the transform kernel), sizes. */
+srs_status srs_power_cube(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype,
+                          const srs_bank* bank, int32_t seg_begin, int32_t seg_end,
+                          const srs_params* params, float* cube, srs_report* report);
+
+/* Stage two over one cube chunk holding segments [seg_begin, seg_end) of data
+ * with n_seg_total segments, in srs_power_cube's layout (host or device per
+ * params->io_on_device).  The running sums live in the context: flags
+ * SRS_SLIDE_FIRST starts them at zero, SRS_SLIDE_LAST finishes the search and
+ * writes nsigma_map [n_rows][n_t0] (may be NULL) and the top params->top_k
+ * candidates (template_idx = row r, bin = column n), ordered by value
+ * descending, then row, then column.  Chunks may come in any order between a
+ * FIRST and a LAST call; a single call may carry both flags.  Uses t_coh,
+ * f_lo, f_hi, top_k and io_on_device of params.  report: slide_ms. */
+srs_status srs_stack_slide(srs_ctx* ctx, const float* cube, int32_t seg_begin, int32_t seg_end,
+                           int32_t n_seg_total, const srs_bank* bank, const srs_slide_grid* grid,
+                           const srs_params* params, int32_t flags, float* nsigma_map,
+                           srs_candidate* cands, int32_t* n_cands, srs_report* report);
+
+/* Both stages over all whole segments of the strain.  cube_budget_bytes > 0
+ * bounds the device cube: the data is processed in chunks of segments that
+ * fit, and the running sums carry over between chunks (the partial-sum
+ * caching of Sec. VI); 0 = one chunk.  Outputs as srs_stack_slide's LAST
+ * call.  report: device_ms (everything), spread_ms (cube kernels), slide_ms
+ * (stack-slide kernels), n_spectra (n_beta x segments). */
+srs_status srs_slide_search(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype,
+                            const srs_bank* bank, const srs_slide_grid* grid, const srs_params* params,
+                            int64_t cube_budget_bytes, float* nsigma_map, srs_candidate* cands,
+                            int32_t* n_cands, srs_report* report);
 
 /* ------------------------------------------------------------------------
  * Learned proposal.  A small network looks at a coarse-template n_sigma map

@@ -90,19 +90,26 @@ def n_sigma_track(P_track):
     return float(np.sum((P_track - 2.0) / 2.0) / np.sqrt(n))
 
 
-def stack_slide(cube, rows_mc, rows_c, n_t0, n_total, bank, f0, t_coh, f_lo, n_b):
+def stack_slide(cube, rows_mc, rows_c, n_t0, n_total, bank, f0, t_coh, f_lo, n_b, with_abs=False):
     """n_sigma[r][n] for theta = {rows_mc[r], t0 = (n + rows_c[r]) T} over a
     cube P[k][j][i] that holds every segment i < n_total.  Also returns the
-    number of track segments N_seg[r][n] inside the data."""
+    number of track segments N_seg[r][n] inside the data, and with
+    with_abs=True the sums of |P - 2| / 2 along each track (for rounding
+    bounds)."""
     R = len(rows_mc)
     out = np.zeros((R, n_t0))
     nseg = np.zeros((R, n_t0), dtype=np.int64)
+    absum = np.zeros((R, n_t0))
     for r in range(R):
         k, j = track(rows_mc[r], rows_c[r], f0, t_coh, f_lo, n_b, bank, n_total)
         for n in range(n_t0):
             first = first_segment(n, rows_c[r])
             L = max(0, min(len(k), n_total - first))
             i = first + np.arange(L)
-            out[r, n] = n_sigma_track(cube[k[:L], j[:L], i])
+            P = cube[k[:L], j[:L], i]
+            out[r, n] = n_sigma_track(P)
             nseg[r, n] = L
+            absum[r, n] = float(np.sum(np.abs(np.asarray(P, dtype=np.float64) - 2.0) / 2.0))
+    if with_abs:
+        return out, nseg, absum
     return out, nseg

@@ -24,7 +24,8 @@ SRS_PLAIN_FP64, SRS_MIXED = 0, 1
 EXPORTS = ("srs_create", "srs_destroy", "srs_last_error", "srs_plan", "srs_search", "srs_search_async", "srs_sync",
            "srs_segment_spectra", "srs_segment_spectra_cufft", "srs_time_map", "srs_segment_spectra_static", "srs_make_strain",
            "srs_patches", "srs_mlp_forward", "srs_mlp_grad", "srs_mlp_train", "srs_score_map", "srs_refine",
-           "srs_search_proposed")
+           "srs_search_proposed", "srs_power_cube", "srs_stack_slide", "srs_slide_search")
+SRS_SLIDE_FIRST, SRS_SLIDE_LAST = 1, 2
 MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 297, 64, 19137
 
 
@@ -59,7 +60,16 @@ class _Report(ctypes.Structure):
                 ("sigma", ctypes.c_double), ("beta_es", ctypes.c_double), ("chunk", ctypes.c_int32),
                 ("n_items", ctypes.c_int32), ("kernel_launches", ctypes.c_int32), ("spread_ms", ctypes.c_double),
                 ("cta_threads", ctypes.c_int32), ("staging", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("fft_ms", ctypes.c_double)]
+                ("fft_ms", ctypes.c_double), ("slide_ms", ctypes.c_double)]
+
+
+class _Bank(ctypes.Structure):
+    _fields_ = [("beta_min", ctypes.c_double), ("beta_max", ctypes.c_double), ("n_beta", ctypes.c_int32)]
+
+
+class _SlideGrid(ctypes.Structure):
+    _fields_ = [("f0", ctypes.c_double), ("mc", ctypes.c_void_p), ("c", ctypes.c_void_p),
+                ("n_rows", ctypes.c_int32), ("n_t0", ctypes.c_int32)]
 
 
 class _Injection(ctypes.Structure):
@@ -142,6 +152,17 @@ def lib():
             fn.restype = i32
             fn.argtypes = [vp, vp, i64, i32, vp, i32, i32, i32, ctypes.POINTER(_Params), vp,
                            ctypes.POINTER(_Report)]
+        L.srs_power_cube.restype = i32
+        L.srs_power_cube.argtypes = [vp, vp, i64, i32, ctypes.POINTER(_Bank), i32, i32, ctypes.POINTER(_Params), vp,
+                                     ctypes.POINTER(_Report)]
+        L.srs_stack_slide.restype = i32
+        L.srs_stack_slide.argtypes = [vp, vp, i32, i32, i32, ctypes.POINTER(_Bank), ctypes.POINTER(_SlideGrid),
+                                      ctypes.POINTER(_Params), i32, vp, vp, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(_Report)]
+        L.srs_slide_search.restype = i32
+        L.srs_slide_search.argtypes = [vp, vp, i64, i32, ctypes.POINTER(_Bank), ctypes.POINTER(_SlideGrid),
+                                       ctypes.POINTER(_Params), i64, vp, vp, ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(_Report)]
         L.srs_time_map.restype = i32
         L.srs_time_map.argtypes = [vp, vp, i32, vp, vp, i32, ctypes.POINTER(_Params), i64, vp, vp]
         f32p = ctypes.POINTER(ctypes.c_float)
@@ -321,6 +342,128 @@ class Context:
                 int(seg_end), ctypes.byref(p), F.ctypes.data, ctypes.byref(rep))
         self._check(st)
         return F, _report_dict(rep)
+
+    # ----- two-stage search: power cube + stack-slide ----------------------
+    @staticmethod
+    def _bank(bank):
+        return _Bank(float(bank[0]), float(bank[1]), int(bank[2]))
+
+    @staticmethod
+    def _grid(rows_mc, rows_c, n_t0, f0):
+        mc = np.ascontiguousarray(rows_mc, dtype=np.float64)
+        c = np.ascontiguousarray(rows_c, dtype=np.float64)
+        if mc.shape != c.shape:
+            raise ValueError("rows_mc and rows_c must have the same length")
+        g = _SlideGrid(float(f0), mc.ctypes.data, c.ctypes.data, mc.size, int(n_t0))
+        return g, (mc, c)   # keep the arrays alive with the struct
+
+    def power_cube(self, strain, bank, seg_begin, seg_end, params):
+        """srs_power_cube: float32 [n_beta, n_bins, seg_end - seg_begin] powers of
+        every segment under each bank entry (bank = (beta_min, beta_max, n_beta));
+        numpy for host strain, torch for a CUDA tensor."""
+        dt = _dtype_code(strain)
+        p = params.c()
+        rep = _Report()
+        n_bins = int(round((params.f_hi - params.f_lo) * params.t_coh))
+        shape = (int(bank[2]), n_bins, seg_end - seg_begin)
+        b = self._bank(bank)
+        if _is_torch_cuda(strain):
+            import torch
+            p.io_on_device = 1
+            out = torch.empty(shape, dtype=torch.float32, device=strain.device)
+            st = self._lib.srs_power_cube(self._h, strain.data_ptr(), strain.numel(), dt, ctypes.byref(b),
+                                          int(seg_begin), int(seg_end), ctypes.byref(p), out.data_ptr(),
+                                          ctypes.byref(rep))
+        else:
+            strain = np.ascontiguousarray(strain)
+            p.io_on_device = 0
+            out = np.empty(shape, dtype=np.float32)
+            st = self._lib.srs_power_cube(self._h, strain.ctypes.data, strain.size, dt, ctypes.byref(b),
+                                          int(seg_begin), int(seg_end), ctypes.byref(p), out.ctypes.data,
+                                          ctypes.byref(rep))
+        self._check(st)
+        return out, _report_dict(rep)
+
+    def stack_slide(self, cube, seg_begin, n_seg_total, bank, rows_mc, rows_c, n_t0, params, f0=None,
+                    first=True, last=True, want_map=True):
+        """srs_stack_slide over a cube chunk [n_beta, n_bins, chunk segments]
+        holding segments [seg_begin, seg_begin + chunk).  With last=True returns
+        (candidates, n_sigma map [rows, n_t0] or None, report); otherwise
+        (None, None, report).  numpy cube: host I/O; torch CUDA cube: device I/O."""
+        f0 = params.f_lo if f0 is None else f0
+        g, keep = self._grid(rows_mc, rows_c, n_t0, f0)
+        b = self._bank(bank)
+        p = params.c()
+        rep = _Report()
+        n_cands = ctypes.c_int32(0)
+        flags = (SRS_SLIDE_FIRST if first else 0) | (SRS_SLIDE_LAST if last else 0)
+        n_bins = int(round((params.f_hi - params.f_lo) * params.t_coh))
+        if tuple(cube.shape[:2]) != (int(bank[2]), n_bins) or len(cube.shape) != 3:
+            raise ValueError("cube must be [n_beta, n_bins, segments]")
+        if _is_torch_cuda(cube) and (cube.dtype != __import__("torch").float32 or not cube.is_contiguous()):
+            raise ValueError("a device cube must be a contiguous float32 tensor")
+        seg_end = int(seg_begin) + int(cube.shape[2])
+        R = keep[0].size
+        if _is_torch_cuda(cube):
+            import torch
+            p.io_on_device = 1
+            m = torch.empty((R, int(n_t0)), dtype=torch.float32, device=cube.device) if (last and want_map) else None
+            c = torch.empty((params.top_k, 3), dtype=torch.int32, device=cube.device) if last else None
+            st = self._lib.srs_stack_slide(self._h, cube.data_ptr(), int(seg_begin), seg_end, int(n_seg_total),
+                                           ctypes.byref(b), ctypes.byref(g), ctypes.byref(p), flags,
+                                           m.data_ptr() if m is not None else None,
+                                           c.data_ptr() if c is not None else None, ctypes.byref(n_cands),
+                                           ctypes.byref(rep))
+            self._check(st)
+            return (c[:n_cands.value] if c is not None else None), m, _report_dict(rep)
+        cube = np.ascontiguousarray(cube, dtype=np.float32)
+        p.io_on_device = 0
+        m = np.empty((R, int(n_t0)), dtype=np.float32) if (last and want_map) else None
+        c = np.zeros(params.top_k, dtype=CAND_DTYPE) if last else None
+        st = self._lib.srs_stack_slide(self._h, cube.ctypes.data, int(seg_begin), seg_end, int(n_seg_total),
+                                       ctypes.byref(b), ctypes.byref(g), ctypes.byref(p), flags,
+                                       m.ctypes.data if m is not None else None,
+                                       c.ctypes.data if c is not None else None, ctypes.byref(n_cands),
+                                       ctypes.byref(rep))
+        self._check(st)
+        return (c[:n_cands.value] if c is not None else None), m, _report_dict(rep)
+
+    def slide_search(self, strain, bank, rows_mc, rows_c, n_t0, params, f0=None, cube_budget_bytes=0,
+                     want_map=True, out=None):
+        """srs_slide_search: power cube + stack-slide over the whole strain.
+        Host numpy strain returns (candidates, map or None, report); a torch
+        CUDA strain returns ({"map", "cands"} tensors, report)."""
+        f0 = params.f_lo if f0 is None else f0
+        g, keep = self._grid(rows_mc, rows_c, n_t0, f0)
+        b = self._bank(bank)
+        dt = _dtype_code(strain)
+        p = params.c()
+        rep = _Report()
+        n_cands = ctypes.c_int32(0)
+        R = keep[0].size
+        if _is_torch_cuda(strain):
+            import torch
+            p.io_on_device = 1
+            if out is None:
+                out = {"map": torch.empty((R, int(n_t0)), dtype=torch.float32, device=strain.device)
+                       if want_map else None,
+                       "cands": torch.empty((params.top_k, 3), dtype=torch.int32, device=strain.device)}
+            mp = out["map"].data_ptr() if out.get("map") is not None else None
+            st = self._lib.srs_slide_search(self._h, strain.data_ptr(), strain.numel(), dt, ctypes.byref(b),
+                                            ctypes.byref(g), ctypes.byref(p), int(cube_budget_bytes), mp,
+                                            out["cands"].data_ptr(), ctypes.byref(n_cands), ctypes.byref(rep))
+            self._check(st)
+            return out, _report_dict(rep)
+        strain = np.ascontiguousarray(strain)
+        p.io_on_device = 0
+        m = np.empty((R, int(n_t0)), dtype=np.float32) if want_map else None
+        c = np.zeros(params.top_k, dtype=CAND_DTYPE)
+        st = self._lib.srs_slide_search(self._h, strain.ctypes.data, strain.size, dt, ctypes.byref(b),
+                                        ctypes.byref(g), ctypes.byref(p), int(cube_budget_bytes),
+                                        m.ctypes.data if m is not None else None, c.ctypes.data,
+                                        ctypes.byref(n_cands), ctypes.byref(rep))
+        self._check(st)
+        return c[:n_cands.value], m, _report_dict(rep)
 
     # ----- learned proposal -----------------------------------------------
     def make_strain(self, n, fs, seed, injections=(), f_hi=60.0, noise=True, out=None):

@@ -23,6 +23,40 @@
 
 using namespace srs;
 
+namespace srs {
+
+// Strain on the device: the caller's pointer, or a copy of the first
+// `samples` samples of the caller's host array.
+srs_status stage_strain(srs_ctx* ctx, const void* strain, int64_t samples, int32_t dtype, int on_device,
+                        const void** dev) {
+  if (on_device) {
+    *dev = strain;
+    return SRS_OK;
+  }
+  size_t bytes = (size_t)samples * (dtype == SRS_F64 ? 8 : 4);
+  SRS_CK(ctx->strain.ensure(bytes), "alloc strain");
+  SRS_CK(cudaMemcpyAsync(ctx->strain.p, strain, bytes, cudaMemcpyHostToDevice, ctx->stream), "copy strain");
+  *dev = ctx->strain.p;
+  return SRS_OK;
+}
+
+srs_status check_common(srs_ctx* ctx, const void* strain, int32_t dtype, const srs_params* params) {
+  if (!ctx) return SRS_ERR_ARG;
+  {
+    // an error left by an earlier unchecked runtime call must not be blamed on this call
+    const cudaError_t stale = cudaGetLastError();
+    if (stale != cudaSuccess) std::fprintf(stderr, "srs: cleared stale CUDA error: %s\n", cudaGetErrorString(stale));
+  }
+  if (!strain) return set_err(ctx, SRS_ERR_ARG, "strain is NULL");
+  if (!params) return set_err(ctx, SRS_ERR_ARG, "params is NULL");
+  if (dtype != SRS_F32 && dtype != SRS_F64) return set_err(ctx, SRS_ERR_ARG, "dtype must be SRS_F32 or SRS_F64");
+  if (params->io_on_device != 0 && params->io_on_device != 1) return set_err(ctx, SRS_ERR_ARG, "io_on_device must be 0 or 1");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_err(ctx, cudaGetLastError(), "cudaSetDevice");
+  return SRS_OK;
+}
+
+}  // namespace srs
+
 namespace {
 
 void fill_radices(const Plan& pl, int8_t* r) {
@@ -54,6 +88,7 @@ MixedArgs mixed_args(const Plan& pl, const srs_ctx* ctx, int seg_begin, int seg_
   a.aa.n_s = pl.n_s;
   a.aa.span = pl.span;
   a.aa.n_anchor = pl.n_anchor;
+  a.aa.local = pl.local ? 1 : 0;
   a.fft_fixed = (pl.n_fine == 1200 && pl.radices == std::vector<int32_t>{4, 4, 3, 5, 5}) ? 1200 : 0;
   a.kc = (float)pl.k_c;
   a.kc_int = (pl.k_c >= 1.0 && pl.k_c < 1073741824.0 && pl.k_c == std::floor(pl.k_c)) ? (int)pl.k_c : 0;
@@ -90,6 +125,7 @@ PlainArgs plain_args(const Plan& pl, const srs_ctx* ctx, int seg_begin, int seg_
 
 AnchorArgs anchor_args(const Plan& pl) {
   AnchorArgs aa;
+  aa.local = pl.local ? 1 : 0;
   aa.fs = pl.fs;
   aa.t_coh = pl.t_coh;
   aa.f_c = pl.f_c;
@@ -131,36 +167,6 @@ srs_status upload_tables(srs_ctx* ctx, const Plan& pl) {
     SRS_CK(cudaMemcpyAsync(ctx->item_off.p, pl.item_off.data(), pl.item_off.size() * 4, cudaMemcpyHostToDevice, ctx->stream), "copy item_off");
   }
   SRS_CK(cudaStreamSynchronize(ctx->stream), "sync tables");
-  return SRS_OK;
-}
-
-// Strain on the device: the caller's pointer, or a copy of the first
-// `samples` samples of the caller's host array.
-srs_status stage_strain(srs_ctx* ctx, const void* strain, int64_t samples, int32_t dtype, int on_device,
-                        const void** dev) {
-  if (on_device) {
-    *dev = strain;
-    return SRS_OK;
-  }
-  size_t bytes = (size_t)samples * (dtype == SRS_F64 ? 8 : 4);
-  SRS_CK(ctx->strain.ensure(bytes), "alloc strain");
-  SRS_CK(cudaMemcpyAsync(ctx->strain.p, strain, bytes, cudaMemcpyHostToDevice, ctx->stream), "copy strain");
-  *dev = ctx->strain.p;
-  return SRS_OK;
-}
-
-srs_status check_common(srs_ctx* ctx, const void* strain, int32_t dtype, const srs_params* params) {
-  if (!ctx) return SRS_ERR_ARG;
-  {
-    // an error left by an earlier unchecked runtime call must not be blamed on this call
-    const cudaError_t stale = cudaGetLastError();
-    if (stale != cudaSuccess) std::fprintf(stderr, "srs: cleared stale CUDA error: %s\n", cudaGetErrorString(stale));
-  }
-  if (!strain) return set_err(ctx, SRS_ERR_ARG, "strain is NULL");
-  if (!params) return set_err(ctx, SRS_ERR_ARG, "params is NULL");
-  if (dtype != SRS_F32 && dtype != SRS_F64) return set_err(ctx, SRS_ERR_ARG, "dtype must be SRS_F32 or SRS_F64");
-  if (params->io_on_device != 0 && params->io_on_device != 1) return set_err(ctx, SRS_ERR_ARG, "io_on_device must be 0 or 1");
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_err(ctx, cudaGetLastError(), "cudaSetDevice");
   return SRS_OK;
 }
 
@@ -235,10 +241,11 @@ void find_event_nodes(srs_ctx* ctx) {
 // Plan for this call, reusing the context's last plan (and its device tables)
 // when the call kind, sizes, parameters and templates are the same.
 srs_status get_plan(srs_ctx* ctx, int kind, const srs_params* params, const double* mc, int32_t n_templates,
-                    int64_t n_samples, int32_t dtype, bool spectra_mode, int32_t a, int32_t b, const Plan** out) {
+                    int64_t n_samples, int32_t dtype, bool spectra_mode, int32_t a, int32_t b, const Plan** out,
+                    const double* betas_in = nullptr, bool local = false) {
   srs_params key_p = *params;
   key_p.io_on_device = 0;
-  std::vector<unsigned char> key = make_key(kind, &key_p, n_samples, dtype, mc, n_templates, a, b);
+  std::vector<unsigned char> key = make_key(kind, &key_p, n_samples, dtype, betas_in ? betas_in : mc, n_templates, a, b);
   if (ctx->have_plan && key == ctx->plan_key) {
     *out = &ctx->plan;
     return SRS_OK;
@@ -247,7 +254,7 @@ srs_status get_plan(srs_ctx* ctx, int kind, const srs_params* params, const doub
   // a new plan means new tables: a captured graph may point at the old ones
   destroy_graph(ctx);
   std::string msg;
-  srs_status s = make_plan(*params, mc, n_templates, n_samples, spectra_mode, a, b, ctx->plan, msg);
+  srs_status s = make_plan(*params, mc, n_templates, n_samples, spectra_mode, a, b, ctx->plan, msg, betas_in, local);
   if (s != SRS_OK) return set_err(ctx, s, msg);
   s = upload_tables(ctx, ctx->plan);
   if (s != SRS_OK) return s;
@@ -951,6 +958,59 @@ srs_status time_map_impl(srs_ctx* ctx, const double* mc, int32_t n_templates, co
 
 }  // namespace
 
+namespace srs {
+
+std::vector<double> bank_betas(const srs_bank& bank) {
+  std::vector<double> b((size_t)bank.n_beta);
+  const double step = bank.n_beta > 1 ? (bank.beta_max - bank.beta_min) / (bank.n_beta - 1) : 0.0;
+  for (int32_t k = 0; k < bank.n_beta; ++k) b[(size_t)k] = bank.beta_min + k * step;
+  return b;
+}
+
+srs_status check_bank(srs_ctx* ctx, const srs_bank* bank) {
+  if (!bank) return set_err(ctx, SRS_ERR_ARG, "bank is NULL");
+  if (bank->n_beta < 1 || bank->n_beta > 65536) return set_err(ctx, SRS_ERR_ARG, "bank size must be in [1, 65536]");
+  if (!(bank->beta_min > 0) || !std::isfinite(bank->beta_max) || !(bank->beta_max >= bank->beta_min))
+    return set_err(ctx, SRS_ERR_ARG, "bank needs 0 < beta_min <= beta_max");
+  if (bank->n_beta > 1 && !(bank->beta_max > bank->beta_min))
+    return set_err(ctx, SRS_ERR_ARG, "a bank of several entries needs beta_max > beta_min");
+  return SRS_OK;
+}
+
+srs_status clear_err_flag(srs_ctx* ctx) {
+  SRS_CK(ctx->errflag.ensure(64), "alloc error flag");
+  SRS_CK(cudaMemsetAsync(ctx->errflag.p, 0, 64, ctx->stream), "memset error flag");
+  return SRS_OK;
+}
+
+srs_status read_err_flag(srs_ctx* ctx) { return check_err_flag(ctx); }
+
+srs_status cube_device(srs_ctx* ctx, const float* s32, int64_t n_samples, const std::vector<double>& bank,
+                       int32_t seg_begin, int32_t seg_end, const srs_params* params, float* dcube, int* launches,
+                       const Plan** plan_out) {
+  const Plan* plp = nullptr;
+  srs_status s = get_plan(ctx, 3, params, nullptr, (int32_t)bank.size(), n_samples, SRS_F32, true, seg_begin, seg_end,
+                          &plp, bank.data(), true);
+  if (s != SRS_OK) return s;
+  const Plan& pl = *plp;
+  if (plan_out) *plan_out = plp;
+  if (pl.precision != SRS_MIXED) return set_err(ctx, SRS_ERR_UNSUPPORTED, "the power cube runs the mixed form only");
+  MixedArgs a = mixed_args(pl, ctx, seg_begin, seg_end - seg_begin);
+  const float* x = nullptr;
+  s = strain_f32(ctx, s32, SRS_F32, (int64_t)seg_end * pl.n_s, pl.n_s, &x, &a.use_tma);
+  if (s != SRS_OK) return s;
+  a.cube_out = dcube;
+  SRS_CK(ctx->queue.ensure(64), "alloc queue");
+  SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
+  SRS_CK(launch_mixed(true, pl.w, x, ctx->items.as<Item>(), (int)pl.items.size(), ctx->betas.as<double>(),
+                      ctx->queue.as<int>(), a, nullptr, nullptr, ctx->errflag.as<int>(), ctx->n_sm, 0, ctx->stream),
+         "k_mixed (power cube)");
+  if (launches) ++*launches;
+  return SRS_OK;
+}
+
+}  // namespace srs
+
 extern "C" {
 
 srs_status srs_create(srs_ctx** out, int device, void* cuda_stream) {
@@ -1008,6 +1068,8 @@ void srs_destroy(srs_ctx* c) {
   for (cudaEvent_t& e : c->pev)
     if (e) cudaEventDestroy(e);
   if (c->fft_plan_ok) cufft_api().destroy(c->fft_plan);
+  for (cudaEvent_t e : c->slide_ev)
+    if (e) cudaEventDestroy(e);
   if (c->hflag) cudaFreeHost(c->hflag);
   for (DevBuf* b : c->all_buffers()) b->release();
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -1047,6 +1109,72 @@ srs_status srs_search(srs_ctx* ctx, const void* strain, int64_t n_samples, int32
                       int32_t* n_cands, srs_report* report) {
   try {
     return search_impl(ctx, strain, n_samples, dtype, mc, n_templates, params, stat_map, cands, n_cands, report);
+  } catch (const std::bad_alloc&) {
+    return set_err(ctx, SRS_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return set_err(ctx, SRS_ERR_ARG, "unexpected host error");
+  }
+}
+
+srs_status srs_power_cube(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype, const srs_bank* bank,
+                          int32_t seg_begin, int32_t seg_end, const srs_params* params, float* cube,
+                          srs_report* report) {
+  try {
+    srs_status s = check_common(ctx, strain, dtype, params);
+    if (s != SRS_OK) return s;
+    s = check_bank(ctx, bank);
+    if (s != SRS_OK) return s;
+    if (!cube) return set_err(ctx, SRS_ERR_ARG, "cube is NULL");
+    if (params->precision != SRS_MIXED) return set_err(ctx, SRS_ERR_UNSUPPORTED, "the power cube runs the mixed form only");
+    const int64_t n_s = (int64_t)std::llround(params->t_coh * params->fs);
+    if (n_s < 1 || seg_begin < 0 || seg_end <= seg_begin || (int64_t)seg_end * n_s > n_samples)
+      return set_err(ctx, SRS_ERR_ARG, "need 0 <= seg_begin < seg_end <= segments in the strain");
+    const std::vector<double> bb = bank_betas(*bank);
+    const int on_dev = params->io_on_device;
+    const void* dstrain = nullptr;
+    s = stage_strain(ctx, strain, (int64_t)seg_end * n_s, dtype, on_dev, &dstrain);
+    if (s != SRS_OK) return s;
+    SRS_CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
+    const float* s32 = nullptr;
+    int tma = 0, launches = 0;
+    s = strain_f32(ctx, dstrain, dtype, (int64_t)seg_end * n_s, n_s, &s32, &tma);
+    if (s != SRS_OK) return s;
+    if (dtype == SRS_F64) ++launches;
+    s = clear_err_flag(ctx);
+    if (s != SRS_OK) return s;
+    const int64_t n_bins = std::llround((params->f_hi - params->f_lo) * params->t_coh);
+    const size_t bytes = (size_t)bank->n_beta * (size_t)std::max<int64_t>(n_bins, 1) * (size_t)(seg_end - seg_begin) * 4;
+    float* dcube = cube;
+    if (!on_dev) {
+      SRS_CK(ctx->cube.ensure(bytes), "alloc cube");
+      dcube = ctx->cube.as<float>();
+    }
+    SRS_CK(cudaEventRecord(ctx->ev2, ctx->stream), "event");
+    const Plan* pl = nullptr;
+    s = cube_device(ctx, s32, n_samples, bb, seg_begin, seg_end, params, dcube, &launches, &pl);
+    if (s != SRS_OK) return s;
+    SRS_CK(cudaEventRecord(ctx->ev1, ctx->stream), "event");
+    if (!on_dev) SRS_CK(cudaMemcpyAsync(cube, dcube, bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy cube");
+    SRS_CK(cudaStreamSynchronize(ctx->stream), "power cube");
+    s = check_err_flag(ctx);
+    if (s != SRS_OK) return s;
+    if (report) {
+      std::memset(report, 0, sizeof *report);
+      report->device_ms = elapsed_ms(ctx->ev0, ctx->ev1);
+      report->spread_ms = elapsed_ms(ctx->ev2, ctx->ev1);
+      report->n_spectra = (int64_t)bank->n_beta * (seg_end - seg_begin);
+      report->spectra_per_s = report->device_ms > 0 ? report->n_spectra / (report->device_ms * 1e-3) : 0.0;
+      report->w = pl->w;
+      report->n_fine = pl->n_fine;
+      report->sigma = pl->sigma;
+      report->beta_es = pl->beta_es;
+      report->chunk = pl->chunk;
+      report->n_items = (int32_t)pl->items.size();
+      report->cta_threads = pl->threads;
+      report->staging = tma;
+      report->kernel_launches = launches;
+    }
+    return SRS_OK;
   } catch (const std::bad_alloc&) {
     return set_err(ctx, SRS_ERR_OOM, "host allocation failed");
   } catch (...) {

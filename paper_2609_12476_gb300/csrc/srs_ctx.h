@@ -82,6 +82,12 @@ struct srs_ctx {
   cudaGraphNode_t graph_ev_node[2] = {nullptr, nullptr};
   srs::DevBuf items, order, grid, anchors, partial, betas, nseg, item_off, corr, tw, keys, topk_a, topk_b, cands, queue, strain,
       strain32, errflag, map, S, F, psi, th, im, ii;
+  // two-stage search: power cube chunk, stack-slide tracks and running sums
+  srs::DevBuf cube, slide_cell, slide_len, slide_beta0, slide_frac, slide_Z, slide_map;
+  bool have_slide = false;
+  bool slide_open = false;                // running sums started (SRS_SLIDE_FIRST) and not yet finished
+  std::vector<unsigned char> slide_key;   // what slide_cell / slide_len were computed for
+  std::vector<cudaEvent_t> slide_ev;      // per chunk: cube start, slide start, slide end
   // learned proposal
   srs::DevBuf xb, yb, z1, logits, dz, lossv, grad, wts, adam_m, adam_v, w1h, w2h, idx, patches, cells_m, cells_b,
       sp_items, sp_bins, sp_partial, sp_cells, sp_out, sp_betas, cmap, ccands, inj;
@@ -89,7 +95,8 @@ struct srs_ctx {
     return {&items, &order, &grid, &anchors, &partial, &betas, &nseg, &item_off, &corr, &tw, &keys, &topk_a, &topk_b, &cands,
             &queue, &strain, &strain32, &errflag, &map, &S, &F, &psi, &th, &im, &ii, &xb, &yb, &z1, &logits, &dz,
             &lossv, &grad, &wts, &adam_m, &adam_v, &w1h, &w2h, &idx, &patches, &cells_m, &cells_b, &sp_items,
-            &sp_bins, &sp_partial, &sp_cells, &sp_out, &sp_betas, &cmap, &ccands, &inj};
+            &sp_bins, &sp_partial, &sp_cells, &sp_out, &sp_betas, &cmap, &ccands, &inj, &cube, &slide_cell,
+            &slide_len, &slide_beta0, &slide_frac, &slide_Z, &slide_map};
   }
 };
 
@@ -125,6 +132,24 @@ srs_status search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
 srs_status sync_impl(srs_ctx* ctx, srs_report* report);
 srs_status strain_f32(srs_ctx* ctx, const void* dstrain, int32_t dtype, int64_t samples, int64_t n_s,
                       const float** out, int* use_tma);
+// Strain on the device (the caller's pointer, or a staged copy of `samples` host samples).
+srs_status stage_strain(srs_ctx* ctx, const void* strain, int64_t samples, int32_t dtype, int on_device,
+                        const void** dev);
+// Argument checks every strain-taking entry point shares.
+srs_status check_common(srs_ctx* ctx, const void* strain, int32_t dtype, const srs_params* params);
+// The local resampling bank (Sec. III.B): n_beta values uniform over [beta_min, beta_max].
+std::vector<double> bank_betas(const srs_bank& bank);
+srs_status check_bank(srs_ctx* ctx, const srs_bank* bank);
+// Power cube of segments [seg_begin, seg_end), every bank entry, from FP32
+// device strain (mixed form, per-segment templates), into the device cube
+// [n_beta][n_bins][seg_end - seg_begin].  Queued on the context's stream
+// without a sync; the caller clears and checks the error flag.
+srs_status cube_device(srs_ctx* ctx, const float* s32, int64_t n_samples, const std::vector<double>& bank,
+                       int32_t seg_begin, int32_t seg_end, const srs_params* params, float* dcube, int* launches,
+                       const Plan** plan_out);
+// Clear / read the device error flag of the mixed spreader.
+srs_status clear_err_flag(srs_ctx* ctx);
+srs_status read_err_flag(srs_ctx* ctx);
 bool tma_disabled();
 
 }  // namespace srs

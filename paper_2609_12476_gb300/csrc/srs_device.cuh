@@ -40,7 +40,8 @@ constexpr double kSeriesMaxY = 0.125;
 // Taylor coefficients of delta in the sample index.
 __device__ __forceinline__ Anchor compute_anchor(double b, int i, int ai, const AnchorArgs& aa) {
   const double inv_fs = 1.0 / aa.fs, inv_t = 1.0 / aa.t_coh;
-  const double t_i0 = (double)i * (double)aa.n_s * inv_fs;
+  // local: the segment's own 0PN template starts at its first sample
+  const double t_i0 = aa.local ? 0.0 : (double)i * (double)aa.n_s * inv_fs;
   const double a = 1.0 - (8.0 / 3.0) * b * t_i0;
   const double inv_a = 1.0 / a;
   const double a58 = exp(0.625 * log(a));                       // a^(5/8)
@@ -114,6 +115,19 @@ __device__ __forceinline__ uint32_t mixed_psi(const Anchor& A, int l) {
   const float cq = fmaf(fmaf(fmaf(A.p5, lf, A.p4), lf, A.p3), lf, A.p2) * (lf * lf);
   const float cpsi = fmaf(A.p1lo, lf, cq);
   return A.psi0 + (uint32_t)l * A.n1 + (uint32_t)__float2int_rn(cpsi * 4294967296.0f);
+}
+
+// Top-k sort key of a map cell: larger value first, then smaller flat index
+// (value bits made order-preserving as unsigned, flat index complemented).
+__device__ __forceinline__ unsigned long long make_key(float v, uint32_t flat) {
+  uint32_t u = __float_as_uint(v);
+  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  return ((unsigned long long)u << 32) | (unsigned long long)(~flat);
+}
+__device__ __forceinline__ float key_value(unsigned long long k) {
+  uint32_t u = (uint32_t)(k >> 32);
+  u = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+  return __uint_as_float(u);
 }
 
 }  // namespace srs

@@ -52,6 +52,7 @@ struct Plan {
   int32_t n_seg_total = 0, n_bins = 0, half_bins = 0;  // k = b - half_bins
   double f_c = 0, k_c = 0;                               // demodulation frequency, f_c * t_coh
   int32_t n_templates = 0, top_k = 0, precision = 1, cut = 1;
+  bool local = false;                                    // per-segment templates (t_i0 = 0 in every segment)
   // NUFFT
   int32_t n_fine = 0, w = 0;
   double sigma = 0, beta_es = 0;
@@ -79,9 +80,13 @@ struct Plan {
 double chirp_beta(double mc, double f);
 
 // Host planner (srs_plan.cpp).  Returns SRS_OK or an error with `msg` set.
+// With betas_in != NULL the templates are given by their chirp parameters
+// (mc is ignored); with local = true every segment is resampled with a 0PN
+// template that starts at the segment's first sample (spectra mode only).
 srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
                      int64_t n_samples, bool need_segments_all, int32_t seg_begin,
-                     int32_t seg_end, Plan& out, std::string& msg);
+                     int32_t seg_end, Plan& out, std::string& msg,
+                     const double* betas_in = nullptr, bool local = false);
 void fill_info(const Plan& pl, srs_plan_info* info);
 // Threads per CTA of the mixed spreader and the run / span / anchor layout that follows.
 void set_cta(Plan& pl, int32_t threads);

@@ -447,7 +447,11 @@ k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_
         const float c = a.corr[b];
         const float fx = G.x * c, fy = G.y * c;
         if (SPECTRA) {
-          Fout[((long long)it.m * a.seg_range + (i - a.seg_begin)) * a.n_bins + b] = make_double2(fx, fy);
+          if (a.cube_out)
+            a.cube_out[((long long)it.m * a.n_bins + b) * a.seg_range + (i - a.seg_begin)] =
+                2.0f * fmaf(fx, fx, fy * fy) * a.inv_ns;
+          else
+            Fout[((long long)it.m * a.seg_range + (i - a.seg_begin)) * a.n_bins + b] = make_double2(fx, fy);
         } else {
           // (P - 2) / 2 with P = 2 |F|^2 / n_s (mu = sigma = 2)
           Z[b] += fmaf(fx, fx, fy * fy) * a.inv_ns - 1.0f;
@@ -556,16 +560,7 @@ k_plain(const TIN* __restrict__ strain, const double* __restrict__ betas, const 
 // ---------------------------------------------------------------------------
 // Statistic and top-k keys
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long make_key(float v, uint32_t flat) {
-  uint32_t u = __float_as_uint(v);
-  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-  return ((unsigned long long)u << 32) | (unsigned long long)(~flat);
-}
-__device__ __forceinline__ float key_value(unsigned long long k) {
-  uint32_t u = (uint32_t)(k >> 32);
-  u = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
-  return __uint_as_float(u);
-}
+// make_key / key_value: srs_device.cuh
 
 // Mixed form: n_sigma[m][b] = (sum over the template's items of Z) / sqrt(nseg_m),
 // items summed in order (FP64) so the result does not depend on scheduling.

@@ -14,6 +14,7 @@ struct AnchorArgs {
   double fs, t_coh, f_c;
   long long n_s;
   int span, n_anchor;
+  int local;                      // 1: every segment's template starts at its first sample (t_i0 = 0)
 };
 
 struct MixedArgs {
@@ -36,6 +37,7 @@ struct MixedArgs {
   const float* tw;                // [2 n_fine] interleaved exp(-2 pi i m / n_fine)
   const int* order;               // [n_items] queue position -> item, or NULL (item order)
   float2* grid_out;               // spectra mode: write the spread grid [template][segment][n_fine]
+  float* cube_out;                // spectra mode: write P = 2|F|^2/n_s to [template][bin][segment - seg_begin]
                                   // here and skip FFT / deconvolution (the cuFFT comparison), or NULL
   int8_t radices[16];
 };

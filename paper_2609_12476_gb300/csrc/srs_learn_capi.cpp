@@ -285,6 +285,7 @@ srs_status refine_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
   a.aa.n_s = pl.n_s;
   a.aa.span = pl.span;
   a.aa.n_anchor = pl.n_anchor;
+  a.aa.local = 0;
   SRS_CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
   SRS_CK(launch_sparse_bins(s32, ctx->sp_items.as<SparseItem>(), (int)items.size(), ctx->sp_betas.as<double>(),
                             ctx->sp_bins.as<int>(), a, ctx->sp_partial.as<float>(), ctx->n_sm, ctx->stream),

@@ -175,6 +175,7 @@ srs_status run(void* stream_v, const void* strain, int64_t n_samples, int32_t dt
   a.aa.n_s = pl.n_s;
   a.aa.span = pl.span;
   a.aa.n_anchor = pl.n_anchor;
+  a.aa.local = 0;
   a.fft_fixed = (pl.n_fine == 1200 && pl.radices == std::vector<int32_t>{4, 4, 3, 5, 5}) ? 1200 : 0;
   a.kc = (float)pl.k_c;
   a.kc_int = (pl.k_c >= 1.0 && pl.k_c < 1073741824.0 && pl.k_c == std::floor(pl.k_c)) ? (int)pl.k_c : 0;

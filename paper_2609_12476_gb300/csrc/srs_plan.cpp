@@ -105,10 +105,12 @@ double chirp_beta(double mc, double f) {
 }
 
 srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates, int64_t n_samples,
-                     bool spectra_mode, int32_t seg_begin, int32_t seg_end, Plan& pl, std::string& msg) {
+                     bool spectra_mode, int32_t seg_begin, int32_t seg_end, Plan& pl, std::string& msg,
+                     const double* betas_in, bool local) {
   char buf[256];
   auto fail = [&](srs_status s, const char* m) { msg = m; return s; };
-  if (!mc || n_templates <= 0) return fail(SRS_ERR_ARG, "need at least one template (mc != NULL)");
+  if ((!mc && !betas_in) || n_templates <= 0) return fail(SRS_ERR_ARG, "need at least one template (mc != NULL)");
+  if (local && !spectra_mode) return fail(SRS_ERR_ARG, "per-segment templates are a spectra-mode plan");
   if (!(p.fs > 0) || !(p.t_coh > 0)) return fail(SRS_ERR_ARG, "fs and t_coh must be positive");
   double ns_d = p.t_coh * p.fs;
   if (!is_int(ns_d, 1e-9) || ns_d < 1) return fail(SRS_ERR_ARG, "t_coh * fs must be a positive integer");
@@ -133,6 +135,7 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
   pl.k_c = pl.f_c * p.t_coh;
   pl.precision = p.precision;
   pl.cut = p.cut_segments ? 1 : 0;
+  pl.local = local;
   pl.n_templates = n_templates;
   if (n_samples < pl.n_s) return fail(SRS_ERR_ARG, "strain shorter than one segment");
   if (pl.n_s > (1 << 24)) return fail(SRS_ERR_UNSUPPORTED, "segments longer than 2^24 samples");
@@ -154,8 +157,14 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
   const double beta_scale = 96.0 / 5.0 * std::pow(kPi, 8.0 / 3.0) * std::pow(p.f_ref, 8.0 / 3.0);
   const double exit_frac = 1.0 - std::pow(p.f_ref / p.f_hi, 8.0 / 3.0);
   for (int32_t m = 0; m < n_templates; ++m) {
-    if (!(mc[m] > 0) || !std::isfinite(mc[m])) return fail(SRS_ERR_ARG, "chirp masses must be positive and finite");
-    double b = beta_scale * std::pow(kGMsunC3 * mc[m], 5.0 / 3.0);
+    double b;
+    if (betas_in) {
+      b = betas_in[m];
+      if (!(b > 0) || !std::isfinite(b)) return fail(SRS_ERR_ARG, "chirp parameters beta must be positive and finite");
+    } else {
+      if (!(mc[m] > 0) || !std::isfinite(mc[m])) return fail(SRS_ERR_ARG, "chirp masses must be positive and finite");
+      b = beta_scale * std::pow(kGMsunC3 * mc[m], 5.0 / 3.0);
+    }
     pl.beta[m] = b;
     int32_t ns = pl.n_seg_total;
     if (pl.cut) {
@@ -165,7 +174,8 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
     }
     pl.nseg[m] = ns;
     int32_t last_seg = spectra_mode ? seg_end : ns;
-    double t_last = ((double)last_seg * (double)pl.n_s - 1.0) / p.fs;
+    // the last sample's time on the template's own clock (segment-local: within one segment)
+    double t_last = ((double)(local ? 1 : last_seg) * (double)pl.n_s - 1.0) / p.fs;
     if (!(1.0 - 8.0 / 3.0 * b * t_last > 0.0)) {
       std::snprintf(buf, sizeof buf, "template %d reaches coalescence inside its segments (Sec. II: 1 - 8/3 beta t <= 0)", m);
       msg = buf;
@@ -243,7 +253,7 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
     const double lim6 = 1e-9 / (std::pow(ds, 6) * fmax), lim2 = 0.25 * p.t_coh / (ds * ds);
     pl.allow_128 = true;
     for (int32_t m = 0; m < n_templates; ++m) {
-      int32_t last_seg = spectra_mode ? seg_end : pl.nseg[m];
+      int32_t last_seg = local ? 1 : (spectra_mode ? seg_end : pl.nseg[m]);
       double A = 1.0 - 8.0 / 3.0 * pl.beta[m] * (((double)last_seg * pl.n_s) / p.fs);
       A = std::max(A, 1e-300);
       const double lb = std::log(pl.beta[m]), la = std::log(A);

@@ -1,0 +1,163 @@
+// srs_slide.cu -- stack-slide over the per-segment power cube (Sec. III.C,
+// Eqs. (weights) and (semicoherent_statistic) with equal weights; Sec. VI).
+//
+// Stage two of the two-stage search.  Stage one (k_mixed in spectra mode with
+// per-segment templates) writes P[k][j][i]: bank entry k, bin j, segment i
+// innermost.  A template theta = {Mc, t0 = (n + c) T} reads one power per
+// segment of its track.  Rows r share (Mc, c) and differ only in the whole
+// segment n of t0, so the tracks of one row are one (k_s, j_s) sequence
+// shifted in i: a warp of 32 consecutive n reads 32 consecutive floats of
+// the same cube row at every step, a coalesced 128-byte request.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "srs_device.cuh"
+#include "srs_slide.h"
+
+namespace srs {
+
+namespace {
+
+constexpr int kSlideThreads = 256;   // t0 columns per block
+constexpr int kSlideStage = 2048;    // track cells staged in shared memory at a time
+constexpr int kTrackThreads = 256;
+
+// One (row, track segment) per thread.  The 0PN frequency at the segment's
+// first sample, dt = (s + [c > 0] - c) T after t0 (Eq. f):
+//   A = 1 - (8/3) beta0 dt,  f = f0 A^(-3/8),
+// its nearest bin rint((f - f_lo) T), and the nearest bank entry to the local
+// chirp parameter beta(Mc, f) = beta0 (f / f0)^(8/3) = beta0 / A (Eq. beta).
+// A segment is on the track while A > 0 and its bin is inside the band; the
+// frequency only rises, so the valid segments are a prefix of the row.
+__global__ void k_slide_tracks(const double* __restrict__ beta0, const double* __restrict__ frac, int n_rows,
+                               TrackArgs t, int* __restrict__ cell) {
+  const long long total = (long long)n_rows * t.n_total;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / t.n_total);
+    const int s = (int)(idx - (long long)r * t.n_total);
+    const double b0 = beta0[r];
+    const double c = frac[r];
+    const double dt = ((double)s + (c > 0.0 ? 1.0 : 0.0) - c) * t.t_coh;
+    const double A = 1.0 - (8.0 / 3.0) * b0 * dt;
+    int out = -1;
+    if (A > 0.0) {
+      const double f = t.f0 * exp(-0.375 * log(A));
+      const double jd = rint((f - t.f_lo) * t.t_coh);
+      if (jd >= 0.0 && jd <= (double)(t.n_bins - 1)) {
+        double kd = t.dbeta > 0.0 ? rint((b0 / A - t.beta_min) / t.dbeta) : 0.0;
+        kd = fmin(fmax(kd, 0.0), (double)(t.n_beta - 1));
+        out = (int)kd * t.n_bins + (int)jd;
+      }
+    }
+    cell[idx] = out;
+  }
+}
+
+// len[r] = index of the first -1 in row r (one warp per row).
+__global__ void k_slide_lengths(const int* __restrict__ cell, int n_rows, int n_total, int* __restrict__ len) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n_rows) return;
+  const int* row = cell + (long long)warp * n_total;
+  int L = n_total;
+  for (int s0 = 0; s0 < n_total; s0 += 32) {
+    const int s = s0 + lane;
+    const unsigned end = __ballot_sync(0xffffffffu, s < n_total && row[s] < 0);
+    if (end) {
+      L = s0 + __ffs(end) - 1;
+      break;
+    }
+  }
+  if (lane == 0) len[warp] = L;
+}
+
+// Block = (row r, tile of kSlideThreads t0 columns).  Thread n sums the
+// powers of its track segments s whose segment i = first + s lies in the
+// chunk, first = n + [c > 0], and s < min(len_r, n_total - first).  The
+// row's track cells are staged in shared memory; four accumulators keep four
+// loads in flight per thread.
+__global__ void __launch_bounds__(kSlideThreads)
+k_stack_slide(const float* __restrict__ cube, const int* __restrict__ cell, const int* __restrict__ len,
+              const double* __restrict__ frac, SlideArgs a, float* __restrict__ Z, float* __restrict__ map,
+              unsigned long long* __restrict__ keys) {
+  __shared__ int sc[kSlideStage];
+  const int tiles = (a.n_t0 + kSlideThreads - 1) / kSlideThreads;
+  const int r = blockIdx.x / tiles;
+  const int tile = blockIdx.x - r * tiles;
+  const int n0 = tile * kSlideThreads;
+  const int n = n0 + threadIdx.x;
+  const int e = frac[r] > 0.0 ? 1 : 0;
+  const int L = len[r];
+  const int first = n + e;
+  const int Lp = max(0, min(L, a.n_total - first));           // N_seg(theta) inside the data
+  const int s_lo = max(0, a.seg_begin - first);
+  const int s_hi = n < a.n_t0 ? min(Lp, a.seg_end - first) : 0;
+  // the block's union of track steps inside the chunk
+  const int last_n = min(n0 + kSlideThreads, a.n_t0) - 1;
+  const int S_lo = max(0, a.seg_begin - (last_n + e));
+  const int S_hi = min(L, a.seg_end - (n0 + e));
+  const int* __restrict__ crow = cell + (long long)r * a.n_total;
+  // cube index of track step s: cell_s * ld + (first + s - seg_begin)
+  const long long c0 = (long long)first - a.seg_begin;
+  float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
+  for (int base = S_lo; base < S_hi; base += kSlideStage) {
+    const int cnt = min(kSlideStage, S_hi - base);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += kSlideThreads) sc[t] = crow[base + t];
+    __syncthreads();
+    const int lo = max(s_lo, base), hi = min(s_hi, base + cnt);
+    int s = lo;
+    for (; s + 3 < hi; s += 4) {
+      const float p0 = __ldg(cube + ((long long)sc[s - base] * a.ld + c0 + s));
+      const float p1 = __ldg(cube + ((long long)sc[s + 1 - base] * a.ld + c0 + s + 1));
+      const float p2 = __ldg(cube + ((long long)sc[s + 2 - base] * a.ld + c0 + s + 2));
+      const float p3 = __ldg(cube + ((long long)sc[s + 3 - base] * a.ld + c0 + s + 3));
+      z0 += fmaf(p0, 0.5f, -1.0f);
+      z1 += fmaf(p1, 0.5f, -1.0f);
+      z2 += fmaf(p2, 0.5f, -1.0f);
+      z3 += fmaf(p3, 0.5f, -1.0f);
+    }
+    for (; s < hi; ++s) z0 += fmaf(__ldg(cube + ((long long)sc[s - base] * a.ld + c0 + s)), 0.5f, -1.0f);
+  }
+  if (n >= a.n_t0) return;
+  const long long o = (long long)r * a.n_t0 + n;
+  float z = (z0 + z1) + (z2 + z3);
+  if (!a.first) z += Z[o];
+  if (!a.last) {
+    Z[o] = z;
+    return;
+  }
+  const float v = Lp > 0 ? z / sqrtf((float)Lp) : 0.f;
+  if (map) map[o] = v;
+  keys[o] = make_key(v, (uint32_t)o);
+}
+
+}  // namespace
+
+cudaError_t launch_slide_tracks(const double* beta0, const double* frac, int n_rows, const TrackArgs& t,
+                                int* cell, int* len, int n_sm, cudaStream_t st) {
+  const long long total = (long long)n_rows * t.n_total;
+  if (total <= 0) return cudaSuccess;
+  long long blocks = (total + kTrackThreads - 1) / kTrackThreads;
+  if (blocks > (long long)n_sm * 32) blocks = (long long)n_sm * 32;
+  k_slide_tracks<<<(unsigned)blocks, kTrackThreads, 0, st>>>(beta0, frac, n_rows, t, cell);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long threads = (long long)n_rows * 32;
+  k_slide_lengths<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(cell, n_rows, t.n_total, len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stack_slide(const float* cube, const int* cell, const int* len, const double* frac,
+                               const SlideArgs& a, float* Z, float* map, unsigned long long* keys,
+                               cudaStream_t st) {
+  const long long tiles = (a.n_t0 + kSlideThreads - 1) / kSlideThreads;
+  const long long blocks = tiles * a.n_rows;
+  if (blocks <= 0) return cudaSuccess;
+  k_stack_slide<<<(unsigned)blocks, kSlideThreads, 0, st>>>(cube, cell, len, frac, a, Z, map, keys);
+  return cudaGetLastError();
+}
+
+}  // namespace srs
