@@ -5,12 +5,19 @@ segment sum, n_sigma, top-k) over the workload's templates and segments.
 Metric: segment spectra per second (templates x segments) at eps = 1e-6.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload semicoherent_2h|batched_6h|large_24h]
+                  [--workload semicoherent_2h|batched_6h|large_24h|learned_6h|
+                              stackslide_6h|stackslide_24h]
 
 Default workload: 2 h of float64 strain at 256 Hz (240 segments of 30 s),
 64 chirp-mass templates log-spaced 2e-2..5e-2 Msun, 40-60 Hz, eps 1e-6,
 top-32, one injected chirp; synthetic seeded data.  Inputs are smaller than
 L2, so L2 is flushed (256 MB write) before every timed step.
+
+The stackslide workloads time the two-stage search instead: a power cube of
+every segment under each of the 69 local resampling templates, then the
+stack-slide over {Mc, t0} templates (one step = both stages over the whole
+strain).  The default line carries the same measurement on stackslide_24h as
+its "two_stage" object.
 
 --impl reference times the FP64 CPU oracle (direct non-uniform DFT) on the
 host cores on a bounded sample of the same workload.
@@ -44,9 +51,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="semicoherent_2h", choices=sorted(srs_synth.WORKLOADS) + ["learned_6h"])
+    ap.add_argument("--workload", default="semicoherent_2h",
+                    choices=sorted(srs_synth.WORKLOADS) + sorted(srs_synth.SLIDE_WORKLOADS) + ["learned_6h"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 and cuFFT comparisons")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-two-stage", action="store_true", help="skip the two-stage (cube + stack-slide) measurement")
     return ap.parse_args()
 
 
@@ -157,15 +166,17 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w = workload(args.workload, 0)
+    slide_wl = args.workload in srs_synth.SLIDE_WORKLOADS
+    w = srs_synth.make_slide_workload(args.workload) if slide_wl else workload(args.workload, 0)
+    rate = cpu_oracle_cube_rate if slide_wl else cpu_oracle_rate
     steps, warm = args.steps, args.warmup
     budget = min(20.0, max(0.2, 150.0 / max(1, steps + warm)))
     for _ in range(warm):
-        cpu_oracle_rate(w, budget_s=budget * 0.25)
+        rate(w, budget_s=budget * 0.25)
     vals, secs = [], []
     info = None
     for s in range(steps):
-        info = cpu_oracle_rate(w, budget_s=budget, seed=1000 + s)
+        info = rate(w, budget_s=budget, seed=1000 + s)
         vals.append(info["value"])
         secs.append(info["seconds"])
     v = float(np.mean(vals))
@@ -173,7 +184,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
             "warmup": warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic (seeded N(0,1) noise + 0PN chirps)",
-            "config": {"workload": args.workload, "templates": int(len(w["mc"])), "spectra_per_step": sum_spectra(w),
+            "config": {"workload": args.workload, "templates": int(len(w["mc"])),
+                       "spectra_per_step": (int(w["bank"][2]) * int(w["n_total"])) if slide_wl else sum_spectra(w),
                        "eps": w["eps"], "l2": "oracle on host cores (no GPU)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
                              "sample": info["sample"]},
@@ -285,6 +297,10 @@ def run_ours(args):
         fftcmp = None
         if not args.no_plain and args.workload == "semicoherent_2h":
             fftcmp = time_fft_comparison(ctx, xd, w, flush)
+        two = None
+        if not args.no_two_stage and args.workload == "semicoherent_2h" and world == 1:
+            two = two_stage_measure(ctx, stream, dev, flush, "stackslide_24h", 10, 3, pk, host_e2e=False)
+            two.pop("_w")
         cpu = None if (args.no_cpu or world > 1) else cpu_oracle_rate(w, ctx=ctx)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -299,7 +315,7 @@ def run_ours(args):
                            "l2": "flushed (256 MB write) before every timed step"},
                 "roofline": roof, "roofline_fma": roof_fma, "roofline_hbm": roof_hbm, "clocks": ck,
                 "gpu_launches": launches,
-                "e2e": e2e, "cpu_baseline": cpu, "plain_fp64": plain, "cufft_comparison": fftcmp,
+                "e2e": e2e, "cpu_baseline": cpu, "plain_fp64": plain, "cufft_comparison": fftcmp, "two_stage": two,
                 "spread_ms_avg": spread_avg, "search_device_ms_avg": rep["device_ms"]}
         print(json.dumps(line), flush=True)
     barrier(world)
@@ -329,19 +345,18 @@ def xu_roofline(n_spec, n_s, w_taps, kernel_ms, n_sm, sm_mhz, traffic):
             "slots_per_sample": w_taps * (1 + XU_EX2_SLOT) + 2}
 
 
-def profile_traffic(name):
+def profile_traffic(name, sources=("srs_kernels.cu", "srs_device.cuh"), key="traffic_bytes_per_launch"):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the kernel source that is built now (hash of srs_kernels.cu + srs_device.cuh)."""
+    the kernel source that is built now (hash of the kernel's source files)."""
     import hashlib
     try:
         txt = open(os.path.join(ROOT, "profiles", name)).read()
         csrc = os.path.join(ROOT, "paper_2609_12476_gb300", "csrc")
-        h = hashlib.sha256(open(os.path.join(csrc, "srs_kernels.cu"), "rb").read() +
-                           open(os.path.join(csrc, "srs_device.cuh"), "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256(b"".join(open(os.path.join(csrc, f), "rb").read() for f in sources)).hexdigest()[:16]
         if h not in txt:
             return None
         for line in txt.splitlines():
-            if line.startswith("traffic_bytes_per_launch:"):
+            if line.startswith(key + ":"):
                 return int(line.split(":")[1])
     except Exception:
         return None
@@ -404,6 +419,143 @@ def time_fft_comparison(ctx, xd, w, flush, steps=3, seg_end=112):
             "unfused_ms": un[0], "unfused_spread_ms": un[1], "unfused_cufft_ms": un[2],
             "unfused_deconv_ms": un[0] - un[1] - un[2], "grid_bytes": n_spec * un[3] * 8,
             "fused_speedup": un[0] / fu[0] if fu[0] > 0 else None, "steps": steps}
+
+
+def two_stage_measure(ctx, stream, dev, flush, name, steps, warmup, pk, host_e2e=True):
+    """The two-stage search (power cube over the local bank, then the
+    stack-slide over {Mc, t0}) on a slide workload: device time per step with
+    the strain resident, the cube and stack-slide kernels' own times, and the
+    end-to-end rate through the public API from a pinned host strain."""
+    import torch
+    from paper_2609_12476_gb300 import Params
+    w = srs_synth.make_slide_workload(name)
+    p = Params(fs=w["fs"], t_coh=w["t_coh"], f_lo=w["f_lo"], f_hi=w["f_hi"], eps=w["eps"], top_k=w["top_k"])
+    xd = torch.from_numpy(np.ascontiguousarray(w["strain"])).to(dev)
+    args = (w["bank"], w["rows_mc"], w["rows_c"], w["n_total"], p)
+    out = None
+    for _ in range(warmup):
+        out, rep = ctx.slide_search(xd, *args, want_map=False, out=out)
+    torch.cuda.synchronize()
+    clocks = Clocks(dev.index or 0)
+    tot, cube_ms, slide_ms = 0.0, [], []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out, rep = ctx.slide_search(xd, *args, want_map=False, out=out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b)
+        cube_ms.append(rep["spread_ms"])
+        slide_ms.append(rep["slide_ms"])
+    ck = clocks.stop()
+    n_spec = int(rep["n_spectra"])
+    reads = int(rep["slide_reads"])
+    n_tmpl = int(w["rows_mc"].size) * int(w["n_total"])
+    sl = float(np.mean(slide_ms))
+    cb = float(np.mean(cube_ms))
+    sm_mhz = (ck or {}).get("sm_mhz") or (pk or {}).get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    n_s = int(round(w["t_coh"] * w["fs"]))
+    hbm_peak = pk["hbm_gbs"] if pk else 6800.0
+    ach = reads * 4 / (sl * 1e-3) / 1e9
+    res = {"workload": name, "value": n_spec * steps / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / steps,
+           "steps": steps, "warmup": warmup, "spectra_per_step": n_spec,
+           "config": {"strain": "%d samples %s at %g Hz" % (w["n_samples"], w["dtype"], w["fs"]),
+                      "bank": "%d beta uniform %g..%g 1/s" % (w["bank"][2], w["bank"][0], w["bank"][1]),
+                      "templates": "%d rows (Mc, t0 fraction) x %d t0 columns = %d" % (w["rows_mc"].size, w["n_total"],
+                                                                                    n_tmpl),
+                      "eps": w["eps"], "w": rep["w"], "cube_chunks": rep["n_items"],
+                      "l2": "flushed (256 MB write) before every timed step; the cube (%d MB) exceeds L2"
+                            % (n_spec * 600 * 4 // (1 << 20))},
+           "cube_ms": cb, "slide_ms": sl, "templates_per_s": n_tmpl / (sl * 1e-3),
+           "power_reads_per_step": reads,
+           "roofline_cube": xu_roofline(n_spec, n_s, int(rep["w"]), cb, n_sm, sm_mhz,
+                                        profile_traffic("two_stage_24h.md", ("srs_kernels.cu", "srs_device.cuh"),
+                                                        "k_mixed cube traffic_bytes_per_launch")
+                                        if name == "stackslide_24h" else None),
+           "roofline_slide": {"kernel": "k_stack_slide", "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                              "unit": "GB/s", "frac": ach / hbm_peak,
+                              "traffic": profile_traffic("two_stage_24h.md", ("srs_slide.cu", "srs_device.cuh"),
+                                                         "k_stack_slide traffic_bytes_per_launch")
+                              if name == "stackslide_24h" else None,
+                              "peak_source": "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback 6.8 TB/s",
+                              "algorithmic_bytes": "power reads x 4 B: every template reads its track's powers "
+                                                   "once (no reuse between templates, as in Sec. VI's cost model)"},
+           "clocks": ck, "gpu_launches": int(rep["kernel_launches"]) * steps}
+    if host_e2e:
+        host = torch.from_numpy(np.ascontiguousarray(w["strain"])).pin_memory().numpy()
+        for _ in range(2):
+            ctx.slide_search(host, *args, want_map=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            ctx.slide_search(host, *args, want_map=False)
+        e2e_s = time.perf_counter() - t0
+        res["e2e"] = {"value": n_spec * steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(host.nbytes),
+                      "d2h_bytes_per_step": int(p.top_k * 12)}
+    res["_w"] = w
+    return res
+
+
+def cpu_oracle_cube_rate(w, budget_s=12.0, seed=1234):
+    """Oracle power-cube spectra/s on the host cores (direct FP64 NDFT with the
+    segment-local time map), on a seeded random sample of (bank entry, segment)."""
+    import oracle
+    from oracle import slide
+    bank = slide.local_bank(*w["bank"])
+    n_b = int(round((w["f_hi"] - w["f_lo"]) * w["t_coh"]))
+    strain = np.asarray(w["strain"], dtype=np.float64)
+    cores = os.cpu_count() or 1
+    r = np.random.default_rng(seed)
+    n_all = len(bank) * w["n_total"]
+    pick = lambda n: [(int(q // w["n_total"]), int(q % w["n_total"])) for q in r.choice(n_all, size=n, replace=False)]
+    calib = pick(cores)
+    t0 = time.perf_counter()
+    oracle.spectra(strain, w["fs"], w["t_coh"], w["f_lo"], n_b, bank, calib, n_threads=cores, local=True)
+    per = (time.perf_counter() - t0) / len(calib)
+    n = int(max(cores, min(n_all, budget_s / max(per, 1e-6))))
+    sample = pick(n)
+    t0 = time.perf_counter()
+    oracle.spectra(strain, w["fs"], w["t_coh"], w["f_lo"], n_b, bank, sample, n_threads=cores, local=True)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "seconds": dt,
+            "sample": "%d random (bank entry, segment) spectra of %d (seed %d): direct FP64 NDFT, segment-local "
+                      "time map" % (n, n_all, seed)}
+
+
+def run_two_stage(args):
+    import torch
+    from paper_2609_12476_gb300 import Context
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = Context(local, stream=ctx_stream(stream))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    barrier(world)
+    res = two_stage_measure(ctx, stream, dev, flush, args.workload, args.steps, max(3, args.warmup), peaks())
+    total_ms = max_over_ranks(res["ms_per_step"] * args.steps, world)
+    w = res.pop("_w")
+    if rank == 0:
+        value = world * res["spectra_per_step"] * args.steps / (total_ms * 1e-3)
+        cpu = None if (args.no_cpu or world > 1) else cpu_oracle_cube_rate(w)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": res["warmup"], "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded N(0,1) noise + 0PN chirps entering the band)",
+                "config": dict(res["config"], workload=args.workload),
+                "roofline": res["roofline_cube"], "roofline_slide": res["roofline_slide"], "clocks": res["clocks"],
+                "gpu_launches": res["gpu_launches"], "e2e": res.get("e2e"), "cpu_baseline": cpu,
+                "cube_ms": res["cube_ms"], "slide_ms": res["slide_ms"], "templates_per_s": res["templates_per_s"],
+                "power_reads_per_step": res["power_reads_per_step"]}
+        print(json.dumps(line), flush=True)
+    barrier(world)
+    ctx.close()
 
 
 def barrier(world):
@@ -510,6 +662,8 @@ def main():
         run_reference(args)
     elif args.workload == "learned_6h":
         run_learned(args)
+    elif args.workload in srs_synth.SLIDE_WORKLOADS:
+        run_two_stage(args)
     else:
         run_ours(args)
 

@@ -145,6 +145,7 @@ typedef struct {
   int32_t ctas_per_sm;    /* mixed form: resident CTAs per SM the search asked for (0 = as many as fit) */
   double fft_ms;          /* srs_segment_spectra_cufft only: device time of the cuFFT transforms */
   double slide_ms;        /* two-stage calls: device time of the stack-slide kernels */
+  int64_t slide_reads;    /* two-stage calls: cube powers the stack-slide summed (track segments over all templates) */
 } srs_report;
 
 /* Environment variables read by the library (diagnostics and profiling):

@@ -60,7 +60,7 @@ class _Report(ctypes.Structure):
                 ("sigma", ctypes.c_double), ("beta_es", ctypes.c_double), ("chunk", ctypes.c_int32),
                 ("n_items", ctypes.c_int32), ("kernel_launches", ctypes.c_int32), ("spread_ms", ctypes.c_double),
                 ("cta_threads", ctypes.c_int32), ("staging", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("fft_ms", ctypes.c_double), ("slide_ms", ctypes.c_double)]
+                ("fft_ms", ctypes.c_double), ("slide_ms", ctypes.c_double), ("slide_reads", ctypes.c_int64)]
 
 
 class _Bank(ctypes.Structure):

@@ -985,6 +985,132 @@ srs_status clear_err_flag(srs_ctx* ctx) {
 
 srs_status read_err_flag(srs_ctx* ctx) { return check_err_flag(ctx); }
 
+}  // namespace srs
+
+namespace {
+
+// Power-cube work items: [seg_begin, seg_end) of every bank entry in chunks,
+// queued segment-major (all bank entries of one segment chunk, then the next)
+// so that the bank's CTAs share each chunk's samples in L2 and fill the
+// cube's segment-innermost rows in order.
+srs_status cube_items(srs_ctx* ctx, Plan& pl, int32_t chunk, int32_t seg_begin, int32_t seg_end) {
+  make_items(pl, chunk, true, seg_begin, seg_end);
+  pl.order.clear();
+  int32_t most = 0;
+  for (int32_t m = 0; m < pl.n_templates; ++m) most = std::max(most, pl.item_off[m + 1] - pl.item_off[m]);
+  for (int32_t c = 0; c < most; ++c)
+    for (int32_t m = 0; m < pl.n_templates; ++m)
+      if (pl.item_off[m] + c < pl.item_off[m + 1]) pl.order.push_back(pl.item_off[m] + c);
+  SRS_CK(ctx->items.ensure(pl.items.size() * sizeof(Item)), "alloc items");
+  SRS_CK(ctx->order.ensure(pl.order.size() * 4), "alloc order");
+  SRS_CK(cudaMemcpyAsync(ctx->items.p, pl.items.data(), pl.items.size() * sizeof(Item), cudaMemcpyHostToDevice,
+                         ctx->stream), "copy items");
+  SRS_CK(cudaMemcpyAsync(ctx->order.p, pl.order.data(), pl.order.size() * 4, cudaMemcpyHostToDevice, ctx->stream),
+         "copy order");
+  // the host vectors may change on the next plan: finish the copies now
+  SRS_CK(cudaStreamSynchronize(ctx->stream), "copy items");
+  return SRS_OK;
+}
+
+// Layout tuner of the power cube, like the search's (CTA size, staging,
+// segments per item, resident CTAs per SM), timed on the first queue
+// positions (at most kTuneSpectra / 2 spectra) and kept per shape.
+srs_status tune_cube(srs_ctx* ctx, Plan& pl, const float* x, int use_tma, float* dcube, int32_t seg_begin,
+                     int32_t seg_end) {
+  std::vector<unsigned char> key = {'c', 'u', 'b', 'e'};
+  auto put = [&](const void* d, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(d);
+    key.insert(key.end(), c, c + n);
+  };
+  const int32_t range = seg_end - seg_begin;
+  put(&pl.n_s, sizeof pl.n_s);
+  put(&pl.n_bins, sizeof pl.n_bins);
+  put(&pl.n_fine, sizeof pl.n_fine);
+  put(&pl.w, sizeof pl.w);
+  put(&pl.n_templates, sizeof pl.n_templates);
+  put(&range, sizeof range);
+  key.push_back((unsigned char)use_tma);
+  key.push_back((unsigned char)pl.allow_128);
+  const char* lay = std::getenv("SRS_MIXED_LAYOUT");
+  int only_threads = 0, only_gx = -1;
+  if (lay) {
+    const std::string l(lay);
+    key.insert(key.end(), l.begin(), l.end());
+    if (l.rfind("128", 0) == 0) only_threads = 128;
+    if (l.rfind("256", 0) == 0) only_threads = 256;
+    if (l.find(":global") != std::string::npos) only_gx = 1;
+    if (l.find(":tma") != std::string::npos) only_gx = 0;
+  }
+  for (const auto& t : ctx->tuned)
+    if (t.key == key) {
+      set_cta(pl, t.threads);
+      pl.global_x = t.global_x != 0;
+      pl.ctas = t.ctas;
+      srs_status s = cube_items(ctx, pl, t.chunk, seg_begin, seg_end);
+      if (s == SRS_OK) pl.tuned_items = true;
+      return s;
+    }
+  const long long total = (long long)pl.n_templates * range;
+  const long long tune_cap = kTuneSpectra / 2;
+  struct Choice { int chunk, ctas, threads, global_x; };
+  Choice best_c{4, 0, kSpreadThreads, use_tma ? 0 : 1};
+  double best = 1e30;
+  for (int threads : {256, 128}) {
+    if (threads == 128 && !pl.allow_128) continue;
+    if (only_threads && threads != only_threads) continue;
+    set_cta(pl, threads);
+    for (int gx : {0, 1}) {
+      if (gx == 0 && !use_tma) continue;
+      if (only_gx >= 0 && gx != only_gx) continue;
+      for (int ch : {2, 4, 8, 16}) {
+        if (ch > range && ch != 2) continue;
+        srs_status s = cube_items(ctx, pl, ch, seg_begin, seg_end);
+        if (s != SRS_OK) return s;
+        // the first queue positions, up to tune_cap spectra
+        int n_pos = 0;
+        long long spectra = 0;
+        while (n_pos < (int)pl.order.size() && spectra < tune_cap) {
+          const Item& it = pl.items[(size_t)pl.order[(size_t)n_pos++]];
+          spectra += it.i1 - it.i0;
+        }
+        MixedArgs a = mixed_args(pl, ctx, seg_begin, range);
+        a.use_tma = gx ? 0 : 1;
+        a.cube_out = dcube;
+        const int c256[] = {0, 3}, c128[] = {0, 7, 6};
+        const int* ctl = threads == 256 ? c256 : c128;
+        const int n_ct = threads == 256 ? 2 : 3;
+        for (int ci = 0; ci < n_ct; ++ci) {
+          float best_ms = 1e30f;
+          for (int rep = 0; rep < 2; ++rep) {
+            SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
+            SRS_CK(cudaEventRecord(ctx->ev2, ctx->stream), "event");
+            SRS_CK(launch_mixed(true, pl.w, x, ctx->items.as<Item>(), n_pos, ctx->betas.as<double>(),
+                                ctx->queue.as<int>(), a, nullptr, nullptr, ctx->errflag.as<int>(), ctx->n_sm,
+                                ctl[ci], ctx->stream), "k_mixed (cube tuning)");
+            SRS_CK(cudaEventRecord(ctx->ev3, ctx->stream), "event");
+            SRS_CK(cudaEventSynchronize(ctx->ev3), "tuning");
+            best_ms = std::min(best_ms, elapsed_ms(ctx->ev2, ctx->ev3));
+          }
+          const double per = best_ms / (double)std::max<long long>(1, std::min(spectra, total));
+          if (per < best) { best = per; best_c = {ch, ctl[ci], threads, gx}; }
+        }
+      }
+    }
+  }
+  set_cta(pl, best_c.threads);
+  pl.global_x = best_c.global_x != 0;
+  pl.ctas = best_c.ctas;
+  srs_status s = cube_items(ctx, pl, best_c.chunk, seg_begin, seg_end);
+  if (s != SRS_OK) return s;
+  pl.tuned_items = true;
+  ctx->tuned.push_back({key, best_c.chunk, best_c.ctas, best_c.threads, best_c.global_x, best});
+  return SRS_OK;
+}
+
+}  // namespace
+
+namespace srs {
+
 srs_status cube_device(srs_ctx* ctx, const float* s32, int64_t n_samples, const std::vector<double>& bank,
                        int32_t seg_begin, int32_t seg_end, const srs_params* params, float* dcube, int* launches,
                        const Plan** plan_out) {
@@ -992,19 +1118,25 @@ srs_status cube_device(srs_ctx* ctx, const float* s32, int64_t n_samples, const 
   srs_status s = get_plan(ctx, 3, params, nullptr, (int32_t)bank.size(), n_samples, SRS_F32, true, seg_begin, seg_end,
                           &plp, bank.data(), true);
   if (s != SRS_OK) return s;
-  const Plan& pl = *plp;
+  Plan& pl = ctx->plan;
   if (plan_out) *plan_out = plp;
   if (pl.precision != SRS_MIXED) return set_err(ctx, SRS_ERR_UNSUPPORTED, "the power cube runs the mixed form only");
-  MixedArgs a = mixed_args(pl, ctx, seg_begin, seg_end - seg_begin);
   const float* x = nullptr;
-  s = strain_f32(ctx, s32, SRS_F32, (int64_t)seg_end * pl.n_s, pl.n_s, &x, &a.use_tma);
+  int use_tma = 0;
+  s = strain_f32(ctx, s32, SRS_F32, (int64_t)seg_end * pl.n_s, pl.n_s, &x, &use_tma);
   if (s != SRS_OK) return s;
-  a.cube_out = dcube;
   SRS_CK(ctx->queue.ensure(64), "alloc queue");
+  if (!pl.tuned_items) {
+    s = tune_cube(ctx, pl, x, use_tma, dcube, seg_begin, seg_end);
+    if (s != SRS_OK) return s;
+  }
+  MixedArgs a = mixed_args(pl, ctx, seg_begin, seg_end - seg_begin);
+  a.use_tma = (use_tma && !pl.global_x) ? 1 : 0;
+  a.cube_out = dcube;
   SRS_CK(cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream), "memset queue");
   SRS_CK(launch_mixed(true, pl.w, x, ctx->items.as<Item>(), (int)pl.items.size(), ctx->betas.as<double>(),
-                      ctx->queue.as<int>(), a, nullptr, nullptr, ctx->errflag.as<int>(), ctx->n_sm, 0, ctx->stream),
-         "k_mixed (power cube)");
+                      ctx->queue.as<int>(), a, nullptr, nullptr, ctx->errflag.as<int>(), ctx->n_sm, pl.ctas,
+                      ctx->stream), "k_mixed (power cube)");
   if (launches) ++*launches;
   return SRS_OK;
 }

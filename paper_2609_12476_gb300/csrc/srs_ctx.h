@@ -88,6 +88,9 @@ struct srs_ctx {
   bool slide_open = false;                // running sums started (SRS_SLIDE_FIRST) and not yet finished
   std::vector<unsigned char> slide_key;   // what slide_cell / slide_len were computed for
   std::vector<cudaEvent_t> slide_ev;      // per chunk: cube start, slide start, slide end
+  std::vector<int> slide_len_host;        // track length per row (copy of slide_len)
+  std::vector<double> slide_frac_host;    // t0 fraction per row
+  long long slide_reads_total = -1;       // cube powers a whole search over these tracks sums
   // learned proposal
   srs::DevBuf xb, yb, z1, logits, dz, lossv, grad, wts, adam_m, adam_v, w1h, w2h, idx, patches, cells_m, cells_b,
       sp_items, sp_bins, sp_partial, sp_cells, sp_out, sp_betas, cmap, ccands, inj;

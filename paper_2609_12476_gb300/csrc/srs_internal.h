@@ -70,6 +70,7 @@ struct Plan {
   std::vector<Item> items;
   std::vector<int32_t> order;                            // queue position -> item (empty: in item order)
   bool tuned_items = false;                              // items and order are the tuner's choice
+  int32_t ctas = 0;                                      // power cube: resident CTAs per SM the tuner chose (0: all that fit)
   std::vector<int32_t> item_off;                         // [n_templates+1] first item of template m
   // tables (FP64, converted by the launcher)
   std::vector<double> corr;                              // [n_bins] deconvolution factor

@@ -91,11 +91,32 @@ srs_status plan_tracks(srs_ctx* ctx, const srs_bank* bank, const srs_slide_grid*
   SRS_CK(launch_slide_tracks(ctx->slide_beta0.as<double>(), ctx->slide_frac.as<double>(), g->n_rows, t,
                              ctx->slide_cell.as<int>(), ctx->slide_len.as<int>(), ctx->n_sm, ctx->stream),
          "k_slide_tracks");
+  ctx->slide_len_host.assign((size_t)g->n_rows, 0);
+  SRS_CK(cudaMemcpyAsync(ctx->slide_len_host.data(), ctx->slide_len.p, (size_t)g->n_rows * 4, cudaMemcpyDeviceToHost,
+                         ctx->stream), "copy track lengths");
   // the host copies above read caller memory: finish them before returning
   SRS_CK(cudaStreamSynchronize(ctx->stream), "tracks");
+  ctx->slide_frac_host.assign(g->c, g->c + g->n_rows);
   ctx->slide_key.swap(key);
   ctx->have_slide = true;
   return SRS_OK;
+}
+
+// Cube powers one pass sums: over rows and t0 columns, the track segments
+// s < min(len_r, n_total - first) whose segment first + s lies in the chunk.
+long long count_reads(const srs_ctx* ctx, int32_t n_t0, int32_t n_total, int32_t seg_begin, int32_t seg_end) {
+  long long total = 0;
+  for (size_t r = 0; r < ctx->slide_len_host.size(); ++r) {
+    const int L = ctx->slide_len_host[r];
+    const int e = ctx->slide_frac_host[r] > 0.0 ? 1 : 0;
+    for (int32_t n = 0; n < n_t0; ++n) {
+      const int first = n + e;
+      const int hi = std::min(std::min(L, n_total - first), seg_end - first);
+      const int lo = std::max(0, seg_begin - first);
+      if (hi > lo) total += hi - lo;
+    }
+  }
+  return total;
 }
 
 cudaEvent_t slide_event(srs_ctx* ctx, size_t i) {
@@ -144,7 +165,8 @@ srs_status prepare_out(srs_ctx* ctx, const srs_slide_grid* g, const srs_params* 
   return SRS_OK;
 }
 
-// One stack-slide pass over a device cube chunk; with `last`, the top-k too.
+// One stack-slide pass over a device cube chunk (with `last`, it also writes
+// the map and the top-k keys).
 srs_status slide_pass(srs_ctx* ctx, const float* dcube, int32_t seg_begin, int32_t seg_end, int32_t n_total,
                       const srs_slide_grid* g, bool first, bool last, const SlideOut& o, int* launches) {
   SRS_CK(ctx->slide_Z.ensure((size_t)g->n_rows * g->n_t0 * 4), "alloc running sums");
@@ -161,7 +183,11 @@ srs_status slide_pass(srs_ctx* ctx, const float* dcube, int32_t seg_begin, int32
                             ctx->slide_Z.as<float>(), o.dmap, ctx->keys.as<unsigned long long>(), ctx->stream),
          "k_stack_slide");
   ++*launches;
-  if (!last) return SRS_OK;
+  return SRS_OK;
+}
+
+// Top-k of the finished map's keys into the candidates.
+srs_status slide_topk(srs_ctx* ctx, const srs_slide_grid* g, const SlideOut& o, int* launches) {
   const unsigned long long* top = nullptr;
   SRS_CK(launch_topk(ctx->keys.as<unsigned long long>(), o.n_map, o.k, ctx->topk_a.as<unsigned long long>(),
                      ctx->topk_b.as<unsigned long long>(), &top, launches, ctx->stream), "k_topk_tile");
@@ -217,6 +243,8 @@ srs_status stack_slide_impl(srs_ctx* ctx, const float* cube, int32_t seg_begin, 
   SRS_CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
   s = slide_pass(ctx, dcube, seg_begin, seg_end, n_total, g, first, last, o, &launches);
   if (s != SRS_OK) return s;
+  SRS_CK(cudaEventRecord(ctx->ev2, ctx->stream), "event");
+  if (last && (s = slide_topk(ctx, g, o, &launches)) != SRS_OK) return s;
   SRS_CK(cudaEventRecord(ctx->ev1, ctx->stream), "event");
   if (last) {
     s = copy_out(ctx, p, o, nsigma_map, cands);
@@ -228,7 +256,8 @@ srs_status stack_slide_impl(srs_ctx* ctx, const float* cube, int32_t seg_begin, 
   if (report) {
     std::memset(report, 0, sizeof *report);
     report->device_ms = elapsed_ms(ctx->ev0, ctx->ev1);
-    report->slide_ms = report->device_ms;
+    report->slide_ms = elapsed_ms(ctx->ev0, ctx->ev2);
+    report->slide_reads = count_reads(ctx, g->n_t0, n_total, seg_begin, seg_end);
     report->kernel_launches = launches;
   }
   return SRS_OK;
@@ -291,6 +320,8 @@ srs_status slide_search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples
     if (s != SRS_OK) return s;
     SRS_CK(cudaEventRecord(ctx->slide_ev[3 * c + 2], ctx->stream), "event");
   }
+  s = slide_topk(ctx, g, o, &launches);
+  if (s != SRS_OK) return s;
   SRS_CK(cudaEventRecord(ctx->ev1, ctx->stream), "event");
   s = copy_out(ctx, p, o, nsigma_map, cands);
   if (s != SRS_OK) return s;
@@ -306,6 +337,8 @@ srs_status slide_search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples
       report->slide_ms += elapsed_ms(ctx->slide_ev[3 * c + 1], ctx->slide_ev[3 * c + 2]);
     }
     report->n_spectra = (int64_t)bank->n_beta * n_total;
+    if (replanned || ctx->slide_reads_total < 0) ctx->slide_reads_total = count_reads(ctx, g->n_t0, n_total, 0, n_total);
+    report->slide_reads = ctx->slide_reads_total;
     report->spectra_per_s = report->device_ms > 0 ? report->n_spectra / (report->device_ms * 1e-3) : 0.0;
     report->w = pl->w;
     report->n_fine = pl->n_fine;

@@ -79,3 +79,45 @@ def test_six_hour_batched_search_rows_match_oracle():
     """The 6 h / 1024-template search with uneven segment counts (35 to 720
     segments per template): three rows across the bank."""
     _check_rows("batched_6h", [0, 511, 1023])
+
+
+def test_two_stage_24h_sampled_templates_match_oracle():
+    """The 24 h two-stage search in the configuration bench.py times (float32
+    strain on the device, 69-entry bank, 1270 x 2880 {Mc, t0} templates, one
+    cube chunk): sampled templates recomputed by the oracle from their
+    tracks' spectra, the heaviest rows (short tracks) and a light row cut by
+    the end of the data, within the bound the spectra tolerance implies."""
+    from oracle import slide
+    w = srs_synth.make_slide_workload("stackslide_24h")
+    p = Params(fs=w["fs"], t_coh=w["t_coh"], f_lo=w["f_lo"], f_hi=w["f_hi"], eps=w["eps"], top_k=32)
+    ctx = Context(0)
+    try:
+        xd = torch.from_numpy(np.ascontiguousarray(w["strain"])).cuda()
+        out, rep = ctx.slide_search(xd, w["bank"], w["rows_mc"], w["rows_c"], w["n_total"], p)
+        torch.cuda.synchronize()
+        m = out["map"].cpu().numpy()
+        cands = out["cands"].cpu().numpy()
+    finally:
+        ctx.close()
+    n_total, n_s, n_b = w["n_total"], 7680, 600
+    bank = slide.local_bank(*w["bank"])
+    x64 = np.asarray(w["strain"], dtype=np.float64)
+    R = w["rows_mc"].size
+    picks = [(R - 1, 100), (R - 1, 2000), (R - 20, 1234), (0, n_total - 25), (R // 2, n_total - 40)]
+    for r, n in picks:
+        mc, c = w["rows_mc"][r], w["rows_c"][r]
+        k, j = slide.track(mc, c, w["f_lo"], w["t_coh"], w["f_lo"], n_b, bank, n_total)
+        first = slide.first_segment(n, c)
+        L = max(0, min(len(k), n_total - first))
+        assert 0 < L <= 60, (r, n, L)
+        F = oracle.spectra(x64, w["fs"], w["t_coh"], w["f_lo"], n_b, bank,
+                           [(int(k[s]), first + s) for s in range(L)], local=True)
+        P = oracle.power(F[np.arange(L), j[:L]], n_s)
+        ref = slide.n_sigma_track(P)
+        d = 10 * w["eps"] * np.linalg.norm(F, axis=1)
+        dP = (4 * np.abs(F[np.arange(L), j[:L]]) * d + 2 * d ** 2) / n_s
+        tol = np.sum(dP) / (2 * np.sqrt(L)) + L * 2.0 ** -24 * np.sum(np.abs(P - 2) / 2) / np.sqrt(L) + 1e-5
+        assert abs(m[r, n] - ref) <= tol, (r, n, L, float(m[r, n]), ref, tol)
+    v, rr, nn = oracle.topk(m, 32)
+    assert np.array_equal(cands[:, 1], rr) and np.array_equal(cands[:, 2], nn)
+    assert rep["slide_reads"] > 0 and rep["n_items"] == 1
