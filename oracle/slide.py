@@ -15,7 +15,12 @@ Passages followed:
                   band's lower edge: frequency f_j and resampling template
                   beta_k in each segment), Sec. III.A Eq. (f), Sec. II Eq. (beta)
   stack_slide  -> Sec. III.C Eqs. (weights), (semicoherent_statistic) with
-                  equal weights w = 1/sqrt(N_seg(theta)), mu = sigma = 2
+                  mu = sigma = 2: equal weights w = 1/sqrt(N_seg(theta)), or
+                  w proportional to A_i^2 / S_eff (the segment average of the
+                  0PN amplitude squared, Sec. II Eq. (h0) h0 ~ f^(2/3), over
+                  an effective PSD table; rectangular window, Gamma = 1),
+                  normalised so that sum w^2 = 1; powers normalised by S_eff
+                  (Eq. (normalized_power))
 Readings where the paper leaves a choice (each also listed with the design
 notes): the track uses the segments that start at or after t0; its frequency
 in a segment is the 0PN frequency at the segment's first sample, rounded to
@@ -80,6 +85,23 @@ def track(mc, c, f0, t_coh, f_lo, n_b, bank, n_max):
     return np.asarray(ks, dtype=np.int64), np.asarray(js, dtype=np.int64)
 
 
+def amplitude_sq(mc, c, f0, t_coh, s):
+    """Segment average of the squared 0PN amplitude along the track, relative
+    to its value at f0 (Sec. II Eq. (h0): h0 ~ f^(2/3), so A^2 ~ f^(4/3)),
+    over the s-th track segment [dt_s, dt_s + T): 64-point Gauss-Legendre
+    quadrature of (f(t) / f0)^(4/3) by Eq. (f), zero past coalescence."""
+    b0 = beta(mc, f0)
+    dt = (s + (1.0 if c > 0 else 0.0) - c) * t_coh
+    t_c = 3.0 / (8.0 * b0)
+    hi = min(dt + t_coh, t_c)
+    if hi <= dt:
+        return 0.0
+    x, wq = np.polynomial.legendre.leggauss(64)
+    t = dt + (x + 1.0) * 0.5 * (hi - dt)
+    f = np.array([freq(b0, f0, v) for v in t])
+    return float(np.sum(wq * (f / f0) ** (4.0 / 3.0)) * 0.5 * (hi - dt) / t_coh)
+
+
 def n_sigma_track(P_track):
     """Eq. (semicoherent_statistic) over one track's powers with w = 1/sqrt(N)
     (so sum w^2 = 1) and mu = sigma = 2; 0 for an empty track."""
@@ -90,26 +112,51 @@ def n_sigma_track(P_track):
     return float(np.sum((P_track - 2.0) / 2.0) / np.sqrt(n))
 
 
-def stack_slide(cube, rows_mc, rows_c, n_t0, n_total, bank, f0, t_coh, f_lo, n_b, with_abs=False):
+def n_sigma_weighted(P_track, a, s_eff_track):
+    """Eq. (semicoherent_statistic) with weights w_s = a_s / sqrt(sum a_s^2)
+    (Eq. (weights) normalised), a_s = A_s^2 / S_s, and powers normalised by
+    the effective PSD S_s (relative to white unit-variance noise):
+    sum_s w_s (P_s / S_s - 2) / 2.  0 for an empty track."""
+    P = np.asarray(P_track, dtype=np.float64)
+    if P.size == 0:
+        return 0.0
+    S = np.asarray(s_eff_track, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64) / S
+    return float(np.sum(a * (P / S - 2.0) / 2.0) / np.sqrt(np.sum(a * a)))
+
+
+def stack_slide(cube, rows_mc, rows_c, n_t0, n_total, bank, f0, t_coh, f_lo, n_b, with_abs=False,
+                weighting=0, s_eff=None):
     """n_sigma[r][n] for theta = {rows_mc[r], t0 = (n + rows_c[r]) T} over a
-    cube P[k][j][i] that holds every segment i < n_total.  Also returns the
+    cube P[k][j][i] that holds every segment i < n_total.  weighting 0: equal
+    weights; 1: amplitude weights (amplitude_sq).  s_eff: [n_beta][n_bins]
+    effective PSD relative to white noise, or None (white).  Also returns the
     number of track segments N_seg[r][n] inside the data, and with
-    with_abs=True the sums of |P - 2| / 2 along each track (for rounding
-    bounds)."""
+    with_abs=True a bound helper: the sum over the track of
+    (|a P / S| + |2 a|) / 2 / sqrt(sum a^2)."""
     R = len(rows_mc)
     out = np.zeros((R, n_t0))
     nseg = np.zeros((R, n_t0), dtype=np.int64)
     absum = np.zeros((R, n_t0))
     for r in range(R):
         k, j = track(rows_mc[r], rows_c[r], f0, t_coh, f_lo, n_b, bank, n_total)
+        amp = (np.array([amplitude_sq(rows_mc[r], rows_c[r], f0, t_coh, s) for s in range(len(k))])
+               if weighting else np.ones(len(k)))
+        S_all = s_eff[k, j] if s_eff is not None else np.ones(len(k))
         for n in range(n_t0):
             first = first_segment(n, rows_c[r])
             L = max(0, min(len(k), n_total - first))
             i = first + np.arange(L)
             P = cube[k[:L], j[:L], i]
-            out[r, n] = n_sigma_track(P)
+            if weighting or s_eff is not None:
+                out[r, n] = n_sigma_weighted(P, amp[:L], S_all[:L])
+            else:
+                out[r, n] = n_sigma_track(P)
             nseg[r, n] = L
-            absum[r, n] = float(np.sum(np.abs(np.asarray(P, dtype=np.float64) - 2.0) / 2.0))
+            if L:
+                a = amp[:L] / S_all[:L]
+                absum[r, n] = float(np.sum(np.abs(a * np.asarray(P, dtype=np.float64) / S_all[:L]) + 2 * np.abs(a))
+                                    / 2.0 / np.sqrt(np.sum(a * a)))
     if with_abs:
         return out, nseg, absum
     return out, nseg

@@ -76,6 +76,12 @@ SLIDE_MUTANTS = [
      ["test_stack_slide_brute_force_on_a_random_cube"]),
     ("local map referenced to t = 0", "items, n_threads=n_threads, local=True)", "items, n_threads=n_threads, local=False)",
      ["test_power_cube_concentrates_an_entering_chirp"]),
+    ("amplitude to the power 2/3", "(f / f0) ** (4.0 / 3.0)", "(f / f0) ** (2.0 / 3.0)",
+     ["test_amplitude_average_matches_closed_form"]),
+    ("weights not normalised", "/ np.sqrt(np.sum(a * a)))\n\n\ndef stack_slide", ")\n\n\ndef stack_slide",
+     ["test_weighted_stack_slide_closed_forms"]),
+    ("power not divided by the PSD", "a * (P / S - 2.0) / 2.0", "a * (P - 2.0) / 2.0",
+     ["test_weighted_stack_slide_closed_forms"]),
 ]
 
 
@@ -89,12 +95,14 @@ def test_slide_pins_catch_planted_mistake(monkeypatch, name, orig, bad, catchers
     mod = types.ModuleType("oracle.slide_mutant")
     mod.__package__ = "oracle"
     exec(compile(src.replace(orig, bad), "slide_mutant.py", "exec"), mod.__dict__)
-    for fn in ("local_bank", "power_cube", "first_segment", "track", "n_sigma_track", "stack_slide"):
+    for fn in ("local_bank", "power_cube", "first_segment", "track", "n_sigma_track", "stack_slide", "amplitude_sq",
+               "n_sigma_weighted"):
         monkeypatch.setattr(slide, fn, getattr(mod, fn))
     for pin in catchers:
         fn = getattr(spins, pin)
         args = {"test_track_frequency_is_the_phase_derivative": [(6e-2, 0.25), (1e-2, 0.0)],
-                "test_track_length_matches_band_time": [(1e-1, 0.5)]}.get(pin)
+                "test_track_length_matches_band_time": [(1e-1, 0.5)],
+                "test_amplitude_average_matches_closed_form": [(1e-1, 0.6, 34)]}.get(pin)
         with pytest.raises(AssertionError):
             if args:
                 for a in args:

@@ -176,3 +176,72 @@ def test_power_cube_concentrates_an_entering_chirp():
         kk, jj = np.unravel_index(np.argmax(sl), sl.shape)
         assert abs(int(jj) - int(j[s])) <= 1 and abs(int(kk) - int(k[s])) <= 1, (i, kk, jj, k[s], j[s])
         assert sl.max() > 0.35 * amp ** 2 * n_s / 2
+
+
+@pytest.mark.parametrize("mc,c,s", [(1e-2, 0.0, 0), (1e-2, 0.3, 500), (1e-1, 0.0, 30), (1e-1, 0.6, 34), (3e-3, 0.0, 2000)])
+def test_amplitude_average_matches_closed_form(mc, c, s):
+    """A^2 ~ f^(4/3) (Eq. h0) with f = f0 A(t)^(-3/8) (Eq. f) is f0^(4/3)
+    A(t)^(-1/2); its mean over [dt, dt + T) is 2 / (sqrt(A(dt)) + sqrt(A(dt + T)))
+    in units of f0^(4/3).  The oracle integrates numerically."""
+    b0 = srs_synth.chirp_beta(mc, F_LO)
+    dt = (s + (1.0 if c > 0 else 0.0) - c) * T
+    A0, A1 = 1 - 8 / 3 * b0 * dt, 1 - 8 / 3 * b0 * (dt + T)
+    want = 2.0 / (np.sqrt(A0) + np.sqrt(A1))
+    assert slide.amplitude_sq(mc, c, F_LO, T, s) == pytest.approx(want, rel=1e-10)
+
+
+def test_weighted_stack_slide_closed_forms():
+    bank = _bank()
+    rows_mc, rows_c = np.array([9e-2, 4e-2]), np.array([0.25, 0.0])
+    n_total, n_t0 = 80, 60
+    r = np.random.default_rng(4)
+    s_eff = r.uniform(0.5, 3.0, size=(len(bank), N_B))
+    # P / S = 2 everywhere: every template reads 0 under any weights
+    cube = 2.0 * np.repeat(s_eff[:, :, None], n_total, axis=2)
+    ns, L = slide.stack_slide(cube, rows_mc, rows_c, n_t0, n_total, bank, F_LO, T, F_LO, N_B, weighting=1,
+                              s_eff=s_eff)
+    assert np.allclose(ns, 0.0, atol=1e-12)
+    # P / S = 2 + 2 c on one template's track: c sum(a) / sqrt(sum a^2), a = A^2 / S
+    r0, n0, cval = 0, 11, 0.5
+    k, j = slide.track(rows_mc[r0], rows_c[r0], F_LO, T, F_LO, N_B, bank, n_total)
+    first = slide.first_segment(n0, rows_c[r0])
+    Lp = min(len(k), n_total - first)
+    cube[k[:Lp], j[:Lp], first + np.arange(Lp)] += 2.0 * cval * s_eff[k[:Lp], j[:Lp]]
+    ns, L = slide.stack_slide(cube, rows_mc, rows_c, n_t0, n_total, bank, F_LO, T, F_LO, N_B, weighting=1,
+                              s_eff=s_eff)
+    a = np.array([slide.amplitude_sq(rows_mc[r0], rows_c[r0], F_LO, T, s) for s in range(Lp)]) / s_eff[k[:Lp], j[:Lp]]
+    assert ns[r0, n0] == pytest.approx(cval * a.sum() / np.sqrt((a * a).sum()), rel=1e-12)
+    # equal weights and a white PSD give the unweighted statistic
+    cube2 = srs_synth.random_cube(len(bank), N_B, n_total, seed=9).astype(np.float64)
+    u, _ = slide.stack_slide(cube2, rows_mc, rows_c, n_t0, n_total, bank, F_LO, T, F_LO, N_B)
+    w, _ = slide.stack_slide(cube2, rows_mc, rows_c, n_t0, n_total, bank, F_LO, T, F_LO, N_B,
+                             s_eff=np.ones((len(bank), N_B)))
+    assert np.allclose(u, w, rtol=1e-12, atol=1e-12)
+    # one PSD scale for power and weights cancels
+    w1, _ = slide.stack_slide(cube2 * 3.0, rows_mc, rows_c, n_t0, n_total, bank, F_LO, T, F_LO, N_B, weighting=1,
+                              s_eff=np.full((len(bank), N_B), 3.0))
+    w0, _ = slide.stack_slide(cube2, rows_mc, rows_c, n_t0, n_total, bank, F_LO, T, F_LO, N_B, weighting=1)
+    assert np.allclose(w1, w0, rtol=1e-12, atol=1e-12)
+
+
+def test_weighted_stack_slide_brute_force():
+    bank = slide.local_bank(3e-8, 7e-4, 10)
+    n_total, n_t0 = 30, 30
+    cube = srs_synth.random_cube(len(bank), N_B, n_total, seed=6).astype(np.float64)
+    s_eff = np.random.default_rng(2).uniform(0.7, 1.6, size=(len(bank), N_B))
+    rows_mc, rows_c = np.array([1e-1, 6e-2]), np.array([0.5, 0.0])
+    ns, L = slide.stack_slide(cube, rows_mc, rows_c, n_t0, n_total, bank, F_LO, T, F_LO, N_B, weighting=1,
+                              s_eff=s_eff)
+    for r in range(2):
+        k, j = slide.track(rows_mc[r], rows_c[r], F_LO, T, F_LO, N_B, bank, n_total)
+        for n in range(n_t0):
+            num, den = 0.0, 0.0
+            for s in range(len(k)):
+                i = n + (1 if rows_c[r] > 0 else 0) + s
+                if i >= n_total:
+                    break
+                a = slide.amplitude_sq(rows_mc[r], rows_c[r], F_LO, T, s) / s_eff[k[s], j[s]]
+                num += a * (cube[k[s], j[s], i] / s_eff[k[s], j[s]] - 2.0) / 2.0
+                den += a * a
+            want = num / np.sqrt(den) if den > 0 else 0.0
+            assert ns[r, n] == pytest.approx(want, rel=1e-12, abs=1e-12)
