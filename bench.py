@@ -451,6 +451,12 @@ def two_stage_measure(ctx, stream, dev, flush, name, steps, warmup, pk, host_e2e
     ck = clocks.stop()
     n_spec = int(rep["n_spectra"])
     reads = int(rep["slide_reads"])
+    # the same search with amplitude weights (Eq. weights, A^2 ~ f^(4/3)): its stack-slide time
+    wsl = []
+    for it in range(4):
+        _, rw = ctx.slide_search(xd, *args, want_map=False, weighting=1)
+        if it:
+            wsl.append(rw["slide_ms"])
     n_tmpl = int(w["rows_mc"].size) * int(w["n_total"])
     sl = float(np.mean(slide_ms))
     cb = float(np.mean(cube_ms))
@@ -469,6 +475,7 @@ def two_stage_measure(ctx, stream, dev, flush, name, steps, warmup, pk, host_e2e
                       "l2": "flushed (256 MB write) before every timed step; the cube (%d MB) exceeds L2"
                             % (n_spec * 600 * 4 // (1 << 20))},
            "cube_ms": cb, "slide_ms": sl, "templates_per_s": n_tmpl / (sl * 1e-3),
+           "slide_ms_amplitude_weights": float(np.mean(wsl)),
            "power_reads_per_step": reads,
            "roofline_cube": xu_roofline(n_spec, n_s, int(rep["w"]), cb, n_sm, sm_mhz,
                                         profile_traffic("two_stage_24h.md", ("srs_kernels.cu", "srs_device.cuh"),
@@ -552,6 +559,7 @@ def run_two_stage(args):
                 "roofline": res["roofline_cube"], "roofline_slide": res["roofline_slide"], "clocks": res["clocks"],
                 "gpu_launches": res["gpu_launches"], "e2e": res.get("e2e"), "cpu_baseline": cpu,
                 "cube_ms": res["cube_ms"], "slide_ms": res["slide_ms"], "templates_per_s": res["templates_per_s"],
+                "slide_ms_amplitude_weights": res["slide_ms_amplitude_weights"],
                 "power_reads_per_step": res["power_reads_per_step"]}
         print(json.dumps(line), flush=True)
     barrier(world)

@@ -258,9 +258,10 @@ srs_status srs_time_map(srs_ctx* ctx, const double* mc, int32_t n_templates,
  * after t0, the bin nearest the 0PN frequency at the segment's first sample
  * (Eq. f) and the bank entry nearest the local chirp parameter beta(Mc, f)
  * (Eq. beta); the track ends where that bin leaves the band, at coalescence,
- * or at the end of the data.  n_sigma = sum (P - 2)/2 / sqrt(N_seg(theta))
- * (Eq. semicoherent_statistic, equal weights, mu = sigma = 2); 0 when the
- * track has no segment in the data.
+ * or at the end of the data.  n_sigma = sum w (P - 2)/2 with sum w^2 = 1
+ * (Eq. semicoherent_statistic, mu = sigma = 2; equal weights 1/sqrt(N_seg),
+ * or the amplitude / PSD weights of srs_slide_grid); 0 when the track has no
+ * segment in the data.
  * ------------------------------------------------------------------------ */
 
 /* The local resampling bank: n_beta chirp parameters uniform over
@@ -273,13 +274,26 @@ typedef struct {
 /* Stack-slide templates theta = {Mc, t0}.  Row r has chirp mass mc[r] (Msun)
  * and t0 fraction c[r] in [0, 1); column n has t0 = (n + c[r]) t_coh, so the
  * map is [n_rows][n_t0].  mc and c are host arrays.  f0 in [f_lo, f_hi) is
- * the frequency at t0 (the paper: the band's lower edge). */
+ * the frequency at t0 (the paper: the band's lower edge).
+ * Weights (Sec. III.C Eq. weights, rectangular window Gamma = 1): segment s
+ * of a track gets a_s = A_s^2 / S_s, normalised so that sum a_s^2 = 1 over
+ * the track's segments in the data, where
+ *   A_s^2 = 1 (SRS_WEIGHT_EQUAL), or the segment average of (f / f0)^(4/3)
+ *           along the track (SRS_WEIGHT_AMPLITUDE; Sec. II Eq. h0, h0 ~ f^(2/3));
+ *   S_s   = s_eff[k_s][j_s], the effective PSD of bank entry k, bin j
+ *           relative to white unit-variance noise (host [n_beta][n_bins],
+ *           every entry > 0), or 1 when s_eff is NULL.
+ * The powers are normalised by the same S (Eq. normalized_power):
+ * n_sigma = sum_s a_s (P_s / S_s - 2) / 2 / sqrt(sum_s a_s^2). */
+enum { SRS_WEIGHT_EQUAL = 0, SRS_WEIGHT_AMPLITUDE = 1 };
 typedef struct {
   double f0;
   const double* mc;
   const double* c;
   int32_t n_rows;
   int32_t n_t0;
+  int32_t weighting;
+  const float* s_eff;
 } srs_slide_grid;
 
 /* Flags of srs_stack_slide. */

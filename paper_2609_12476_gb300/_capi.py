@@ -26,6 +26,7 @@ EXPORTS = ("srs_create", "srs_destroy", "srs_last_error", "srs_plan", "srs_searc
            "srs_patches", "srs_mlp_forward", "srs_mlp_grad", "srs_mlp_train", "srs_score_map", "srs_refine",
            "srs_search_proposed", "srs_power_cube", "srs_stack_slide", "srs_slide_search")
 SRS_SLIDE_FIRST, SRS_SLIDE_LAST = 1, 2
+SRS_WEIGHT_EQUAL, SRS_WEIGHT_AMPLITUDE = 0, 1
 MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 297, 64, 19137
 
 
@@ -69,7 +70,8 @@ class _Bank(ctypes.Structure):
 
 class _SlideGrid(ctypes.Structure):
     _fields_ = [("f0", ctypes.c_double), ("mc", ctypes.c_void_p), ("c", ctypes.c_void_p),
-                ("n_rows", ctypes.c_int32), ("n_t0", ctypes.c_int32)]
+                ("n_rows", ctypes.c_int32), ("n_t0", ctypes.c_int32), ("weighting", ctypes.c_int32),
+                ("s_eff", ctypes.c_void_p)]
 
 
 class _Injection(ctypes.Structure):
@@ -349,13 +351,15 @@ class Context:
         return _Bank(float(bank[0]), float(bank[1]), int(bank[2]))
 
     @staticmethod
-    def _grid(rows_mc, rows_c, n_t0, f0):
+    def _grid(rows_mc, rows_c, n_t0, f0, weighting=0, s_eff=None):
         mc = np.ascontiguousarray(rows_mc, dtype=np.float64)
         c = np.ascontiguousarray(rows_c, dtype=np.float64)
         if mc.shape != c.shape:
             raise ValueError("rows_mc and rows_c must have the same length")
-        g = _SlideGrid(float(f0), mc.ctypes.data, c.ctypes.data, mc.size, int(n_t0))
-        return g, (mc, c)   # keep the arrays alive with the struct
+        se = None if s_eff is None else np.ascontiguousarray(s_eff, dtype=np.float32)
+        g = _SlideGrid(float(f0), mc.ctypes.data, c.ctypes.data, mc.size, int(n_t0), int(weighting),
+                       se.ctypes.data if se is not None else None)
+        return g, (mc, c, se)   # keep the arrays alive with the struct
 
     def power_cube(self, strain, bank, seg_begin, seg_end, params):
         """srs_power_cube: float32 [n_beta, n_bins, seg_end - seg_begin] powers of
@@ -385,13 +389,13 @@ class Context:
         return out, _report_dict(rep)
 
     def stack_slide(self, cube, seg_begin, n_seg_total, bank, rows_mc, rows_c, n_t0, params, f0=None,
-                    first=True, last=True, want_map=True):
+                    first=True, last=True, want_map=True, weighting=0, s_eff=None):
         """srs_stack_slide over a cube chunk [n_beta, n_bins, chunk segments]
         holding segments [seg_begin, seg_begin + chunk).  With last=True returns
         (candidates, n_sigma map [rows, n_t0] or None, report); otherwise
         (None, None, report).  numpy cube: host I/O; torch CUDA cube: device I/O."""
         f0 = params.f_lo if f0 is None else f0
-        g, keep = self._grid(rows_mc, rows_c, n_t0, f0)
+        g, keep = self._grid(rows_mc, rows_c, n_t0, f0, weighting, s_eff)
         b = self._bank(bank)
         p = params.c()
         rep = _Report()
@@ -429,12 +433,12 @@ class Context:
         return (c[:n_cands.value] if c is not None else None), m, _report_dict(rep)
 
     def slide_search(self, strain, bank, rows_mc, rows_c, n_t0, params, f0=None, cube_budget_bytes=0,
-                     want_map=True, out=None):
+                     want_map=True, out=None, weighting=0, s_eff=None):
         """srs_slide_search: power cube + stack-slide over the whole strain.
         Host numpy strain returns (candidates, map or None, report); a torch
         CUDA strain returns ({"map", "cands"} tensors, report)."""
         f0 = params.f_lo if f0 is None else f0
-        g, keep = self._grid(rows_mc, rows_c, n_t0, f0)
+        g, keep = self._grid(rows_mc, rows_c, n_t0, f0, weighting, s_eff)
         b = self._bank(bank)
         dt = _dtype_code(strain)
         p = params.c()

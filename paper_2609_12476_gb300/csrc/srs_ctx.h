@@ -83,7 +83,7 @@ struct srs_ctx {
   srs::DevBuf items, order, grid, anchors, partial, betas, nseg, item_off, corr, tw, keys, topk_a, topk_b, cands, queue, strain,
       strain32, errflag, map, S, F, psi, th, im, ii;
   // two-stage search: power cube chunk, stack-slide tracks and running sums
-  srs::DevBuf cube, slide_cell, slide_len, slide_beta0, slide_frac, slide_Z, slide_map;
+  srs::DevBuf cube, slide_cell, slide_coef, slide_w2, slide_seff, slide_len, slide_beta0, slide_frac, slide_Z, slide_map;
   bool have_slide = false;
   bool slide_open = false;                // running sums started (SRS_SLIDE_FIRST) and not yet finished
   std::vector<unsigned char> slide_key;   // what slide_cell / slide_len were computed for
@@ -99,7 +99,7 @@ struct srs_ctx {
             &queue, &strain, &strain32, &errflag, &map, &S, &F, &psi, &th, &im, &ii, &xb, &yb, &z1, &logits, &dz,
             &lossv, &grad, &wts, &adam_m, &adam_v, &w1h, &w2h, &idx, &patches, &cells_m, &cells_b, &sp_items,
             &sp_bins, &sp_partial, &sp_cells, &sp_out, &sp_betas, &cmap, &ccands, &inj, &cube, &slide_cell,
-            &slide_len, &slide_beta0, &slide_frac, &slide_Z, &slide_map};
+            &slide_coef, &slide_w2, &slide_seff, &slide_len, &slide_beta0, &slide_frac, &slide_Z, &slide_map};
   }
 };
 

@@ -30,8 +30,12 @@ constexpr int kTrackThreads = 256;
 // chirp parameter beta(Mc, f) = beta0 (f / f0)^(8/3) = beta0 / A (Eq. beta).
 // A segment is on the track while A > 0 and its bin is inside the band; the
 // frequency only rises, so the valid segments are a prefix of the row.
+// Weight: A_s^2 ~ f^(4/3) = f0^(4/3) A^(-1/2) (Sec. II Eq. h0 with Eq. f); its
+// mean over the segment, in units of f0^(4/3), is
+//   (1/T) int A(u)^(-1/2) du = 2 / (sqrt(A_start) + sqrt(A_end)),
+// written without the difference of square roots.
 __global__ void k_slide_tracks(const double* __restrict__ beta0, const double* __restrict__ frac, int n_rows,
-                               TrackArgs t, int* __restrict__ cell) {
+                               TrackArgs t, int* __restrict__ cell, float2* __restrict__ coef) {
   const long long total = (long long)n_rows * t.n_total;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -42,6 +46,7 @@ __global__ void k_slide_tracks(const double* __restrict__ beta0, const double* _
     const double dt = ((double)s + (c > 0.0 ? 1.0 : 0.0) - c) * t.t_coh;
     const double A = 1.0 - (8.0 / 3.0) * b0 * dt;
     int out = -1;
+    float2 cf = make_float2(0.f, 0.f);
     if (A > 0.0) {
       const double f = t.f0 * exp(-0.375 * log(A));
       const double jd = rint((f - t.f_lo) * t.t_coh);
@@ -49,24 +54,49 @@ __global__ void k_slide_tracks(const double* __restrict__ beta0, const double* _
         double kd = t.dbeta > 0.0 ? rint((b0 / A - t.beta_min) / t.dbeta) : 0.0;
         kd = fmin(fmax(kd, 0.0), (double)(t.n_beta - 1));
         out = (int)kd * t.n_bins + (int)jd;
+        double a = 1.0;
+        if (t.weighting == SRS_WEIGHT_AMPLITUDE) {
+          const double A1 = fmax(1.0 - (8.0 / 3.0) * b0 * (dt + t.t_coh), 0.0);
+          a = 2.0 / (sqrt(A) + sqrt(A1));
+        }
+        const double S = t.s_eff ? (double)t.s_eff[out] : 1.0;
+        a /= S;
+        cf = make_float2((float)(0.5 * a / S), (float)a);
       }
     }
     cell[idx] = out;
+    coef[idx] = cf;
   }
 }
 
-// len[r] = index of the first -1 in row r (one warp per row).
-__global__ void k_slide_lengths(const int* __restrict__ cell, int n_rows, int n_total, int* __restrict__ len) {
+// len[r] = index of the first -1 in row r, and w2[r][s] = sum_{s' < s} a_s'^2
+// for s <= len[r] (an inclusive warp scan per 32 steps; one warp per row).
+__global__ void k_slide_lengths(const int* __restrict__ cell, const float2* __restrict__ coef, int n_rows,
+                                int n_total, int* __restrict__ len, double* __restrict__ w2) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n_rows) return;
   const int* row = cell + (long long)warp * n_total;
+  const float2* crow = coef + (long long)warp * n_total;
+  double* wrow = w2 + (long long)warp * (n_total + 1);
+  if (lane == 0) wrow[0] = 0.0;
   int L = n_total;
+  double run = 0.0;
   for (int s0 = 0; s0 < n_total; s0 += 32) {
     const int s = s0 + lane;
-    const unsigned end = __ballot_sync(0xffffffffu, s < n_total && row[s] < 0);
+    const bool on = s < n_total && row[s] >= 0;
+    const unsigned end = __ballot_sync(0xffffffffu, s < n_total && !on);
+    const float a = on ? crow[s].y : 0.f;
+    double v = (double)a * (double)a;
+    for (int d = 1; d < 32; d <<= 1) {
+      const double u = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d) v += u;
+    }
+    const int stop = end ? s0 + __ffs(end) - 1 : n_total;   // first step past the track
+    if (s < stop) wrow[s + 1] = run + v;
+    run += __shfl_sync(0xffffffffu, v, 31);
     if (end) {
-      L = s0 + __ffs(end) - 1;
+      L = stop;
       break;
     }
   }
@@ -76,13 +106,16 @@ __global__ void k_slide_lengths(const int* __restrict__ cell, int n_rows, int n_
 // Block = (row r, tile of kSlideThreads t0 columns).  Thread n sums the
 // powers of its track segments s whose segment i = first + s lies in the
 // chunk, first = n + [c > 0], and s < min(len_r, n_total - first).  The
-// row's track cells are staged in shared memory; four accumulators keep four
-// loads in flight per thread.
+// row's track cells (and, WEIGHTED, their FMA coefficients) are staged in
+// shared memory; four accumulators keep four loads in flight per thread.
+// Without weights every term is P / 2 - 1.
+template <bool WEIGHTED>
 __global__ void __launch_bounds__(kSlideThreads)
-k_stack_slide(const float* __restrict__ cube, const int* __restrict__ cell, const int* __restrict__ len,
-              const double* __restrict__ frac, SlideArgs a, float* __restrict__ Z, float* __restrict__ map,
-              unsigned long long* __restrict__ keys) {
+k_stack_slide(const float* __restrict__ cube, const int* __restrict__ cell, const float2* __restrict__ coef,
+              const int* __restrict__ len, const double* __restrict__ w2, const double* __restrict__ frac,
+              SlideArgs a, float* __restrict__ Z, float* __restrict__ map, unsigned long long* __restrict__ keys) {
   __shared__ int sc[kSlideStage];
+  __shared__ float2 sw[WEIGHTED ? kSlideStage : 1];
   const int tiles = (a.n_t0 + kSlideThreads - 1) / kSlideThreads;
   const int r = blockIdx.x / tiles;
   const int tile = blockIdx.x - r * tiles;
@@ -99,27 +132,43 @@ k_stack_slide(const float* __restrict__ cube, const int* __restrict__ cell, cons
   const int S_lo = max(0, a.seg_begin - (last_n + e));
   const int S_hi = min(L, a.seg_end - (n0 + e));
   const int* __restrict__ crow = cell + (long long)r * a.n_total;
+  const float2* __restrict__ wrow = coef + (long long)r * a.n_total;
   // cube index of track step s: cell_s * ld + (first + s - seg_begin)
   const long long c0 = (long long)first - a.seg_begin;
   float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
   for (int base = S_lo; base < S_hi; base += kSlideStage) {
     const int cnt = min(kSlideStage, S_hi - base);
     __syncthreads();
-    for (int t = threadIdx.x; t < cnt; t += kSlideThreads) sc[t] = crow[base + t];
+    for (int t = threadIdx.x; t < cnt; t += kSlideThreads) {
+      sc[t] = crow[base + t];
+      if (WEIGHTED) sw[t] = wrow[base + t];
+    }
     __syncthreads();
     const int lo = max(s_lo, base), hi = min(s_hi, base + cnt);
     int s = lo;
+    // term of track step s: a_s (P / S_s - 2) / 2 = sw.x P - sw.y
     for (; s + 3 < hi; s += 4) {
       const float p0 = __ldg(cube + ((long long)sc[s - base] * a.ld + c0 + s));
       const float p1 = __ldg(cube + ((long long)sc[s + 1 - base] * a.ld + c0 + s + 1));
       const float p2 = __ldg(cube + ((long long)sc[s + 2 - base] * a.ld + c0 + s + 2));
       const float p3 = __ldg(cube + ((long long)sc[s + 3 - base] * a.ld + c0 + s + 3));
-      z0 += fmaf(p0, 0.5f, -1.0f);
-      z1 += fmaf(p1, 0.5f, -1.0f);
-      z2 += fmaf(p2, 0.5f, -1.0f);
-      z3 += fmaf(p3, 0.5f, -1.0f);
+      if (WEIGHTED) {
+        const float2 w0 = sw[s - base], w1 = sw[s + 1 - base], w2_ = sw[s + 2 - base], w3 = sw[s + 3 - base];
+        z0 += fmaf(p0, w0.x, -w0.y);
+        z1 += fmaf(p1, w1.x, -w1.y);
+        z2 += fmaf(p2, w2_.x, -w2_.y);
+        z3 += fmaf(p3, w3.x, -w3.y);
+      } else {
+        z0 += fmaf(p0, 0.5f, -1.0f);
+        z1 += fmaf(p1, 0.5f, -1.0f);
+        z2 += fmaf(p2, 0.5f, -1.0f);
+        z3 += fmaf(p3, 0.5f, -1.0f);
+      }
     }
-    for (; s < hi; ++s) z0 += fmaf(__ldg(cube + ((long long)sc[s - base] * a.ld + c0 + s)), 0.5f, -1.0f);
+    for (; s < hi; ++s) {
+      const float2 w = WEIGHTED ? sw[s - base] : make_float2(0.5f, 1.0f);
+      z0 += fmaf(__ldg(cube + ((long long)sc[s - base] * a.ld + c0 + s)), w.x, -w.y);
+    }
   }
   if (n >= a.n_t0) return;
   const long long o = (long long)r * a.n_t0 + n;
@@ -129,7 +178,10 @@ k_stack_slide(const float* __restrict__ cube, const int* __restrict__ cell, cons
     Z[o] = z;
     return;
   }
-  const float v = Lp > 0 ? z / sqrtf((float)Lp) : 0.f;
+  // FP32 from here: the FP64 units are few on this part
+  // sum of a_s^2 over the track's segments in the data (N_seg itself without weights)
+  const float norm = Lp <= 0 ? 0.f : WEIGHTED ? (float)w2[(long long)r * (a.n_total + 1) + Lp] : (float)Lp;
+  const float v = norm > 0.f ? z / sqrtf(norm) : 0.f;
   if (map) map[o] = v;
   keys[o] = make_key(v, (uint32_t)o);
 }
@@ -137,26 +189,29 @@ k_stack_slide(const float* __restrict__ cube, const int* __restrict__ cell, cons
 }  // namespace
 
 cudaError_t launch_slide_tracks(const double* beta0, const double* frac, int n_rows, const TrackArgs& t,
-                                int* cell, int* len, int n_sm, cudaStream_t st) {
+                                int* cell, float2* coef, int* len, double* w2, int n_sm, cudaStream_t st) {
   const long long total = (long long)n_rows * t.n_total;
   if (total <= 0) return cudaSuccess;
   long long blocks = (total + kTrackThreads - 1) / kTrackThreads;
   if (blocks > (long long)n_sm * 32) blocks = (long long)n_sm * 32;
-  k_slide_tracks<<<(unsigned)blocks, kTrackThreads, 0, st>>>(beta0, frac, n_rows, t, cell);
+  k_slide_tracks<<<(unsigned)blocks, kTrackThreads, 0, st>>>(beta0, frac, n_rows, t, cell, coef);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long threads = (long long)n_rows * 32;
-  k_slide_lengths<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(cell, n_rows, t.n_total, len);
+  k_slide_lengths<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(cell, coef, n_rows, t.n_total, len, w2);
   return cudaGetLastError();
 }
 
-cudaError_t launch_stack_slide(const float* cube, const int* cell, const int* len, const double* frac,
-                               const SlideArgs& a, float* Z, float* map, unsigned long long* keys,
-                               cudaStream_t st) {
+cudaError_t launch_stack_slide(const float* cube, const int* cell, const float2* coef, const int* len,
+                               const double* w2, const double* frac, const SlideArgs& a, float* Z, float* map,
+                               unsigned long long* keys, cudaStream_t st) {
   const long long tiles = (a.n_t0 + kSlideThreads - 1) / kSlideThreads;
   const long long blocks = tiles * a.n_rows;
   if (blocks <= 0) return cudaSuccess;
-  k_stack_slide<<<(unsigned)blocks, kSlideThreads, 0, st>>>(cube, cell, len, frac, a, Z, map, keys);
+  if (a.weighted)
+    k_stack_slide<true><<<(unsigned)blocks, kSlideThreads, 0, st>>>(cube, cell, coef, len, w2, frac, a, Z, map, keys);
+  else
+    k_stack_slide<false><<<(unsigned)blocks, kSlideThreads, 0, st>>>(cube, cell, coef, len, w2, frac, a, Z, map, keys);
   return cudaGetLastError();
 }
 

@@ -17,6 +17,8 @@ struct TrackArgs {
   double beta_min;    // first bank entry (1/s)
   double dbeta;       // bank spacing (1/s); 0 for a one-entry bank
   int n_beta, n_bins, n_total;
+  int weighting;      // SRS_WEIGHT_EQUAL or SRS_WEIGHT_AMPLITUDE
+  const float* s_eff; // [n_beta][n_bins] effective PSD relative to white noise, or NULL
 };
 
 // One stack-slide pass over the cube chunk that holds segments
@@ -27,19 +29,22 @@ struct SlideArgs {
   int n_rows, n_t0, n_total;
   int seg_begin, seg_end, ld;
   int first, last;
+  int weighted;       // 0: equal weights and a white PSD (every coefficient is (1/2, 1))
 };
 
 // cell[r][s] = k_s n_bins + j_s of the s-th segment of row r's track, -1 past
-// its end; len[r] = the track's length.  beta0[r] = beta(Mc_r, f0), frac[r] =
-// the row's t0 fraction c in [0, 1).
+// its end; coef[r][s] = (a_s / (2 S_s), a_s) with a_s = A_s^2 / S_s, so that
+// the segment's term a_s (P / S_s - 2) / 2 is one FMA; len[r] = the track's
+// length; w2[r][L] = sum_{s < L} a_s^2 (n_total + 1 entries per row).
+// beta0[r] = beta(Mc_r, f0), frac[r] = the row's t0 fraction c in [0, 1).
 cudaError_t launch_slide_tracks(const double* beta0, const double* frac, int n_rows, const TrackArgs& t,
-                                int* cell, int* len, int n_sm, cudaStream_t st);
+                                int* cell, float2* coef, int* len, double* w2, int n_sm, cudaStream_t st);
 
-// Stack-slide: Z[r][n] (+)= sum over the chunk's track segments of (P - 2) / 2;
-// with a.last, map[r][n] = Z / sqrt(N_seg) (0 for an empty track) and keys for
-// the top-k.  map may be NULL.
-cudaError_t launch_stack_slide(const float* cube, const int* cell, const int* len, const double* frac,
-                               const SlideArgs& a, float* Z, float* map, unsigned long long* keys,
-                               cudaStream_t st);
+// Stack-slide: Z[r][n] (+)= sum over the chunk's track segments of
+// a_s (P / S_s - 2) / 2; with a.last, map[r][n] = Z / sqrt(w2[r][N_seg]) (0
+// for an empty track) and keys for the top-k.  map may be NULL.
+cudaError_t launch_stack_slide(const float* cube, const int* cell, const float2* coef, const int* len,
+                               const double* w2, const double* frac, const SlideArgs& a, float* Z, float* map,
+                               unsigned long long* keys, cudaStream_t st);
 
 }  // namespace srs

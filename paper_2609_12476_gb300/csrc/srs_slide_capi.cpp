@@ -42,6 +42,17 @@ srs_status check_grid(srs_ctx* ctx, const srs_slide_grid* g, const srs_params* p
     if (!(g->mc[r] > 0) || !std::isfinite(g->mc[r])) return set_err(ctx, SRS_ERR_ARG, "chirp masses must be positive and finite");
     if (!(g->c[r] >= 0.0 && g->c[r] < 1.0)) return set_err(ctx, SRS_ERR_ARG, "t0 fractions must lie in [0, 1)");
   }
+  if (g->weighting != SRS_WEIGHT_EQUAL && g->weighting != SRS_WEIGHT_AMPLITUDE)
+    return set_err(ctx, SRS_ERR_ARG, "weighting must be SRS_WEIGHT_EQUAL or SRS_WEIGHT_AMPLITUDE");
+  return SRS_OK;
+}
+
+srs_status check_s_eff(srs_ctx* ctx, const srs_slide_grid* g, const srs_bank* bank, int32_t n_bins) {
+  if (!g->s_eff) return SRS_OK;
+  const size_t n = (size_t)bank->n_beta * n_bins;
+  for (size_t q = 0; q < n; ++q)
+    if (!(g->s_eff[q] > 0.0f) || !std::isfinite(g->s_eff[q]))
+      return set_err(ctx, SRS_ERR_ARG, "s_eff entries must be positive and finite");
   return SRS_OK;
 }
 
@@ -66,6 +77,10 @@ srs_status plan_tracks(srs_ctx* ctx, const srs_bank* bank, const srs_slide_grid*
   put(&p->f_lo, sizeof(double));
   put(&n_bins, sizeof n_bins);
   put(&n_total, sizeof n_total);
+  put(&g->weighting, sizeof g->weighting);
+  const size_t n_seff = g->s_eff ? (size_t)bank->n_beta * n_bins : 0;
+  put(&n_seff, sizeof n_seff);
+  if (n_seff) put(g->s_eff, n_seff * sizeof(float));
   *replanned = false;
   if (ctx->have_slide && key == ctx->slide_key) return SRS_OK;
   ctx->have_slide = false;
@@ -76,7 +91,13 @@ srs_status plan_tracks(srs_ctx* ctx, const srs_bank* bank, const srs_slide_grid*
   SRS_CK(ctx->slide_beta0.ensure(b0.size() * 8), "alloc tracks");
   SRS_CK(ctx->slide_frac.ensure(b0.size() * 8), "alloc tracks");
   SRS_CK(ctx->slide_cell.ensure((size_t)g->n_rows * n_total * 4), "alloc tracks");
+  SRS_CK(ctx->slide_coef.ensure((size_t)g->n_rows * n_total * 8), "alloc tracks");
+  SRS_CK(ctx->slide_w2.ensure((size_t)g->n_rows * (n_total + 1) * 8), "alloc tracks");
   SRS_CK(ctx->slide_len.ensure((size_t)g->n_rows * 4), "alloc tracks");
+  if (n_seff) {
+    SRS_CK(ctx->slide_seff.ensure(n_seff * 4), "alloc s_eff");
+    SRS_CK(cudaMemcpyAsync(ctx->slide_seff.p, g->s_eff, n_seff * 4, cudaMemcpyHostToDevice, ctx->stream), "copy s_eff");
+  }
   SRS_CK(cudaMemcpyAsync(ctx->slide_beta0.p, b0.data(), b0.size() * 8, cudaMemcpyHostToDevice, ctx->stream), "copy tracks");
   SRS_CK(cudaMemcpyAsync(ctx->slide_frac.p, g->c, b0.size() * 8, cudaMemcpyHostToDevice, ctx->stream), "copy tracks");
   TrackArgs t;
@@ -88,8 +109,11 @@ srs_status plan_tracks(srs_ctx* ctx, const srs_bank* bank, const srs_slide_grid*
   t.n_beta = bank->n_beta;
   t.n_bins = n_bins;
   t.n_total = n_total;
+  t.weighting = g->weighting;
+  t.s_eff = n_seff ? ctx->slide_seff.as<float>() : nullptr;
   SRS_CK(launch_slide_tracks(ctx->slide_beta0.as<double>(), ctx->slide_frac.as<double>(), g->n_rows, t,
-                             ctx->slide_cell.as<int>(), ctx->slide_len.as<int>(), ctx->n_sm, ctx->stream),
+                             ctx->slide_cell.as<int>(), ctx->slide_coef.as<float2>(), ctx->slide_len.as<int>(),
+                             ctx->slide_w2.as<double>(), ctx->n_sm, ctx->stream),
          "k_slide_tracks");
   ctx->slide_len_host.assign((size_t)g->n_rows, 0);
   SRS_CK(cudaMemcpyAsync(ctx->slide_len_host.data(), ctx->slide_len.p, (size_t)g->n_rows * 4, cudaMemcpyDeviceToHost,
@@ -179,8 +203,10 @@ srs_status slide_pass(srs_ctx* ctx, const float* dcube, int32_t seg_begin, int32
   a.ld = seg_end - seg_begin;
   a.first = first ? 1 : 0;
   a.last = last ? 1 : 0;
-  SRS_CK(launch_stack_slide(dcube, ctx->slide_cell.as<int>(), ctx->slide_len.as<int>(), ctx->slide_frac.as<double>(), a,
-                            ctx->slide_Z.as<float>(), o.dmap, ctx->keys.as<unsigned long long>(), ctx->stream),
+  a.weighted = (g->weighting != SRS_WEIGHT_EQUAL || g->s_eff) ? 1 : 0;
+  SRS_CK(launch_stack_slide(dcube, ctx->slide_cell.as<int>(), ctx->slide_coef.as<float2>(), ctx->slide_len.as<int>(),
+                            ctx->slide_w2.as<double>(), ctx->slide_frac.as<double>(), a, ctx->slide_Z.as<float>(),
+                            o.dmap, ctx->keys.as<unsigned long long>(), ctx->stream),
          "k_stack_slide");
   ++*launches;
   return SRS_OK;
@@ -215,6 +241,7 @@ srs_status stack_slide_impl(srs_ctx* ctx, const float* cube, int32_t seg_begin, 
   if (s != SRS_OK) return s;
   if ((s = check_bank(ctx, bank)) != SRS_OK) return s;
   if ((s = check_grid(ctx, g, p)) != SRS_OK) return s;
+  if ((s = check_s_eff(ctx, g, bank, n_bins)) != SRS_OK) return s;
   if (!cube) return set_err(ctx, SRS_ERR_ARG, "cube is NULL");
   if (flags & ~(SRS_SLIDE_FIRST | SRS_SLIDE_LAST)) return set_err(ctx, SRS_ERR_ARG, "unknown flags");
   const bool first = flags & SRS_SLIDE_FIRST, last = flags & SRS_SLIDE_LAST;
@@ -272,6 +299,7 @@ srs_status slide_search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples
   if ((s = check_slide_params(ctx, p, &n_bins)) != SRS_OK) return s;
   if ((s = check_bank(ctx, bank)) != SRS_OK) return s;
   if ((s = check_grid(ctx, g, p)) != SRS_OK) return s;
+  if ((s = check_s_eff(ctx, g, bank, n_bins)) != SRS_OK) return s;
   if (!cands || !n_cands) return set_err(ctx, SRS_ERR_ARG, "cands and n_cands are required");
   if (budget < 0) return set_err(ctx, SRS_ERR_ARG, "cube_budget_bytes must be >= 0");
   if (p->precision != SRS_MIXED) return set_err(ctx, SRS_ERR_UNSUPPORTED, "the power cube runs the mixed form only");

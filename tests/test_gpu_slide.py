@@ -4,15 +4,16 @@ FP64 oracle (oracle.slide), through the C ABI.
 Tolerances: cube powers within the bound that rel-L2(F) <= 10 eps per
 spectrum implies, |dP_b| <= (4 |F_b| d + 2 d^2) / n_s with d = 10 eps ||F||;
 stack-slide sums on a given cube within the FP32 summation bound
-L u sum|P - 2|/2 / sqrt(L) (u = 2^-24, L track segments) plus the final
-scaling; end-to-end n_sigma within the sum of both over the track."""
+(L + 2) u sum_s (|a_s P_s / S_s| + 2 |a_s|) / 2 / sqrt(sum a^2) (u = 2^-24, L
+track segments; the FMA coefficients are FP32 too) plus the final scaling;
+end-to-end n_sigma within the sum of both over the track."""
 import numpy as np
 import pytest
 
 import oracle
 import srs_synth
 from oracle import slide
-from paper_2609_12476_gb300 import Context, Params, SrsError
+from paper_2609_12476_gb300 import SRS_WEIGHT_AMPLITUDE, Context, Params, SrsError
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -79,8 +80,7 @@ def _random_case(n_total=240, seed=11):
 
 
 def _slide_tol(L, absum, ref):
-    Lf = np.maximum(L, 1).astype(np.float64)
-    return (Lf * U32 * absum + 4 * U32 * np.abs(ref) * np.sqrt(Lf)) / np.sqrt(Lf) + 1e-6
+    return (np.asarray(L, dtype=np.float64) + 2) * U32 * absum + 4 * U32 * np.abs(ref) + 1e-6
 
 
 def test_stack_slide_matches_oracle_on_a_random_cube(ctx):
@@ -99,6 +99,28 @@ def test_stack_slide_matches_oracle_on_a_random_cube(ctx):
     assert np.array_equal(cands["template_idx"], rr) and np.array_equal(cands["bin"], nn)
     assert np.array_equal(cands["value"], v.astype(np.float32))
     assert rep["slide_ms"] > 0
+
+
+def test_weighted_stack_slide_matches_oracle(ctx):
+    """Amplitude weights (segment-averaged f^(4/3)) over a seeded effective-PSD
+    table, on a seeded chi-square cube, against the oracle."""
+    bank, cube, rows_mc, rows_c = _random_case(n_total=160, seed=21)
+    n_total = cube.shape[2]
+    s_eff = np.random.default_rng(8).uniform(0.5, 3.0, size=(69, N_B)).astype(np.float32)
+    ref, L, absum = slide.stack_slide(cube, rows_mc, rows_c, 120, n_total, bank, F_LO, T, F_LO, N_B,
+                                      with_abs=True, weighting=1, s_eff=s_eff.astype(np.float64))
+    cands, m, _ = ctx.stack_slide(cube, 0, n_total, BANK, rows_mc, rows_c, 120, _params(),
+                                  weighting=SRS_WEIGHT_AMPLITUDE, s_eff=s_eff)
+    err = np.abs(m - ref)
+    tol = _slide_tol(L, absum, ref)
+    assert np.all(err <= tol), float(np.max(err / tol))
+    v, rr, nn = oracle.topk(m, 32)
+    assert np.array_equal(cands["template_idx"], rr) and np.array_equal(cands["bin"], nn)
+    # equal weights over a white table are the unweighted statistic
+    _, m0, _ = ctx.stack_slide(cube, 0, n_total, BANK, rows_mc, rows_c, 120, _params())
+    _, m1, _ = ctx.stack_slide(cube, 0, n_total, BANK, rows_mc, rows_c, 120, _params(),
+                               s_eff=np.ones((69, N_B), np.float32))
+    assert np.allclose(m0, m1, rtol=1e-6, atol=1e-6)
 
 
 def test_stack_slide_chunks_carry_partial_sums(ctx):
@@ -125,7 +147,7 @@ def test_stack_slide_chunks_carry_partial_sums(ctx):
                         last=True)
 
 
-def _track_nsigma(x, mc, c, n, n_total, bank, eps=1e-6):
+def _track_nsigma(x, mc, c, n, n_total, bank, eps=1e-6, weighting=0):
     """Oracle n_sigma of one template from its track's spectra, with the
     tolerance those spectra's error bound implies."""
     k, j = slide.track(mc, c, F_LO, T, F_LO, N_B, bank, n_total)
@@ -138,9 +160,11 @@ def _track_nsigma(x, mc, c, n, n_total, bank, eps=1e-6):
     Fj = F[np.arange(L), j[:L]]
     P = oracle.power(Fj, N_S)
     dP = _p_bound(F, eps)[np.arange(L), j[:L]]
-    ref = slide.n_sigma_track(P)
-    absum = np.sum(np.abs(P - 2.0) / 2.0)
-    tol = np.sum(dP) / (2 * np.sqrt(L)) + L * U32 * absum / np.sqrt(L) + 1e-5 * abs(ref) + 1e-5
+    a = (np.array([slide.amplitude_sq(mc, c, F_LO, T, s) for s in range(L)]) if weighting else np.ones(L))
+    norm = np.sqrt(np.sum(a * a))
+    ref = slide.n_sigma_weighted(P, a, np.ones(L)) if weighting else slide.n_sigma_track(P)
+    absum = np.sum(a * (np.abs(P) + 2.0)) / 2.0 / norm
+    tol = np.sum(a * dP) / (2 * norm) + (L + 2) * U32 * absum + 1e-5 * abs(ref) + 1e-5
     return ref, tol, L
 
 
@@ -166,6 +190,21 @@ def test_slide_search_end_to_end(ctx, strain_2h):
     picks = [(r, n), (int(rng.integers(rows_mc.size)), int(rng.integers(n_t0))), (0, n_t0 - 3)]
     for r_, n_ in picks:
         ref, tol, L = _track_nsigma(x, rows_mc[r_], rows_c[r_], n_, n_total, bank)
+        assert abs(m[r_, n_] - ref) <= tol, (r_, n_, L, m[r_, n_], ref, tol)
+
+
+def test_weighted_slide_search_end_to_end(ctx, strain_2h):
+    """Amplitude weights in the whole search: the entering chirp is still the
+    loudest template, and sampled templates match the weighted oracle."""
+    x, inj = strain_2h
+    bank = slide.local_bank(*BANK)
+    n_total = x.size // N_S
+    rows_mc, rows_c = srs_synth.slide_rows(srs_synth.log_templates(3e-2, 8e-2, 9), F_HI, T, bin_step=1.0)
+    cands, m, _ = ctx.slide_search(x, BANK, rows_mc, rows_c, n_total, _params(), weighting=SRS_WEIGHT_AMPLITUDE)
+    r, n = int(cands["template_idx"][0]), int(cands["bin"][0])
+    assert abs(np.log(rows_mc[r] / inj[0]["mc"])) < 0.15 and abs((n + rows_c[r]) * T - inj[0]["t_start"]) <= T
+    for r_, n_ in [(r, n), (3, 17), (len(rows_mc) - 1, n_total - 5)]:
+        ref, tol, L = _track_nsigma(x, rows_mc[r_], rows_c[r_], n_, n_total, bank, weighting=1)
         assert abs(m[r_, n_] - ref) <= tol, (r_, n_, L, m[r_, n_], ref, tol)
 
 
@@ -198,5 +237,9 @@ def test_slide_argument_errors(ctx, strain_2h):
         ctx.slide_search(x, (7e-4, 3e-8, 69), [1e-2], [0.0], 10, p)  # bank upside down
     with pytest.raises(SrsError):
         ctx.power_cube(x, BANK, 5, 5, p)                             # empty segment range
+    with pytest.raises(SrsError):
+        ctx.slide_search(x, BANK, [1e-2], [0.0], 10, p, weighting=2)  # unknown weighting
+    with pytest.raises(SrsError):
+        ctx.slide_search(x, BANK, [1e-2], [0.0], 10, p, s_eff=np.zeros((69, N_B), np.float32))  # PSD not positive
     with pytest.raises(SrsError):
         ctx.power_cube(x, BANK, 0, 1, Params(fs=FS, t_coh=T, f_lo=F_LO, f_hi=F_HI, eps=1e-9))  # below the mixed floor
