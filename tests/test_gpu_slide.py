@@ -243,3 +243,31 @@ def test_slide_argument_errors(ctx, strain_2h):
         ctx.slide_search(x, BANK, [1e-2], [0.0], 10, p, s_eff=np.zeros((69, N_B), np.float32))  # PSD not positive
     with pytest.raises(SrsError):
         ctx.power_cube(x, BANK, 0, 1, Params(fs=FS, t_coh=T, f_lo=F_LO, f_hi=F_HI, eps=1e-9))  # below the mixed floor
+
+
+def test_slide_edge_cases(ctx):
+    """Degenerate sizes of the two-stage search against the oracle: a one-entry
+    bank, a single t0 column, t0 columns past the data (empty tracks read 0),
+    top_k larger than the map, f0 inside the band, and one-segment cube chunks."""
+    x = srs_synth.strain_with_chirps(int(40 * T * FS), FS, 3, [])
+    n_total = 40
+    p = _params(top_k=64)
+    # one-entry bank, f0 = 45 Hz, more t0 columns than segments
+    bank1 = (2e-6, 2e-6, 1)
+    rows_mc, rows_c = np.array([2e-3, 8e-2]), np.array([0.0, 0.5])
+    cube, _ = ctx.power_cube(x, bank1, 0, n_total, p)
+    cands, m, _ = ctx.stack_slide(cube, 0, n_total, bank1, rows_mc, rows_c, 50, p, f0=45.0)
+    ref, L, absum = slide.stack_slide(cube.astype(np.float64), rows_mc, rows_c, 50, n_total,
+                                      slide.local_bank(*bank1), 45.0, T, F_LO, N_B, with_abs=True)
+    assert np.all(np.abs(m - ref) <= _slide_tol(L, absum, ref))
+    assert np.all(m[:, n_total:] == 0.0) and np.all(L[:, n_total:] == 0)
+    assert len(cands) == 64
+    v, rr, nn = oracle.topk(m, 64)
+    assert np.array_equal(cands["template_idx"], rr) and np.array_equal(cands["bin"], nn)
+    # a single t0 column, the whole search in one-segment chunks
+    rows_mc2, rows_c2 = srs_synth.slide_rows(srs_synth.log_templates(5e-3, 9e-2, 4), F_HI, T, bin_step=3.0)
+    _, m_one, _ = ctx.slide_search(x, BANK, rows_mc2, rows_c2, 1, _params())
+    per_seg = 69 * N_B * 4
+    _, m_many, rep = ctx.slide_search(x, BANK, rows_mc2, rows_c2, 1, _params(), cube_budget_bytes=per_seg)
+    assert rep["n_items"] == n_total and m_one.shape == (rows_mc2.size, 1)
+    assert np.allclose(m_one, m_many, rtol=1e-5, atol=1e-4)
