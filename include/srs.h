@@ -189,14 +189,19 @@ srs_status srs_search(srs_ctx* ctx, const void* strain, int64_t n_samples, int32
                       float* stat_map, srs_candidate* cands, int32_t* n_cands,
                       srs_report* report);
 
-/* Stream-ordered form of srs_search for device-resident data (params->io_on_device
- * must be 1; strain, stat_map and cands are device pointers).  Enqueues the
- * same device sequence on the context's stream and returns without waiting;
- * *n_cands is set at once.  Outputs are valid, and a device-side failure (a
- * staging wait that gave up) is reported, only after srs_sync; keep the
- * buffers alive until then.  Calls may be queued back to back; a new shape's
+/* Stream-ordered form of srs_search.  Enqueues the same device sequence on
+ * the context's stream and returns without waiting; *n_cands is set at once.
+ * Outputs are valid, and a device-side failure (a staging wait that gave up)
+ * is reported, only after srs_sync; keep every buffer alive and the strain
+ * unchanged until then.  Calls may be queued back to back; a new shape's
  * first call still plans and tunes synchronously.  Errors found on the host
- * (arguments, planning) return at once. */
+ * (arguments, planning) return at once.
+ *   params->io_on_device = 1: strain, stat_map and cands are device pointers.
+ *   params->io_on_device = 0: host pointers.  The strain goes up on a second
+ *     stream into one of two device staging buffers, so a queued call's
+ *     upload overlaps the previous call's search; the results come back
+ *     when the stream reaches them.  Page-locked (pinned) host buffers are
+ *     needed for the copies to overlap; pageable ones work, without overlap. */
 srs_status srs_search_async(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype,
                             const double* mc, int32_t n_templates, const srs_params* params,
                             float* stat_map, srs_candidate* cands, int32_t* n_cands);

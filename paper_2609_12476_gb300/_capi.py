@@ -293,20 +293,34 @@ class Context:
         return c[:n_cands.value], m, _report_dict(rep)
 
     def search_async(self, strain, mc, params, out):
-        """srs_search_async: enqueue a search over a torch CUDA strain into the
+        """srs_search_async: enqueue a search and return at once; results and
+        device status become final at sync().  A torch CUDA strain fills the
         device tensors of `out` ({"map": float32 [templates, n_bins] or None,
-        "cands": int32 [top_k, 3]}) and return at once; results and device
-        status become final at sync()."""
-        if not _is_torch_cuda(strain):
-            raise ValueError("search_async needs a torch CUDA strain")
+        "cands": int32 [top_k, 3]}); a numpy strain (pinned memory for
+        overlap) fills the numpy arrays of `out` ({"map": float32 or None,
+        "cands": CAND_DTYPE [top_k]}).  Keep strain and out alive and unchanged
+        until sync()."""
         mc = np.ascontiguousarray(mc, dtype=np.float64)
         p = params.c()
-        p.io_on_device = 1
         n_cands = ctypes.c_int32(0)
-        mp = out["map"].data_ptr() if out.get("map") is not None else None
-        st = self._lib.srs_search_async(self._h, strain.data_ptr(), strain.numel(), _dtype_code(strain),
-                                        mc.ctypes.data, mc.size, ctypes.byref(p), mp, out["cands"].data_ptr(),
-                                        ctypes.byref(n_cands))
+        if _is_torch_cuda(strain):
+            p.io_on_device = 1
+            mp = out["map"].data_ptr() if out.get("map") is not None else None
+            st = self._lib.srs_search_async(self._h, strain.data_ptr(), strain.numel(), _dtype_code(strain),
+                                            mc.ctypes.data, mc.size, ctypes.byref(p), mp, out["cands"].data_ptr(),
+                                            ctypes.byref(n_cands))
+        else:
+            if not (isinstance(strain, np.ndarray) and strain.flags["C_CONTIGUOUS"]):
+                raise ValueError("a host strain must be a C-contiguous numpy array (kept alive until sync)")
+            p.io_on_device = 0
+            c = out["cands"]
+            if c.dtype != CAND_DTYPE or c.size < params.top_k or not c.flags["C_CONTIGUOUS"]:
+                raise ValueError("out['cands'] must be a contiguous CAND_DTYPE array of top_k entries")
+            m = out.get("map")
+            st = self._lib.srs_search_async(self._h, strain.ctypes.data, strain.size, _dtype_code(strain),
+                                            mc.ctypes.data, mc.size, ctypes.byref(p),
+                                            m.ctypes.data if m is not None else None, c.ctypes.data,
+                                            ctypes.byref(n_cands))
         self._check(st)
         return int(n_cands.value)
 

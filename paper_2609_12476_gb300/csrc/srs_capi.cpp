@@ -448,8 +448,7 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
   srs_status s = check_common(ctx, strain, dtype, params);
   if (s != SRS_OK) return s;
   if (!cands || !n_cands) return set_err(ctx, SRS_ERR_ARG, "cands and n_cands are required");
-  if (async_mode && params->io_on_device != 1)
-    return set_err(ctx, SRS_ERR_ARG, "srs_search_async needs device buffers (params.io_on_device = 1)");
+
   // events of this call: the context's own, or the next asynchronous slot
   int slot = -1;
   cudaEvent_t e0 = ctx->ev0, e1 = ctx->ev1, e2 = ctx->ev2, e3 = ctx->ev3;
@@ -479,8 +478,36 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
   const int on_dev = params->io_on_device;
   int32_t max_seg = *std::max_element(pl.nseg.begin(), pl.nseg.end());
   const void* dstrain = nullptr;
-  s = stage_strain(ctx, strain, (int64_t)max_seg * pl.n_s, dtype, on_dev, &dstrain);
-  if (s != SRS_OK) return s;
+  if (async_mode && !on_dev) {
+    // Host strain, asynchronous: upload into one of two staging buffers on the
+    // copy stream (after the search that last used that buffer has copied it
+    // out), then copy it on the search stream into the context's strain
+    // buffer, the one a captured graph reads.
+    const size_t bytes = (size_t)max_seg * pl.n_s * (f64 ? 8 : 4);
+    if (!ctx->copy_stream) SRS_CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "copy stream");
+    for (int b = 0; b < 2; ++b) {
+      if (!ctx->stage_ready[b]) SRS_CK(cudaEventCreateWithFlags(&ctx->stage_ready[b], cudaEventDisableTiming), "event");
+      if (!ctx->stage_free[b]) SRS_CK(cudaEventCreateWithFlags(&ctx->stage_free[b], cudaEventDisableTiming), "event");
+    }
+    const int b = slot & 1;
+    DevBuf& stage = b ? ctx->strain_stage1 : ctx->strain_stage0;
+    if (stage.cap < bytes) {
+      // a new buffer: nothing may still read the old one
+      SRS_CK(cudaStreamSynchronize(ctx->stream), "staging");
+      SRS_CK(stage.ensure(bytes), "alloc staging");
+    }
+    SRS_CK(ctx->strain.ensure(bytes), "alloc strain");
+    SRS_CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->stage_free[b], 0), "staging");
+    SRS_CK(cudaMemcpyAsync(stage.p, strain, bytes, cudaMemcpyHostToDevice, ctx->copy_stream), "copy strain");
+    SRS_CK(cudaEventRecord(ctx->stage_ready[b], ctx->copy_stream), "event");
+    SRS_CK(cudaStreamWaitEvent(ctx->stream, ctx->stage_ready[b], 0), "staging");
+    SRS_CK(cudaMemcpyAsync(ctx->strain.p, stage.p, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "stage strain");
+    SRS_CK(cudaEventRecord(ctx->stage_free[b], ctx->stream), "event");
+    dstrain = ctx->strain.p;
+  } else {
+    s = stage_strain(ctx, strain, (int64_t)max_seg * pl.n_s, dtype, on_dev, &dstrain);
+    if (s != SRS_OK) return s;
+  }
 
   const long long n_map = (long long)n_templates * pl.n_bins;
   const int k = (int)std::min<long long>(pl.top_k, n_map);
@@ -673,6 +700,13 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
     SRS_CK(cudaMemcpyAsync(ctx->hflag + (async_mode ? 8 * (1 + slot) : 0), search_errflag(ctx), 5 * sizeof(int),
                            cudaMemcpyDeviceToHost, ctx->stream), "read error flag");
   if (async_mode) {
+    if (!on_dev) {
+      // host results: written when the stream reaches them (pinned buffers overlap)
+      SRS_CK(cudaMemcpyAsync(cands, dc, (size_t)k * sizeof(srs_candidate), cudaMemcpyDeviceToHost, ctx->stream),
+             "copy cands");
+      if (stat_map)
+        SRS_CK(cudaMemcpyAsync(stat_map, dmap, n_map * 4, cudaMemcpyDeviceToHost, ctx->stream), "copy map");
+    }
     ctx->async_n = slot + 1;
     srs_report& r = ctx->async_rep;
     std::memset(&r, 0, sizeof r);
@@ -1202,6 +1236,14 @@ void srs_destroy(srs_ctx* c) {
   if (c->fft_plan_ok) cufft_api().destroy(c->fft_plan);
   for (cudaEvent_t e : c->slide_ev)
     if (e) cudaEventDestroy(e);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
+  for (int b = 0; b < 2; ++b) {
+    if (c->stage_ready[b]) cudaEventDestroy(c->stage_ready[b]);
+    if (c->stage_free[b]) cudaEventDestroy(c->stage_free[b]);
+  }
   if (c->hflag) cudaFreeHost(c->hflag);
   for (DevBuf* b : c->all_buffers()) b->release();
   if (c->ev0) cudaEventDestroy(c->ev0);

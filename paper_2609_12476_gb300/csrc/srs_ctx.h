@@ -75,6 +75,10 @@ struct srs_ctx {
   bool fft_plan_ok = false;
   int fft_n = 0;
   long long fft_batch = 0;
+  // asynchronous searches from host strain: two device staging buffers filled
+  // on a copy stream, so that the next call's upload overlaps this call's search
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t stage_ready[2] = {nullptr, nullptr}, stage_free[2] = {nullptr, nullptr};
   // events around a whole proposal search (it runs searches that use the others)
   cudaEvent_t pev[2] = {nullptr, nullptr};
   // the captured graph (kept for its event-record nodes, re-pointed per launch)
@@ -83,6 +87,7 @@ struct srs_ctx {
   srs::DevBuf items, order, grid, anchors, partial, betas, nseg, item_off, corr, tw, keys, topk_a, topk_b, cands, queue, strain,
       strain32, errflag, map, S, F, psi, th, im, ii;
   // two-stage search: power cube chunk, stack-slide tracks and running sums
+  srs::DevBuf strain_stage0, strain_stage1;
   srs::DevBuf cube, slide_cell, slide_coef, slide_w2, slide_seff, slide_len, slide_beta0, slide_frac, slide_Z, slide_map;
   bool have_slide = false;
   bool slide_open = false;                // running sums started (SRS_SLIDE_FIRST) and not yet finished
@@ -99,7 +104,8 @@ struct srs_ctx {
             &queue, &strain, &strain32, &errflag, &map, &S, &F, &psi, &th, &im, &ii, &xb, &yb, &z1, &logits, &dz,
             &lossv, &grad, &wts, &adam_m, &adam_v, &w1h, &w2h, &idx, &patches, &cells_m, &cells_b, &sp_items,
             &sp_bins, &sp_partial, &sp_cells, &sp_out, &sp_betas, &cmap, &ccands, &inj, &cube, &slide_cell,
-            &slide_coef, &slide_w2, &slide_seff, &slide_len, &slide_beta0, &slide_frac, &slide_Z, &slide_map};
+            &slide_coef, &slide_w2, &slide_seff, &slide_len, &slide_beta0, &slide_frac, &slide_Z, &slide_map,
+            &strain_stage0, &strain_stage1};
   }
 };
 

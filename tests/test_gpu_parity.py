@@ -334,9 +334,20 @@ def test_async_searches_match_synchronous(ctx):
     ctx.sync()
     for a, b in zip(outs, ref):
         assert torch.allclose(a["map"], b, rtol=1e-5, atol=1e-5)
-    # host buffers are refused
+    # host buffers (pinned strain, numpy outputs): uploads overlap the previous
+    # search through two staging buffers; each call sees its own strain
+    from paper_2609_12476_gb300 import CAND_DTYPE
+    hs = [x.cpu().pin_memory().numpy() for x in xs]
+    hout = [{"map": np.empty(tuple(ref[0].shape), np.float32), "cands": np.zeros(8, CAND_DTYPE)} for _ in range(7)]
+    for k in range(7):
+        ctx.search_async(hs[k % 3], mc, p, hout[k])
+    ctx.sync()
+    for k in range(7):
+        assert np.allclose(hout[k]["map"], ref[k % 3].cpu().numpy(), rtol=1e-5, atol=1e-5)
+        c_ref, _, _ = ctx.search(hs[k % 3], mc, p, stat_map=False)
+        assert np.array_equal(hout[k]["cands"][["template_idx", "bin"]], c_ref[["template_idx", "bin"]])
     with pytest.raises(ValueError):
-        ctx.search_async(xs[0].cpu().numpy(), mc, p, outs[0])
+        ctx.search_async(hs[0], mc, p, {"map": None, "cands": np.zeros(3, CAND_DTYPE)})   # too few candidates
 
 
 def test_search_degenerate_sizes(ctx):
