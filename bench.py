@@ -303,6 +303,17 @@ def run_ours(args):
         roof_hbm = {"kernel": "k_mixed", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                     "frac": ach / hbm_peak, "traffic": traffic,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback 6.8 TB/s"}
+        # issue view: warp instructions per launch (ncu, committed summary) per
+        # kernel time against 4 warp instructions per clock per SM
+        inst = profile_traffic("k_mixed_semicoherent_2h.md", key="inst_executed_per_launch") \
+            if args.workload == "semicoherent_2h" else None
+        roof_issue = None
+        if inst:
+            ach_i = inst / (spread_avg * 1e-3) / 1e12
+            peak_i = 4 * n_sm * sm_mhz * 1e6 / 1e12
+            roof_issue = {"kernel": "k_mixed", "bound": "issue", "achieved": ach_i, "peak": peak_i,
+                          "unit": "Twarp-inst/s", "frac": ach_i / peak_i, "inst_per_launch": inst,
+                          "peak_source": "4 schedulers x 1 warp instruction/clk x %d SMs x %.0f MHz" % (n_sm, sm_mhz)}
         plain = None
         if not args.no_plain:
             plain = time_plain(ctx, xd, w, stream, flush, n_spec, n_bins, info, pk)
@@ -325,7 +336,8 @@ def run_ours(args):
                            "staging": "tma" if rep["staging"] else "global loads",
                            "precision": "mixed: FP64 time-map anchors, FP32 spread/FFT/power",
                            "l2": "flushed (256 MB write) before every timed step"},
-                "roofline": roof, "roofline_fma": roof_fma, "roofline_hbm": roof_hbm, "clocks": ck,
+                "roofline": roof, "roofline_fma": roof_fma, "roofline_hbm": roof_hbm, "roofline_issue": roof_issue,
+                "clocks": ck,
                 "gpu_launches": launches,
                 "e2e": e2e, "cpu_baseline": cpu, "plain_fp64": plain, "cufft_comparison": fftcmp, "two_stage": two,
                 "spread_ms_avg": spread_avg, "search_device_ms_avg": rep["device_ms"]}
