@@ -291,32 +291,30 @@ __device__ __forceinline__ TapIn tap_inputs(const Anchor& A, const float* __rest
 // Spread the samples [j_begin, j_end) of one lane into `grid`.  The lane keeps
 // the W cells [Bm, Bm + W) of its kernel footprint in registers.  The warp
 // walks cell by cell: each lane adds all of its samples whose first cell is
-// Bm, then every lane moves its window one cell on (flushing acc[0] with a
-// shared-memory atomic), so the shift is warp-uniform.
+// Bm, then every lane flushes cell Bm with a shared-memory atomic and moves
+// its window one cell on, so the step is warp-uniform.  The window is a ring:
+// the walk is unrolled W times so that, at step R of the unrolled loop, cell
+// Bm + t lives in register acc[(t + R) % W] and moving on renames registers
+// instead of copying them.
 template <int W, bool INT_KC>
-__device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2* __restrict__ grid,
-                                           const Anchor A, int j_begin, int j_end, int l_base,
-                                           const MixedArgs& a) {
+struct CellWalk {
   float2 acc[W];
-#pragma unroll
-  for (int t = 0; t < W; ++t) acc[t] = make_float2(0.f, 0.f);
-  const int n = a.n_fine;
-  // ES kernel in base 2: phi(z) = 2^(E sqrt(1 - z^2) - E); with Z = E z,
-  // E sqrt(1 - z^2) = sqrt((E - Z)(E + Z)), and tap t has Z = Z0 + t H.
-  const float E = a.es_beta_log2e;
-  const float H = E * a.two_over_w;
+  TapIn p;
+  int j, j_end, l_base, Bm;
+  bool live;
+  unsigned mask;
+  float H;
   TapConst kc;
-  kc.es_scale = exp2f(-E);
-  kc.eh32 = H * 2.3283064365386963e-10f;
-  kc.two_e = 2.0f * E;
-  const float2 HH = make_float2(H, H), mHH = make_float2(-H, -H);
-  const unsigned mask = __activemask();
-  int j = j_begin;
-  bool live = j < j_end;
-  TapIn p = {0, 0.f, 0.f, 0.f, 0.f};
-  if (live) p = tap_inputs<INT_KC>(A, xs, j, l_base, W, kc, a);
-  int Bm = p.l0;  // fine-grid cell of acc[0]
-  while (__any_sync(mask, live)) {
+  Anchor A;
+  const float* __restrict__ xs;
+  float2* __restrict__ grid;
+  const MixedArgs* a;
+
+  // one cell of the walk at ring offset R; false once no lane has samples left
+  template <int R>
+  __device__ __forceinline__ bool cell() {
+    if (!__any_sync(mask, live)) return false;
+    const float2 HH = make_float2(H, H), mHH = make_float2(-H, -H);
     while (live && p.l0 == Bm) {
       const float2 cv = make_float2(p.cre, p.cim);
       const float2 aa = make_float2(p.a0, p.a0), bb = make_float2(p.b0, p.b0);
@@ -327,36 +325,83 @@ __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2*
         const float2 q = __fmul2_rn(__ffma2_rn(tt, mHH, aa), __ffma2_rn(tt, HH, bb));
         const float p0 = ex2_approx(sqrt_approx(fabsf(q.x)));
         const float p1 = ex2_approx(sqrt_approx(fabsf(q.y)));
-        acc[t] = __ffma2_rn(make_float2(p0, p0), cv, acc[t]);
-        acc[t + 1] = __ffma2_rn(make_float2(p1, p1), cv, acc[t + 1]);
+        acc[(t + R) % W] = __ffma2_rn(make_float2(p0, p0), cv, acc[(t + R) % W]);
+        acc[(t + 1 + R) % W] = __ffma2_rn(make_float2(p1, p1), cv, acc[(t + 1 + R) % W]);
       }
       if (W & 1) {
         const float tl = (float)(W - 1);
         const float pl = ex2_approx(sqrt_approx(fabsf(fmaf(tl, -H, p.a0) * fmaf(tl, H, p.b0))));
-        acc[W - 1] = __ffma2_rn(make_float2(pl, pl), cv, acc[W - 1]);
+        acc[(W - 1 + R) % W] = __ffma2_rn(make_float2(pl, pl), cv, acc[(W - 1 + R) % W]);
       }
       ++j;
       live = j < j_end;
-      if (live) p = tap_inputs<INT_KC>(A, xs, j, l_base, W, kc, a);
+      if (live) p = tap_inputs<INT_KC>(A, xs, j, l_base, W, kc, *a);
     }
-    // cell Bm is complete for this lane
-    if (acc[0].x != 0.f || acc[0].y != 0.f) {
-      atomicAdd(&grid[Bm].x, acc[0].x);
-      atomicAdd(&grid[Bm].y, acc[0].y);
-    }
-#pragma unroll
-    for (int t = 0; t < W - 1; ++t) acc[t] = acc[t + 1];
-    acc[W - 1] = make_float2(0.f, 0.f);
-    Bm = (Bm + 1 == n) ? 0 : Bm + 1;
+    // cell Bm is complete for this lane; its register becomes cell Bm + W
+    atomicAdd(&grid[Bm].x, acc[R % W].x);
+    atomicAdd(&grid[Bm].y, acc[R % W].y);
+    acc[R % W] = make_float2(0.f, 0.f);
+    Bm = (Bm + 1 == a->n_fine) ? 0 : Bm + 1;
+    return true;
   }
+
+  // the cells still in the window when the walk ends at ring offset R
+  template <int R>
+  __device__ __forceinline__ void flush() {
 #pragma unroll
-  for (int t = 0; t < W - 1; ++t) {
-    int c = Bm + t;
-    if (c >= n) c -= n;
-    if (acc[t].x != 0.f || acc[t].y != 0.f) {
-      atomicAdd(&grid[c].x, acc[t].x);
-      atomicAdd(&grid[c].y, acc[t].y);
+    for (int t = 0; t < W - 1; ++t) {
+      int c = Bm + t;
+      if (c >= a->n_fine) c -= a->n_fine;
+      const float2 v = acc[(t + R) % W];
+      if (v.x != 0.f || v.y != 0.f) {
+        atomicAdd(&grid[c].x, v.x);
+        atomicAdd(&grid[c].y, v.y);
+      }
     }
+  }
+
+  // ring offsets R .. W-1 of one turn; false once the walk has ended
+  template <int R>
+  __device__ __forceinline__ bool turn() {
+    if constexpr (R == W) {
+      return true;
+    } else {
+      if (!cell<R>()) {
+        flush<R>();
+        return false;
+      }
+      return turn<R + 1>();
+    }
+  }
+};
+
+template <int W, bool INT_KC>
+__device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2* __restrict__ grid,
+                                           const Anchor A, int j_begin, int j_end, int l_base,
+                                           const MixedArgs& a) {
+  CellWalk<W, INT_KC> w;
+#pragma unroll
+  for (int t = 0; t < W; ++t) w.acc[t] = make_float2(0.f, 0.f);
+  // ES kernel in base 2: phi(z) = 2^(E sqrt(1 - z^2) - E); with Z = E z,
+  // E sqrt(1 - z^2) = sqrt((E - Z)(E + Z)), and tap t has Z = Z0 + t H.
+  const float E = a.es_beta_log2e;
+  w.H = E * a.two_over_w;
+  w.kc.es_scale = exp2f(-E);
+  w.kc.eh32 = w.H * 2.3283064365386963e-10f;
+  w.kc.two_e = 2.0f * E;
+  w.mask = __activemask();
+  w.A = A;
+  w.xs = xs;
+  w.grid = grid;
+  w.a = &a;
+  w.j = j_begin;
+  w.j_end = j_end;
+  w.l_base = l_base;
+  w.live = j_begin < j_end;
+  w.p = {0, 0.f, 0.f, 0.f, 0.f};
+  if (w.live) w.p = tap_inputs<INT_KC>(A, xs, j_begin, l_base, W, w.kc, a);
+  w.Bm = w.p.l0;  // fine-grid cell of ring offset 0
+  while (w.template turn<0>()) {
   }
 }
 
