@@ -339,6 +339,7 @@ srs_status autotune_mixed(srs_ctx* ctx, Plan& pl, const float* s32, int use_tma,
   put(&pl.n_spectra, sizeof pl.n_spectra);
   key.push_back((unsigned char)use_tma);
   key.push_back((unsigned char)pl.allow_128);
+  key.push_back((unsigned char)pl.lanes128);
   // SRS_MIXED_LAYOUT=<threads>:<tma|global>[:<chunk>:<ctas>] restricts the
   // search to one layout (used to check every layout against the same
   // reference, and to profile one fixed configuration).
@@ -1065,6 +1066,7 @@ srs_status tune_cube(srs_ctx* ctx, Plan& pl, const float* x, int use_tma, float*
   put(&range, sizeof range);
   key.push_back((unsigned char)use_tma);
   key.push_back((unsigned char)pl.allow_128);
+  key.push_back((unsigned char)pl.lanes128);
   const char* lay = std::getenv("SRS_MIXED_LAYOUT");
   int only_threads = 0, only_gx = -1;
   if (lay) {

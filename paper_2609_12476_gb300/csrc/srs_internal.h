@@ -65,6 +65,8 @@ struct Plan {
   int32_t threads = 256;                                 // threads per CTA of the mixed spreader
   int32_t run = 0, span = 0, n_anchor = 0;               // samples per thread / per warp / anchors per segment
   bool allow_128 = false;                                // 128-thread CTAs keep the anchor expansion accurate
+  int32_t lanes128 = 32;                                 // lanes per FP64 anchor in 128-thread CTAs (32, or 16
+                                                         // where a whole warp's span is too long for the expansion)
   bool global_x = false;                                 // spreader reads samples from global memory (no TMA staging)
   int32_t chunk = 0;
   std::vector<Item> items;
@@ -89,7 +91,8 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
                      int32_t seg_end, Plan& out, std::string& msg,
                      const double* betas_in = nullptr, bool local = false);
 void fill_info(const Plan& pl, srs_plan_info* info);
-// Threads per CTA of the mixed spreader and the run / span / anchor layout that follows.
+// Threads per CTA of the mixed spreader and the run / span / anchor layout that
+// follows: one FP64 anchor per 32 lanes (per lanes128 lanes in 128-thread CTAs).
 void set_cta(Plan& pl, int32_t threads);
 // Samples per thread of the mixed spreader for CTAs of `threads` threads (odd).
 int32_t run_for(int64_t n_s, int32_t threads);

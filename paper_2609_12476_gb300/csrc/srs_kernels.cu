@@ -472,7 +472,9 @@ k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_
         const int j0 = (warp * 32 + lane) * a.run;
         const int j1 = min(j0 + a.run, a.n_s);
         const float* xsrc = GLOBAL_X ? strain + (long long)i * a.n_s : xs;
-        if (j0 < a.n_s) spread_run<W, INT_KC>(xsrc, g0, anc[(i - it.i0) * a.n_anchor + warp], j0, j1, warp * a.span, a);
+        // the anchor of this lane's span (one per warp, or per half-warp)
+        const int ai = j0 / a.span;
+        if (j0 < a.n_s) spread_run<W, INT_KC>(xsrc, g0, anc[(i - it.i0) * a.n_anchor + ai], j0, j1, ai * a.span, a);
       }
       __syncthreads();
       if (!GLOBAL_X && tid == 0 && i + 1 < it.i1) bulk_load(xs, strain + (long long)(i + 1) * a.n_s, seg_bytes, &s_bar);

@@ -242,15 +242,21 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
     // Local degree-5 expansion over one span must be accurate to 1e-9 cycles at
     // the band edge: bound the first omitted term, coef_6 beta^5 A^(-43/8) / 6!
     // (d^6 delta / ds^6 / 6!), at the smallest A = 1 - 8/3 beta t of any segment.
-    // Checked for 256-thread CTAs (required) and 128-thread CTAs (twice the span; allowed if it holds).
+    // Checked for 256-thread CTAs (required) and for 128-thread CTAs, whose
+    // runs are twice as long: with an anchor per warp if that holds, else with
+    // an anchor per half-warp (the 256-thread span again); 128-thread CTAs are
+    // allowed if either holds.
     double fmax = std::max(std::fabs(p.f_lo), std::fabs(p.f_hi));
     const double ds_half = 32.0 * (double)run_for(pl.n_s, 128) / p.fs;
+    const double ds_quarter = 16.0 * (double)run_for(pl.n_s, 128) / p.fs;
     const double ds = pl.span / p.fs;
     // d^6 delta / ds^6 / 6! = coef_6 beta^5 A^(-43/8) / 720 and d^2 delta / ds^2 / 2 = beta A^(-11/8) / 2,
     // through logarithms (one log of beta and of A per template)
     const double c6 = 2438.3333333333333 / 720.0;
     const double lim6_half = 1e-9 / (std::pow(ds_half, 6) * fmax), lim2_half = 0.25 * p.t_coh / (ds_half * ds_half);
     const double lim6 = 1e-9 / (std::pow(ds, 6) * fmax), lim2 = 0.25 * p.t_coh / (ds * ds);
+    const double lim6_q = 1e-9 / (std::pow(ds_quarter, 6) * fmax), lim2_q = 0.25 * p.t_coh / (ds_quarter * ds_quarter);
+    bool warp_anchor_128 = true;
     pl.allow_128 = true;
     for (int32_t m = 0; m < n_templates; ++m) {
       int32_t last_seg = local ? 1 : (spectra_mode ? seg_end : pl.nseg[m]);
@@ -259,13 +265,15 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
       const double lb = std::log(pl.beta[m]), la = std::log(A);
       const double e6 = c6 * std::exp(5.0 * lb - 43.0 / 8.0 * la);
       const double e2 = 0.5 * std::exp(lb - 11.0 / 8.0 * la);
-      if (e6 > lim6_half || e2 > lim2_half) pl.allow_128 = false;
+      if (e6 > lim6_half || e2 > lim2_half) warp_anchor_128 = false;
+      if (e6 > lim6_q || e2 > lim2_q) pl.allow_128 = false;
       if (e6 > lim6 || e2 > lim2) {
         std::snprintf(buf, sizeof buf, "template %d chirps too fast for the mixed form's anchor spacing; use SRS_PLAIN_FP64", m);
         msg = buf;
         return SRS_ERR_UNSUPPORTED;
       }
     }
+    pl.lanes128 = warp_anchor_128 ? 32 : 16;
   }
 
   // Deconvolution: with fine grid spacing h = 2 pi / n and kernel half-width
@@ -371,7 +379,7 @@ int32_t run_for(int64_t n_s, int32_t threads) {
 void set_cta(Plan& pl, int32_t threads) {
   pl.threads = threads;
   pl.run = run_for(pl.n_s, threads);
-  pl.span = 32 * pl.run;
+  pl.span = (threads == 128 ? pl.lanes128 : 32) * pl.run;
   pl.n_anchor = (int32_t)((pl.n_s + pl.span - 1) / pl.span);
 }
 

@@ -271,3 +271,27 @@ def test_slide_edge_cases(ctx):
     _, m_many, rep = ctx.slide_search(x, BANK, rows_mc2, rows_c2, 1, _params(), cube_budget_bytes=per_seg)
     assert rep["n_items"] == n_total and m_one.shape == (rows_mc2.size, 1)
     assert np.allclose(m_one, m_many, rtol=1e-5, atol=1e-4)
+
+
+@pytest.mark.parametrize("layout", ["128:global", "128:tma", "256:tma", "256:global"])
+def test_power_cube_every_layout_against_oracle(monkeypatch, strain_2h, layout):
+    """Every spreader layout the cube tuner can pick, on the bank's fastest
+    chirps: 128-thread CTAs take an FP64 anchor per half-warp there, because a
+    whole warp's span is too long for the anchor expansion at beta = 7e-4."""
+    monkeypatch.setenv("SRS_MIXED_LAYOUT", layout)
+    x, _ = strain_2h
+    from paper_2609_12476_gb300 import srs_plan
+    c = Context(0)
+    try:
+        cube, rep = c.power_cube(x, BANK, 40, 42, _params())
+    finally:
+        c.close()
+    assert rep["cta_threads"] == int(layout.split(":")[0])
+    bank = slide.local_bank(*BANK)
+    ks = [0, 34, 66, 67, 68]
+    F = oracle.spectra(x, FS, T, F_LO, N_B, bank, [(k, i) for k in ks for i in (40, 41)], local=True)
+    F = F.reshape(len(ks), 2, N_B)
+    P = oracle.power(F, N_S).transpose(0, 2, 1)
+    tol = _p_bound(F, 1e-6).transpose(0, 2, 1) + 1e-6 * P + 1e-6
+    err = np.abs(cube[ks] - P)
+    assert np.all(err <= tol), (layout, float(np.max(err / tol)))
