@@ -185,6 +185,13 @@ def test_slide_search_end_to_end(ctx, strain_2h):
     assert cands["value"][0] > 20
     v, rr, nn = oracle.topk(m, 32)
     assert np.array_equal(cands["template_idx"], rr) and np.array_equal(cands["bin"], nn)
+    # the power reads the library reports are the oracle tracks' segments inside the data
+    reads = 0
+    for r_ in range(rows_mc.size):
+        k, _ = slide.track(rows_mc[r_], rows_c[r_], F_LO, T, F_LO, N_B, bank, n_total)
+        first = np.arange(n_t0) + (1 if rows_c[r_] > 0 else 0)
+        reads += int(np.sum(np.clip(np.minimum(len(k), n_total - first), 0, None)))
+    assert rep["slide_reads"] == reads
     # sampled templates against the oracle: the winner, a quiet one, one cut by the data's end
     rng = np.random.default_rng(1)
     picks = [(r, n), (int(rng.integers(rows_mc.size)), int(rng.integers(n_t0))), (0, n_t0 - 3)]
