@@ -226,6 +226,12 @@ srs_status srs_segment_spectra(srs_ctx* ctx, const void* strain, int64_t n_sampl
                                int32_t seg_begin, int32_t seg_end, const srs_params* params,
                                double* F, srs_report* report);
 
+/* Diagnostic: runs the spreader's bounded staging wait on a transfer that never
+ * comes (one thread, about one second) and returns what a search would:
+ * SRS_ERR_TIMEOUT with the give-up recorded in srs_last_error().  The wait
+ * ends by its own limit, so no kernel hangs and the context stays usable. */
+srs_status srs_selftest_wait(srs_ctx* ctx);
+
 /* Timed comparison only: the same segment spectra as srs_segment_spectra()
  * in the mixed form, computed unfused.  k_mixed writes each segment's spread
  * grid (n_fine complex float, Sec. III.B spreading step) to device memory,

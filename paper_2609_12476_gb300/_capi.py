@@ -24,7 +24,7 @@ SRS_PLAIN_FP64, SRS_MIXED = 0, 1
 EXPORTS = ("srs_create", "srs_destroy", "srs_last_error", "srs_plan", "srs_search", "srs_search_async", "srs_sync",
            "srs_segment_spectra", "srs_segment_spectra_cufft", "srs_time_map", "srs_segment_spectra_static", "srs_make_strain",
            "srs_patches", "srs_mlp_forward", "srs_mlp_grad", "srs_mlp_train", "srs_score_map", "srs_refine",
-           "srs_search_proposed", "srs_power_cube", "srs_stack_slide", "srs_slide_search")
+           "srs_search_proposed", "srs_power_cube", "srs_stack_slide", "srs_slide_search", "srs_selftest_wait")
 SRS_SLIDE_FIRST, SRS_SLIDE_LAST = 1, 2
 SRS_WEIGHT_EQUAL, SRS_WEIGHT_AMPLITUDE = 0, 1
 MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 297, 64, 19137
@@ -154,6 +154,8 @@ def lib():
             fn.restype = i32
             fn.argtypes = [vp, vp, i64, i32, vp, i32, i32, i32, ctypes.POINTER(_Params), vp,
                            ctypes.POINTER(_Report)]
+        L.srs_selftest_wait.restype = i32
+        L.srs_selftest_wait.argtypes = [vp]
         L.srs_power_cube.restype = i32
         L.srs_power_cube.argtypes = [vp, vp, i64, i32, ctypes.POINTER(_Bank), i32, i32, ctypes.POINTER(_Params), vp,
                                      ctypes.POINTER(_Report)]
@@ -358,6 +360,11 @@ class Context:
                 int(seg_end), ctypes.byref(p), F.ctypes.data, ctypes.byref(rep))
         self._check(st)
         return F, _report_dict(rep)
+
+    def selftest_wait(self):
+        """srs_selftest_wait: the bounded staging wait's give-up path; raises
+        SrsError (SRS_ERR_TIMEOUT) as a search whose wait gave up would."""
+        self._check(self._lib.srs_selftest_wait(self._h))
 
     # ----- two-stage search: power cube + stack-slide ----------------------
     @staticmethod

@@ -1358,6 +1358,16 @@ srs_status srs_power_cube(srs_ctx* ctx, const void* strain, int64_t n_samples, i
   }
 }
 
+srs_status srs_selftest_wait(srs_ctx* ctx) {
+  if (!ctx) return SRS_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_err(ctx, cudaGetLastError(), "cudaSetDevice");
+  srs_status s = clear_err_flag(ctx);
+  if (s != SRS_OK) return s;
+  SRS_CK(launch_wait_selftest(ctx->errflag.as<int>(), ctx->stream), "k_wait_selftest");
+  SRS_CK(cudaStreamSynchronize(ctx->stream), "self-test");
+  return check_err_flag(ctx);
+}
+
 srs_status srs_segment_spectra_cufft(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype,
                                      const double* mc, int32_t n_templates, int32_t seg_begin, int32_t seg_end,
                                      const srs_params* params, double* F, srs_report* report) {

@@ -237,6 +237,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
+// Self-test of the bounded staging wait: one thread arms an mbarrier for a
+// 16-byte transfer that is never issued and waits on it exactly as k_mixed
+// does; the wait gives up after its cycle limit and the error flag records
+// it.  Nothing faults and nothing hangs.
+__global__ void k_wait_selftest(int* __restrict__ err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               ::"r"((uint32_t)__cvta_generic_to_shared(&bar)), "r"(16u) : "memory");
+  if (!mbar_wait(&bar, 0u) && atomicExch(err, 1) == 0) {
+    err[1] = -1;
+    err[2] = -1;
+    err[3] = 0;
+    err[4] = (int)blockIdx.x;
+  }
+}
+
 // Tap inputs of one sample: first fine-grid cell l0 (wrapped into [0, n)),
 // a0 = E (1 - z0) and b0 = E (1 + z0) for the kernel argument z0 of tap 0
 // (E = beta log2 e, so that tap t's exponent is sqrt((a0 - t H)(b0 + t H))
@@ -938,6 +956,11 @@ cudaError_t launch_reduce_mixed_top32(const float* partial, const int* item_off,
   if (blocks > (long long)n_sm * 4) blocks = (long long)n_sm * 4;
   k_reduce_mixed_top32<<<(unsigned)blocks, 256, 0, st>>>(partial, item_off, nseg, n_templates, n_bins, map, k,
                                                           scratch, ticket, cands);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(int* err, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(err);
   return cudaGetLastError();
 }
 

@@ -72,6 +72,9 @@ cudaError_t launch_reduce_mixed_top32(const float* partial, const int* item_off,
                                       srs_candidate* cands, int n_sm, cudaStream_t st);
 // F[s][b] = G[s][k(b)] * corr[b] for the grids G of n_spec spectra (after an
 // external FFT), k(b) = b - half_bins wrapped into [0, n_fine).
+// Arms an mbarrier for a transfer that never comes and waits on it with the
+// spreader's bounded wait: err[0] = 1 once the wait gives up (about 1 s).
+cudaError_t launch_wait_selftest(int* err, cudaStream_t st);
 cudaError_t launch_grid_deconv(const float2* grid, long long n_spec, int n_fine, int n_bins, int half_bins,
                                const float* corr, double2* F, int n_sm, cudaStream_t st);
 cudaError_t launch_finish_plain(const double* S, const int* nseg, int n_templates, int n_bins, float* map,

@@ -217,6 +217,20 @@ def test_errors_are_status_codes(ctx):
     assert len(c) == 4 and np.isfinite(m).all()
 
 
+def test_bounded_wait_gives_up_with_a_status(ctx):
+    """The spreader's staging wait, armed for a transfer that never comes,
+    gives up after its cycle limit: the call returns SRS_ERR_TIMEOUT with the
+    give-up recorded, nothing hangs, and the context keeps working."""
+    import time
+    t0 = time.perf_counter()
+    with pytest.raises(SrsError) as ei:
+        ctx.selftest_wait()
+    assert ei.value.status == -4 and "gave up" in str(ei.value)
+    assert time.perf_counter() - t0 < 30
+    c, m, _ = ctx.search(srs_synth.white_noise(3 * 7680, 3), [3e-2], Params(top_k=4))
+    assert len(c) == 4 and np.all(np.isfinite(m))
+
+
 @pytest.mark.parametrize("chunk", [1, 2, 3, 16])
 def test_chunked_items_and_many_items_per_cta(ctx, two_hours, chunk):
     """Work items of several segments, and more items than resident CTAs, give
