@@ -226,6 +226,24 @@ srs_status srs_segment_spectra(srs_ctx* ctx, const void* strain, int64_t n_sampl
                                int32_t seg_begin, int32_t seg_end, const srs_params* params,
                                double* F, srs_report* report);
 
+/* Detection statistics (host only; no context or GPU needed).
+ * Threshold (Sec. III.C Eq. n_sigma^th): the n_sigma^th with
+ * P(n_sigma > n_sigma^th | H0) = p_fa for one template whose track has n_seg
+ * segments with weights w[n_seg] (any positive scale; normalised here so that
+ * sum w^2 = 1), or equal weights when w is NULL.  Under H0,
+ * n_sigma = sum w_i (E_i - 1) with E_i ~ Exp(1) (P_i ~ chi^2 with 2 dof):
+ * for equal weights a scaled chi^2 with 2 n_seg dof, otherwise a generalised
+ * chi^2, evaluated as a mixture of Gamma laws (Moschopoulos 1985).
+ * SRS_ERR_ARG for n_seg < 1, p_fa outside (0, 1) or a weight <= 0. */
+srs_status srs_nsigma_threshold(const double* w, int32_t n_seg, double p_fa, double* n_sigma_th);
+
+/* Detection non-centrality (Eq. non-centrality_threshold), equal weights: the
+ * total non-centrality Lambda = sum_i lambda_i for which n_sigma exceeds the
+ * p_fa threshold with probability p_det (sum P is then non-central chi^2 with
+ * 2 n_seg dof).  The paper quotes Lambda_1 = 46.5 for n_seg = 1, p_fa = 1e-6,
+ * p_det = 0.95. */
+srs_status srs_detection_noncentrality(int32_t n_seg, double p_fa, double p_det, double* lambda);
+
 /* Diagnostic: runs the spreader's bounded staging wait on a transfer that never
  * comes (one thread, about one second) and returns what a search would:
  * SRS_ERR_TIMEOUT with the give-up recorded in srs_last_error().  The wait

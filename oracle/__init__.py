@@ -13,7 +13,9 @@ Each function states the passage of the paper it follows:
   semicoherent / n_sigma                 -> Sec. III.C Eqs. (weights),
                                              (semicoherent_statistic)
   topk                                   -> ordering (n_sigma desc, template asc, bin asc)
-The learned-proposal reference (MLP forward/backward) lives in oracle.mlp.
+The learned-proposal reference (MLP forward/backward) lives in oracle.mlp, the
+two-stage search (power cube, tracks, stack-slide) in oracle.slide, and the
+detection thresholds in oracle.stats.
 """
 import ctypes
 import os

@@ -24,7 +24,8 @@ SRS_PLAIN_FP64, SRS_MIXED = 0, 1
 EXPORTS = ("srs_create", "srs_destroy", "srs_last_error", "srs_plan", "srs_search", "srs_search_async", "srs_sync",
            "srs_segment_spectra", "srs_segment_spectra_cufft", "srs_time_map", "srs_segment_spectra_static", "srs_make_strain",
            "srs_patches", "srs_mlp_forward", "srs_mlp_grad", "srs_mlp_train", "srs_score_map", "srs_refine",
-           "srs_search_proposed", "srs_power_cube", "srs_stack_slide", "srs_slide_search", "srs_selftest_wait")
+           "srs_search_proposed", "srs_power_cube", "srs_stack_slide", "srs_slide_search", "srs_selftest_wait",
+           "srs_nsigma_threshold", "srs_detection_noncentrality")
 SRS_SLIDE_FIRST, SRS_SLIDE_LAST = 1, 2
 SRS_WEIGHT_EQUAL, SRS_WEIGHT_AMPLITUDE = 0, 1
 MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 297, 64, 19137
@@ -154,6 +155,11 @@ def lib():
             fn.restype = i32
             fn.argtypes = [vp, vp, i64, i32, vp, i32, i32, i32, ctypes.POINTER(_Params), vp,
                            ctypes.POINTER(_Report)]
+        L.srs_nsigma_threshold.restype = i32
+        L.srs_nsigma_threshold.argtypes = [vp, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+        L.srs_detection_noncentrality.restype = i32
+        L.srs_detection_noncentrality.argtypes = [i32, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.POINTER(ctypes.c_double)]
         L.srs_selftest_wait.restype = i32
         L.srs_selftest_wait.argtypes = [vp]
         L.srs_power_cube.restype = i32
@@ -194,6 +200,30 @@ def lib():
                                                  vp, ctypes.c_char_p, ctypes.c_size_t]
         _LIB = L
     return _LIB
+
+
+def nsigma_threshold(n_seg, p_fa, weights=None):
+    """srs_nsigma_threshold: n_sigma^th at false-alarm probability p_fa for a
+    track of n_seg segments, equal weights or the given positive weights."""
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    if w is not None and w.size != n_seg:
+        raise ValueError("weights must have n_seg entries")
+    out = ctypes.c_double(0.0)
+    st = lib().srs_nsigma_threshold(w.ctypes.data if w is not None else None, int(n_seg), float(p_fa),
+                                    ctypes.byref(out))
+    if st != SRS_OK:
+        raise SrsError(st, "srs_nsigma_threshold rejected its arguments")
+    return out.value
+
+
+def detection_noncentrality(n_seg, p_fa, p_det):
+    """srs_detection_noncentrality: the total non-centrality a signal needs
+    to cross the p_fa threshold with probability p_det (equal weights)."""
+    out = ctypes.c_double(0.0)
+    st = lib().srs_detection_noncentrality(int(n_seg), float(p_fa), float(p_det), ctypes.byref(out))
+    if st != SRS_OK:
+        raise SrsError(st, "srs_detection_noncentrality rejected its arguments")
+    return out.value
 
 
 def _report_dict(r):

@@ -1,0 +1,200 @@
+// srs_stats.cpp -- detection statistics of the semicoherent search (host only):
+// the n_sigma threshold at a false-alarm probability (Sec. III.C Eq.
+// n_sigma^th) and the total non-centrality a signal needs to be detected
+// (Eq. non-centrality_threshold).
+//
+// Under H0 each normalised power P_i is chi^2 with 2 degrees of freedom, so
+// (P_i - 2)/2 = E_i - 1 with E_i ~ Exp(1), and for weights w (sum w^2 = 1)
+//   n_sigma = sum_i w_i E_i - sum_i w_i.
+// Equal weights: sum E_i ~ Gamma(N, 1), whose survival function for a whole
+// number N is the Poisson sum Q(N, x) = e^-x sum_{k<N} x^k / k!.  Unequal
+// weights: a sum of exponentials with different scales, whose survival
+// function is the mixture of Gamma(N + k) survival functions of Moschopoulos
+// (1985): with b = min w_i, C = prod (b / w_i),
+//   gamma_k = sum_i (1 - b / w_i)^k / k,  delta_0 = 1,
+//   delta_{k+1} = 1/(k+1) sum_{j=1}^{k+1} j gamma_j delta_{k+1-j},
+//   P(sum w_i E_i > q) = C sum_k delta_k Q(N + k, q / b),
+// every term positive.  The mixture weights C delta_k are carried in long
+// double, whose range holds C for tracks of thousands of segments.
+// With a signal, P_i is non-central chi^2 (2 dof, non-centrality lambda_i);
+// for equal weights sum P_i is non-central chi^2 with 2N dof and total
+// non-centrality Lambda, a Poisson(Lambda/2) mixture of central chi^2 with
+// 2(N + j) dof.
+#include <cmath>
+#include <vector>
+
+#include "../../include/srs.h"
+
+namespace {
+
+using ld = long double;
+
+// Q(m, x) for m = m0, m0 + 1, ..., m0 + count - 1 (whole m >= 1): the upper
+// regularized incomplete gamma function, by Q(m + 1, x) = Q(m, x) + p(m, x)
+// with the Poisson term p(m, x) = e^-x x^m / m!, in logs.
+void gamma_q_run(int64_t m0, int64_t count, ld x, std::vector<ld>& out) {
+  out.assign((size_t)count, 0.0L);
+  if (x <= 0) {
+    for (auto& v : out) v = 1.0L;
+    return;
+  }
+  const ld lx = std::log(x);
+  // Q(m0, x) = sum_{k < m0} p(k, x): add from the largest term outwards
+  const int64_t kmax = m0 - 1;
+  const int64_t kpk = std::min<int64_t>(kmax, (int64_t)std::floor(x));
+  auto logp = [&](int64_t k) { return -x + (ld)k * lx - std::lgamma((ld)k + 1.0L); };
+  const ld lref = logp(kpk);
+  ld s = 0;
+  for (int64_t k = kpk; k >= 0; --k) {
+    const ld t = std::exp(logp(k) - lref);
+    s += t;
+    if (t < 1e-22L * s) break;
+  }
+  for (int64_t k = kpk + 1; k <= kmax; ++k) {
+    const ld t = std::exp(logp(k) - lref);
+    s += t;
+    if (t < 1e-22L * s) break;
+  }
+  ld q = s * std::exp(lref);
+  for (int64_t c = 0; c < count; ++c) {
+    out[(size_t)c] = std::min<ld>(q, 1.0L);
+    q += std::exp(logp(m0 + c));
+  }
+}
+
+// The law of sum_i w_i E_i for positive weights as a mixture of Gamma(N + k,
+// scale b) laws: mixture weights d_k = C delta_k (Moschopoulos 1985), built
+// once; sf(q) = sum_k d_k Q(N + k, q / b).
+struct ExpMixture {
+  int64_t n = 0;
+  ld b = 1;
+  std::vector<ld> d;
+
+  explicit ExpMixture(const std::vector<ld>& w) {
+    n = (int64_t)w.size();
+    b = w[0];
+    for (ld v : w) b = std::min(b, v);
+    ld logC = 0;
+    std::vector<ld> r(w.size()), rk(w.size(), 1.0L);
+    for (size_t i = 0; i < w.size(); ++i) {
+      logC += std::log(b / w[i]);
+      r[i] = 1.0L - b / w[i];
+    }
+    // C is far below double range for long tracks (long double reaches ~1e-4900)
+    d.push_back(std::exp(logC));
+    std::vector<ld> gam(1, 0.0L);
+    ld sum_d = d[0], peak = d[0];
+    const int64_t kcap = 60000;
+    for (int64_t k = 1; k <= kcap && sum_d < 1.0L - 1e-18L; ++k) {
+      ld g = 0;
+      for (size_t i = 0; i < w.size(); ++i) {
+        rk[i] *= r[i];
+        g += rk[i];
+      }
+      gam.push_back(g / (ld)k);
+      ld dk = 0;
+      for (int64_t j = 1; j <= k; ++j) dk += (ld)j * gam[(size_t)j] * d[(size_t)(k - j)];
+      dk /= (ld)k;
+      d.push_back(dk);
+      sum_d += dk;
+      peak = std::max(peak, dk);
+      if (dk < 1e-24L * peak && dk < d[(size_t)(k - 1)]) break;   // past the mode, negligible
+    }
+  }
+
+  ld sf(ld q) const {
+    std::vector<ld> Q;
+    gamma_q_run(n, (int64_t)d.size(), q / b, Q);
+    ld s = 0;
+    for (size_t k = 0; k < d.size(); ++k) s += d[k] * Q[k];
+    return std::min<ld>(s, 1.0L);
+  }
+};
+
+// P(chi^2_{2N}(Lambda) > x): Poisson(Lambda / 2) mixture of Q(N + j, x / 2).
+ld noncentral_sf(int64_t n, ld lambda, ld x) {
+  const ld mu = lambda / 2;
+  const int64_t jpk = (int64_t)std::floor(mu);
+  const int64_t span = (int64_t)(12.0L * std::sqrt(mu + 1.0L)) + 30;
+  const int64_t j0 = std::max<int64_t>(0, jpk - span), j1 = jpk + span;
+  std::vector<ld> Q;
+  gamma_q_run(n + j0, j1 - j0 + 1, x / 2, Q);
+  ld s = 0;
+  for (int64_t j = j0; j <= j1; ++j) {
+    const ld lp = mu > 0 ? -mu + (ld)j * std::log(mu) - std::lgamma((ld)j + 1.0L) : (j == 0 ? 0.0L : -INFINITY);
+    s += std::exp(lp) * Q[(size_t)(j - j0)];
+  }
+  return std::min<ld>(s, 1.0L);
+}
+
+// The q > lo with sf(q) = p for a decreasing sf, by bisection on log sf.
+template <typename F>
+ld invert_sf(F sf, ld lo, ld hi, ld p) {
+  while (sf(hi) > p) hi = lo + 2 * (hi - lo);
+  const ld lp = std::log(p);
+  for (int it = 0; it < 200; ++it) {
+    const ld mid = 0.5L * (lo + hi);
+    const ld v = sf(mid);
+    if ((v > 0 ? std::log(v) : -INFINITY) > lp) lo = mid; else hi = mid;
+    if (hi - lo <= 1e-15L * hi) break;
+  }
+  return 0.5L * (lo + hi);
+}
+
+}  // namespace
+
+extern "C" {
+
+srs_status srs_nsigma_threshold(const double* w, int32_t n_seg, double p_fa, double* n_sigma_th) {
+  if (!n_sigma_th || n_seg < 1 || n_seg > 10000000 || !(p_fa > 0 && p_fa < 1)) return SRS_ERR_ARG;
+  std::vector<ld> ww((size_t)n_seg, 1.0L);
+  if (w) {
+    ld s2 = 0;
+    for (int32_t i = 0; i < n_seg; ++i) {
+      if (!(w[i] > 0) || !std::isfinite(w[i])) return SRS_ERR_ARG;
+      ww[(size_t)i] = w[i];
+      s2 += (ld)w[i] * w[i];
+    }
+    const ld inv = 1.0L / std::sqrt(s2);
+    for (auto& v : ww) v *= inv;
+  } else {
+    for (auto& v : ww) v = 1.0L / std::sqrt((ld)n_seg);
+  }
+  ld sum_w = 0;
+  for (ld v : ww) sum_w += v;
+  const ld mean = sum_w;   // E[sum w E] = sum w; its variance is sum w^2 = 1
+  const ExpMixture mix(ww);
+  auto sf = [&](ld q) { return mix.sf(q); };
+  const ld q = invert_sf(sf, mean, mean + 10.0L, (ld)p_fa);
+  *n_sigma_th = (double)(q - sum_w);
+  return SRS_OK;
+}
+
+srs_status srs_detection_noncentrality(int32_t n_seg, double p_fa, double p_det, double* lambda) {
+  if (!lambda || n_seg < 1 || n_seg > 10000000 || !(p_fa > 0 && p_fa < 1) || !(p_det > 0 && p_det < 1))
+    return SRS_ERR_ARG;
+  const int64_t n = n_seg;
+  // threshold on S = sum P (chi^2 with 2N dof under H0)
+  auto sf0 = [&](ld s) {
+    std::vector<ld> Q;
+    gamma_q_run(n, 1, s / 2, Q);
+    return Q[0];
+  };
+  const ld s_th = invert_sf(sf0, 2.0L * n, 2.0L * n + 10.0L * std::sqrt((ld)n), (ld)p_fa);
+  if ((ld)p_det <= sf0(s_th)) {
+    *lambda = 0.0;
+    return SRS_OK;
+  }
+  // the Lambda with P(S > s_th | Lambda) = p_det: increasing in Lambda
+  ld lo = 0, hi = 1;
+  while (noncentral_sf(n, hi, s_th) < p_det) hi *= 2;
+  for (int it = 0; it < 200; ++it) {
+    const ld mid = 0.5L * (lo + hi);
+    if (noncentral_sf(n, mid, s_th) < p_det) lo = mid; else hi = mid;
+    if (hi - lo <= 1e-13L * hi) break;
+  }
+  *lambda = (double)(0.5L * (lo + hi));
+  return SRS_OK;
+}
+
+}  // extern "C"

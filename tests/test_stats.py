@@ -1,0 +1,87 @@
+"""Detection statistics: the oracle (oracle.stats) pinned by the printed
+detection non-centrality, a closed form and Monte Carlo; then the library's
+host functions (srs_nsigma_threshold, srs_detection_noncentrality) against
+the oracle.  CPU only: these functions need no GPU."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import stats
+from paper_2609_12476_gb300 import SrsError, detection_noncentrality, nsigma_threshold
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))
+
+
+def test_oracle_detection_noncentrality_matches_paper():
+    g = GOLD["detection_noncentrality"]
+    lam = stats.detection_noncentrality(g["n_seg"], g["p_fa"], g["p_det"])
+    assert round(lam, 1) == g["lambda_printed"]
+
+
+def test_oracle_one_segment_threshold_closed_form():
+    # one segment: n_sigma = E - 1 with E ~ Exp(1), so th = -ln(p_fa) - 1
+    for p in (1e-2, 1e-6, 1e-9):
+        assert stats.nsigma_threshold_equal(1, p) == pytest.approx(-np.log(p) - 1.0, rel=1e-10)
+        assert stats.nsigma_threshold_weighted([1.0], p) == pytest.approx(-np.log(p) - 1.0, rel=1e-9)
+
+
+def test_oracle_weighted_law_monte_carlo():
+    """The hypoexponential survival function against 4e6 seeded draws."""
+    w = np.array([0.3, 0.5, 0.9, 1.4, 2.0])
+    e = np.random.default_rng(17).exponential(1.0, size=(4_000_000, w.size))
+    q_all = e @ w
+    for q in (4.0, 7.0, 10.0):
+        emp = np.mean(q_all > q)
+        sf = stats.weighted_exp_sf(w, q)
+        assert abs(emp - sf) <= 4 * np.sqrt(sf * (1 - sf) / q_all.size) + 1e-7, (q, emp, sf)
+
+
+def test_oracle_weighted_threshold_tends_to_equal():
+    n = 12
+    w = 1.0 + 1e-3 * np.arange(n)
+    assert stats.nsigma_threshold_weighted(w, 1e-6) == pytest.approx(stats.nsigma_threshold_equal(n, 1e-6), rel=2e-3)
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 35, 240, 2880])
+@pytest.mark.parametrize("p_fa", [1e-2, 1e-6, 1e-9])
+def test_library_equal_weight_threshold(n, p_fa):
+    assert nsigma_threshold(n, p_fa) == pytest.approx(stats.nsigma_threshold_equal(n, p_fa), rel=1e-9, abs=1e-9)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_library_weighted_threshold(seed):
+    r = np.random.default_rng(seed)
+    n = int(r.integers(2, 16))
+    w = np.sort(r.uniform(0.4, 2.5, n))
+    w[1:] += 1e-3 * np.arange(1, n)          # distinct, for the oracle's closed form
+    for p in (1e-3, 1e-6):
+        assert nsigma_threshold(n, p, w) == pytest.approx(stats.nsigma_threshold_weighted(w, p), rel=1e-8)
+
+
+def test_library_weighted_threshold_scale_free_and_long_tracks():
+    # weights are normalised: any common scale gives the same threshold
+    w = np.linspace(1.0, 1.72, 300)
+    assert nsigma_threshold(300, 1e-6, w) == pytest.approx(nsigma_threshold(300, 1e-6, 7.5 * w), rel=1e-12)
+    # amplitude-like weights over a long track stay close to (and above) the equal-weight threshold
+    w = np.linspace(1.0, 1.72, 2880)
+    a, b = nsigma_threshold(2880, 1e-6, w), nsigma_threshold(2880, 1e-6)
+    assert b <= a <= 1.05 * b
+
+
+@pytest.mark.parametrize("n", [1, 3, 35, 100])
+def test_library_detection_noncentrality(n):
+    assert detection_noncentrality(n, 1e-6, 0.95) == pytest.approx(stats.detection_noncentrality(n, 1e-6, 0.95),
+                                                                   rel=1e-9)
+
+
+def test_library_statistics_reject_bad_arguments():
+    with pytest.raises(SrsError):
+        nsigma_threshold(0, 1e-6)
+    with pytest.raises(SrsError):
+        nsigma_threshold(3, 1.5)
+    with pytest.raises(SrsError):
+        nsigma_threshold(3, 1e-6, [1.0, -1.0, 2.0])
+    with pytest.raises(SrsError):
+        detection_noncentrality(10, 1e-6, 1.0)
