@@ -366,7 +366,7 @@ srs_status srs_slide_search(srs_ctx* ctx, const void* strain, int64_t n_samples,
 /* ------------------------------------------------------------------------
  * Learned proposal.  A small network looks at a coarse-template n_sigma map
  * and proposes which fine (template, bin) cells to compute; the full
- * fine-template search stays the fallback and the judge.
+ * fine-template search stays the fallback and the yardstick.
  *   input   a 9 x 33 patch of the coarse map around a cell (templates m-4..m+4,
  *           bins b-16..b+16, zero outside the map), each value through asinh
  *   network 297 -> 64 (ReLU) -> 1 logit; weights used in FP16, sums in FP32;
