@@ -14,6 +14,9 @@ Passages followed:
   track        -> Sec. III.C (the track of theta = {Mc, t0} with f0 at the
                   band's lower edge: frequency f_j and resampling template
                   beta_k in each segment), Sec. III.A Eq. (f), Sec. II Eq. (beta)
+  whiten       -> Sec. III.C Eqs. (normalized_power), (semicoherent_statistic)
+                  with the effective PSD and the background moments mu_i,
+                  sigma_i estimated from the data
   stack_slide  -> Sec. III.C Eqs. (weights), (semicoherent_statistic) with
                   mu = sigma = 2: equal weights w = 1/sqrt(N_seg(theta)), or
                   w proportional to A_i^2 / S_eff (the segment average of the
@@ -125,12 +128,33 @@ def n_sigma_weighted(P_track, a, s_eff_track):
     return float(np.sum(a * (P / S - 2.0) / 2.0) / np.sqrt(np.sum(a * a)))
 
 
+def whiten(cube, s_eff=None):
+    """Normalise a power cube P[k][j][i] for coloured, non-stationary noise
+    (Sec. III.C Eqs. (normalized_power), (semicoherent_statistic)):
+      S[k][j] = mean_i P[k][j][i] / 2 (white unit-variance noise gives
+                E[P] = 2), or the given table;
+      Pt = P / S;  mu_i, sigma_i = mean and (population) standard deviation
+                of Pt over all (k, j) of segment i;
+      out = 2 + 2 (Pt - mu_i) / sigma_i,
+    so that (out - 2) / 2 = (Pt - mu_i) / sigma_i, the term of Eq.
+    (semicoherent_statistic) with empirical moments.  Returns (out, S, mu,
+    sigma)."""
+    P = np.asarray(cube, dtype=np.float64)
+    S = P.mean(axis=2) / 2.0 if s_eff is None else np.asarray(s_eff, dtype=np.float64)
+    Pt = P / S[:, :, None]
+    mu = Pt.mean(axis=(0, 1))
+    sigma = Pt.std(axis=(0, 1))
+    return 2.0 + 2.0 * (Pt - mu) / sigma, S, mu, sigma
+
+
 def stack_slide(cube, rows_mc, rows_c, n_t0, n_total, bank, f0, t_coh, f_lo, n_b, with_abs=False,
-                weighting=0, s_eff=None):
+                weighting=0, s_eff=None, s_eff_in_weights_only=False):
     """n_sigma[r][n] for theta = {rows_mc[r], t0 = (n + rows_c[r]) T} over a
     cube P[k][j][i] that holds every segment i < n_total.  weighting 0: equal
     weights; 1: amplitude weights (amplitude_sq).  s_eff: [n_beta][n_bins]
-    effective PSD relative to white noise, or None (white).  Also returns the
+    effective PSD relative to white noise, or None (white); with
+    s_eff_in_weights_only the cube is already normalised by it (whiten) and
+    s_eff enters the weights alone.  Also returns the
     number of track segments N_seg[r][n] inside the data, and with
     with_abs=True a bound helper: the sum over the track of
     (|a P / S| + |2 a|) / 2 / sqrt(sum a^2)."""
@@ -149,14 +173,18 @@ def stack_slide(cube, rows_mc, rows_c, n_t0, n_total, bank, f0, t_coh, f_lo, n_b
             i = first + np.arange(L)
             P = cube[k[:L], j[:L], i]
             if weighting or s_eff is not None:
-                out[r, n] = n_sigma_weighted(P, amp[:L], S_all[:L])
+                if s_eff_in_weights_only:
+                    a = amp[:L] / S_all[:L]
+                    out[r, n] = n_sigma_weighted(P, a, np.ones(L))
+                else:
+                    out[r, n] = n_sigma_weighted(P, amp[:L], S_all[:L])
             else:
                 out[r, n] = n_sigma_track(P)
             nseg[r, n] = L
             if L:
                 a = amp[:L] / S_all[:L]
-                absum[r, n] = float(np.sum(np.abs(a * np.asarray(P, dtype=np.float64) / S_all[:L]) + 2 * np.abs(a))
-                                    / 2.0 / np.sqrt(np.sum(a * a)))
+                Pn = np.asarray(P, dtype=np.float64) / (1.0 if s_eff_in_weights_only else S_all[:L])
+                absum[r, n] = float(np.sum(np.abs(a * Pn) + 2 * np.abs(a)) / 2.0 / np.sqrt(np.sum(a * a)))
     if with_abs:
         return out, nseg, absum
     return out, nseg

@@ -245,3 +245,32 @@ def test_weighted_stack_slide_brute_force():
                 den += a * a
             want = num / np.sqrt(den) if den > 0 else 0.0
             assert ns[r, n] == pytest.approx(want, rel=1e-12, abs=1e-12)
+
+
+def test_whitening_moments_and_psd_estimate():
+    """After whitening, every segment's values have mean 2 and standard
+    deviation 2 exactly (the identity the normalisation builds in); the PSD
+    estimate recovers a coloured-noise pattern; a white chi-square cube with
+    one louder segment comes back with that segment's scale divided out."""
+    r = np.random.default_rng(3)
+    K, B, N = 6, 50, 400
+    S_true = r.uniform(0.5, 4.0, size=(K, B))
+    cube = srs_synth.random_cube(K, B, N, seed=4).astype(np.float64) * S_true[:, :, None]
+    cube[:, :, 7] *= 3.0                        # a non-stationary segment
+    out, S, mu, sigma = slide.whiten(cube)
+    assert np.allclose(out.mean(axis=(0, 1)), 2.0, atol=1e-12)
+    assert np.allclose(out.std(axis=(0, 1)), 2.0, rtol=1e-12)
+    assert np.median(np.abs(S / S_true - 1.0)) < 0.05
+    # segment 7's mean is 3 x 2, up to 4 standard errors of a mean of K B exponentials
+    assert abs(mu[7] - 3.0 * np.median(mu)) < 4 * 6.0 / np.sqrt(K * B)
+    # a given table is used as is
+    out2, S2, _, _ = slide.whiten(cube, s_eff=S_true)
+    assert np.array_equal(S2, S_true)
+    # with S in the weights only, a white cube and unit weights reduce to the plain statistic
+    bank = _bank()
+    rows_mc, rows_c = np.array([8e-2]), np.array([0.0])
+    cube_w = srs_synth.random_cube(len(bank), N_B, 40, seed=5).astype(np.float64)
+    u, _ = slide.stack_slide(cube_w, rows_mc, rows_c, 30, 40, bank, F_LO, T, F_LO, N_B)
+    v, _ = slide.stack_slide(cube_w, rows_mc, rows_c, 30, 40, bank, F_LO, T, F_LO, N_B,
+                             s_eff=np.ones((len(bank), N_B)), s_eff_in_weights_only=True)
+    assert np.allclose(u, v, rtol=1e-12, atol=1e-12)
