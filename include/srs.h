@@ -313,7 +313,14 @@ typedef struct {
  *           relative to white unit-variance noise (host [n_beta][n_bins],
  *           every entry > 0), or 1 when s_eff is NULL.
  * The powers are normalised by the same S (Eq. normalized_power):
- * n_sigma = sum_s a_s (P_s / S_s - 2) / 2 / sqrt(sum_s a_s^2). */
+ * n_sigma = sum_s a_s (P_s / S_s - 2) / 2 / sqrt(sum_s a_s^2).
+ * whiten = 1: the powers are whitened (srs_cube_whiten: divided by the
+ * effective PSD, then centred and scaled per segment by the empirical
+ * background mean and deviation mu_i, sigma_i), so S enters the weights
+ * alone.  srs_slide_search whitens every cube chunk itself, with s_eff if
+ * given, else with the PSD it estimates from the first chunk (which then
+ * also enters the amplitude weights); srs_stack_slide takes the cube as
+ * already whitened. */
 enum { SRS_WEIGHT_EQUAL = 0, SRS_WEIGHT_AMPLITUDE = 1 };
 typedef struct {
   double f0;
@@ -323,6 +330,7 @@ typedef struct {
   int32_t n_t0;
   int32_t weighting;
   const float* s_eff;
+  int32_t whiten;
 } srs_slide_grid;
 
 /* Flags of srs_stack_slide. */
@@ -337,6 +345,20 @@ enum { SRS_SLIDE_FIRST = 1, SRS_SLIDE_LAST = 2 };
 srs_status srs_power_cube(srs_ctx* ctx, const void* strain, int64_t n_samples, int32_t dtype,
                           const srs_bank* bank, int32_t seg_begin, int32_t seg_end,
                           const srs_params* params, float* cube, srs_report* report);
+
+/* Whitening of a power cube in place (Sec. III.C Eqs. normalized_power,
+ * semicoherent_statistic, with the effective PSD and the background moments
+ * taken from the data).  Device pointers:
+ *   cube   [n_beta][n_bins][n_seg] float (srs_power_cube's layout);
+ *   s_eff  [n_beta][n_bins] float: estimate = 1 writes
+ *          S = mean over segments of P / 2 into it; estimate = 0 reads it;
+ *   mu, sigma [n_seg] float or NULL: each segment's mean and (population)
+ *          standard deviation of P / S over all (beta, bin).
+ * Afterwards P = 2 + 2 (P / S - mu_i) / sigma_i, so the stack-slide's
+ * (P - 2) / 2 is (P / S - mu_i) / sigma_i.  Queued on the context's stream
+ * and waited for. */
+srs_status srs_cube_whiten(srs_ctx* ctx, float* cube, int32_t n_beta, int32_t n_bins, int32_t n_seg,
+                           float* s_eff, int32_t estimate, float* mu, float* sigma);
 
 /* Stage two over one cube chunk holding segments [seg_begin, seg_end) of data
  * with n_seg_total segments, in srs_power_cube's layout (host or device per

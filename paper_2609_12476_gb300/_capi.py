@@ -25,7 +25,7 @@ EXPORTS = ("srs_create", "srs_destroy", "srs_last_error", "srs_plan", "srs_searc
            "srs_segment_spectra", "srs_segment_spectra_cufft", "srs_time_map", "srs_segment_spectra_static", "srs_make_strain",
            "srs_patches", "srs_mlp_forward", "srs_mlp_grad", "srs_mlp_train", "srs_score_map", "srs_refine",
            "srs_search_proposed", "srs_power_cube", "srs_stack_slide", "srs_slide_search", "srs_selftest_wait",
-           "srs_nsigma_threshold", "srs_detection_noncentrality")
+           "srs_nsigma_threshold", "srs_detection_noncentrality", "srs_cube_whiten")
 SRS_SLIDE_FIRST, SRS_SLIDE_LAST = 1, 2
 SRS_WEIGHT_EQUAL, SRS_WEIGHT_AMPLITUDE = 0, 1
 MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 297, 64, 19137
@@ -72,7 +72,7 @@ class _Bank(ctypes.Structure):
 class _SlideGrid(ctypes.Structure):
     _fields_ = [("f0", ctypes.c_double), ("mc", ctypes.c_void_p), ("c", ctypes.c_void_p),
                 ("n_rows", ctypes.c_int32), ("n_t0", ctypes.c_int32), ("weighting", ctypes.c_int32),
-                ("s_eff", ctypes.c_void_p)]
+                ("s_eff", ctypes.c_void_p), ("whiten", ctypes.c_int32)]
 
 
 class _Injection(ctypes.Structure):
@@ -155,6 +155,8 @@ def lib():
             fn.restype = i32
             fn.argtypes = [vp, vp, i64, i32, vp, i32, i32, i32, ctypes.POINTER(_Params), vp,
                            ctypes.POINTER(_Report)]
+        L.srs_cube_whiten.restype = i32
+        L.srs_cube_whiten.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp, vp]
         L.srs_nsigma_threshold.restype = i32
         L.srs_nsigma_threshold.argtypes = [vp, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
         L.srs_detection_noncentrality.restype = i32
@@ -402,14 +404,14 @@ class Context:
         return _Bank(float(bank[0]), float(bank[1]), int(bank[2]))
 
     @staticmethod
-    def _grid(rows_mc, rows_c, n_t0, f0, weighting=0, s_eff=None):
+    def _grid(rows_mc, rows_c, n_t0, f0, weighting=0, s_eff=None, whiten=False):
         mc = np.ascontiguousarray(rows_mc, dtype=np.float64)
         c = np.ascontiguousarray(rows_c, dtype=np.float64)
         if mc.shape != c.shape:
             raise ValueError("rows_mc and rows_c must have the same length")
         se = None if s_eff is None else np.ascontiguousarray(s_eff, dtype=np.float32)
         g = _SlideGrid(float(f0), mc.ctypes.data, c.ctypes.data, mc.size, int(n_t0), int(weighting),
-                       se.ctypes.data if se is not None else None)
+                       se.ctypes.data if se is not None else None, 1 if whiten else 0)
         return g, (mc, c, se)   # keep the arrays alive with the struct
 
     def power_cube(self, strain, bank, seg_begin, seg_end, params):
@@ -440,13 +442,13 @@ class Context:
         return out, _report_dict(rep)
 
     def stack_slide(self, cube, seg_begin, n_seg_total, bank, rows_mc, rows_c, n_t0, params, f0=None,
-                    first=True, last=True, want_map=True, weighting=0, s_eff=None):
+                    first=True, last=True, want_map=True, weighting=0, s_eff=None, whiten=False):
         """srs_stack_slide over a cube chunk [n_beta, n_bins, chunk segments]
         holding segments [seg_begin, seg_begin + chunk).  With last=True returns
         (candidates, n_sigma map [rows, n_t0] or None, report); otherwise
         (None, None, report).  numpy cube: host I/O; torch CUDA cube: device I/O."""
         f0 = params.f_lo if f0 is None else f0
-        g, keep = self._grid(rows_mc, rows_c, n_t0, f0, weighting, s_eff)
+        g, keep = self._grid(rows_mc, rows_c, n_t0, f0, weighting, s_eff, whiten)
         b = self._bank(bank)
         p = params.c()
         rep = _Report()
@@ -483,13 +485,30 @@ class Context:
         self._check(st)
         return (c[:n_cands.value] if c is not None else None), m, _report_dict(rep)
 
+    def cube_whiten(self, cube, s_eff=None):
+        """srs_cube_whiten on a torch CUDA cube [n_beta, n_bins, n_seg] in place:
+        returns (s_eff [n_beta, n_bins], mu [n_seg], sigma [n_seg]) as tensors;
+        the PSD is estimated from the cube unless s_eff is given."""
+        import torch
+        if not (_is_torch_cuda(cube) and cube.dtype == torch.float32 and cube.is_contiguous() and cube.dim() == 3):
+            raise ValueError("cube must be a contiguous float32 CUDA tensor [n_beta, n_bins, n_seg]")
+        K, B, N = (int(v) for v in cube.shape)
+        est = s_eff is None
+        S = torch.empty((K, B), dtype=torch.float32, device=cube.device) if est else \
+            torch.as_tensor(s_eff, dtype=torch.float32, device=cube.device).contiguous()
+        mu = torch.empty(N, dtype=torch.float32, device=cube.device)
+        sg = torch.empty(N, dtype=torch.float32, device=cube.device)
+        self._check(self._lib.srs_cube_whiten(self._h, cube.data_ptr(), K, B, N, S.data_ptr(), 1 if est else 0,
+                                              mu.data_ptr(), sg.data_ptr()))
+        return S, mu, sg
+
     def slide_search(self, strain, bank, rows_mc, rows_c, n_t0, params, f0=None, cube_budget_bytes=0,
-                     want_map=True, out=None, weighting=0, s_eff=None):
+                     want_map=True, out=None, weighting=0, s_eff=None, whiten=False):
         """srs_slide_search: power cube + stack-slide over the whole strain.
         Host numpy strain returns (candidates, map or None, report); a torch
         CUDA strain returns ({"map", "cands"} tensors, report)."""
         f0 = params.f_lo if f0 is None else f0
-        g, keep = self._grid(rows_mc, rows_c, n_t0, f0, weighting, s_eff)
+        g, keep = self._grid(rows_mc, rows_c, n_t0, f0, weighting, s_eff, whiten)
         b = self._bank(bank)
         dt = _dtype_code(strain)
         p = params.c()

@@ -88,7 +88,8 @@ struct srs_ctx {
       strain32, errflag, map, S, F, psi, th, im, ii;
   // two-stage search: power cube chunk, stack-slide tracks and running sums
   srs::DevBuf strain_stage0, strain_stage1;
-  srs::DevBuf cube, slide_cell, slide_coef, slide_w2, slide_seff, slide_len, slide_beta0, slide_frac, slide_Z, slide_map;
+  srs::DevBuf cube, slide_cell, slide_coef, slide_w2, slide_seff, slide_len, slide_beta0, slide_frac, slide_Z, slide_map,
+      white_s, white_sums, white_musig;
   bool have_slide = false;
   bool slide_open = false;                // running sums started (SRS_SLIDE_FIRST) and not yet finished
   std::vector<unsigned char> slide_key;   // what slide_cell / slide_len were computed for
@@ -105,7 +106,7 @@ struct srs_ctx {
             &lossv, &grad, &wts, &adam_m, &adam_v, &w1h, &w2h, &idx, &patches, &cells_m, &cells_b, &sp_items,
             &sp_bins, &sp_partial, &sp_cells, &sp_out, &sp_betas, &cmap, &ccands, &inj, &cube, &slide_cell,
             &slide_coef, &slide_w2, &slide_seff, &slide_len, &slide_beta0, &slide_frac, &slide_Z, &slide_map,
-            &strain_stage0, &strain_stage1};
+            &strain_stage0, &strain_stage1, &white_s, &white_sums, &white_musig};
   }
 };
 

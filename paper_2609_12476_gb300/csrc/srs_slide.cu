@@ -10,6 +10,7 @@
 // the same cube row at every step, a coalesced 128-byte request.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "srs_device.cuh"
@@ -61,7 +62,9 @@ __global__ void k_slide_tracks(const double* __restrict__ beta0, const double* _
         }
         const double S = t.s_eff ? (double)t.s_eff[out] : 1.0;
         a /= S;
-        cf = make_float2((float)(0.5 * a / S), (float)a);
+        // a whitened cube is divided by S already: S enters the weight alone
+        const double Sp = t.s_in_weights_only ? 1.0 : S;
+        cf = make_float2((float)(0.5 * a / Sp), (float)a);
       }
     }
     cell[idx] = out;
@@ -186,7 +189,89 @@ k_stack_slide(const float* __restrict__ cube, const int* __restrict__ cell, cons
   keys[o] = make_key(v, (uint32_t)o);
 }
 
+// Whitening (Sec. III.C: powers normalised by the effective PSD, background
+// moments mu_i, sigma_i taken from the data).
+// S[r] = mean over the row's n_seg segments of P / 2: one warp per row.
+__global__ void k_cube_psd(const float* __restrict__ cube, long long rows, int ld, int n_seg, float* __restrict__ S) {
+  const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  const float* row = cube + r * ld;
+  float s = 0.f;
+  for (int i = lane; i < n_seg; i += 32) s += row[i];
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+  if (lane == 0) S[r] = fmaxf(s / (2.0f * (float)n_seg), 1e-30f);
+}
+
+// Per segment i: sum and sum of squares over rows of P / S.  Block = 256
+// consecutive segments x a tile of rows (coalesced along i); FP32 within the
+// tile, FP64 atomics across tiles.
+__global__ void k_cube_moments(const float* __restrict__ cube, long long rows, int ld, int n_seg,
+                               const float* __restrict__ S, int rows_per_block, double* __restrict__ sums) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const long long r0 = (long long)blockIdx.y * rows_per_block;
+  const long long r1 = min(rows, r0 + rows_per_block);
+  if (i >= n_seg) return;
+  float s = 0.f, q = 0.f;
+  for (long long r = r0; r < r1; ++r) {
+    const float v = cube[r * ld + i] / S[r];
+    s += v;
+    q = fmaf(v, v, q);
+  }
+  atomicAdd(&sums[i], (double)s);
+  atomicAdd(&sums[n_seg + i], (double)q);
+}
+
+// mu_i and 1 / sigma_i (population moments over all rows).
+__global__ void k_cube_moments_finish(const double* __restrict__ sums, long long rows, int n_seg,
+                                      float2* __restrict__ musig, float* __restrict__ mu, float* __restrict__ sigma) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_seg) return;
+  const double m = sums[i] / (double)rows;
+  const double var = fmax(sums[n_seg + i] / (double)rows - m * m, 1e-30);
+  const double sd = sqrt(var);
+  musig[i] = make_float2((float)m, (float)(1.0 / sd));
+  if (mu) mu[i] = (float)m;
+  if (sigma) sigma[i] = (float)sd;
+}
+
+// P <- 2 + 2 (P / S - mu_i) / sigma_i, in place.
+__global__ void k_cube_apply(float* __restrict__ cube, long long rows, int ld, int n_seg,
+                             const float* __restrict__ S, const float2* __restrict__ musig) {
+  const long long total = rows * (long long)n_seg;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long r = idx / n_seg;
+    const int i = (int)(idx - r * n_seg);
+    float* p = cube + r * ld + i;
+    const float2 ms = musig[i];
+    *p = fmaf(2.0f * ms.y, *p / S[r] - ms.x, 2.0f);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_cube_whiten(float* cube, long long rows, int ld, int n_seg, float* S, bool estimate_s,
+                               double* sums, float2* musig, float* mu, float* sigma, int n_sm, cudaStream_t st) {
+  if (rows <= 0 || n_seg <= 0) return cudaSuccess;
+  cudaError_t e;
+  if (estimate_s) {
+    k_cube_psd<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(cube, rows, ld, n_seg, S);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if ((e = cudaMemsetAsync(sums, 0, (size_t)2 * n_seg * sizeof(double), st)) != cudaSuccess) return e;
+  // tiles of 64 rows, more where the grid's y extent (65535) would not hold them
+  const int per = (int)std::max<long long>(64, (rows + 65534) / 65535);
+  const dim3 g((unsigned)((n_seg + 255) / 256), (unsigned)((rows + per - 1) / per));
+  k_cube_moments<<<g, 256, 0, st>>>(cube, rows, ld, n_seg, S, per, sums);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_cube_moments_finish<<<(unsigned)((n_seg + 255) / 256), 256, 0, st>>>(sums, rows, n_seg, musig, mu, sigma);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  long long blocks = (rows * (long long)n_seg + 255) / 256;
+  if (blocks > (long long)n_sm * 16) blocks = (long long)n_sm * 16;
+  k_cube_apply<<<(unsigned)blocks, 256, 0, st>>>(cube, rows, ld, n_seg, S, musig);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_slide_tracks(const double* beta0, const double* frac, int n_rows, const TrackArgs& t,
                                 int* cell, float2* coef, int* len, double* w2, int n_sm, cudaStream_t st) {

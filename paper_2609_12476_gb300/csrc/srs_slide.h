@@ -19,6 +19,7 @@ struct TrackArgs {
   int n_beta, n_bins, n_total;
   int weighting;      // SRS_WEIGHT_EQUAL or SRS_WEIGHT_AMPLITUDE
   const float* s_eff; // [n_beta][n_bins] effective PSD relative to white noise, or NULL
+  int s_in_weights_only;  // 1: the cube is whitened already; s_eff enters the weights alone
 };
 
 // One stack-slide pass over the cube chunk that holds segments
@@ -46,5 +47,13 @@ cudaError_t launch_slide_tracks(const double* beta0, const double* frac, int n_r
 cudaError_t launch_stack_slide(const float* cube, const int* cell, const float2* coef, const int* len,
                                const double* w2, const double* frac, const SlideArgs& a, float* Z, float* map,
                                unsigned long long* keys, cudaStream_t st);
+
+// Whitening of a cube [rows = n_beta n_bins][ld] over its first n_seg
+// segments, in place (Sec. III.C): S[r] = mean_i P / 2 (estimate_s), then
+// per segment mu_i, sigma_i of P / S over all rows, then
+// P <- 2 + 2 (P / S - mu_i) / sigma_i.  mu, sigma (device, n_seg floats) may
+// be NULL.  sums is device scratch of 2 n_seg doubles, musig of n_seg float2.
+cudaError_t launch_cube_whiten(float* cube, long long rows, int ld, int n_seg, float* S, bool estimate_s,
+                               double* sums, float2* musig, float* mu, float* sigma, int n_sm, cudaStream_t st);
 
 }  // namespace srs

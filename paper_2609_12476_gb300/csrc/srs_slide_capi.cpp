@@ -44,6 +44,7 @@ srs_status check_grid(srs_ctx* ctx, const srs_slide_grid* g, const srs_params* p
   }
   if (g->weighting != SRS_WEIGHT_EQUAL && g->weighting != SRS_WEIGHT_AMPLITUDE)
     return set_err(ctx, SRS_ERR_ARG, "weighting must be SRS_WEIGHT_EQUAL or SRS_WEIGHT_AMPLITUDE");
+  if (g->whiten != 0 && g->whiten != 1) return set_err(ctx, SRS_ERR_ARG, "whiten must be 0 or 1");
   return SRS_OK;
 }
 
@@ -59,7 +60,7 @@ srs_status check_s_eff(srs_ctx* ctx, const srs_slide_grid* g, const srs_bank* ba
 // Tracks of every row (cell and length tables), recomputed only when the
 // bank, grid, band or data length change.  *replanned says whether they did.
 srs_status plan_tracks(srs_ctx* ctx, const srs_bank* bank, const srs_slide_grid* g, const srs_params* p,
-                       int32_t n_bins, int32_t n_total, bool* replanned) {
+                       int32_t n_bins, int32_t n_total, bool* replanned, const float* s_eff_host) {
   std::vector<unsigned char> key;
   auto put = [&](const void* d, size_t n) {
     const unsigned char* c = static_cast<const unsigned char*>(d);
@@ -78,9 +79,10 @@ srs_status plan_tracks(srs_ctx* ctx, const srs_bank* bank, const srs_slide_grid*
   put(&n_bins, sizeof n_bins);
   put(&n_total, sizeof n_total);
   put(&g->weighting, sizeof g->weighting);
-  const size_t n_seff = g->s_eff ? (size_t)bank->n_beta * n_bins : 0;
+  put(&g->whiten, sizeof g->whiten);
+  const size_t n_seff = s_eff_host ? (size_t)bank->n_beta * n_bins : 0;
   put(&n_seff, sizeof n_seff);
-  if (n_seff) put(g->s_eff, n_seff * sizeof(float));
+  if (n_seff) put(s_eff_host, n_seff * sizeof(float));
   *replanned = false;
   if (ctx->have_slide && key == ctx->slide_key) return SRS_OK;
   ctx->have_slide = false;
@@ -96,7 +98,7 @@ srs_status plan_tracks(srs_ctx* ctx, const srs_bank* bank, const srs_slide_grid*
   SRS_CK(ctx->slide_len.ensure((size_t)g->n_rows * 4), "alloc tracks");
   if (n_seff) {
     SRS_CK(ctx->slide_seff.ensure(n_seff * 4), "alloc s_eff");
-    SRS_CK(cudaMemcpyAsync(ctx->slide_seff.p, g->s_eff, n_seff * 4, cudaMemcpyHostToDevice, ctx->stream), "copy s_eff");
+    SRS_CK(cudaMemcpyAsync(ctx->slide_seff.p, s_eff_host, n_seff * 4, cudaMemcpyHostToDevice, ctx->stream), "copy s_eff");
   }
   SRS_CK(cudaMemcpyAsync(ctx->slide_beta0.p, b0.data(), b0.size() * 8, cudaMemcpyHostToDevice, ctx->stream), "copy tracks");
   SRS_CK(cudaMemcpyAsync(ctx->slide_frac.p, g->c, b0.size() * 8, cudaMemcpyHostToDevice, ctx->stream), "copy tracks");
@@ -111,6 +113,7 @@ srs_status plan_tracks(srs_ctx* ctx, const srs_bank* bank, const srs_slide_grid*
   t.n_total = n_total;
   t.weighting = g->weighting;
   t.s_eff = n_seff ? ctx->slide_seff.as<float>() : nullptr;
+  t.s_in_weights_only = g->whiten ? 1 : 0;
   SRS_CK(launch_slide_tracks(ctx->slide_beta0.as<double>(), ctx->slide_frac.as<double>(), g->n_rows, t,
                              ctx->slide_cell.as<int>(), ctx->slide_coef.as<float2>(), ctx->slide_len.as<int>(),
                              ctx->slide_w2.as<double>(), ctx->n_sm, ctx->stream),
@@ -192,7 +195,8 @@ srs_status prepare_out(srs_ctx* ctx, const srs_slide_grid* g, const srs_params* 
 // One stack-slide pass over a device cube chunk (with `last`, it also writes
 // the map and the top-k keys).
 srs_status slide_pass(srs_ctx* ctx, const float* dcube, int32_t seg_begin, int32_t seg_end, int32_t n_total,
-                      const srs_slide_grid* g, bool first, bool last, const SlideOut& o, int* launches) {
+                      const srs_slide_grid* g, bool first, bool last, const SlideOut& o, int* launches,
+                      bool s_used) {
   SRS_CK(ctx->slide_Z.ensure((size_t)g->n_rows * g->n_t0 * 4), "alloc running sums");
   SlideArgs a;
   a.n_rows = g->n_rows;
@@ -203,7 +207,7 @@ srs_status slide_pass(srs_ctx* ctx, const float* dcube, int32_t seg_begin, int32
   a.ld = seg_end - seg_begin;
   a.first = first ? 1 : 0;
   a.last = last ? 1 : 0;
-  a.weighted = (g->weighting != SRS_WEIGHT_EQUAL || g->s_eff) ? 1 : 0;
+  a.weighted = (g->weighting != SRS_WEIGHT_EQUAL || s_used) ? 1 : 0;
   SRS_CK(launch_stack_slide(dcube, ctx->slide_cell.as<int>(), ctx->slide_coef.as<float2>(), ctx->slide_len.as<int>(),
                             ctx->slide_w2.as<double>(), ctx->slide_frac.as<double>(), a, ctx->slide_Z.as<float>(),
                             o.dmap, ctx->keys.as<unsigned long long>(), ctx->stream),
@@ -250,7 +254,7 @@ srs_status stack_slide_impl(srs_ctx* ctx, const float* cube, int32_t seg_begin, 
     return set_err(ctx, SRS_ERR_ARG, "need 0 <= seg_begin < seg_end <= n_seg_total");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_err(ctx, cudaGetLastError(), "cudaSetDevice");
   bool replanned = false;
-  s = plan_tracks(ctx, bank, g, p, n_bins, n_total, &replanned);
+  s = plan_tracks(ctx, bank, g, p, n_bins, n_total, &replanned, g->s_eff);
   if (s != SRS_OK) return s;
   if (!first && (!ctx->slide_open || replanned))
     return set_err(ctx, SRS_ERR_ARG, "a stack-slide chunk without SRS_SLIDE_FIRST must continue an open search of the same templates");
@@ -268,7 +272,7 @@ srs_status stack_slide_impl(srs_ctx* ctx, const float* cube, int32_t seg_begin, 
   }
   int launches = 0;
   SRS_CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
-  s = slide_pass(ctx, dcube, seg_begin, seg_end, n_total, g, first, last, o, &launches);
+  s = slide_pass(ctx, dcube, seg_begin, seg_end, n_total, g, first, last, o, &launches, g->s_eff != nullptr);
   if (s != SRS_OK) return s;
   SRS_CK(cudaEventRecord(ctx->ev2, ctx->stream), "event");
   if (last && (s = slide_topk(ctx, g, o, &launches)) != SRS_OK) return s;
@@ -317,12 +321,27 @@ srs_status slide_search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples
   const std::vector<double> bb = bank_betas(*bank);
 
   bool replanned = false;
-  s = plan_tracks(ctx, bank, g, p, n_bins, n_total, &replanned);
-  if (s != SRS_OK) return s;
+  const bool white = g->whiten != 0;
+  // without whitening the tracks are known now; with it, the estimated PSD
+  // (amplitude weights) is known after the first chunk
+  if (!white || g->s_eff || g->weighting == SRS_WEIGHT_EQUAL) {
+    s = plan_tracks(ctx, bank, g, p, n_bins, n_total, &replanned, g->s_eff);
+    if (s != SRS_OK) return s;
+  }
   SlideOut o;
   s = prepare_out(ctx, g, p, nsigma_map, cands, &o);
   if (s != SRS_OK) return s;
   SRS_CK(ctx->cube.ensure(per_seg * (size_t)chunk), "alloc cube");
+  const long long rows = (long long)bank->n_beta * n_bins;
+  bool s_used = g->s_eff != nullptr;
+  if (white) {
+    SRS_CK(ctx->white_s.ensure((size_t)rows * 4), "alloc whitening");
+    SRS_CK(ctx->white_sums.ensure((size_t)2 * chunk * 8), "alloc whitening");
+    SRS_CK(ctx->white_musig.ensure((size_t)chunk * 8), "alloc whitening");
+    if (g->s_eff)
+      SRS_CK(cudaMemcpyAsync(ctx->white_s.p, g->s_eff, (size_t)rows * 4, cudaMemcpyHostToDevice, ctx->stream),
+             "copy s_eff");
+  }
   // every event is created before the first launch
   for (size_t e = 0; e < (size_t)n_chunks * 3; ++e)
     if (!slide_event(ctx, e)) return set_err(ctx, SRS_ERR_CUDA, "cudaEventCreate failed");
@@ -343,8 +362,26 @@ srs_status slide_search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples
     SRS_CK(cudaEventRecord(ctx->slide_ev[3 * c], ctx->stream), "event");
     s = cube_device(ctx, s32, (int64_t)n_total * n_s, bb, a, b, p, ctx->cube.as<float>(), &launches, &pl);
     if (s != SRS_OK) return s;
+    if (white) {
+      // the PSD from the first chunk (unless given), the moments per chunk
+      const bool estimate = !g->s_eff && c == 0;
+      SRS_CK(launch_cube_whiten(ctx->cube.as<float>(), rows, b - a, b - a, ctx->white_s.as<float>(), estimate,
+                                ctx->white_sums.as<double>(), ctx->white_musig.as<float2>(), nullptr, nullptr,
+                                ctx->n_sm, ctx->stream), "k_cube_whiten");
+      launches += estimate ? 4 : 3;
+      if (c == 0 && !g->s_eff && g->weighting == SRS_WEIGHT_AMPLITUDE) {
+        // the estimated PSD enters the amplitude weights: tracks after the first chunk
+        std::vector<float> s_host((size_t)rows);
+        SRS_CK(cudaMemcpyAsync(s_host.data(), ctx->white_s.p, (size_t)rows * 4, cudaMemcpyDeviceToHost,
+                               ctx->stream), "copy PSD estimate");
+        SRS_CK(cudaStreamSynchronize(ctx->stream), "PSD estimate");
+        s = plan_tracks(ctx, bank, g, p, n_bins, n_total, &replanned, s_host.data());
+        if (s != SRS_OK) return s;
+        s_used = true;
+      }
+    }
     SRS_CK(cudaEventRecord(ctx->slide_ev[3 * c + 1], ctx->stream), "event");
-    s = slide_pass(ctx, ctx->cube.as<float>(), a, b, n_total, g, c == 0, c == n_chunks - 1, o, &launches);
+    s = slide_pass(ctx, ctx->cube.as<float>(), a, b, n_total, g, c == 0, c == n_chunks - 1, o, &launches, s_used);
     if (s != SRS_OK) return s;
     SRS_CK(cudaEventRecord(ctx->slide_ev[3 * c + 2], ctx->stream), "event");
   }
@@ -384,6 +421,25 @@ srs_status slide_search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples
 }  // namespace
 
 extern "C" {
+
+srs_status srs_cube_whiten(srs_ctx* ctx, float* cube, int32_t n_beta, int32_t n_bins, int32_t n_seg, float* s_eff,
+                           int32_t estimate, float* mu, float* sigma) {
+  if (!ctx) return SRS_ERR_ARG;
+  try {
+    if (!cube || !s_eff || n_beta < 1 || n_bins < 1 || n_seg < 1 || (estimate != 0 && estimate != 1))
+      return set_err(ctx, SRS_ERR_ARG, "need a device cube and s_eff, positive sizes, estimate 0 or 1");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_err(ctx, cudaGetLastError(), "cudaSetDevice");
+    SRS_CK(ctx->white_sums.ensure((size_t)2 * n_seg * 8), "alloc whitening");
+    SRS_CK(ctx->white_musig.ensure((size_t)n_seg * 8), "alloc whitening");
+    SRS_CK(launch_cube_whiten(cube, (long long)n_beta * n_bins, n_seg, n_seg, s_eff, estimate != 0,
+                              ctx->white_sums.as<double>(), ctx->white_musig.as<float2>(), mu, sigma, ctx->n_sm,
+                              ctx->stream), "k_cube_whiten");
+    SRS_CK(cudaStreamSynchronize(ctx->stream), "whitening");
+    return SRS_OK;
+  } catch (...) {
+    return set_err(ctx, SRS_ERR_ARG, "unexpected host error");
+  }
+}
 
 srs_status srs_stack_slide(srs_ctx* ctx, const float* cube, int32_t seg_begin, int32_t seg_end, int32_t n_seg_total,
                            const srs_bank* bank, const srs_slide_grid* grid, const srs_params* params, int32_t flags,

@@ -37,6 +37,17 @@ def white_noise(n, seed, dtype=np.float64):
     return np.random.default_rng(seed).standard_normal(n).astype(dtype, copy=False)
 
 
+def coloured_noise(n, fs, seed, asd):
+    """n samples of stationary Gaussian noise with amplitude spectral density
+    proportional to asd(f) (a callable on an array of frequencies in Hz),
+    scaled to unit variance at the asd's value 1: white N(0, 1) noise from
+    PCG64 stream `seed`, shaped in the frequency domain."""
+    x = white_noise(n, seed)
+    X = np.fft.rfft(x)
+    f = np.fft.rfftfreq(n, 1.0 / fs)
+    return np.fft.irfft(X * np.asarray(asd(f), dtype=np.float64), n)
+
+
 def chirp(n, fs, mc_msun, f0, amp, phi0=0.0, t_start=0.0):
     """A cos(phi(t)) for t = t_start + j/fs, j < n, zero before t_start.
 

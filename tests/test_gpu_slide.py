@@ -302,3 +302,68 @@ def test_power_cube_every_layout_against_oracle(monkeypatch, strain_2h, layout):
     tol = _p_bound(F, 1e-6).transpose(0, 2, 1) + 1e-6 * P + 1e-6
     err = np.abs(cube[ks] - P)
     assert np.all(err <= tol), (layout, float(np.max(err / tol)))
+
+
+def test_cube_whitening_matches_oracle(ctx):
+    """srs_cube_whiten on a seeded chi-square cube shaped by a PSD pattern,
+    with the PSD estimated and with it given, against oracle.slide.whiten;
+    then the stack-slide over the whitened cube with PSD weights."""
+    bank = slide.local_bank(*BANK)
+    n_seg = 120
+    r = np.random.default_rng(12)
+    S_true = r.uniform(0.5, 4.0, size=(69, N_B))
+    host = (srs_synth.random_cube(69, N_B, n_seg, 13).astype(np.float64) * S_true[:, :, None])
+    host[:, :, 5] *= 2.5                                       # one louder segment
+    host = host.astype(np.float32)
+    ref, S_ref, mu_ref, sg_ref = slide.whiten(host.astype(np.float64))
+    cd = torch.from_numpy(host.copy()).cuda()
+    S, mu, sg = ctx.cube_whiten(cd)
+    assert np.allclose(S.cpu().numpy(), S_ref, rtol=2e-5)
+    assert np.allclose(mu.cpu().numpy(), mu_ref, rtol=2e-5) and np.allclose(sg.cpu().numpy(), sg_ref, rtol=2e-5)
+    out = cd.cpu().numpy()
+    assert np.allclose(out, ref, rtol=1e-4, atol=2e-4), float(np.max(np.abs(out - ref)))
+    # a given PSD table is used as is
+    cd2 = torch.from_numpy(host.copy()).cuda()
+    ctx.cube_whiten(cd2, s_eff=S_true.astype(np.float32))
+    ref2, _, _, _ = slide.whiten(host.astype(np.float64), s_eff=S_true.astype(np.float32).astype(np.float64))
+    assert np.allclose(cd2.cpu().numpy(), ref2, rtol=1e-4, atol=2e-4)
+    # stack-slide over the whitened cube: amplitude weights over the estimated PSD, S in the weights alone
+    rows_mc, rows_c = srs_synth.slide_rows(srs_synth.log_templates(2e-2, 1e-1, 5), F_HI, T, bin_step=4.0)
+    S32 = S.cpu().numpy()
+    _, m, _ = ctx.stack_slide(cd, 0, n_seg, BANK, rows_mc, rows_c, 100, _params(), weighting=SRS_WEIGHT_AMPLITUDE,
+                              s_eff=S32, whiten=True)
+    want, L, absum = slide.stack_slide(out.astype(np.float64), rows_mc, rows_c, 100, n_seg, bank, F_LO, T, F_LO, N_B,
+                                       with_abs=True, weighting=1, s_eff=S32.astype(np.float64),
+                                       s_eff_in_weights_only=True)
+    assert np.all(np.abs(m.cpu().numpy() - want) <= _slide_tol(L, absum, want))
+
+
+def test_whitened_search_in_coloured_noise(ctx):
+    """Noise whose PSD falls by 2.5x across the band: unwhitened, the noise-only
+    stack-slide statistic is far from N(0, 1); whitened (PSD estimated from the
+    data, empirical per-segment moments), it is N(0, 1) to a few percent, and
+    an entering chirp is found.  The search equals power cube + whitening +
+    stack-slide called one by one."""
+    # amplitude spectral density 1.5 at 40 Hz, 0.94 at 60 Hz, flat below 30 Hz
+    asd = lambda f: 0.5 + (np.maximum(np.abs(f), 30.0) / 40.0) ** -2.0
+    n = int(7200 * FS)
+    mcs = srs_synth.log_templates(3e-2, 8e-2, 9)
+    noise = srs_synth.coloured_noise(n, FS, 21, asd)
+    rows_mc, rows_c = srs_synth.slide_rows(mcs, F_HI, T, bin_step=2.0)
+    n_total = n // N_S
+    p = _params()
+    _, m_raw, _ = ctx.slide_search(noise, BANK, rows_mc, rows_c, n_total - 60, p)
+    _, m_w, _ = ctx.slide_search(noise, BANK, rows_mc, rows_c, n_total - 60, p, whiten=True)
+    assert abs(float(np.mean(m_w))) < 0.1 and 0.85 < float(np.std(m_w)) < 1.15
+    assert abs(float(np.mean(m_raw))) > 0.3 or abs(float(np.std(m_raw)) - 1.0) > 0.3
+    inj = [{"mc": float(mcs[4]), "f0": F_LO, "amp": 0.08, "t_start": 1500.0, "phi0": 1.0}]
+    x = noise + srs_synth.strain_with_chirps(n, FS, 0, inj, noise=False)
+    c, m, rep = ctx.slide_search(x, BANK, rows_mc, rows_c, n_total - 60, p, whiten=True)
+    r, col = int(c["template_idx"][0]), int(c["bin"][0])
+    assert abs(np.log(rows_mc[r] / inj[0]["mc"])) < 0.15 and abs((col + rows_c[r]) * T - 1500.0) <= T
+    # the same through the three calls
+    xd = torch.from_numpy(x).cuda()
+    cube, _ = ctx.power_cube(xd, BANK, 0, n_total, p)
+    ctx.cube_whiten(cube)
+    _, m3, _ = ctx.stack_slide(cube, 0, n_total, BANK, rows_mc, rows_c, n_total - 60, p, whiten=True)
+    assert np.allclose(m3.cpu().numpy(), m, rtol=1e-4, atol=1e-4)

@@ -78,10 +78,14 @@ SLIDE_MUTANTS = [
      ["test_power_cube_concentrates_an_entering_chirp"]),
     ("amplitude to the power 2/3", "(f / f0) ** (4.0 / 3.0)", "(f / f0) ** (2.0 / 3.0)",
      ["test_amplitude_average_matches_closed_form"]),
-    ("weights not normalised", "/ np.sqrt(np.sum(a * a)))\n\n\ndef stack_slide", ")\n\n\ndef stack_slide",
+    ("weights not normalised", "/ np.sqrt(np.sum(a * a)))\n\n\ndef whiten", ")\n\n\ndef whiten",
      ["test_weighted_stack_slide_closed_forms"]),
     ("power not divided by the PSD", "a * (P / S - 2.0) / 2.0", "a * (P - 2.0) / 2.0",
      ["test_weighted_stack_slide_closed_forms"]),
+    ("whitening without the segment deviation", "return 2.0 + 2.0 * (Pt - mu) / sigma, S, mu, sigma",
+     "return 2.0 + 2.0 * (Pt - mu), S, mu, sigma", ["test_whitening_moments_and_psd_estimate"]),
+    ("PSD estimate without the factor 2", "S = P.mean(axis=2) / 2.0 if s_eff is None", "S = P.mean(axis=2) if s_eff is None",
+     ["test_whitening_moments_and_psd_estimate"]),
 ]
 
 
@@ -96,7 +100,7 @@ def test_slide_pins_catch_planted_mistake(monkeypatch, name, orig, bad, catchers
     mod.__package__ = "oracle"
     exec(compile(src.replace(orig, bad), "slide_mutant.py", "exec"), mod.__dict__)
     for fn in ("local_bank", "power_cube", "first_segment", "track", "n_sigma_track", "stack_slide", "amplitude_sq",
-               "n_sigma_weighted"):
+               "n_sigma_weighted", "whiten"):
         monkeypatch.setattr(slide, fn, getattr(mod, fn))
     for pin in catchers:
         fn = getattr(spins, pin)
