@@ -237,12 +237,15 @@ srs_status srs_segment_spectra(srs_ctx* ctx, const void* strain, int64_t n_sampl
  * SRS_ERR_ARG for n_seg < 1, p_fa outside (0, 1) or a weight <= 0. */
 srs_status srs_nsigma_threshold(const double* w, int32_t n_seg, double p_fa, double* n_sigma_th);
 
-/* Detection non-centrality (Eq. non-centrality_threshold), equal weights: the
- * total non-centrality Lambda = sum_i lambda_i for which n_sigma exceeds the
- * p_fa threshold with probability p_det (sum P is then non-central chi^2 with
- * 2 n_seg dof).  The paper quotes Lambda_1 = 46.5 for n_seg = 1, p_fa = 1e-6,
- * p_det = 0.95. */
-srs_status srs_detection_noncentrality(int32_t n_seg, double p_fa, double p_det, double* lambda);
+/* Detection non-centrality (Eq. non-centrality_threshold): the total
+ * non-centrality Lambda = sum_i lambda_i for which n_sigma exceeds the p_fa
+ * threshold with probability p_det.  Equal weights (w NULL): sum P is
+ * non-central chi^2 with 2 n_seg dof, evaluated exactly.  Weights w[n_seg]:
+ * the signal's share of segment i is lambda_i = Lambda w_i / sum w (weights
+ * that follow A_i^2 / S_i follow the signal power), and the weighted sum is
+ * evaluated by Imhof's inversion of its characteristic function.  The paper
+ * quotes Lambda_1 = 46.5 for n_seg = 1, p_fa = 1e-6, p_det = 0.95. */
+srs_status srs_detection_noncentrality(const double* w, int32_t n_seg, double p_fa, double p_det, double* lambda);
 
 /* Diagnostic: runs the spreader's bounded staging wait on a transfer that never
  * comes (one thread, about one second) and returns what a search would:

@@ -59,3 +59,22 @@ def nsigma_threshold_weighted(w, p_fa):
     f = lambda q: np.log(weighted_exp_sf(w, q)) - np.log(p_fa)
     q = brentq(f, lo, hi, xtol=1e-13)
     return q - mean
+
+
+def detection_probability_mc(w, lam_total, threshold, n_draws, seed):
+    """Monte Carlo P(n_sigma > threshold) for weights w (normalised to
+    sum w^2 = 1) and a signal of total non-centrality lam_total split as
+    lambda_i = lam_total w_i / sum w: P_i ~ non-central chi^2 with 2 dof."""
+    w = np.asarray(w, dtype=np.float64)
+    w = w / np.sqrt(np.sum(w * w))
+    lam = lam_total * w / np.sum(w)
+    r = np.random.default_rng(seed)
+    hits = 0
+    done = 0
+    while done < n_draws:
+        m = min(500_000, n_draws - done)
+        P = r.noncentral_chisquare(2.0, lam, size=(m, w.size))
+        ns = (P - 2.0) / 2.0 @ w
+        hits += int(np.sum(ns > threshold))
+        done += m
+    return hits / n_draws

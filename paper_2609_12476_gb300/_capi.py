@@ -160,7 +160,7 @@ def lib():
         L.srs_nsigma_threshold.restype = i32
         L.srs_nsigma_threshold.argtypes = [vp, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
         L.srs_detection_noncentrality.restype = i32
-        L.srs_detection_noncentrality.argtypes = [i32, ctypes.c_double, ctypes.c_double,
+        L.srs_detection_noncentrality.argtypes = [vp, i32, ctypes.c_double, ctypes.c_double,
                                                   ctypes.POINTER(ctypes.c_double)]
         L.srs_selftest_wait.restype = i32
         L.srs_selftest_wait.argtypes = [vp]
@@ -218,11 +218,16 @@ def nsigma_threshold(n_seg, p_fa, weights=None):
     return out.value
 
 
-def detection_noncentrality(n_seg, p_fa, p_det):
+def detection_noncentrality(n_seg, p_fa, p_det, weights=None):
     """srs_detection_noncentrality: the total non-centrality a signal needs
-    to cross the p_fa threshold with probability p_det (equal weights)."""
+    to cross the p_fa threshold with probability p_det (equal weights, or the
+    given positive weights with the signal split in proportion to them)."""
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    if w is not None and w.size != n_seg:
+        raise ValueError("weights must have n_seg entries")
     out = ctypes.c_double(0.0)
-    st = lib().srs_detection_noncentrality(int(n_seg), float(p_fa), float(p_det), ctypes.byref(out))
+    st = lib().srs_detection_noncentrality(w.ctypes.data if w is not None else None, int(n_seg), float(p_fa),
+                                           float(p_det), ctypes.byref(out))
     if st != SRS_OK:
         raise SrsError(st, "srs_detection_noncentrality rejected its arguments")
     return out.value

@@ -85,3 +85,21 @@ def test_library_statistics_reject_bad_arguments():
         nsigma_threshold(3, 1e-6, [1.0, -1.0, 2.0])
     with pytest.raises(SrsError):
         detection_noncentrality(10, 1e-6, 1.0)
+
+
+def test_library_weighted_detection_noncentrality_monte_carlo():
+    """With unequal weights the library's Lambda^det gives p_det = 0.95 under
+    2e6 seeded draws of the weighted non-central sum (threshold from the
+    oracle's exact hypoexponential law)."""
+    w = np.array([0.6, 0.8, 1.0, 1.3, 1.7, 2.2])
+    p_fa, p_det = 1e-4, 0.95
+    lam = detection_noncentrality(w.size, p_fa, p_det, weights=w)
+    th = stats.nsigma_threshold_weighted(w, p_fa)
+    est = stats.detection_probability_mc(w, lam, th, 2_000_000, seed=31)
+    assert abs(est - p_det) < 4 * np.sqrt(p_det * (1 - p_det) / 2_000_000), (lam, est)
+    # equal weights given explicitly take the exact route; nearly equal ones agree with it
+    n = 12
+    exact = detection_noncentrality(n, 1e-6, 0.95)
+    assert detection_noncentrality(n, 1e-6, 0.95, weights=np.ones(n)) == exact
+    near = detection_noncentrality(n, 1e-6, 0.95, weights=1.0 + 1e-4 * np.arange(n))
+    assert near == pytest.approx(exact, rel=1e-5)
