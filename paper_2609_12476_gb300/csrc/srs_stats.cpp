@@ -14,8 +14,8 @@
 //   gamma_k = sum_i (1 - b / w_i)^k / k,  delta_0 = 1,
 //   delta_{k+1} = 1/(k+1) sum_{j=1}^{k+1} j gamma_j delta_{k+1-j},
 //   P(sum w_i E_i > q) = C sum_k delta_k Q(N + k, q / b),
-// every term positive.  The mixture weights C delta_k are carried in long
-// double, whose range holds C for tracks of thousands of segments.
+// every term positive.  The mixture weights C delta_k are carried as scaled
+// deltas with C in logs (see ExpMixture).
 // With a signal, P_i is non-central chi^2 (2 dof, non-centrality lambda_i);
 // for equal weights sum P_i is non-central chi^2 with 2N dof and total
 // non-centrality Lambda, a Poisson(Lambda/2) mixture of central chi^2 with
@@ -73,50 +73,65 @@ void gamma_q_run(int64_t m0, int64_t count, ld x, std::vector<ld>& out) {
 
 // The law of sum_i w_i E_i for positive weights as a mixture of Gamma(N + k,
 // scale b) laws: mixture weights d_k = C delta_k (Moschopoulos 1985), built
-// once; sf(q) = sum_k d_k Q(N + k, q / b).
+// once; sf(q) = sum_k d_k Q(N + k, q / b).  C = prod (b / w_i) leaves every
+// floating-point range on long tracks with spread weights (e^-17500 for a
+// 26-day 0PN track over 40-60 Hz), so the recurrence runs on
+// deltas scaled by e^shift, rescaled whenever they grow past 1e250, and C
+// enters in logs: d_k = exp(logC - shift) delta_hat_k.
 struct ExpMixture {
   int64_t n = 0;
   ld b = 1;
-  std::vector<ld> d;
+  std::vector<double> dh;   // delta_k e^shift
+  double log_factor = 0;    // logC - shift: d_k = exp(log_factor) dh_k
 
   explicit ExpMixture(const std::vector<ld>& w) {
     n = (int64_t)w.size();
     b = w[0];
     for (ld v : w) b = std::min(b, v);
-    ld logC = 0;
-    std::vector<ld> r(w.size()), rk(w.size(), 1.0L);
+    double logC = 0;
+    std::vector<double> r(w.size()), rk(w.size(), 1.0);
     for (size_t i = 0; i < w.size(); ++i) {
-      logC += std::log(b / w[i]);
-      r[i] = 1.0L - b / w[i];
+      logC += (double)std::log(b / w[i]);
+      r[i] = (double)(1.0L - b / w[i]);
     }
-    // C is far below double range for long tracks (long double reaches ~1e-4900)
-    d.push_back(std::exp(logC));
-    std::vector<ld> gam(1, 0.0L);
-    ld sum_d = d[0], peak = d[0];
-    const int64_t kcap = 60000;
-    for (int64_t k = 1; k <= kcap && sum_d < 1.0L - 1e-18L; ++k) {
-      ld g = 0;
+    double shift = 0;                 // dh_k = delta_k e^shift
+    dh.push_back(1.0);
+    std::vector<double> gam(1, 0.0);
+    double sum_dh = 1.0, peak = 1.0;
+    const int64_t kcap = 200000;
+    auto total = [&]() { return std::exp(logC - shift + std::log(sum_dh)); };
+    for (int64_t k = 1; k <= kcap; ++k) {
+      if (k % 16 == 0 && total() >= 1.0 - 1e-15) break;
+      double g = 0;
       for (size_t i = 0; i < w.size(); ++i) {
         rk[i] *= r[i];
         g += rk[i];
       }
-      gam.push_back(g / (ld)k);
-      ld dk = 0;
-      for (int64_t j = 1; j <= k; ++j) dk += (ld)j * gam[(size_t)j] * d[(size_t)(k - j)];
-      dk /= (ld)k;
-      d.push_back(dk);
-      sum_d += dk;
+      gam.push_back(g / (double)k);
+      double dk = 0;
+      for (int64_t j = 1; j <= k; ++j) dk += (double)j * gam[(size_t)j] * dh[(size_t)(k - j)];
+      dk /= (double)k;
+      dh.push_back(dk);
+      sum_dh += dk;
       peak = std::max(peak, dk);
-      if (dk < 1e-24L * peak && dk < d[(size_t)(k - 1)]) break;   // past the mode, negligible
+      if (peak > 1e250) {             // rescale the stored deltas
+        for (double& v : dh) v *= 1e-250;
+        sum_dh *= 1e-250;
+        peak *= 1e-250;
+        shift -= 250.0 * std::log(10.0);
+      }
+      if (dk < 1e-30 * peak && dk < dh[(size_t)(k - 1)] && total() > 0.5) break;   // past the mode, negligible
     }
+    log_factor = logC - shift;
   }
 
   ld sf(ld q) const {
     std::vector<ld> Q;
-    gamma_q_run(n, (int64_t)d.size(), q / b, Q);
+    gamma_q_run(n, (int64_t)dh.size(), q / b, Q);
     ld s = 0;
-    for (size_t k = 0; k < d.size(); ++k) s += d[k] * Q[k];
-    return std::min<ld>(s, 1.0L);
+    for (size_t k = 0; k < dh.size(); ++k) s += (ld)dh[k] * Q[k];
+    if (!(s > 0)) return 0.0L;
+    return std::min<ld>(std::exp((ld)log_factor + std::log(s)), 1.0L);
   }
 };
 

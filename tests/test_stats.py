@@ -103,3 +103,18 @@ def test_library_weighted_detection_noncentrality_monte_carlo():
     assert detection_noncentrality(n, 1e-6, 0.95, weights=np.ones(n)) == exact
     near = detection_noncentrality(n, 1e-6, 0.95, weights=1.0 + 1e-4 * np.arange(n))
     assert near == pytest.approx(exact, rel=1e-5)
+
+
+def test_library_weighted_threshold_on_a_month_long_track():
+    """A 26-day track (Mc = 1e-3 across 40-60 Hz: 76 158 segments) with
+    segment-averaged f^(4/3) weights: the mixture's constant C = prod b / w_i
+    is e^-17500 there, far outside floating-point range, and the threshold
+    still comes out just above the equal-weight one."""
+    import srs_synth
+    b0 = srs_synth.chirp_beta(1e-3, 40.0)
+    L = int(3 / (8 * b0) * (1 - (40 / 60) ** (8 / 3)) / 30.0)
+    s = np.arange(L)
+    a = 2.0 / (np.sqrt(1 - 8 / 3 * b0 * s * 30.0) + np.sqrt(np.maximum(1 - 8 / 3 * b0 * (s + 1) * 30.0, 0.0)))
+    assert L > 70000 and a.max() / a.min() > 1.7
+    te, tw = nsigma_threshold(L, 1e-6), nsigma_threshold(L, 1e-6, a)
+    assert te < tw < 1.01 * te
