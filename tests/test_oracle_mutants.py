@@ -113,3 +113,34 @@ def test_slide_pins_catch_planted_mistake(monkeypatch, name, orig, bad, catchers
                     fn(*a)
             else:
                 fn()
+
+
+# Mistakes planted in the statistics oracle (oracle/stats.py), caught by the
+# oracle pins of test_stats.py.
+STATS_MUTANTS = [
+    ("chi-square with 2N - 1 dof", "return brentq(lambda lam: ncx2.sf(s, 2 * n_seg, lam) - p_det",
+     "return brentq(lambda lam: ncx2.sf(s, 2 * n_seg - 1, lam) - p_det",
+     ["test_oracle_detection_noncentrality_matches_paper"]),
+    ("threshold not centred", "return (s - 2.0 * n_seg) / (2.0 * np.sqrt(n_seg))", "return s / (2.0 * np.sqrt(n_seg))",
+     ["test_oracle_one_segment_threshold_closed_form"]),
+    ("hypoexponential coefficient inverted", "c *= wi / (wi - wj)", "c *= wj / (wi - wj)",
+     ["test_oracle_weighted_law_monte_carlo"]),
+]
+
+
+@pytest.mark.parametrize("name,orig,bad,catchers", STATS_MUTANTS, ids=[m[0] for m in STATS_MUTANTS])
+def test_stats_pins_catch_planted_mistake(monkeypatch, name, orig, bad, catchers):
+    import types
+    import test_stats as spins
+    from oracle import stats
+    src = open(stats.__file__).read()
+    assert src.count(orig) == 1, name
+    mod = types.ModuleType("oracle.stats_mutant")
+    mod.__package__ = "oracle"
+    exec(compile(src.replace(orig, bad), "stats_mutant.py", "exec"), mod.__dict__)
+    for fn in ("nsigma_threshold_equal", "detection_noncentrality", "weighted_exp_sf", "nsigma_threshold_weighted",
+               "detection_probability_mc"):
+        monkeypatch.setattr(stats, fn, getattr(mod, fn))
+    for pin in catchers:
+        with pytest.raises(Exception):
+            getattr(spins, pin)()
