@@ -1,4 +1,4 @@
-"""Learned proposal: training data, training, calibration and the recall judge.
+"""Learned proposal: training data, training, calibration and the recall reference.
 
 Host orchestration of the library's kernels (every computation runs in
 libsrs: strain synthesis, searches, patches, the network, refinement):
@@ -269,7 +269,7 @@ def detection_threshold(nseg, p_fa):
 def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t_obs, n_real, per_real, seed,
              p_fa=1e-6, amp_range=(0.01, 0.1), nms=NO_NMS, fine_rows=1, component_top=0, nms_by_nsigma=False):
     """Recall of injections over the same realisations in four searches:
-      full            every fine template (the judge)
+      full            every fine template (the recall reference)
       proposal        the network's proposal at its noise-calibrated threshold
                       (the library's srs_search_proposed)
       nsigma_equal    the proposal without the network at equal cost: the same
@@ -296,7 +296,7 @@ def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t
     for r in range(n_real):
         inj, _cells = injections_on_grid(rng, coarse_mc, params, per_real, amp_range)
         x = ctx.make_strain(n, params.fs, seed * 1000003 + 7 + r, inj, f_hi=params.f_hi)
-        # full fine search (the judge)
+        # full fine search (the recall reference)
         fmap = torch.empty((Mf, n_bins), dtype=torch.float32, device=x.device)
         res, rep = ctx.search(x, fine_mc, params, out={"map": fmap, "cands": torch.empty((params.top_k, 3),
                               dtype=torch.int32, device=x.device)})

@@ -1,6 +1,6 @@
 """The learned proposal end to end on the GPU, at reduced size: training data
 made by the search itself, training by the library's kernels, calibration at
-a 1e-3 noise false-alarm rate, and the recall judge (the full fine-template
+a 1e-3 noise false-alarm rate, and the recall reference (the full fine-template
 search).  With many loud injections per map the coarse n_sigma map is full of
 ridges; the network must still find the injections' own cells, and beat the
 proposal without a network given the same number of coarse cells."""
