@@ -247,6 +247,22 @@ srs_status srs_nsigma_threshold(const double* w, int32_t n_seg, double p_fa, dou
  * quotes Lambda_1 = 46.5 for n_seg = 1, p_fa = 1e-6, p_det = 0.95. */
 srs_status srs_detection_noncentrality(const double* w, int32_t n_seg, double p_fa, double p_det, double* lambda);
 
+/* Receiver operating characteristic of one signal (Sec. III.C, Fig. roc for a
+ * single signal; the left side of Eq. non-centrality_threshold):
+ *   p_det[q] = P(n_sigma > n_sigma^th(p_fa[q]) | lambda, w),  q < n_points,
+ * for one template whose track has n_seg segments with weights w[n_seg] (any
+ * positive scale; NULL: equal weights) and signal non-centralities
+ * lambda[n_seg] >= 0 per segment (the signal's normalised power there; NULL:
+ * no signal, so p_det = p_fa).  Equal weights: exact (sum P is non-central
+ * chi^2 with 2 n_seg dof and non-centrality sum lambda_i).  Unequal weights:
+ * the threshold from the exact central law, then Imhof's integral, whose
+ * absolute error stays below about 1e-9; its cost grows as n_seg^2 per point.
+ * All arrays are host memory owned by the caller; p_det has n_points entries.
+ * SRS_ERR_ARG for n_seg < 1, n_points < 1, a p_fa outside (0, 1), a weight
+ * <= 0 or a lambda that is negative or not finite. */
+srs_status srs_detection_probability(const double* w, const double* lambda, int32_t n_seg, const double* p_fa,
+                                     int32_t n_points, double* p_det);
+
 /* Diagnostic: runs the spreader's bounded staging wait on a transfer that never
  * comes (one thread, about one second) and returns what a search would:
  * SRS_ERR_TIMEOUT with the give-up recorded in srs_last_error().  The wait

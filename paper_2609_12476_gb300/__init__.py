@@ -8,9 +8,9 @@ include/srs.h); this package only loads it and marshals arguments:
     cands, stat_map, report = ctx.search(strain, mc, Params())
 """
 from ._capi import (CAND_DTYPE, EXPORTS, SRS_F32, SRS_F64, SRS_MIXED, SRS_PLAIN_FP64, SRS_WEIGHT_AMPLITUDE,
-                    SRS_WEIGHT_EQUAL, Context, Params, SrsError, detection_noncentrality, lib, nsigma_threshold,
-                    srs_plan)
+                    SRS_WEIGHT_EQUAL, Context, Params, SrsError, detection_noncentrality, detection_probability,
+                    lib, nsigma_threshold, srs_plan)
 
 __all__ = ["CAND_DTYPE", "EXPORTS", "SRS_F32", "SRS_F64", "SRS_MIXED", "SRS_PLAIN_FP64", "SRS_WEIGHT_AMPLITUDE",
-           "SRS_WEIGHT_EQUAL", "Context", "Params", "SrsError", "detection_noncentrality", "lib",
+           "SRS_WEIGHT_EQUAL", "Context", "Params", "SrsError", "detection_noncentrality", "detection_probability", "lib",
            "nsigma_threshold", "srs_plan"]

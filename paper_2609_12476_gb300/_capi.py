@@ -25,7 +25,8 @@ EXPORTS = ("srs_create", "srs_destroy", "srs_last_error", "srs_plan", "srs_searc
            "srs_segment_spectra", "srs_segment_spectra_cufft", "srs_time_map", "srs_segment_spectra_static", "srs_make_strain",
            "srs_patches", "srs_mlp_forward", "srs_mlp_grad", "srs_mlp_train", "srs_score_map", "srs_refine",
            "srs_search_proposed", "srs_power_cube", "srs_stack_slide", "srs_slide_search", "srs_selftest_wait",
-           "srs_nsigma_threshold", "srs_detection_noncentrality", "srs_cube_whiten")
+           "srs_nsigma_threshold", "srs_detection_noncentrality", "srs_detection_probability",
+           "srs_cube_whiten")
 SRS_SLIDE_FIRST, SRS_SLIDE_LAST = 1, 2
 SRS_WEIGHT_EQUAL, SRS_WEIGHT_AMPLITUDE = 0, 1
 MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 297, 64, 19137
@@ -162,6 +163,8 @@ def lib():
         L.srs_detection_noncentrality.restype = i32
         L.srs_detection_noncentrality.argtypes = [vp, i32, ctypes.c_double, ctypes.c_double,
                                                   ctypes.POINTER(ctypes.c_double)]
+        L.srs_detection_probability.restype = i32
+        L.srs_detection_probability.argtypes = [vp, vp, i32, vp, i32, vp]
         L.srs_selftest_wait.restype = i32
         L.srs_selftest_wait.argtypes = [vp]
         L.srs_power_cube.restype = i32
@@ -231,6 +234,26 @@ def detection_noncentrality(n_seg, p_fa, p_det, weights=None):
     if st != SRS_OK:
         raise SrsError(st, "srs_detection_noncentrality rejected its arguments")
     return out.value
+
+
+def detection_probability(n_seg, p_fa, lambdas=None, weights=None):
+    """srs_detection_probability: P(n_sigma > n_sigma^th(p_fa)) for a signal
+    with per-segment non-centralities `lambdas` (None: no signal), equal
+    weights or the given positive weights.  p_fa may be a scalar or a sequence
+    (the points of a ROC curve); the result has the same shape."""
+    pf = np.ascontiguousarray(np.atleast_1d(p_fa), dtype=np.float64)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    lam = None if lambdas is None else np.ascontiguousarray(lambdas, dtype=np.float64)
+    for a, name in ((w, "weights"), (lam, "lambdas")):
+        if a is not None and a.size != n_seg:
+            raise ValueError(f"{name} must have n_seg entries")
+    out = np.zeros(pf.size, dtype=np.float64)
+    st = lib().srs_detection_probability(w.ctypes.data if w is not None else None,
+                                         lam.ctypes.data if lam is not None else None, int(n_seg),
+                                         pf.ctypes.data, int(pf.size), out.ctypes.data)
+    if st != SRS_OK:
+        raise SrsError(st, "srs_detection_probability rejected its arguments")
+    return float(out[0]) if np.ndim(p_fa) == 0 else out
 
 
 def _report_dict(r):

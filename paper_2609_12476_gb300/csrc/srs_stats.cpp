@@ -28,7 +28,9 @@
 //   rho(u)   = prod_i (1 + w_i^2 u^2)^(1/2) exp(sum_i lambda_i w_i^2 u^2 / (2 (1 + w_i^2 u^2))),
 // accurate at the detection probabilities asked for here (not at 1e-6 tails,
 // where the threshold comes from the exact central mixture).  Weights that
-// are all equal take the exact equal-weight route.
+// are all equal take the exact equal-weight route.  The ROC of one signal
+// (Fig. roc: p_det against p_fa) is the same probability at the thresholds of
+// a list of p_fa, with the per-segment non-centralities lambda_i given.
 #include <cmath>
 #include <vector>
 
@@ -216,6 +218,35 @@ ld invert_sf(F sf, ld lo, ld hi, ld p) {
   return 0.5L * (lo + hi);
 }
 
+// Weights normalised to sum w^2 = 1 (w NULL: equal weights).  False when a
+// weight is not positive and finite; *unequal says whether any two differ.
+bool unit_weights(const double* w, int32_t n, std::vector<double>& ww, bool* unequal) {
+  ww.assign((size_t)n, 1.0 / std::sqrt((double)n));
+  *unequal = false;
+  if (!w) return true;
+  double s2 = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    if (!(w[i] > 0) || !std::isfinite(w[i])) return false;
+    s2 += w[i] * w[i];
+    if (std::fabs(w[i] - w[0]) > 1e-12 * std::fabs(w[0])) *unequal = true;
+  }
+  for (int32_t i = 0; i < n; ++i) ww[(size_t)i] = w[i] / std::sqrt(s2);
+  return true;
+}
+
+// Equal weights: the threshold on S = sum P (chi^2 with 2N dof under H0) and
+// its exact false-alarm probability.
+ld sum_threshold(int64_t n, double p_fa, ld* sf_at) {
+  auto sf0 = [&](ld s) {
+    std::vector<ld> Q;
+    gamma_q_run(n, 1, s / 2, Q);
+    return Q[0];
+  };
+  const ld s_th = invert_sf(sf0, 2.0L * n, 2.0L * n + 10.0L * std::sqrt((ld)n), (ld)p_fa);
+  if (sf_at) *sf_at = sf0(s_th);
+  return s_th;
+}
+
 }  // namespace
 
 extern "C" {
@@ -249,26 +280,13 @@ srs_status srs_detection_noncentrality(const double* w, int32_t n_seg, double p_
   if (!lambda || n_seg < 1 || n_seg > 10000000 || !(p_fa > 0 && p_fa < 1) || !(p_det > 0 && p_det < 1))
     return SRS_ERR_ARG;
   bool unequal = false;
-  if (w)
-    for (int32_t i = 1; i < n_seg; ++i)
-      if (std::fabs(w[i] - w[0]) > 1e-12 * std::fabs(w[0])) unequal = true;
-  if (w) {
-    for (int32_t i = 0; i < n_seg; ++i)
-      if (!(w[i] > 0) || !std::isfinite(w[i])) return SRS_ERR_ARG;
-  }
+  std::vector<double> ww;
+  if (!unit_weights(w, n_seg, ww, &unequal)) return SRS_ERR_ARG;
   if (unequal) {
     // unequal weights: the threshold on n_sigma from the exact central law,
     // then Lambda from Imhof's integral with lambda_i = Lambda w_i / sum w
-    std::vector<double> ww((size_t)n_seg);
-    double s2 = 0, s1 = 0;
-    for (int32_t i = 0; i < n_seg; ++i) {
-      if (!(w[i] > 0) || !std::isfinite(w[i])) return SRS_ERR_ARG;
-      s2 += w[i] * w[i];
-    }
-    for (int32_t i = 0; i < n_seg; ++i) {
-      ww[(size_t)i] = w[i] / std::sqrt(s2);
-      s1 += ww[(size_t)i];
-    }
+    double s1 = 0;
+    for (double v : ww) s1 += v;
     double th = 0;
     srs_status s = srs_nsigma_threshold(ww.data(), n_seg, p_fa, &th);
     if (s != SRS_OK) return s;
@@ -294,14 +312,9 @@ srs_status srs_detection_noncentrality(const double* w, int32_t n_seg, double p_
     return SRS_OK;
   }
   const int64_t n = n_seg;
-  // threshold on S = sum P (chi^2 with 2N dof under H0)
-  auto sf0 = [&](ld s) {
-    std::vector<ld> Q;
-    gamma_q_run(n, 1, s / 2, Q);
-    return Q[0];
-  };
-  const ld s_th = invert_sf(sf0, 2.0L * n, 2.0L * n + 10.0L * std::sqrt((ld)n), (ld)p_fa);
-  if ((ld)p_det <= sf0(s_th)) {
+  ld sf_th = 0;
+  const ld s_th = sum_threshold(n, p_fa, &sf_th);
+  if ((ld)p_det <= sf_th) {
     *lambda = 0.0;
     return SRS_OK;
   }
@@ -314,6 +327,42 @@ srs_status srs_detection_noncentrality(const double* w, int32_t n_seg, double p_
     if (hi - lo <= 1e-13L * hi) break;
   }
   *lambda = (double)(0.5L * (lo + hi));
+  return SRS_OK;
+}
+
+srs_status srs_detection_probability(const double* w, const double* lambda, int32_t n_seg, const double* p_fa,
+                                     int32_t n_points, double* p_det) {
+  if (!p_fa || !p_det || n_seg < 1 || n_seg > 10000000 || n_points < 1) return SRS_ERR_ARG;
+  for (int32_t q = 0; q < n_points; ++q)
+    if (!(p_fa[q] > 0 && p_fa[q] < 1)) return SRS_ERR_ARG;
+  std::vector<double> ww, lam((size_t)n_seg, 0.0);
+  bool unequal = false;
+  if (!unit_weights(w, n_seg, ww, &unequal)) return SRS_ERR_ARG;
+  double total = 0;
+  if (lambda) {
+    for (int32_t i = 0; i < n_seg; ++i) {
+      if (!(lambda[i] >= 0) || !std::isfinite(lambda[i])) return SRS_ERR_ARG;
+      lam[(size_t)i] = lambda[i];
+      total += lambda[i];
+    }
+  }
+  for (int32_t q = 0; q < n_points; ++q) {
+    if (!unequal) {
+      // sum P is non-central chi^2 with 2N dof and non-centrality sum lambda_i
+      ld sf_th = 0;
+      const ld s_th = sum_threshold(n_seg, p_fa[q], &sf_th);
+      p_det[q] = (double)(total > 0 ? noncentral_sf(n_seg, (ld)total, s_th) : sf_th);
+      continue;
+    }
+    double th = 0;
+    const srs_status s = srs_nsigma_threshold(ww.data(), n_seg, p_fa[q], &th);
+    if (s != SRS_OK) return s;
+    double s1 = 0;
+    for (double v : ww) s1 += v;
+    // n_sigma = sum w (P - 2) / 2 > th  <=>  sum w P > 2 th + 2 sum w
+    const double v = Imhof{ww, lam, 2.0 * th + 2.0 * s1}.sf();
+    p_det[q] = std::min(1.0, std::max(0.0, v));
+  }
   return SRS_OK;
 }
 

@@ -125,6 +125,12 @@ STATS_MUTANTS = [
      ["test_oracle_one_segment_threshold_closed_form"]),
     ("hypoexponential coefficient inverted", "c *= wi / (wi - wj)", "c *= wj / (wi - wj)",
      ["test_oracle_weighted_law_monte_carlo"]),
+    ("characteristic function's factor 2", "z = 1.0 - 2.0j * w * t", "z = 1.0 - 1.0j * w * t",
+     ["test_oracle_weighted_noncentral_law_reduces_to_textbook_laws"]),
+    ("signal term without its weight", "np.exp(1j * lam * w * t / z)", "np.exp(1j * lam * t / z)",
+     ["test_oracle_detection_probability_monte_carlo"]),
+    ("inversion with the wrong sign", "return 0.5 + (head + c - s) / np.pi", "return 0.5 - (head + c - s) / np.pi",
+     ["test_oracle_weighted_noncentral_law_reduces_to_textbook_laws"]),
 ]
 
 
@@ -139,7 +145,7 @@ def test_stats_pins_catch_planted_mistake(monkeypatch, name, orig, bad, catchers
     mod.__package__ = "oracle"
     exec(compile(src.replace(orig, bad), "stats_mutant.py", "exec"), mod.__dict__)
     for fn in ("nsigma_threshold_equal", "detection_noncentrality", "weighted_exp_sf", "nsigma_threshold_weighted",
-               "detection_probability_mc"):
+               "detection_probability_mc", "weighted_noncentral_sf", "detection_probability"):
         monkeypatch.setattr(stats, fn, getattr(mod, fn))
     for pin in catchers:
         with pytest.raises(Exception):

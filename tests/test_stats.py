@@ -1,7 +1,8 @@
 """Detection statistics: the oracle (oracle.stats) pinned by the printed
-detection non-centrality, a closed form and Monte Carlo; then the library's
-host functions (srs_nsigma_threshold, srs_detection_noncentrality) against
-the oracle.  CPU only: these functions need no GPU."""
+detection non-centrality, a closed form, textbook laws and Monte Carlo; then
+the library's host functions (srs_nsigma_threshold,
+srs_detection_noncentrality, srs_detection_probability) against the oracle.
+CPU only: these functions need no GPU."""
 import json
 import os
 
@@ -9,7 +10,9 @@ import numpy as np
 import pytest
 
 from oracle import stats
-from paper_2609_12476_gb300 import SrsError, detection_noncentrality, nsigma_threshold
+from scipy.stats import chi2, ncx2
+
+from paper_2609_12476_gb300 import SrsError, detection_noncentrality, detection_probability, nsigma_threshold
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))
 
@@ -118,3 +121,96 @@ def test_library_weighted_threshold_on_a_month_long_track():
     assert L > 70000 and a.max() / a.min() > 1.7
     te, tw = nsigma_threshold(L, 1e-6), nsigma_threshold(L, 1e-6, a)
     assert te < tw < 1.01 * te
+
+
+def test_oracle_weighted_noncentral_law_reduces_to_textbook_laws():
+    """The characteristic-function inversion with equal weights is scipy's
+    non-central chi^2 with 2N dof and total non-centrality sum lambda_i,
+    however the signal is split; without a signal and unequal weights it is
+    the hypoexponential law (sum w P = 2 sum w E)."""
+    for n, lam, x in [(1, [5.0], 12.0), (3, [1.0, 2.0, 7.0], 20.0), (4, [30.0, 0.0, 0.0, 0.0], 25.0),
+                      (2, [0.4, 0.6], 60.0)]:
+        got = stats.weighted_noncentral_sf(np.ones(n), lam, x)
+        assert got == pytest.approx(ncx2.sf(x, 2 * n, sum(lam)), rel=1e-6, abs=1e-14), (n, lam, x)
+    assert stats.weighted_noncentral_sf(np.ones(6), np.zeros(6), 15.0) == pytest.approx(chi2.sf(15.0, 12), rel=1e-12)
+    w = np.array([0.3, 0.5, 0.9, 1.4, 2.0])
+    for q in (4.0, 10.0, 40.0, 60.0):
+        got = stats.weighted_noncentral_sf(w, np.zeros(5), q)
+        assert got == pytest.approx(stats.weighted_exp_sf(w, q / 2), rel=1e-8, abs=1e-15), q
+
+
+def test_oracle_detection_probability_monte_carlo():
+    """Unequal weights and an unequal signal split against 2e6 seeded draws of
+    the weighted non-central sum."""
+    w = np.array([0.5, 0.9, 1.1, 1.6, 2.3])
+    lam = np.array([0.5, 6.0, 2.0, 9.0, 1.0])
+    r = np.random.default_rng(41)
+    n_draws = 2_000_000
+    P = r.noncentral_chisquare(2.0, lam, size=(n_draws, w.size))
+    wn = w / np.sqrt(np.sum(w * w))
+    ns = (P - 2.0) / 2.0 @ wn
+    for p_fa in (1e-3, 1e-2, 1e-1):
+        th = stats.nsigma_threshold_weighted(w, p_fa)
+        emp = float(np.mean(ns > th))
+        pd = stats.detection_probability(w, lam, p_fa)
+        assert abs(emp - pd) <= 4 * np.sqrt(pd * (1 - pd) / n_draws), (p_fa, emp, pd)
+
+
+@pytest.mark.parametrize("n", [1, 3, 35, 300])
+def test_library_detection_probability_equal_weights(n):
+    r = np.random.default_rng(n)
+    lam = r.uniform(0.0, 2.0, n) * (60.0 / n)
+    pf = [1e-8, 1e-6, 1e-3, 0.1]
+    got = detection_probability(n, pf, lam)
+    want = [stats.detection_probability(None, lam, p) for p in pf]
+    assert got == pytest.approx(want, rel=1e-9, abs=1e-15)
+    # equal weights given explicitly take the same exact route
+    assert np.array_equal(detection_probability(n, pf, lam, weights=np.full(n, 3.0)), got)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_library_detection_probability_weighted(seed):
+    r = np.random.default_rng(100 + seed)
+    n = int(r.integers(2, 9))
+    w = np.sort(r.uniform(0.4, 2.5, n))
+    w[1:] += 1e-3 * np.arange(1, n)          # distinct, for the oracle's threshold
+    lam = r.uniform(0.0, 12.0, n)
+    pf = [1e-6, 1e-4, 1e-2]
+    got = detection_probability(n, pf, lam, weights=w)
+    want = [stats.detection_probability(w, lam, p) for p in pf]
+    assert got == pytest.approx(want, rel=1e-6, abs=1e-9)
+
+
+def test_library_roc_properties():
+    """No signal gives p_det = p_fa; p_det rises with p_fa and with the
+    signal; at the library's Lambda^det with lambda_i = Lambda w_i / sum w it
+    is p_det."""
+    w = np.array([0.6, 0.8, 1.0, 1.3, 1.7, 2.2])
+    pf = np.logspace(-9, -1, 9)
+    for weights in (None, w):
+        assert detection_probability(6, pf, None, weights) == pytest.approx(pf, rel=1e-6, abs=1e-11)
+        lo = detection_probability(6, pf, np.full(6, 2.0), weights)
+        hi = detection_probability(6, pf, np.full(6, 4.0), weights)
+        assert np.all(np.diff(lo) > 0) and np.all(hi > lo)
+    for weights in (None, w):
+        lam_det = detection_noncentrality(6, 1e-6, 0.95, weights=weights)
+        ww = np.ones(6) if weights is None else weights / np.sqrt(np.sum(weights ** 2))
+        assert detection_probability(6, 1e-6, lam_det * ww / ww.sum(), weights) == pytest.approx(0.95, abs=1e-8)
+    # the paper's one-segment number: Lambda = 46.5 at p_fa = 1e-6 gives p_det = 0.95
+    g = GOLD["detection_noncentrality"]
+    assert detection_probability(1, g["p_fa"], [g["lambda_printed"]]) == pytest.approx(g["p_det"], abs=2e-3)
+
+
+def test_library_detection_probability_rejects_bad_arguments():
+    with pytest.raises(SrsError):
+        detection_probability(3, 0.0)
+    with pytest.raises(SrsError):
+        detection_probability(3, [1e-6, 1.0])
+    with pytest.raises(SrsError):
+        detection_probability(3, 1e-6, [1.0, -0.5, 2.0])
+    with pytest.raises(SrsError):
+        detection_probability(3, 1e-6, [1.0, np.nan, 2.0])
+    with pytest.raises(SrsError):
+        detection_probability(3, 1e-6, None, [1.0, 0.0, 2.0])
+    with pytest.raises(SrsError):
+        detection_probability(0, 1e-6)
