@@ -14,6 +14,8 @@ Workload shapes (30 s segments, 40-60 Hz band, chirp masses 5e-4..1e-1 Msun)
 follow the paper's search (abstract, Sec. III.C, Sec. IV).
 """
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -53,15 +55,27 @@ def chirp(n, fs, mc_msun, f0, amp, phi0=0.0, t_start=0.0):
 
     phi(t) - phi0 = 2 pi f0 * (3 / (5 beta)) * (1 - (1 - (8/3) beta (t - t_start))^(5/8))
     (Eq. (phi) minus its value at t_start); zero after coalescence."""
-    beta = chirp_beta(mc_msun, f0)
-    t = np.arange(n, dtype=np.float64) / fs - t_start
-    x = (8.0 / 3.0) * beta * t
     out = np.zeros(n)
+    add_chirp(out, fs, mc_msun, f0, amp, phi0, t_start)
+    return out
+
+
+def add_chirp(out, fs, mc_msun, f0, amp, phi0=0.0, t_start=0.0, j_first=0):
+    """out[j] += chirp sample j_first + j, evaluated only over the samples where
+    the chirp is live (the same values as chirp's, sample by sample)."""
+    n = out.size
+    beta = chirp_beta(mc_msun, f0)
+    j0 = min(n, max(0, int(np.floor(t_start * fs)) - 1 - j_first))
+    t_end = t_start + 3.0 / (8.0 * beta)
+    j1 = n if not np.isfinite(t_end) or t_end * fs + 2 - j_first >= n else \
+        min(n, max(j0, int(np.ceil(t_end * fs)) + 2 - j_first))
+    t = np.arange(j_first + j0, j_first + j1, dtype=np.float64) / fs - t_start
+    x = (8.0 / 3.0) * beta * t
     live = (t >= 0) & (x < 1.0)
     core = -np.expm1(0.625 * np.log1p(-x[live]))
     phase = 2.0 * np.pi * f0 * (3.0 / (5.0 * beta)) * core + phi0
-    out[live] = amp * np.cos(phase)
-    return out
+    seg = out[j0:j1]
+    seg[live] += amp * np.cos(phase)
 
 
 def log_templates(mc_lo, mc_hi, count):
@@ -75,9 +89,16 @@ def strain_with_chirps(n, fs, seed, injections, dtype=np.float64, noise=True):
     """Noise (seed) plus the listed chirps; each injection is a dict with keys
     mc, f0, amp and optionally phi0, t_start."""
     x = white_noise(n, seed) if noise else np.zeros(n)
-    for inj in injections:
-        x = x + chirp(n, fs, inj["mc"], inj["f0"], inj["amp"], inj.get("phi0", 0.0),
-                      inj.get("t_start", 0.0))
+    block = 1 << 20
+
+    def fill(j):                    # every chirp, in order, over samples [j, j + block)
+        v = x[j:j + block]
+        for inj in injections:
+            add_chirp(v, fs, inj["mc"], inj["f0"], inj["amp"], inj.get("phi0", 0.0), inj.get("t_start", 0.0), j)
+
+    if injections:
+        with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as pool:
+            list(pool.map(fill, range(0, n, block)))
     return x.astype(dtype, copy=False)
 
 

@@ -1,6 +1,6 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py
 times (device-resident strain, autotuned layout, graph replay): the whole map
-of the 2 h and 6 h searches comes from the GPU; the FP64 oracle recomputes
+of the 2 h, 6 h and 24 h searches comes from the GPU; the FP64 oracle recomputes
 whole rows of it (every segment of a sampled template) one spectrum at a time,
 and the rows must agree within the bound the spectra tolerance implies."""
 import numpy as np
@@ -79,6 +79,13 @@ def test_six_hour_batched_search_rows_match_oracle():
     """The 6 h / 1024-template search with uneven segment counts (35 to 720
     segments per template): three rows across the bank."""
     _check_rows("batched_6h", [0, 511, 1023])
+
+
+def test_large_24h_search_rows_match_oracle():
+    """The 24 h / 4096-template search on float32 strain (7.2 M spectra, 64
+    injections): the heaviest template (35 segments), a middle one (374) and
+    the lightest, which spans all 2880 segments."""
+    _check_rows("large_24h", [4095, 3000, 0])
 
 
 def test_two_stage_24h_sampled_templates_match_oracle():
