@@ -15,18 +15,25 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "srs_oracle.c")
 MUTANTS = [
     # (name, original text, mistake, pins that must fail)
     ("spectrum sign", "im[b] -= x[j] * sin(ang);", "im[b] += x[j] * sin(ang);",
-     ["test_tone_in_tau_gives_exactly_n", "test_uniform_limit_is_the_fft"]),
+     ["test_tone_in_tau_gives_exactly_n", "test_uniform_limit_is_the_fft", "test_tiny_spectra_against_brute_force"]),
     ("resampled-time exponent", "(-expm1((5.0 / 8.0) * log1p(-x)))", "(-expm1((3.0 / 8.0) * log1p(-x)))",
      ["test_delta_matches_high_precision_eq_new_t", "test_tone_in_tau_gives_exactly_n",
-      "test_delta_derivative_is_frequency_ratio"]),
+      "test_delta_derivative_is_frequency_ratio", "test_tiny_spectra_against_brute_force"]),
     ("bin frequency off by one", "double fb = f_lo + (double)b / t_coh;", "double fb = f_lo + (double)(b + 1) / t_coh;",
-     ["test_uniform_limit_is_the_fft", "test_noiseless_exact_template_chirp_concentrates_power"]),
+     ["test_uniform_limit_is_the_fft", "test_noiseless_exact_template_chirp_concentrates_power",
+      "test_tiny_spectra_against_brute_force"]),
     ("beta frequency power", "pow(f0, 8.0 / 3.0);\n}", "pow(f0, 5.0 / 3.0);\n}",
      ["test_beta_range_matches_paper", "test_band_crossing_times_match_paper"]),
     ("whole-segment rounding", "double k = floor(t / t_coh);", "double k = ceil(t / t_coh);",
      ["test_injection_segment_count_matches_paper"]),
     ("duration exponent", "(1.0 - pow(f0 / f_end, 8.0 / 3.0))", "(1.0 - pow(f0 / f_end, 5.0 / 3.0))",
      ["test_injection_segment_count_matches_paper", "test_frequency_reaches_f_end_after_duration"]),
+    ("segment start one segment late", "double t_i0 = J->local ? 0.0 : (double)i * (double)J->n_s / J->fs;",
+     "double t_i0 = J->local ? 0.0 : (double)(i + 1) * (double)J->n_s / J->fs;",
+     ["test_tiny_spectra_against_brute_force"]),
+    ("local map referenced to the data start", "double t_i0 = J->local ? 0.0 : (double)i * (double)J->n_s / J->fs;",
+     "double t_i0 = (double)i * (double)J->n_s / J->fs;",
+     ["test_tiny_spectra_against_brute_force"]),
 ]
 
 

@@ -121,6 +121,36 @@ def test_tone_in_tau_gives_exactly_n():
     assert abs((Fx[bin0] - 1j * Fy[bin0]) - np.exp(-2j * th).sum()) < 1e-9
 
 
+def test_tiny_spectra_against_brute_force():
+    """Brute force on a tiny input: 3 segments of 64 samples of seeded noise,
+    12 bins, two templates, global (t_i0 = i T) and segment-local (t_i0 = 0)
+    time maps.  Every term x_j exp(-2 pi i f_b delta_j) is evaluated at 40
+    digits with delta_j from Eq. (new_t) literally; the oracle must agree to
+    1e-12 of the spectrum's norm."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    fs, T, f_lo, n_b = 16.0, 4.0, 1.0, 12
+    n = int(fs * T)
+    x = srs_synth.white_noise(3 * n, seed=23)
+    betas = [4e-3, 2.5e-2]                 # (8/3) beta t < 1 over the 12 s
+    items = [(m, i) for m in range(2) for i in range(3)]
+    for local in (False, True):
+        F = oracle.spectra(x, fs, T, f_lo, n_b, betas, items, local=local)
+        for q, (m, i) in enumerate(items):
+            B = mpmath.mpf(betas[m])
+            tau = lambda t: -mpmath.mpf(3) / 5 * (1 - mpmath.mpf(8) / 3 * B * t) ** (mpmath.mpf(5) / 8) / B
+            t_i0 = mpmath.mpf(0 if local else i * T)
+            d = [tau(t_i0 + mpmath.mpf(j) / fs) - tau(t_i0) for j in range(n)]
+            ref = np.empty(n_b, dtype=complex)
+            for b in range(n_b):
+                fb = mpmath.mpf(f_lo) + mpmath.mpf(b) / T
+                acc = mpmath.mpc(0)
+                for j in range(n):
+                    acc += mpmath.mpf(float(x[i * n + j])) * mpmath.expjpi(-2 * fb * d[j])
+                ref[b] = complex(acc)
+            assert np.max(np.abs(F[q] - ref)) <= 1e-12 * np.linalg.norm(ref), (local, m, i)
+
+
 def test_uniform_limit_is_the_fft():
     """beta -> 0 makes delta_j = j / fs, so with the full mode set the NDFT is the
     plain DFT: F(f_b) = fft(x)[(b - N/2) mod N] for f_b = (b - N/2) / T."""
