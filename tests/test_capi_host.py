@@ -1,6 +1,7 @@
 """The C ABI library on the host: it builds, loads, exports every entry point
 of include/srs.h, and its planner (no GPU) agrees with the pinned oracle and
 rejects bad arguments with the documented status codes."""
+import ctypes
 import os
 import re
 
@@ -148,3 +149,24 @@ def test_component_rule_against_breadth_first_search():
             for c in comp[:top]:
                 expect[c] = True
         assert (component_cells(score, th, ns, top) == expect).all(), trial
+
+
+def test_without_a_gpu_compute_calls_fail_loudly():
+    """No CPU path: without a CUDA device, creating a context fails with
+    SRS_ERR_CUDA, and the entry points refuse a NULL context with SRS_ERR_ARG
+    instead of computing anything."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2609_12476_gb300 import Context
+    with pytest.raises(SrsError) as e:
+        Context(0)
+    assert e.value.status == -3          # SRS_ERR_CUDA
+    L = _capi.lib()
+    n = ctypes.c_int32(0)
+    p = Params().c()
+    x = np.zeros(7680 * 2)
+    mc = np.array([1e-2])
+    st = L.srs_search(None, x.ctypes.data, x.size, 1, mc.ctypes.data, 1, ctypes.byref(p), None, None,
+                      ctypes.byref(n), None)
+    assert st == -1                      # SRS_ERR_ARG
