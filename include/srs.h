@@ -243,8 +243,10 @@ srs_status srs_nsigma_threshold(const double* w, int32_t n_seg, double p_fa, dou
  * non-central chi^2 with 2 n_seg dof, evaluated exactly.  Weights w[n_seg]:
  * the signal's share of segment i is lambda_i = Lambda w_i / sum w (weights
  * that follow A_i^2 / S_i follow the signal power), and the weighted sum is
- * evaluated by Imhof's inversion of its characteristic function.  The paper
- * quotes Lambda_1 = 46.5 for n_seg = 1, p_fa = 1e-6, p_det = 0.95. */
+ * evaluated by Imhof's inversion of its characteristic function inside a
+ * bisection on Lambda (about 40 evaluations, each costing order n_seg^2).
+ * The paper quotes Lambda_1 = 46.5 for n_seg = 1, p_fa = 1e-6, p_det = 0.95.
+ * SRS_ERR_ARG for n_seg < 1, p_fa or p_det outside (0, 1) or a weight <= 0. */
 srs_status srs_detection_noncentrality(const double* w, int32_t n_seg, double p_fa, double p_det, double* lambda);
 
 /* Receiver operating characteristic of one signal (Sec. III.C, Fig. roc for a
