@@ -141,6 +141,7 @@ STATS_MUTANTS = [
 ]
 
 
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")     # a planted mistake may give a probability outside [0, 1]
 @pytest.mark.parametrize("name,orig,bad,catchers", STATS_MUTANTS, ids=[m[0] for m in STATS_MUTANTS])
 def test_stats_pins_catch_planted_mistake(monkeypatch, name, orig, bad, catchers):
     import types
