@@ -214,3 +214,13 @@ def test_library_detection_probability_rejects_bad_arguments():
         detection_probability(3, 1e-6, None, [1.0, 0.0, 2.0])
     with pytest.raises(SrsError):
         detection_probability(0, 1e-6)
+
+
+def test_library_two_routes_agree_on_long_tracks():
+    """On tracks too long for the 60-digit oracle, the library's two unequal-
+    weight routes check each other: the threshold from the Gamma mixture must
+    have false-alarm probability p_fa under Imhof's integral (no signal)."""
+    for n in (300, 2880):
+        w = np.linspace(1.0, 1.72, n)
+        for p_fa in (1e-2, 1e-4):
+            assert detection_probability(n, p_fa, None, w) == pytest.approx(p_fa, rel=1e-4)
