@@ -222,5 +222,5 @@ def test_library_two_routes_agree_on_long_tracks():
     have false-alarm probability p_fa under Imhof's integral (no signal)."""
     for n in (300, 2880):
         w = np.linspace(1.0, 1.72, n)
-        for p_fa in (1e-2, 1e-4):
-            assert detection_probability(n, p_fa, None, w) == pytest.approx(p_fa, rel=1e-4)
+        for p_fa in (1e-2, 1e-4, 1e-6):
+            assert detection_probability(n, p_fa, None, w) == pytest.approx(p_fa, rel=1e-5)
