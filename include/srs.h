@@ -233,7 +233,9 @@ srs_status srs_segment_spectra(srs_ctx* ctx, const void* strain, int64_t n_sampl
  * sum w^2 = 1), or equal weights when w is NULL.  Under H0,
  * n_sigma = sum w_i (E_i - 1) with E_i ~ Exp(1) (P_i ~ chi^2 with 2 dof):
  * for equal weights a scaled chi^2 with 2 n_seg dof, otherwise a generalised
- * chi^2, evaluated as a mixture of Gamma laws (Moschopoulos 1985).
+ * chi^2, evaluated as a mixture of Gamma laws (Moschopoulos 1985), or, for
+ * weights spread so widely that the mixture would need too many terms, by
+ * Imhof's inversion of the characteristic function (whichever is cheaper).
  * SRS_ERR_ARG for n_seg < 1, p_fa outside (0, 1) or a weight <= 0. */
 srs_status srs_nsigma_threshold(const double* w, int32_t n_seg, double p_fa, double* n_sigma_th);
 

@@ -85,8 +85,9 @@ struct ExpMixture {
   ld b = 1;
   std::vector<double> dh;   // delta_k e^shift
   double log_factor = 0;    // logC - shift: d_k = exp(log_factor) dh_k
+  bool converged = false;   // the terms left out are negligible (false: kcap was reached first)
 
-  explicit ExpMixture(const std::vector<ld>& w) {
+  ExpMixture(const std::vector<ld>& w, int64_t kcap) {
     n = (int64_t)w.size();
     b = w[0];
     for (ld v : w) b = std::min(b, v);
@@ -100,10 +101,12 @@ struct ExpMixture {
     dh.push_back(1.0);
     std::vector<double> gam(1, 0.0);
     double sum_dh = 1.0, peak = 1.0;
-    const int64_t kcap = 200000;
     auto total = [&]() { return std::exp(logC - shift + std::log(sum_dh)); };
     for (int64_t k = 1; k <= kcap; ++k) {
-      if (k % 16 == 0 && total() >= 1.0 - 1e-15) break;
+      if (k % 16 == 0 && total() >= 1.0 - 1e-15) {
+        converged = true;
+        break;
+      }
       double g = 0;
       for (size_t i = 0; i < w.size(); ++i) {
         rk[i] *= r[i];
@@ -122,7 +125,10 @@ struct ExpMixture {
         peak *= 1e-250;
         shift -= 250.0 * std::log(10.0);
       }
-      if (dk < 1e-30 * peak && dk < dh[(size_t)(k - 1)] && total() > 0.5) break;   // past the mode, negligible
+      if (dk < 1e-30 * peak && dk < dh[(size_t)(k - 1)] && total() > 0.5) {   // past the mode, negligible
+        converged = true;
+        break;
+      }
     }
     log_factor = logC - shift;
   }
@@ -156,11 +162,12 @@ ld noncentral_sf(int64_t n, ld lambda, ld x) {
 // P(sum_i w_i P_i > x) with P_i ~ chi^2_2(lam_i), by Imhof's integral over
 // [0, U]: 15-point Gauss-Legendre panels half a period of the integrand's
 // oscillation (about 4 pi / x) wide, and U where the tail bound
-// int_U^inf du / (u rho(u)) <= 1 / (n U^n prod w_i) drops below 1e-9.
+// int_U^inf du / (u rho(u)) <= 1 / (n U^n prod w_i) drops below `tail`.
 struct Imhof {
   const std::vector<double>& w;
   const std::vector<double>& lam;
   double x;
+  double tail = 1e-9;
 
   double integrand(double u) const {
     if (u <= 0) {
@@ -188,7 +195,7 @@ struct Imhof {
     const double n = (double)w.size();
     double lw = 0;
     for (double v : w) lw += std::log(v);
-    const double U = std::max(1.0, std::exp((-std::log(n * 1e-9) - lw) / n));
+    const double U = std::max(1.0, std::exp((-std::log(n * tail) - lw) / n));
     const double kPi = 3.14159265358979323846;
     const double width = std::min(2.0 * kPi / std::max(x, 1e-3), U);
     const long long panels = std::min<long long>(20000000, (long long)std::ceil(U / width));
@@ -266,11 +273,46 @@ srs_status srs_nsigma_threshold(const double* w, int32_t n_seg, double p_fa, dou
   } else {
     for (auto& v : ww) v = 1.0L / std::sqrt((ld)n_seg);
   }
-  ld sum_w = 0;
-  for (ld v : ww) sum_w += v;
+  ld sum_w = 0, b = ww[0];
+  for (ld v : ww) {
+    sum_w += v;
+    b = std::min(b, v);
+  }
   const ld mean = sum_w;   // E[sum w E] = sum w; its variance is sum w^2 = 1
-  const ExpMixture mix(ww);
-  auto sf = [&](ld q) { return mix.sf(q); };
+  // The mixture index K is a sum of independent negative binomials with
+  // success probabilities b / w_i: mean sum (w_i / b - 1), variance
+  // sum (w_i / b)(w_i / b - 1).  Building K terms costs about K^2 + K n;
+  // Imhof's integral costs about n times its panel count per evaluation.
+  // Weights spread so widely that the mixture costs more take the integral.
+  const ld n = (ld)n_seg;
+  ld km = 0, kv = 0, lw = 0;
+  for (ld v : ww) {
+    km += v / b - 1;
+    kv += (v / b) * (v / b - 1);
+    lw += std::log(v);
+  }
+  const ld k_need = km + 12.0L * std::sqrt(kv) + 100.0L;
+  const ld U = std::max(1.0L, std::exp((-std::log(n * 1e-14L) - lw) / n));
+  const ld x_typ = 2.0L * (mean + 5.0L);
+  const ld panels = std::max(1.0L, U * x_typ / (2.0L * 3.14159265358979323846L));
+  const ld cost_mix = k_need * k_need + k_need * n;
+  const ld cost_imhof = 60.0L * 15.0L * 10.0L * panels * n;   // evaluations x nodes x (atan, log) per weight
+  if (cost_mix <= cost_imhof) {
+    const ExpMixture mix(ww, (int64_t)std::min<ld>(2.0L * k_need + 1000.0L, 5e7L));
+    if (mix.converged) {
+      auto sf = [&](ld q) { return mix.sf(q); };
+      const ld q = invert_sf(sf, mean, mean + 10.0L, (ld)p_fa);
+      *n_sigma_th = (double)(q - sum_w);
+      return SRS_OK;
+    }
+  }
+  // sum w E > q  <=>  sum w P > 2 q with P = 2 E ~ chi^2_2
+  std::vector<double> wd(ww.begin(), ww.end()), zero(ww.size(), 0.0);
+  auto sf = [&](ld q) {
+    Imhof im{wd, zero, (double)(2.0L * q)};
+    im.tail = 1e-14;
+    return (ld)std::max(0.0, im.sf());
+  };
   const ld q = invert_sf(sf, mean, mean + 10.0L, (ld)p_fa);
   *n_sigma_th = (double)(q - sum_w);
   return SRS_OK;

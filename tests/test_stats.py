@@ -224,3 +224,13 @@ def test_library_two_routes_agree_on_long_tracks():
         w = np.linspace(1.0, 1.72, n)
         for p_fa in (1e-2, 1e-4, 1e-6):
             assert detection_probability(n, p_fa, None, w) == pytest.approx(p_fa, rel=1e-5)
+
+
+@pytest.mark.parametrize("n,spread", [(20, 1e3), (10, 1e4), (6, 1e6)])
+def test_library_threshold_for_widely_spread_weights(n, spread):
+    """Weights spread over 3 to 6 decades: the Gamma mixture would need far
+    too many terms, and the library takes Imhof's integral instead; the
+    threshold still matches the oracle's exact hypoexponential law."""
+    w = np.linspace(1.0, spread, n)
+    for p in (1e-3, 1e-6):
+        assert nsigma_threshold(n, p, w) == pytest.approx(stats.nsigma_threshold_weighted(w, p), rel=1e-8)
