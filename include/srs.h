@@ -236,7 +236,9 @@ srs_status srs_segment_spectra(srs_ctx* ctx, const void* strain, int64_t n_sampl
  * chi^2, evaluated as a mixture of Gamma laws (Moschopoulos 1985), or, for
  * weights spread so widely that the mixture would need too many terms, by
  * Imhof's inversion of the characteristic function (whichever is cheaper).
- * SRS_ERR_ARG for n_seg < 1, p_fa outside (0, 1) or a weight <= 0. */
+ * SRS_ERR_ARG for n_seg < 1, p_fa outside (0, 1) or a weight <= 0;
+ * SRS_ERR_UNSUPPORTED when both routes would take about 1e12 operations or
+ * more (unequal weights on tracks of about a million segments). */
 srs_status srs_nsigma_threshold(const double* w, int32_t n_seg, double p_fa, double* n_sigma_th);
 
 /* Detection non-centrality (Eq. non-centrality_threshold): the total

@@ -297,6 +297,7 @@ srs_status srs_nsigma_threshold(const double* w, int32_t n_seg, double p_fa, dou
   const ld panels = std::max(1.0L, U * x_typ / (2.0L * 3.14159265358979323846L));
   const ld cost_mix = k_need * k_need + k_need * n;
   const ld cost_imhof = 60.0L * 15.0L * 10.0L * panels * n;   // evaluations x nodes x (atan, log) per weight
+  if (std::min(cost_mix, cost_imhof) > 1e12L) return SRS_ERR_UNSUPPORTED;   // many minutes either way
   if (cost_mix <= cost_imhof) {
     const ExpMixture mix(ww, (int64_t)std::min<ld>(2.0L * k_need + 1000.0L, 5e7L));
     if (mix.converged) {

@@ -234,3 +234,13 @@ def test_library_threshold_for_widely_spread_weights(n, spread):
     w = np.linspace(1.0, spread, n)
     for p in (1e-3, 1e-6):
         assert nsigma_threshold(n, p, w) == pytest.approx(stats.nsigma_threshold_weighted(w, p), rel=1e-8)
+
+
+def test_library_refuses_weighted_thresholds_it_cannot_finish():
+    """Unequal weights on a two-million-segment track would take either route
+    far too long: the call says so instead of running for hours."""
+    n = 2_000_000
+    with pytest.raises(SrsError) as e:
+        nsigma_threshold(n, 1e-6, np.linspace(1.0, 2.0, n))
+    assert e.value.status == -5          # SRS_ERR_UNSUPPORTED
+    assert nsigma_threshold(n, 1e-6) > 0  # equal weights stay exact and cheap
