@@ -64,7 +64,7 @@ def nsigma_threshold_weighted(w, p_fa):
     w = np.asarray(w, dtype=np.float64)
     w = w / np.sqrt(np.sum(w * w))
     mean = float(np.sum(w))
-    lo, hi = mean, mean + 40.0
+    lo, hi = 0.0, mean + 40.0          # q > 0: the law of a sum of positive terms starts there
     f = lambda q: np.log(weighted_exp_sf(w, q)) - np.log(p_fa)
     q = brentq(f, lo, hi, xtol=1e-13)
     return q - mean

@@ -103,10 +103,6 @@ struct ExpMixture {
     double sum_dh = 1.0, peak = 1.0;
     auto total = [&]() { return std::exp(logC - shift + std::log(sum_dh)); };
     for (int64_t k = 1; k <= kcap; ++k) {
-      if (k % 16 == 0 && total() >= 1.0 - 1e-15) {
-        converged = true;
-        break;
-      }
       double g = 0;
       for (size_t i = 0; i < w.size(); ++i) {
         rk[i] *= r[i];
@@ -161,7 +157,7 @@ ld noncentral_sf(int64_t n, ld lambda, ld x) {
 
 // P(sum_i w_i P_i > x) with P_i ~ chi^2_2(lam_i), by Imhof's integral over
 // [0, U]: 15-point Gauss-Legendre panels half a period of the integrand's
-// oscillation (about 4 pi / x) wide, and U where the tail bound
+// fastest oscillation wide, and U where the tail bound
 // int_U^inf du / (u rho(u)) <= 1 / (n U^n prod w_i) drops below `tail`.
 struct Imhof {
   const std::vector<double>& w;
@@ -197,7 +193,11 @@ struct Imhof {
     for (double v : w) lw += std::log(v);
     const double U = std::max(1.0, std::exp((-std::log(n * tail) - lw) / n));
     const double kPi = 3.14159265358979323846;
-    const double width = std::min(2.0 * kPi / std::max(x, 1e-3), U);
+    // theta'(u) is at most x / 2 + sum w_i (1 + lambda_i / 2) in magnitude:
+    // panels of half its period
+    double rate = 0.5 * x;
+    for (size_t i = 0; i < w.size(); ++i) rate += w[i] * (1.0 + 0.5 * lam[i]);
+    const double width = std::min(kPi / std::max(rate, 1e-3), U);
     const long long panels = std::min<long long>(20000000, (long long)std::ceil(U / width));
     const double h = U / (double)panels;
     double acc = 0;
@@ -211,10 +211,21 @@ struct Imhof {
   }
 };
 
-// The q > lo with sf(q) = p for a decreasing sf, by bisection on log sf.
+// The q >= 0 with sf(q) = p for a decreasing sf with sf(0) = 1 (the law of
+// a sum of non-negative terms), by bisection on log sf; [lo, hi] is a first
+// bracket, widened as needed.
 template <typename F>
 ld invert_sf(F sf, ld lo, ld hi, ld p) {
-  while (sf(hi) > p) hi = lo + 2 * (hi - lo);
+  if (sf(lo) <= p) {
+    hi = lo;
+    lo = 0;
+  } else {
+    while (sf(hi) > p) {
+      const ld d = hi - lo;
+      lo = hi;
+      hi += 2 * d;
+    }
+  }
   const ld lp = std::log(p);
   for (int it = 0; it < 200; ++it) {
     const ld mid = 0.5L * (lo + hi);

@@ -25,7 +25,7 @@ def test_oracle_detection_noncentrality_matches_paper():
 
 def test_oracle_one_segment_threshold_closed_form():
     # one segment: n_sigma = E - 1 with E ~ Exp(1), so th = -ln(p_fa) - 1
-    for p in (1e-2, 1e-6, 1e-9):
+    for p in (0.9, 0.5, 1e-2, 1e-6, 1e-9):
         assert stats.nsigma_threshold_equal(1, p) == pytest.approx(-np.log(p) - 1.0, rel=1e-10)
         assert stats.nsigma_threshold_weighted([1.0], p) == pytest.approx(-np.log(p) - 1.0, rel=1e-9)
 
@@ -244,3 +244,26 @@ def test_library_refuses_weighted_thresholds_it_cannot_finish():
         nsigma_threshold(n, 1e-6, np.linspace(1.0, 2.0, n))
     assert e.value.status == -5          # SRS_ERR_UNSUPPORTED
     assert nsigma_threshold(n, 1e-6) > 0  # equal weights stay exact and cheap
+
+
+def test_library_thresholds_across_the_whole_p_fa_range():
+    """p_fa from 0.9 (a threshold below the mean) down to 1e-20, equal and
+    unequal weights, against the oracle."""
+    w = np.array([0.5, 0.9, 1.1, 1.6, 2.3])
+    for p in (0.9, 0.5, 1e-12, 1e-15, 1e-20):
+        assert nsigma_threshold(5, p, w) == pytest.approx(stats.nsigma_threshold_weighted(w, p), rel=1e-9, abs=1e-12)
+        assert nsigma_threshold(7, p) == pytest.approx(stats.nsigma_threshold_equal(7, p), rel=1e-9, abs=1e-12)
+    for n, p_fa, p_det in ((1, 0.5, 0.99), (3, 0.9, 0.95), (40, 0.7, 0.8), (1, 1e-12, 0.9999)):
+        assert detection_noncentrality(n, p_fa, p_det) == pytest.approx(stats.detection_noncentrality(n, p_fa, p_det),
+                                                                        rel=1e-9)
+
+
+def test_library_detection_probability_loud_and_uneven_signals():
+    """A loud signal (lambda 300 per segment) and signals concentrated in a few
+    segments: the integral's panels follow the fastest oscillation."""
+    w = np.array([0.5, 0.9, 1.1, 1.6, 2.3])
+    pf = [1e-9, 1e-6, 1e-3, 0.5]
+    for lam in ([300.0] * 5, [50.0, 0.0, 0.0, 0.0, 80.0], [20.0, 5.0, 1.0, 0.0, 3.0]):
+        got = detection_probability(5, pf, np.array(lam), w)
+        want = [stats.detection_probability(w, np.array(lam), p) for p in pf]
+        assert got == pytest.approx(want, rel=1e-6, abs=1e-9), lam
