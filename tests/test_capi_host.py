@@ -170,3 +170,42 @@ def test_without_a_gpu_compute_calls_fail_loudly():
     st = L.srs_search(None, x.ctypes.data, x.size, 1, mc.ctypes.data, 1, ctypes.byref(p), None, None,
                       ctypes.byref(n), None)
     assert st == -1                      # SRS_ERR_ARG
+
+
+def test_plan_invariants_on_random_configurations():
+    """Seeded random bands, rates, segment lengths, tolerances and banks: the
+    fine grid is a 2^a 3^b 5^c size of at least sigma n_bins, the width follows
+    the eps rule for sigma = 2, and beta and the segment counts match the oracle."""
+    r = np.random.default_rng(77)
+    done = 0
+    while done < 40:
+        fs = float(r.choice([64.0, 128.0, 256.0, 512.0]))
+        t_coh = float(r.choice([8.0, 16.0, 30.0, 60.0]))
+        f_lo = float(r.integers(5, int(fs / 2) - 10))
+        f_hi = float(min(fs / 2, f_lo + r.integers(2, 40)))
+        eps = float(10 ** r.uniform(-6.5, -2))
+        mc = np.exp(r.uniform(np.log(5e-4), np.log(1e-1), size=5))
+        n_total = int(r.integers(1, 200))
+        p = Params(fs=fs, t_coh=t_coh, f_lo=f_lo, f_hi=f_hi, f_ref=f_lo, eps=eps)
+        try:
+            info, beta, nseg = srs_plan(p, mc, int(n_total * t_coh * fs))
+        except SrsError as e:
+            if e.status == -6:      # a template coalesces inside its first segment (Sec. II duration)
+                assert min(3.0 / (8.0 * oracle.beta(m, f_lo)) for m in mc) < t_coh, (fs, f_lo, mc)
+            else:                   # e.g. a band too wide for the shared-memory FFT
+                assert e.status in (-1, -5), (fs, t_coh, f_lo, f_hi, eps, str(e))
+            continue
+        done += 1
+        n_fine, n_bins = info["n_fine"], info["n_bins"]
+        assert n_bins == round((f_hi - f_lo) * t_coh)
+        m = n_fine
+        for q in (2, 3, 5):
+            while m % q == 0:
+                m //= q
+        assert m == 1 and n_fine >= info["sigma"] * n_bins - 1e-9
+        if abs(info["sigma"] - 2.0) < 1e-12:
+            assert info["w"] == int(np.ceil(np.log10(1.0 / eps))) + 1
+        for k in range(5):
+            b = oracle.beta(mc[k], f_lo)
+            assert beta[k] == pytest.approx(b, rel=1e-13)
+            assert nseg[k] == oracle.nseg(b, f_lo, f_hi, t_coh, n_total)
