@@ -50,7 +50,9 @@
  *   - SRS_ERR_DOMAIN: a computed segment reaches coalescence
  *     (1 - (8/3) beta t <= 0, Sec. II), possible with cut_segments = 0.
  *   - SRS_ERR_UNSUPPORTED: a combination this build does not run (e.g. the
- *     mixed form below its FP32 floor, eps < 2e-7).
+ *     mixed form below its FP32 floor, eps < 2e-7, or a template chirping
+ *     too fast for the mixed form's anchor spacing, such as Mc = 0.1 in a
+ *     band that starts at 80 Hz or above; SRS_PLAIN_FP64 runs those).
  *   - SRS_ERR_CUDA / SRS_ERR_OOM: a CUDA call failed / device memory ran out;
  *     the context stays usable for smaller problems.
  *   - Threading: one context per host thread.
