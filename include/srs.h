@@ -52,7 +52,8 @@
  *   - SRS_ERR_UNSUPPORTED: a combination this build does not run (e.g. the
  *     mixed form below its FP32 floor, eps < 2e-7, or a template chirping
  *     too fast for the mixed form's anchor spacing, such as Mc = 0.1 in a
- *     band that starts at 80 Hz or above; SRS_PLAIN_FP64 runs those).
+ *     band that starts at 80 Hz or above; SRS_PLAIN_FP64 runs those; or
+ *     more than 2^31 - 1 segment spectra in one call).
  *   - SRS_ERR_CUDA / SRS_ERR_OOM: a CUDA call failed / device memory ran out;
  *     the context stays usable for smaller problems.
  *   - Threading: one context per host thread.

@@ -183,6 +183,10 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
     }
     pl.n_spectra += spectra_mode ? (seg_end - seg_begin) : ns;
   }
+  // work items, their first-segment rows and the kernels' item indices are
+  // 32-bit: one call covers at most 2^31 - 1 segment spectra
+  if (pl.n_spectra > (int64_t)INT32_MAX)
+    return fail(SRS_ERR_UNSUPPORTED, "more than 2^31 - 1 segment spectra in one call; split the template list");
 
   // ES kernel width and shape from eps (Barnett et al. 2019): with
   // oversampling sigma the aliasing error falls like exp(-pi w sqrt(1 - 1/sigma));

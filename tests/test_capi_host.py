@@ -209,3 +209,20 @@ def test_plan_invariants_on_random_configurations():
             b = oracle.beta(mc[k], f_lo)
             assert beta[k] == pytest.approx(b, rel=1e-13)
             assert nseg[k] == oracle.nseg(b, f_lo, f_hi, t_coh, n_total)
+
+
+def test_plan_refuses_more_spectra_than_32_bit_items_hold():
+    """A year of data for the lightest template (Mc = 5e-4 stays in band for
+    its first N segments, about 83 days): enough copies of it to pass 2^31 - 1
+    segment spectra are refused before any table is built (the largest count
+    that fits is planned too, but that builds 2 GB of host tables, so the test
+    plans a smaller one)."""
+    n = int(365 * 86400 * 256)
+    _, _, nseg = srs_plan(Params(), [5e-4], n)
+    per = int(nseg[0])
+    fit = (2 ** 31 - 1) // per
+    with pytest.raises(SrsError) as e:
+        srs_plan(Params(), np.full(fit + 1, 5e-4), n)
+    assert e.value.status == -5
+    info, _, _ = srs_plan(Params(), np.full(fit // 64, 5e-4), n)
+    assert info["n_spectra"] == (fit // 64) * per
