@@ -396,7 +396,9 @@ srs_status srs_cube_whiten(srs_ctx* ctx, float* cube, int32_t n_beta, int32_t n_
  * candidates (template_idx = row r, bin = column n), ordered by value
  * descending, then row, then column.  Chunks may come in any order between a
  * FIRST and a LAST call; a single call may carry both flags.  Uses t_coh,
- * f_lo, f_hi, top_k and io_on_device of params.  report: slide_ms. */
+ * f_lo, f_hi, top_k and io_on_device of params.  report: slide_ms.
+ * SRS_ERR_UNSUPPORTED when n_beta * n_bins reaches 2^31 (32-bit track cells)
+ * or the track table or map would hold more than 2e9 entries. */
 srs_status srs_stack_slide(srs_ctx* ctx, const float* cube, int32_t seg_begin, int32_t seg_end,
                            int32_t n_seg_total, const srs_bank* bank, const srs_slide_grid* grid,
                            const srs_params* params, int32_t flags, float* nsigma_map,

@@ -48,7 +48,10 @@ srs_status check_grid(srs_ctx* ctx, const srs_slide_grid* g, const srs_params* p
   return SRS_OK;
 }
 
-srs_status check_s_eff(srs_ctx* ctx, const srs_slide_grid* g, const srs_bank* bank, int32_t n_bins) {
+srs_status check_cells_and_s_eff(srs_ctx* ctx, const srs_slide_grid* g, const srs_bank* bank, int32_t n_bins) {
+  // track cells k n_bins + j are 32-bit on the device
+  if ((long long)bank->n_beta * n_bins > 2147483647LL)
+    return set_err(ctx, SRS_ERR_UNSUPPORTED, "n_beta * n_bins must stay below 2^31 for the stack-slide's cell table");
   if (!g->s_eff) return SRS_OK;
   const size_t n = (size_t)bank->n_beta * n_bins;
   for (size_t q = 0; q < n; ++q)
@@ -245,7 +248,7 @@ srs_status stack_slide_impl(srs_ctx* ctx, const float* cube, int32_t seg_begin, 
   if (s != SRS_OK) return s;
   if ((s = check_bank(ctx, bank)) != SRS_OK) return s;
   if ((s = check_grid(ctx, g, p)) != SRS_OK) return s;
-  if ((s = check_s_eff(ctx, g, bank, n_bins)) != SRS_OK) return s;
+  if ((s = check_cells_and_s_eff(ctx, g, bank, n_bins)) != SRS_OK) return s;
   if (!cube) return set_err(ctx, SRS_ERR_ARG, "cube is NULL");
   if (flags & ~(SRS_SLIDE_FIRST | SRS_SLIDE_LAST)) return set_err(ctx, SRS_ERR_ARG, "unknown flags");
   const bool first = flags & SRS_SLIDE_FIRST, last = flags & SRS_SLIDE_LAST;
@@ -303,7 +306,7 @@ srs_status slide_search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples
   if ((s = check_slide_params(ctx, p, &n_bins)) != SRS_OK) return s;
   if ((s = check_bank(ctx, bank)) != SRS_OK) return s;
   if ((s = check_grid(ctx, g, p)) != SRS_OK) return s;
-  if ((s = check_s_eff(ctx, g, bank, n_bins)) != SRS_OK) return s;
+  if ((s = check_cells_and_s_eff(ctx, g, bank, n_bins)) != SRS_OK) return s;
   if (!cands || !n_cands) return set_err(ctx, SRS_ERR_ARG, "cands and n_cands are required");
   if (budget < 0) return set_err(ctx, SRS_ERR_ARG, "cube_budget_bytes must be >= 0");
   if (p->precision != SRS_MIXED) return set_err(ctx, SRS_ERR_UNSUPPORTED, "the power cube runs the mixed form only");
