@@ -318,6 +318,7 @@ srs_status srs_nsigma_threshold(const double* w, int32_t n_seg, double p_fa, dou
       return SRS_OK;
     }
   }
+  if (cost_imhof > 1e12L) return SRS_ERR_UNSUPPORTED;   // the mixture did not converge either
   // sum w E > q  <=>  sum w P > 2 q with P = 2 E ~ chi^2_2
   std::vector<double> wd(ww.begin(), ww.end()), zero(ww.size(), 0.0);
   auto sf = [&](ld q) {
