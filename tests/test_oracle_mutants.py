@@ -34,6 +34,13 @@ MUTANTS = [
     ("local map referenced to the data start", "double t_i0 = J->local ? 0.0 : (double)i * (double)J->n_s / J->fs;",
      "double t_i0 = (double)i * (double)J->n_s / J->fs;",
      ["test_tiny_spectra_against_brute_force"]),
+    ("literal resampled-time exponent", "pow(1.0 - (8.0 / 3.0) * beta * t, 5.0 / 8.0) / beta;",
+     "pow(1.0 - (8.0 / 3.0) * beta * t, 3.0 / 8.0) / beta;",
+     ["test_tau_literal_matches_high_precision_eq_new_t", "test_tau_derivative_is_frequency_ratio",
+      "test_tau_difference_is_the_segment_local_delta"]),
+    ("literal resampled time without 1/beta", "pow(1.0 - (8.0 / 3.0) * beta * t, 5.0 / 8.0) / beta;",
+     "pow(1.0 - (8.0 / 3.0) * beta * t, 5.0 / 8.0);",
+     ["test_tau_derivative_is_frequency_ratio"]),
 ]
 
 
@@ -58,6 +65,38 @@ def test_pins_pass_on_the_unmodified_oracle(tmp_path, monkeypatch):
     monkeypatch.setattr(oracle, "_LIB", oracle.load(str(so)))
     for _, _, _, catchers in MUTANTS:
         for pin in catchers:
+            getattr(pins, pin)()
+
+
+# Mistakes planted in the numpy half of the oracle (power, segment sum,
+# n_sigma), caught by the semicoherent pins.
+SUM_MUTANTS = [
+    ("one segment short", "for i in range(int(nsegs[m]))]", "for i in range(int(nsegs[m]) - 1)]",
+     ["test_semicoherent_exact_chirp_closed_form", "test_semicoherent_against_per_item_brute_force"]),
+    ("powers summed into the wrong row", "S[m] += P[k]", "S[0] += P[k]",
+     ["test_semicoherent_exact_chirp_closed_form", "test_semicoherent_against_per_item_brute_force"]),
+    ("segments counted from the second", "items = [(m, i) for m in range(len(betas)) for i in range(int(nsegs[m]))]",
+     "items = [(m, i + 1) for m in range(len(betas)) for i in range(int(nsegs[m]))]",
+     ["test_semicoherent_against_per_item_brute_force"]),
+    ("n_sigma divided by N", "(S - 2.0 * nseg_) / (2.0 * np.sqrt(nseg_))", "(S - 2.0 * nseg_) / (2.0 * nseg_)",
+     ["test_semicoherent_exact_chirp_closed_form", "test_semicoherent_against_per_item_brute_force"]),
+    ("power without its factor 2", "return 2.0 * np.abs(F) ** 2 / n_s", "return np.abs(F) ** 2 / n_s",
+     ["test_semicoherent_exact_chirp_closed_form", "test_semicoherent_against_per_item_brute_force"]),
+]
+
+
+@pytest.mark.parametrize("name,orig,bad,catchers", SUM_MUTANTS, ids=[m[0] for m in SUM_MUTANTS])
+def test_sum_pins_catch_planted_mistake(monkeypatch, name, orig, bad, catchers):
+    import types
+    src = open(oracle.__file__).read()
+    assert src.count(orig) == 1, name
+    mod = types.ModuleType("oracle_mutant")
+    mod.__package__ = "oracle"
+    exec(compile(src.replace(orig, bad), "oracle_mutant.py", "exec"), mod.__dict__)
+    for fn in ("power", "n_sigma", "semicoherent"):
+        monkeypatch.setattr(oracle, fn, getattr(mod, fn))
+    for pin in catchers:
+        with pytest.raises(AssertionError):
             getattr(pins, pin)()
 
 

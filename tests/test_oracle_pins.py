@@ -221,3 +221,102 @@ def test_topk_order_against_brute_force():
     v, m, b = oracle.topk(M, 20)
     brute = sorted(((-M[i, j], i, j) for i in range(7) for j in range(9)))[:20]
     assert [(-a, i, j) for a, i, j in brute] == list(zip(v, m, b))
+
+
+def test_tau_literal_matches_high_precision_eq_new_t():
+    """orc_tau is Eq. (new_t) as printed (t0 = 0); at 60 digits the same formula
+    must agree with the FP64 evaluation to a few ulps of tau itself."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 60
+    for mc, t in ((5e-4, 0.0), (5e-4, 86399.0), (1e-2, 4321.5), (1e-1, 1000.0), (3e-2, 7199.99609375)):
+        b = oracle.beta(mc, 40.0)
+        B = mpmath.mpf(b)
+        ref = -mpmath.mpf(3) / 5 * (1 - mpmath.mpf(8) / 3 * B * mpmath.mpf(t)) ** (mpmath.mpf(5) / 8) / B
+        got = oracle.tau(b, t)
+        assert abs(got - float(ref)) <= 4e-16 * abs(float(ref))
+
+
+def test_tau_derivative_is_frequency_ratio():
+    """d tau / dt = f(t) / f0 (Sec. III.B: the resampled signal is monochromatic at
+    f0), with f from Eq. (f), a separate formula."""
+    for mc in (1e-2, 1e-1):
+        b = oracle.beta(mc, 40.0)
+        for t, h in ((0.0, 0.25), (500.0, 0.25), (900.0, 0.125)):
+            slope = (oracle.tau(b, t + h) - oracle.tau(b, t - h)) / (2 * h)
+            assert slope == pytest.approx(oracle.freq(b, 40.0, t) / 40.0, rel=1e-7)
+
+
+def test_tau_difference_is_the_segment_local_delta():
+    """tau(t_i0 + s) - tau(t_i0) from the literal Eq. (new_t) equals the oracle's
+    cancellation-free delta to the rounding of the large constant -(3/5)/beta."""
+    for mc, t_i0 in ((2e-2, 3000.0), (1e-1, 600.0), (5e-4, 80000.0)):
+        b = oracle.beta(mc, 40.0)
+        big = abs(oracle.tau(b, t_i0))
+        for s in (0.5, 13.0, 29.99609375):
+            diff = oracle.tau(b, t_i0 + s) - oracle.tau(b, t_i0)
+            assert abs(diff - oracle.delta(b, t_i0, s)[0]) <= 8e-16 * big
+
+
+def test_semicoherent_exact_chirp_closed_form():
+    """Sec. III.C on a noiseless chirp resampled with its own beta: in each of the
+    template's first N_seg segments the chirp is a tone at f0 (Sec. III.B), so the
+    power at f0's bin is A^2 n_s / 2 (up to the O(1/n_s) cross term), the sum is
+    S = N_seg A^2 n_s / 2 and n_sigma = (S - 2 N_seg) / (2 sqrt(N_seg)) (equal
+    weights).  Two templates with different segment counts: the exact one (row 1)
+    and a mismatched one (row 0), whose power spreads over many bins."""
+    fs, T, f_lo, f_hi = 256.0, 30.0, 40.0, 60.0
+    mc, f0, A = 3e-2, 45.0, 0.05
+    n_s = int(fs * T)
+    x = srs_synth.chirp(6 * n_s, fs, mc, f0, A)
+    b_true = oracle.beta(mc, f0)
+    betas = [3.0 * b_true, b_true]
+    nsegs = [3, 5]
+    n_b = int((f_hi - f_lo) * T)
+    S, ns = oracle.semicoherent(x, fs, T, f_lo, n_b, betas, nsegs)
+    b0 = int(round((f0 - f_lo) * T))
+    N = nsegs[1]
+    S_ref = N * A * A * n_s / 2.0
+    assert S.shape == (2, n_b) and ns.shape == (2, n_b)
+    assert S[1, b0] == pytest.approx(S_ref, rel=5e-3)
+    assert ns[1, b0] == pytest.approx((S_ref - 2.0 * N) / (2.0 * np.sqrt(N)), rel=1e-2)
+    # off the peak the exact row holds leakage only: its n_sigma is -sqrt(N) (S ~ 0)
+    off = np.delete(S[1], b0)
+    assert off.max() < 1e-3 * S[1, b0]
+    assert np.allclose(np.delete(ns[1], b0), -np.sqrt(N), atol=1e-2)
+    # the mismatched template's power stays below the exact one's everywhere,
+    # and its row is normalised by its own segment count (sum of P >= 0)
+    assert S[0].max() < 0.5 * S[1, b0]
+    assert ns[0].min() >= -np.sqrt(nsegs[0]) - 1e-12
+
+
+def test_semicoherent_against_per_item_brute_force():
+    """The semicoherent sum assembled item by item on a tiny input: each (m, i)
+    spectrum is summed term by term at 40 digits with delta from Eq. (new_t) as
+    printed, its power is 2|F|^2/n_s (Eq. normalized_power), template m adds its
+    first N_seg(m) segments, n_sigma = (S - 2N)/(2 sqrt N) (Eqs. weights,
+    semicoherent_statistic).  Seeded noise plus a chirp, so every segment's
+    contribution differs."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    fs, T, f_lo, n_b = 16.0, 4.0, 1.0, 10
+    n = int(fs * T)
+    x = srs_synth.white_noise(5 * n, seed=29) + srs_synth.chirp(5 * n, fs, 40.0, 3.0, 0.7)
+    betas = [4e-3, 1.5e-2]                 # (8/3) beta t < 1 over the 20 s
+    nsegs = [2, 4]
+    S, ns = oracle.semicoherent(x, fs, T, f_lo, n_b, betas, nsegs)
+    S_ref = np.zeros((2, n_b))
+    for m in range(2):
+        B = mpmath.mpf(betas[m])
+        tau = lambda t: -mpmath.mpf(3) / 5 * (1 - mpmath.mpf(8) / 3 * B * t) ** (mpmath.mpf(5) / 8) / B
+        for i in range(nsegs[m]):
+            t_i0 = mpmath.mpf(i * T)
+            d = [tau(t_i0 + mpmath.mpf(j) / fs) - tau(t_i0) for j in range(n)]
+            for b in range(n_b):
+                fb = mpmath.mpf(f_lo) + mpmath.mpf(b) / T
+                acc = mpmath.mpc(0)
+                for j in range(n):
+                    acc += mpmath.mpf(float(x[i * n + j])) * mpmath.expjpi(-2 * fb * d[j])
+                S_ref[m, b] += float(2 * abs(acc) ** 2 / n)
+    ns_ref = np.array([(S_ref[m] - 2.0 * nsegs[m]) / (2.0 * np.sqrt(nsegs[m])) for m in range(2)])
+    assert np.max(np.abs(S - S_ref)) <= 1e-11 * np.max(S_ref)
+    assert np.max(np.abs(ns - ns_ref)) <= 1e-11 * np.max(np.abs(ns_ref))
