@@ -5,13 +5,15 @@ segment sum, n_sigma, top-k) over the workload's templates and segments.
 Metric: segment spectra per second (templates x segments) at eps = 1e-6.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload semicoherent_2h|batched_6h|large_24h|learned_6h|
+                  [--workload semicoherent_2h|batched_6h|large_24h|learned_6h|learned_24h|
                               stackslide_6h|stackslide_24h]
 
-Default workload: 2 h of float64 strain at 256 Hz (240 segments of 30 s),
-64 chirp-mass templates log-spaced 2e-2..5e-2 Msun, 40-60 Hz, eps 1e-6,
-top-32, one injected chirp; synthetic seeded data.  Inputs are smaller than
-L2, so L2 is flushed (256 MB write) before every timed step.
+Default workload (large_24h): 24 h of float32 strain at 256 Hz (2880
+segments of 30 s, 88 MB), 4096 chirp-mass templates log-spaced 5e-4..1e-1
+Msun whose in-band segment counts run from 35 to 2880 (7 236 457 segment
+spectra per search), 40-60 Hz, eps 1e-6, top-32, 64 injected chirps;
+synthetic seeded data.  Every step writes the n_sigma map (4096 x 600 float32)
+and the candidates; L2 is flushed (256 MB write) before every timed step.
 
 The stackslide workloads time the two-stage search instead: a power cube of
 every segment under each of the 69 local resampling templates, then the
@@ -51,11 +53,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="semicoherent_2h",
-                    choices=sorted(srs_synth.WORKLOADS) + sorted(srs_synth.SLIDE_WORKLOADS) + ["learned_6h"])
+    ap.add_argument("--workload", default="large_24h",
+                    choices=sorted(srs_synth.WORKLOADS) + sorted(srs_synth.SLIDE_WORKLOADS) + ["learned_6h",
+                                                                                                  "learned_24h"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 and cuFFT comparisons")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-two-stage", action="store_true", help="skip the two-stage (cube + stack-slide) measurement")
+    ap.add_argument("--sweep", action="store_true",
+                    help="learned workloads: also measure the other proposal rules (time and recall)")
+    ap.add_argument("--templates-every", type=int, default=1,
+                    help="keep every S-th template of the workload (a reduced case for ncu captures; the JSON "
+                         "line then describes that case, not the benchmark)")
     return ap.parse_args()
 
 
@@ -63,8 +71,10 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def workload(name, rank):
+def workload(name, rank, every=1):
     w = srs_synth.make_workload(name, seed=srs_synth.WORKLOADS[name]["seed"] + rank)
+    if every > 1:
+        w["mc"] = np.ascontiguousarray(w["mc"][::every])
     return w
 
 
@@ -185,7 +195,7 @@ def run_reference(args):
             "warmup": warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic (seeded N(0,1) noise + 0PN chirps)",
             "config": {"workload": args.workload, "templates": int(len(w["mc"])),
-                       "spectra_per_step": (int(w["bank"][2]) * int(w["n_total"])) if slide_wl else sum_spectra(w),
+                       "spectra_per_step": (int(w["bank"][2]) * int(w["n_total"])) if slide_wl else oracle_spectra(w),
                        "eps": w["eps"], "l2": "oracle on host cores (no GPU)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
                              "sample": info["sample"]},
@@ -193,10 +203,13 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def sum_spectra(w):
-    from paper_2609_12476_gb300 import srs_plan
-    info, _, _ = srs_plan(params_for(w, 1), w["mc"], w["n_samples"])
-    return int(info["n_spectra"])
+def oracle_spectra(w):
+    """Segment spectra of one search, counted by the oracle's segment rule (the
+    reference arm loads nothing of the library)."""
+    import oracle
+    n_tot = int(w["n_samples"] // round(w["t_coh"] * w["fs"]))
+    return int(sum(oracle.nseg(oracle.beta(m, w["f_ref"]), w["f_ref"], w["f_hi"], w["t_coh"], n_tot)
+                   for m in w["mc"]))
 
 
 def run_ours(args):
@@ -209,7 +222,7 @@ def run_ours(args):
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = workload(args.workload, rank)
+    w = workload(args.workload, rank, args.templates_every)
     p = params_for(w, SRS_MIXED)
     info, _, nseg = srs_plan(p, w["mc"], w["n_samples"])
     n_spec = int(info["n_spectra"])
@@ -221,10 +234,12 @@ def run_ours(args):
     xd = torch.from_numpy(np.ascontiguousarray(w["strain"])).to(dev)
     torch.cuda.synchronize()
     n_bins = info["n_bins"]
-    out = {"map": None, "cands": torch.empty((p.top_k, 3), dtype=torch.int32, device=dev)}
+    # every step writes the n_sigma map and the candidates (the search's outputs)
+    out = {"map": torch.empty((len(w["mc"]), n_bins), dtype=torch.float32, device=dev),
+           "cands": torch.empty((p.top_k, 3), dtype=torch.int32, device=dev)}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
-        ctx.search(xd, w["mc"], p, stat_map=False, out=out)
+        ctx.search(xd, w["mc"], p, out=out)
     torch.cuda.synchronize()
     barrier(world)
     clocks = Clocks(local) if rank == 0 else None
@@ -232,12 +247,15 @@ def run_ours(args):
     torch.cuda.synchronize()
     # steps are queued back to back (srs_search_async); each step's events
     # bracket its own device sequence, the L2 flush runs between them
+    # the NVTX range marks the timed steps for ncu (--nvtx --nvtx-include "timed/")
+    torch.cuda.nvtx.range_push("timed")
     for s in range(args.steps):
         flush.zero_()
         ev[s][0].record(stream)
         ctx.search_async(xd, w["mc"], p, out)
         ev[s][1].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     rep = ctx.sync()
     ck = clocks.stop() if clocks else None
     spread_ms = [rep["spread_ms"]]                # mean over the timed steps (library events)
@@ -247,15 +265,17 @@ def run_ours(args):
     value = world * n_spec * args.steps / (total_ms * 1e-3)
 
     # end to end through the public API with pinned host buffers: every step
-    # uploads its strain and reads its candidates back (srs_search_async with
-    # host pointers: the next step's upload overlaps this step's search)
+    # uploads its strain and reads its n_sigma map and candidates back
+    # (srs_search_async with host pointers: the next step's upload overlaps
+    # this step's search; the map copies are stream-ordered into one buffer)
     from paper_2609_12476_gb300 import CAND_DTYPE
     host = torch.from_numpy(np.ascontiguousarray(w["strain"])).pin_memory()
     hnp = host.numpy()
-    houts = [{"map": None,
+    hmap = torch.zeros((len(w["mc"]), n_bins), dtype=torch.float32).pin_memory().numpy()
+    houts = [{"map": hmap,
               "cands": torch.zeros(p.top_k * 3, dtype=torch.int32).pin_memory().numpy().view(CAND_DTYPE)}
              for _ in range(args.steps)]
-    ref_c, _, _ = ctx.search(hnp, w["mc"], p, stat_map=False)
+    ref_c, ref_map, _ = ctx.search(hnp, w["mc"], p)
     for _ in range(2):
         ctx.search_async(hnp, w["mc"], p, houts[0])
     ctx.sync()
@@ -268,11 +288,16 @@ def run_ours(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     if not np.array_equal(houts[-1]["cands"]["template_idx"][:4], ref_c["template_idx"][:4]):
         raise RuntimeError("end-to-end candidates differ from the synchronous search")
+    # the two calls may run differently tuned layouts (FP32 partial sums over
+    # other segment chunks), so the maps agree to FP32 rounding, not bit for bit
+    if not np.allclose(hmap, ref_map, rtol=1e-5, atol=1e-5):
+        raise RuntimeError("end-to-end n_sigma map differs from the synchronous search")
     max_seg = int(max(nseg))
     h2d = max_seg * int(info["n_s"]) * hnp.itemsize
-    d2h = p.top_k * 12
+    d2h = p.top_k * 12 + hmap.nbytes
     e2e = {"value": world * n_spec * args.steps / e2e_s, "unit": UNIT,
-           "api": "srs_search_async from pinned host memory, one srs_sync after the last step",
+           "api": "srs_search_async from pinned host memory (strain in; n_sigma map and candidates out), "
+                  "one srs_sync after the last step",
            "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
@@ -283,7 +308,9 @@ def run_ours(args):
         spread_avg = float(np.mean(spread_ms))
         sm_mhz = (ck or {}).get("sm_mhz") or (pk or {}).get("sm_max_mhz", 2070.0)
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-        traffic = profile_traffic("k_mixed_semicoherent_2h.md") if args.workload == "semicoherent_2h" else None
+        # committed ncu figures describe the full workload's launch
+        prof = "k_mixed_%s.md" % args.workload if args.templates_every == 1 else None
+        traffic = profile_traffic(prof) if prof else None
         roof = xu_roofline(n_spec, n_s, w_taps, spread_avg, n_sm, sm_mhz, traffic)
         # FP32-FMA view: the NUFFT's algorithmic FP32 operations per spectrum
         # against the FMA pipes (per sample w taps x 9 + 6; FFT 5 n log2 n;
@@ -295,18 +322,21 @@ def run_ours(args):
                     "frac": achieved_tf / peak_tf, "traffic": traffic,
                     "peak_source": "128 FP32 lanes x %d SMs x 2 flop x %.0f MHz (median SM clock in the timed region)"
                                    % (n_sm, sm_mhz)}
-        # the HBM view the metric asks for: FP32 samples the kernel reads per
-        # spectrum (the working copy) + partial sums it writes
-        alg_bytes = n_spec * n_s * 4 + int(rep["n_items"]) * n_bins * 4
+        # the HBM view the metric asks for: one read of the strain sample per
+        # spectrum in the strain's own type (8 B float64, 4 B float32) + the
+        # partial sums the kernel writes
+        x_bytes = int(np.asarray(w["strain"]).itemsize)
+        alg_bytes = n_spec * n_s * x_bytes + int(rep["n_items"]) * n_bins * 4
         ach = alg_bytes / (spread_avg * 1e-3) / 1e9
         hbm_peak = pk["hbm_gbs"] if pk else 6800.0
         roof_hbm = {"kernel": "k_mixed", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                     "frac": ach / hbm_peak, "traffic": traffic,
+                    "algorithmic_bytes": "%d B per strain sample per spectrum (%s) + 4 B partial sums per "
+                                         "(item, bin)" % (x_bytes, w["dtype"]),
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback 6.8 TB/s"}
         # issue view: warp instructions per launch (ncu, committed summary) per
         # kernel time against 4 warp instructions per clock per SM
-        inst = profile_traffic("k_mixed_semicoherent_2h.md", key="inst_executed_per_launch") \
-            if args.workload == "semicoherent_2h" else None
+        inst = profile_traffic(prof, key="inst_executed_per_launch") if prof else None
         roof_issue = None
         if inst:
             ach_i = inst / (spread_avg * 1e-3) / 1e12
@@ -318,10 +348,10 @@ def run_ours(args):
         if not args.no_plain:
             plain = time_plain(ctx, xd, w, stream, flush, n_spec, n_bins, info, pk)
         fftcmp = None
-        if not args.no_plain and args.workload == "semicoherent_2h":
-            fftcmp = time_fft_comparison(ctx, xd, w, flush)
+        if not args.no_plain:
+            fftcmp = time_fft_comparison(ctx, xd, w, flush, seg_end=max(2, 7168 // len(w["mc"])))
         two = None
-        if not args.no_two_stage and args.workload == "semicoherent_2h" and world == 1:
+        if not args.no_two_stage and world == 1:
             two = two_stage_measure(ctx, stream, dev, flush, "stackslide_24h", 10, 3, pk, host_e2e=False)
             two.pop("_w")
         cpu = None if (args.no_cpu or world > 1) else cpu_oracle_rate(w, ctx=ctx)
@@ -329,12 +359,16 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded N(0,1) noise + 0PN chirps)",
-                "config": {"workload": args.workload, "templates": int(len(w["mc"])), "spectra_per_step": n_spec,
+                "config": {"workload": args.workload + ("" if args.templates_every == 1
+                                                        else " (every %d-th template)" % args.templates_every),
+                           "templates": int(len(w["mc"])), "spectra_per_step": n_spec,
                            "strain": "%d samples %s at %g Hz" % (w["n_samples"], w["dtype"], w["fs"]),
                            "eps": w["eps"], "w": info["w"], "n_fine": info["n_fine"], "chunk": rep["chunk"],
                            "cta_threads": rep["cta_threads"], "ctas_per_sm": rep["ctas_per_sm"],
                            "staging": "tma" if rep["staging"] else "global loads",
                            "precision": "mixed: FP64 time-map anchors, FP32 spread/FFT/power",
+                           "outputs": "n_sigma map [%d x %d] float32 + top-%d candidates per step"
+                                      % (len(w["mc"]), n_bins, p.top_k),
                            "l2": "flushed (256 MB write) before every timed step"},
                 "roofline": roof, "roofline_fma": roof_fma, "roofline_hbm": roof_hbm, "roofline_issue": roof_issue,
                 "clocks": ck,
@@ -391,25 +425,34 @@ def ctx_stream(stream):
     return stream.cuda_stream
 
 
-def time_plain(ctx, xd, w, stream, flush, n_spec, n_bins, info, pk, steps=3):
+def time_plain(ctx, xd, w, stream, flush, n_spec, n_bins, info, pk):
+    """The same search in the plain FP64 form (map and candidates written).
+    About 1.4e5 spectra/s, so a search of more than 1e5 spectra is timed once,
+    after a warm-up call on the first eight templates."""
     import torch
     from paper_2609_12476_gb300 import SRS_PLAIN_FP64
     pp = params_for(w, SRS_PLAIN_FP64)
-    out = {"map": None, "cands": torch.empty((pp.top_k, 3), dtype=torch.int32, device=xd.device)}
-    ctx.search(xd, w["mc"], pp, stat_map=False, out=out)
+    big = n_spec > 100000
+    steps = 1 if big else 3
+    out = {"map": torch.empty((len(w["mc"]), n_bins), dtype=torch.float32, device=xd.device),
+           "cands": torch.empty((pp.top_k, 3), dtype=torch.int32, device=xd.device)}
+    if big:
+        ctx.search(xd, w["mc"][:8], pp, stat_map=False)
+    else:
+        ctx.search(xd, w["mc"], pp, out=out)
     torch.cuda.synchronize()
     tot, sp = 0.0, []
     for _ in range(steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        _, rep = ctx.search(xd, w["mc"], pp, stat_map=False, out=out)
+        _, rep = ctx.search(xd, w["mc"], pp, out=out)
         b.record(stream)
         torch.cuda.synchronize()
         tot += a.elapsed_time(b)
         sp.append(rep["spread_ms"])
     elem = xd.element_size()
-    ach = n_spec * int(info["n_s"]) * elem / (np.mean(sp) * 1e-3) / 1e9
+    ach = n_spec * int(info["n_s"]) * elem / (np.mean(sp) * 1e-3) / 1e9   # one strain read per spectrum
     hbm_peak = pk["hbm_gbs"] if pk else 6800.0
     return {"value": n_spec * steps / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / steps,
             "kernel": "k_plain", "hbm_achieved_gbs": ach, "hbm_frac": ach / hbm_peak, "steps": steps}
@@ -462,6 +505,7 @@ def two_stage_measure(ctx, stream, dev, flush, name, steps, warmup, pk, host_e2e
     torch.cuda.synchronize()
     clocks = Clocks(dev.index or 0)
     tot, cube_ms, slide_ms = 0.0, [], []
+    torch.cuda.nvtx.range_push("timed")
     for _ in range(steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -472,6 +516,7 @@ def two_stage_measure(ctx, stream, dev, flush, name, steps, warmup, pk, host_e2e
         tot += a.elapsed_time(b)
         cube_ms.append(rep["spread_ms"])
         slide_ms.append(rep["slide_ms"])
+    torch.cuda.nvtx.range_pop()
     ck = clocks.stop()
     n_spec = int(rep["n_spectra"])
     reads = int(rep["slide_reads"])
@@ -488,7 +533,16 @@ def two_stage_measure(ctx, stream, dev, flush, name, steps, warmup, pk, host_e2e
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     n_s = int(round(w["t_coh"] * w["fs"]))
     hbm_peak = pk["hbm_gbs"] if pk else 6800.0
-    ach = reads * 4 / (sl * 1e-3) / 1e9
+    # compulsory bytes of one stack-slide launch (one cube chunk): the cube
+    # read once, the track table (int32 [rows][segments]) and the per-row
+    # lengths and t0 fractions read once, one 8-byte top-k key written per
+    # template
+    n_b = int(round((w["f_hi"] - w["f_lo"]) * w["t_coh"]))
+    n_rows = int(w["rows_mc"].size)
+    cube_bytes = n_spec * n_b * 4
+    comp_bytes = cube_bytes + n_rows * int(w["n_total"]) * 4 + n_rows * (4 + 8) + n_tmpl * 8
+    ach = comp_bytes / (sl * 1e-3) / 1e9
+    ach_l2 = reads * 4 / (sl * 1e-3) / 1e9
     res = {"workload": name, "value": n_spec * steps / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / steps,
            "steps": steps, "warmup": warmup, "spectra_per_step": n_spec,
            "config": {"strain": "%d samples %s at %g Hz" % (w["n_samples"], w["dtype"], w["fs"]),
@@ -506,13 +560,20 @@ def two_stage_measure(ctx, stream, dev, flush, name, steps, warmup, pk, host_e2e
                                                         "k_mixed cube traffic_bytes_per_launch")
                                         if name == "stackslide_24h" else None),
            "roofline_slide": {"kernel": "k_stack_slide", "bound": "hbm", "achieved": ach, "peak": hbm_peak,
-                              "unit": "GB/s", "frac": ach / hbm_peak,
+                              "unit": "GB/s", "frac": ach / hbm_peak, "bytes_per_launch": comp_bytes,
                               "traffic": profile_traffic("two_stage_24h.md", ("srs_slide.cu", "srs_device.cuh"),
                                                          "k_stack_slide traffic_bytes_per_launch")
                               if name == "stackslide_24h" else None,
                               "peak_source": "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback 6.8 TB/s",
-                              "algorithmic_bytes": "power reads x 4 B: every template reads its track's powers "
-                                                   "once (no reuse between templates, as in Sec. VI's cost model)"},
+                              "algorithmic_bytes": "compulsory: the power cube read once (%d MB), the track table "
+                                                   "read once, one 8 B top-k key written per template"
+                                                   % (cube_bytes >> 20)},
+           "slide_load_path": {"kernel": "k_stack_slide", "achieved": ach_l2, "unit": "GB/s",
+                               "bytes": "power reads x 4 B: every template reads its track's powers once, as in "
+                                        "Sec. VI's cost model; L1 and L2 serve most of them (neighbouring t0 "
+                                        "columns and chirp masses share tracks), so this is load-path "
+                                        "throughput, not HBM traffic",
+                               "power_reads": reads},
            "clocks": ck, "gpu_launches": int(rep["kernel_launches"]) * steps}
     if host_e2e:
         host = torch.from_numpy(np.ascontiguousarray(w["strain"])).pin_memory().numpy()
@@ -580,7 +641,8 @@ def run_two_stage(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded N(0,1) noise + 0PN chirps entering the band)",
                 "config": dict(res["config"], workload=args.workload),
-                "roofline": res["roofline_cube"], "roofline_slide": res["roofline_slide"], "clocks": res["clocks"],
+                "roofline": res["roofline_cube"], "roofline_slide": res["roofline_slide"],
+                "slide_load_path": res["slide_load_path"], "clocks": res["clocks"],
                 "gpu_launches": res["gpu_launches"], "e2e": res.get("e2e"), "cpu_baseline": cpu,
                 "cube_ms": res["cube_ms"], "slide_ms": res["slide_ms"], "templates_per_s": res["templates_per_s"],
                 "slide_ms_amplitude_weights": res["slide_ms_amplitude_weights"],
@@ -606,17 +668,41 @@ def max_over_ranks(v, world):
     return float(t.item())
 
 
+# Learned-proposal workloads: observation time, injections per timed map, and
+# the realisations x injections of the two recall evaluations.
+LEARNED = {
+    "learned_6h": {"t_obs": 21600.0, "per_map": 8, "evals": ((8, 8), (2, 64)), "plain_subset": False},
+    "learned_24h": {"t_obs": 86400.0, "per_map": 64, "evals": ((2, 64),), "plain_subset": True},
+}
+
+# Proposal rules of the --sweep: (name, calibration FAR, proposal keyword arguments)
+SWEEP = [
+    ("every cell above threshold, FAR 1e-3, +-1 row", 1e-3, {}),
+    ("every cell above threshold, FAR 1e-4, +-1 row", 1e-4, {}),
+    ("every cell above threshold, FAR 1e-4, own row", 1e-4, {"fine_rows": 0}),
+    ("best 3 cells per group, FAR 1e-3, +-1 row", 1e-3, {"component_top": 3}),
+    ("coarse n_sigma peaks (+-4, +-16), FAR 1e-3, own row", 1e-3,
+     {"nms": (4, 16), "nms_by_nsigma": True, "fine_rows": 0}),
+    ("coarse n_sigma peaks (+-8, +-32), FAR 1e-3, own row", 1e-3,
+     {"nms": (8, 32), "nms_by_nsigma": True, "fine_rows": 0}),
+]
+
+
 def run_learned(args):
-    """Learned proposal on the 6 h search shape: coarse bank 256, fine bank
-    4096 (5e-4..1e-1 Msun), network trained on 20k patches made by the search
-    itself, proposal threshold at a 1e-3 noise false-alarm rate.  One timed
-    step = one proposal search (coarse search, network scores, refinement)
-    over a 6 h realisation with 8 injections; value = full-grid-equivalent
-    spectra (the 4096-template search's) per second.  The full fine search is
-    timed on the same realisations."""
+    """Learned proposal on the 6 h or 24 h search shape: coarse bank 256, fine
+    bank 4096 (5e-4..1e-1 Msun), network trained on 20k patches made by the
+    search itself from maps of the same length, proposal threshold at a 1e-3
+    noise false-alarm rate.  One timed step = one proposal search (coarse
+    search, network scores, refinement) over a new realisation; value =
+    full-grid-equivalent spectra (the 4096-template search's) per second.
+    The full fine search is timed on the same realisations.  On 24 h the
+    recall of the plain FP64 form is measured on the fine templates that
+    decide it (+-2 around each injection's own).  --sweep adds the time and
+    recall of the other proposal rules (the measured Pareto front)."""
     import torch
     from paper_2609_12476_gb300 import Context, Params, proposal
 
+    L = LEARNED[args.workload]
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream(0)
     torch.cuda.set_stream(stream)
@@ -624,7 +710,7 @@ def run_learned(args):
     p = Params(eps=1e-6, top_k=32)
     coarse = proposal.log_bank(5e-4, 1e-1, 256)
     fine = proposal.log_bank(5e-4, 1e-1, 4096)
-    t_obs = 21600.0
+    t_obs = L["t_obs"]
     t0 = time.time()
     mlp, losses, _, n_tr = proposal.train_proposal(ctx, coarse, p, t_obs, n_patches=20000, seed=1)
     sth, nth = proposal.calibrate(ctx, mlp, coarse, p, t_obs, 10, seed=5, far=1e-3)
@@ -633,7 +719,7 @@ def run_learned(args):
 
     def strain_for(k):
         # a new realisation per step, made on the device outside the timed events
-        inj, _ = proposal.injections_on_grid(np.random.default_rng(123 + k), coarse, p, 8, (0.01, 0.1))
+        inj, _ = proposal.injections_on_grid(np.random.default_rng(123 + k), coarse, p, L["per_map"], (0.01, 0.1))
         return ctx.make_strain(n, p.fs, 50000 + k, inj, f_hi=p.f_hi)
 
     torch.cuda.synchronize()
@@ -668,22 +754,41 @@ def run_learned(args):
         b.record(stream)
         torch.cuda.synchronize()
         full_ms += a.elapsed_time(b)
-    evr = proposal.evaluate(ctx, mlp, sth, nth, coarse, fine, p, t_obs, 8, 8, seed=9)
-    evd = proposal.evaluate(ctx, mlp, sth, nth, coarse, fine, p, t_obs, 2, 64, seed=19)
+    recall = {}
+    for (n_real, per_real), seed in zip(L["evals"], (9, 19)):
+        ev_ = proposal.evaluate(ctx, mlp, sth, nth, coarse, fine, p, t_obs, n_real, per_real, seed=seed,
+                                plain_subset=L["plain_subset"])
+        keep = [k for k in ev_ if k.startswith("recall") or k.endswith("cells") or k.startswith("plain")
+                or k.endswith("_ms")]
+        recall["recall_%d_per_map" % per_real] = {k: ev_[k] for k in keep}
+    pareto = None
+    if args.sweep:
+        pareto = []
+        n_real, per_real = L["evals"][-1]
+        for name, far, kw in SWEEP:
+            s_th, n_th = proposal.calibrate(ctx, mlp, coarse, p, t_obs, 10, seed=5, far=far,
+                                            nms=kw.get("nms", proposal.NO_NMS),
+                                            component_top=kw.get("component_top", 0),
+                                            nms_by_nsigma=kw.get("nms_by_nsigma", False))
+            e = proposal.evaluate(ctx, mlp, s_th, n_th, coarse, fine, p, t_obs, n_real, per_real, seed=29,
+                                  baselines=False, **kw)
+            pareto.append({"rule": name, "proposal_ms_per_map": e["proposal_ms"] / n_real,
+                           "full_ms_per_map": e["full_ms"] / n_real, "recall_proposal": e["recall_proposal"],
+                           "recall_full": e["recall_full"], "proposal_cells": e["proposal_cells"] / n_real,
+                           "proposed_coarse": e["proposed_coarse"] / n_real})
     line = {"metric": METRIC + " (full-grid equivalent, learned proposal)", "value": value, "unit": UNIT,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded N(0,1) noise + 0PN chirps, made on the device)",
-            "config": {"workload": "learned_6h", "coarse_templates": 256, "fine_templates": 4096,
-                       "strain": "6 h f32 at 256 Hz, 8 injections per step", "proposal_far": 1e-3,
-                       "train_patches": n_tr, "train_and_calibrate_s": train_s,
-                       "l2": "inputs larger than L2 (a new 22 MB realisation per step, 4096-template tables)"},
+            "config": {"workload": args.workload, "coarse_templates": 256, "fine_templates": 4096,
+                       "strain": "%g h f32 at 256 Hz, %d injections per step" % (t_obs / 3600, L["per_map"]),
+                       "proposal_far": 1e-3, "train_patches": n_tr, "train_and_calibrate_s": train_s,
+                       "l2": "inputs larger than L2 (a new realisation per step, 4096-template tables)"},
             "clocks": ck, "full_fine_search": {"value": full_spec * args.steps / (full_ms * 1e-3), "unit": UNIT,
                                                "ms_per_step": full_ms / args.steps},
             "proposal_report_mean": {k: float(np.mean([r[k] for r in reps])) for k in reps[0]},
-            "recall_8_per_map": {k: evr[k] for k in evr if k.startswith("recall") or k.endswith("cells")},
-            "recall_64_per_map": {k: evd[k] for k in evd if k.startswith("recall") or k.endswith("cells")},
-            "final_train_loss": float(losses[-1])}
+            "final_train_loss": float(losses[-1]), "pareto": pareto}
+    line.update(recall)
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -692,7 +797,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "learned_6h":
+    elif args.workload in LEARNED:
         run_learned(args)
     elif args.workload in srs_synth.SLIDE_WORKLOADS:
         run_two_stage(args)

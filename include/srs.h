@@ -556,9 +556,11 @@ srs_status srs_search_proposed(srs_ctx* ctx, const void* strain, int64_t n_sampl
  *                complex double (re, im interleaved), caller-owned
  *   err_msg      optional host buffer of err_len bytes for a message
  * Returns SRS_ERR_ARG (with a message) when the request needs more scratch
- * than SRS_STATIC_SCRATCH_BYTES (many templates x segments, or long float64
- * strain), when a pointer is not a device pointer, or for any argument
- * srs_segment_spectra() would reject.  The first call on a device looks up
+ * than SRS_STATIC_SCRATCH_BYTES (many templates x segments, or many float64
+ * segments: only [seg_begin, seg_end) is converted, 4 B per sample), when
+ * strain or F is not device memory of the current device, or for any
+ * argument srs_segment_spectra() would reject.  SRS_NO_TMA=1 selects the
+ * same sample staging as in srs_segment_spectra().  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) for that device; make
  * that first call before any stream capture.  Every call reuses the same
  * array and clears what must start at zero; calls that overlap on the GPU

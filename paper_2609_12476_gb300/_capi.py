@@ -739,17 +739,24 @@ def segment_spectra_static(strain, mc, seg_begin, seg_end, params, F=None, strea
     import torch
     if not _is_torch_cuda(strain):
         raise TypeError("strain must be a CUDA tensor")
+    if not strain.is_contiguous():
+        raise ValueError("strain must be contiguous")
     mc = np.ascontiguousarray(mc, dtype=np.float64)
     n_bins = int(round((params.f_hi - params.f_lo) * params.t_coh))
+    shape = (mc.size, int(seg_end) - int(seg_begin), n_bins)
     if F is None:
-        F = torch.empty((mc.size, seg_end - seg_begin, n_bins), dtype=torch.complex128, device=strain.device)
+        F = torch.empty(shape, dtype=torch.complex128, device=strain.device)
+    elif (not _is_torch_cuda(F) or F.dtype != torch.complex128 or tuple(F.shape) != shape
+          or not F.is_contiguous() or F.device != strain.device):
+        raise ValueError("F must be a contiguous complex128 tensor of shape %s on %s" % (shape, strain.device))
     s = stream if stream is not None else torch.cuda.current_stream(strain.device)
     p = params.c()
     p.io_on_device = 1
     buf = ctypes.create_string_buffer(256)
-    st = lib().srs_segment_spectra_static(ctypes.c_void_p(s.cuda_stream), strain.data_ptr(), strain.numel(),
-                                          _dtype_code(strain), mc.ctypes.data, mc.size, int(seg_begin),
-                                          int(seg_end), ctypes.byref(p), F.data_ptr(), buf, 256)
+    with torch.cuda.device(strain.device):
+        st = lib().srs_segment_spectra_static(ctypes.c_void_p(s.cuda_stream), strain.data_ptr(), strain.numel(),
+                                              _dtype_code(strain), mc.ctypes.data, mc.size, int(seg_begin),
+                                              int(seg_end), ctypes.byref(p), F.data_ptr(), buf, 256)
     if st != SRS_OK:
         raise SrsError(st, buf.value.decode())
     return F

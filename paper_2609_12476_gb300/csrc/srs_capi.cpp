@@ -93,8 +93,9 @@ MixedArgs mixed_args(const Plan& pl, const srs_ctx* ctx, int seg_begin, int seg_
   a.kc = (float)pl.k_c;
   a.kc_int = (pl.k_c >= 1.0 && pl.k_c < 1073741824.0 && pl.k_c == std::floor(pl.k_c)) ? (int)pl.k_c : 0;
   a.inv_ns = (float)(1.0 / (double)pl.n_s);
-  a.es_beta_log2e = (float)(pl.beta_es * 1.4426950408889634074);
+  a.es_beta_log2e = mixed_es_e(pl);
   a.two_over_w = (float)(2.0 / pl.w);
+  mixed_fixed_point(pl, a);
   a.corr = ctx->corr.as<float>();
   a.tw = ctx->tw.as<float>();
   a.order = pl.order.empty() ? nullptr : ctx->order.as<int>();
@@ -139,7 +140,7 @@ AnchorArgs anchor_args(const Plan& pl) {
 srs_status upload_tables(srs_ctx* ctx, const Plan& pl) {
   const bool mixed = pl.precision == SRS_MIXED;
   if (mixed) {
-    std::vector<float> corr(pl.corr.begin(), pl.corr.end());
+    const std::vector<float> corr = mixed_corr(pl);
     std::vector<float> tw(2 * pl.n_fine);
     for (int m = 0; m < pl.n_fine; ++m) { tw[2 * m] = (float)pl.tw_re[m]; tw[2 * m + 1] = (float)pl.tw_im[m]; }
     SRS_CK(ctx->corr.ensure(corr.size() * 4), "alloc corr");

@@ -160,7 +160,6 @@ srs_status cube_device(srs_ctx* ctx, const float* s32, int64_t n_samples, const 
 // Clear / read the device error flag of the mixed spreader.
 srs_status clear_err_flag(srs_ctx* ctx);
 srs_status read_err_flag(srs_ctx* ctx);
-bool tma_disabled();
 
 }  // namespace srs
 

@@ -15,6 +15,17 @@ __device__ __forceinline__ uint32_t frac_to_u32(double f) {  // f in [0, 1)
   return (uint32_t)(v & 0xffffffffLL);
 }
 
+// f in [0, 1) as 64-bit fixed point (the double's 53 bits), high and low words.
+__device__ __forceinline__ void frac_to_u64(double f, uint32_t& hi, uint32_t& lo) {
+  const double h = floor(f * 4294967296.0);
+  const double r = f * 4294967296.0 - h;                       // exact: f 2^32 has the same ulp as f
+  long long l = __double2ll_rn(r * 4294967296.0);
+  long long hh = (long long)h;
+  if (l >= 4294967296LL) { l -= 4294967296LL; ++hh; }
+  hi = (uint32_t)(hh & 0xffffffffLL);
+  lo = (uint32_t)l;
+}
+
 // Coefficients of the two binomial series of the time map in y = 8/3 beta s / A
 // (Eq. new_t around a point where 1 - 8/3 beta t = A):
 //   1 - (1 - y)^(5/8) = sum_{k>=1} c_k y^k,  c_1 = 5/8, c_{k+1} = c_k (k - 5/8) / (k + 1)
@@ -67,7 +78,7 @@ __device__ __forceinline__ Anchor compute_anchor(double b, int i, int ai, const 
   const double A = a * (1.0 - x);                                 // 1 - 8/3 beta (t_i0 + s0)
   Anchor an;
   double psi = d0 * inv_t;
-  an.psi0 = frac_to_u32(psi - floor(psi));
+  frac_to_u64(psi - floor(psi), an.psi0, an.psi0lo);
   const double E1 = e1 * inv_fs;                                  // d delta / d sample
   double P1 = E1 * inv_t;
   double P1f = P1 - floor(P1);
@@ -75,7 +86,7 @@ __device__ __forceinline__ Anchor compute_anchor(double b, int i, int ai, const 
   an.n1 = (uint32_t)((long long)N1 & 0xffffffffLL);
   an.p1lo = (float)(P1f - N1 * 2.3283064365386962890625e-10);
   double th = aa.f_c * d0;
-  an.th0 = frac_to_u32(th - floor(th));
+  frac_to_u64(th - floor(th), an.th0, an.th0lo);
   double M1 = aa.f_c * E1;
   double M1f = M1 - floor(M1);
   double Mr = rint(M1f * 4294967296.0);
@@ -87,34 +98,99 @@ __device__ __forceinline__ Anchor compute_anchor(double b, int i, int ai, const 
   const double E3 = E2 * r * (11.0 / 9.0);
   const double E4 = E3 * r * (19.0 / 12.0);
   const double E5 = E4 * r * (9.0 / 5.0);
-  an.p2 = (float)(E2 * inv_t);
+  an.q2 = __double2ll_rn(E2 * inv_t * 18446744073709551616.0);       // 2^-64 periods / sample^2
+  an.kq2 = __double2ll_rn(aa.f_c * E2 * 18446744073709551616.0);     // 2^-64 cycles / sample^2
   an.p3 = (float)(E3 * inv_t);
   an.p4 = (float)(E4 * inv_t);
   an.p5 = (float)(E5 * inv_t);
-  an.pad0 = 0.f;
-  an.pad1 = 0.f;
+  an.pad = 0u;
   return an;
+}
+
+// A small FP32 value (periods or cycles) in 2^-64 fixed point, two's complement.
+__device__ __forceinline__ unsigned long long fix64(float v) {
+  return (unsigned long long)__float2ll_rn(v * 18446744073709551616.0f);
+}
+
+// One phase of an anchor's span in 64-bit fixed point (2^-64 of a period or
+// cycle, wrapping at whole periods): value at sample l of
+//   c0 + l c1 + q l^2 + s (P3 l^3 + P4 l^4 + P5 l^5)
+// with c0 64-bit and c1 32-bit fixed point, c1lo the FP32 residual of c1, q the 64-bit
+// quadratic coefficient and s a scale of the higher FP32 terms (1 for the
+// fine-grid phase, k_c for the demodulation phase).
+__device__ __forceinline__ unsigned long long anchor_phase64(const Anchor& A, unsigned long long c0, uint32_t c1,
+                                                             float c1lo, long long q, float s, int l) {
+  const float lf = (float)l;
+  const float q3 = s * fmaf(fmaf(A.p5, lf, A.p4), lf, A.p3) * (lf * lf * lf);
+  // unsigned products: the phase wraps at whole periods (mod 2^64)
+  const unsigned long long L = (unsigned long long)l;
+  return c0 + ((unsigned long long)((uint32_t)l * c1) << 32) + L * fix64(c1lo) +
+         (unsigned long long)q * (L * L) + fix64(q3);
+}
+
+// The anchor's phases at its own sample in 64-bit fixed point.
+__device__ __forceinline__ unsigned long long anchor_psi0(const Anchor& A) {
+  return ((unsigned long long)A.psi0 << 32) | A.psi0lo;
+}
+__device__ __forceinline__ unsigned long long anchor_th0(const Anchor& A) {
+  return ((unsigned long long)A.th0 << 32) | A.th0lo;
 }
 
 // Phase of sample l (0 <= l < span) of an anchor's span: the fine-grid phase
 // Psi (unsigned 32-bit fixed point, periods of t_coh) and the demodulation
-// phase th = f_c delta mod 1 in [-0.5, 0.5] (cycles).
-__device__ __forceinline__ void mixed_phase(const Anchor& A, int l, float kc, uint32_t& Psi, float& th) {
-  const float lf = (float)l;
-  const float cq = fmaf(fmaf(fmaf(A.p5, lf, A.p4), lf, A.p3), lf, A.p2) * (lf * lf);
-  const float cpsi = fmaf(A.p1lo, lf, cq);
-  Psi = A.psi0 + (uint32_t)l * A.n1 + (uint32_t)__float2int_rn(cpsi * 4294967296.0f);
-  const float cth = fmaf(A.m1lo, lf, kc * cq);
-  float t = (float)(int32_t)(A.th0 + (uint32_t)l * A.m1) * 2.3283064365386963e-10f + cth;
-  th = t - rintf(t);
+// phase f_c delta mod 1 (unsigned 32-bit fixed point, cycles).
+__device__ __forceinline__ void mixed_phase_fix(const Anchor& A, int l, float kc, uint32_t& Psi, uint32_t& Th) {
+  const unsigned long long p = anchor_phase64(A, anchor_psi0(A), A.n1, A.p1lo, A.q2, 1.0f, l);
+  const unsigned long long t = anchor_phase64(A, anchor_th0(A), A.m1, A.m1lo, A.kq2, kc, l);
+  Psi = (uint32_t)((p + 0x80000000ull) >> 32);
+  Th = (uint32_t)((t + 0x80000000ull) >> 32);
 }
 
-// The fine-grid phase alone (periods, 32-bit fixed point) of sample l.
-__device__ __forceinline__ uint32_t mixed_psi(const Anchor& A, int l) {
-  const float lf = (float)l;
-  const float cq = fmaf(fmaf(fmaf(A.p5, lf, A.p4), lf, A.p3), lf, A.p2) * (lf * lf);
-  const float cpsi = fmaf(A.p1lo, lf, cq);
-  return A.psi0 + (uint32_t)l * A.n1 + (uint32_t)__float2int_rn(cpsi * 4294967296.0f);
+// The same with the demodulation phase as th in [-0.5, 0.5) cycles.
+__device__ __forceinline__ void mixed_phase(const Anchor& A, int l, float kc, uint32_t& Psi, float& th) {
+  uint32_t Th;
+  mixed_phase_fix(A, l, kc, Psi, Th);
+  th = (float)(int32_t)Th * 2.3283064365386963e-10f;
+}
+
+// Per-lane time map of the spreader.  A lane walks consecutive samples; from
+// the anchor it takes one phase at its first sample and the phase's first,
+// second and third forward differences, all in 64-bit fixed point (2^-64 of
+// a period or cycle), and then steps sample by sample with integer adds
+// (exact apart from the fourth and higher differences of the anchor's
+// polynomial, below 1e-12 periods over a lane's run).
+struct LaneMap {
+  unsigned long long v, d1, d2, d3;
+  __device__ __forceinline__ void step() {
+    v += d1;
+    d1 += d2;
+    d2 += d3;
+  }
+};
+
+// Seed a LaneMap at sample l of an anchor's span (see anchor_phase64 for the
+// arguments): forward differences of the polynomial written out term by term,
+//   D(l^2) = 2l + 1, D^2(l^2) = 2,
+//   D(l^3) = 3l^2 + 3l + 1, D^2(l^3) = 6l + 6, D^3(l^3) = 6,
+//   D(l^4) = 4l^3 + 6l^2 + 4l + 1, D^2(l^4) = 12l^2 + 24l + 14, D^3(l^4) = 24l + 36,
+//   D(l^5) = 5l^4 + 10l^3 + 10l^2 + 5l + 1, D^2(l^5) = 20l^3 + 60l^2 + 70l + 30,
+//   D^3(l^5) = 60l^2 + 180l + 150.
+__device__ __forceinline__ LaneMap lane_map(const Anchor& A, unsigned long long c0, uint32_t c1, float c1lo,
+                                            long long q, float s, int l) {
+  const float lf = (float)l, l2 = lf * lf, l3 = l2 * lf;
+  const float p3 = s * A.p3, p4 = s * A.p4, p5 = s * A.p5;
+  const float d1 = p3 * fmaf(3.f, l2 + lf, 1.f) + p4 * fmaf(4.f, l3 + lf, fmaf(6.f, l2, 1.f)) +
+                   p5 * fmaf(5.f, fmaf(l2, l2, lf), fmaf(10.f, l3 + l2, 1.f));
+  const float d2 = p3 * fmaf(6.f, lf, 6.f) + p4 * fmaf(12.f, l2, fmaf(24.f, lf, 14.f)) +
+                   p5 * fmaf(20.f, l3, fmaf(60.f, l2, fmaf(70.f, lf, 30.f)));
+  const float d3 = 6.f * p3 + p4 * fmaf(24.f, lf, 36.f) + p5 * fmaf(60.f, l2, fmaf(180.f, lf, 150.f));
+  const unsigned long long L = (unsigned long long)l, Q = (unsigned long long)q;
+  LaneMap m;
+  m.v = anchor_phase64(A, c0, c1, c1lo, q, s, l);
+  m.d1 = ((unsigned long long)c1 << 32) + fix64(c1lo) + Q * (2 * L + 1) + fix64(d1);
+  m.d2 = 2 * Q + fix64(d2);
+  m.d3 = fix64(d3);
+  return m;
 }
 
 // Top-k sort key of a map cell: larger value first, then smaller flat index

@@ -34,15 +34,20 @@ struct Item {
 // Eq. new_t expanded around the anchor):
 //   delta(l_a + l)/t_coh = psi0 + P1 l + P2 l^2 + P3 l^3 + P4 l^4 + P5 l^5   [periods]
 //   f_c * delta(l_a + l)   = th0 + M1 l + k_c (P2 l^2 + ... + P5 l^5)          [cycles]
-// psi0, th0: fractions of a period / cycle as unsigned 32-bit fixed point;
-// n1, m1: the linear coefficients as 32-bit fixed point (mod 1) with the
-// rounding residual kept in p1lo / m1lo (FP32); P2..P5 in FP32.
+// psi0, th0: fractions of a period / cycle as 64-bit fixed point, split into
+// the high (psi0, th0) and low (psi0lo, th0lo) 32 bits; n1, m1: the linear
+// coefficients as 32-bit fixed point (mod 1) with the rounding residual kept
+// in p1lo / m1lo (FP32); the quadratic coefficients P2 and k_c P2 as signed
+// 64-bit fixed point in 2^-64 periods / cycles per sample^2 (q2, kq2);
+// P3..P5 in FP32.
 struct Anchor {
   uint32_t psi0, n1, th0, m1;
-  float p1lo, m1lo, p2, p3;
-  float p4, p5, pad0, pad1;
+  long long q2, kq2;
+  float p1lo, m1lo, p3, p4;
+  float p5;
+  uint32_t psi0lo, th0lo, pad;
 };
-static_assert(sizeof(Anchor) == 48, "anchor layout");
+static_assert(sizeof(Anchor) == 64, "anchor layout");
 
 // Everything the kernels need about one call, resolved on the host.
 struct Plan {
@@ -82,6 +87,10 @@ struct Plan {
 // Sec. II Eq. (beta) for chirp mass mc (Msun) at frequency f (Hz), in 1/s.
 double chirp_beta(double mc, double f);
 
+// True when SRS_NO_TMA=1 is set in the environment: the mixed spreader then
+// stages samples without TMA bulk copies (srs_capi.cpp).
+bool tma_disabled();
+
 // Host planner (srs_plan.cpp).  Returns SRS_OK or an error with `msg` set.
 // With betas_in != NULL the templates are given by their chirp parameters
 // (mc is ignored); with local = true every segment is resampled with a 0PN
@@ -91,6 +100,12 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
                      int32_t seg_end, Plan& out, std::string& msg,
                      const double* betas_in = nullptr, bool local = false);
 void fill_info(const Plan& pl, srs_plan_info* info);
+// Deconvolution factors of the mixed form in FP32: the plan's factors times
+// 2^-E (E = beta_ES log2 e), the constant of the ES kernel that the spreader
+// leaves out of its taps.
+std::vector<float> mixed_corr(const Plan& pl);
+// beta_ES log2 e as the mixed-form kernels use it (FP32).
+float mixed_es_e(const Plan& pl);
 // Threads per CTA of the mixed spreader and the run / span / anchor layout that
 // follows: one FP64 anchor per 32 lanes (per lanes128 lanes in 128-thread CTAs).
 void set_cta(Plan& pl, int32_t threads);

@@ -255,130 +255,120 @@ __global__ void k_wait_selftest(int* __restrict__ err) {
   }
 }
 
-// Tap inputs of one sample: first fine-grid cell l0 (wrapped into [0, n)),
-// a0 = E (1 - z0) and b0 = E (1 + z0) for the kernel argument z0 of tap 0
-// (E = beta log2 e, so that tap t's exponent is sqrt((a0 - t H)(b0 + t H))
-// in base 2 with H = 2 E / W), and the demodulated sample
-// c = 2^-E x exp(-2 pi i th) (the 2^-E of the ES kernel folded in).
-struct TapIn {
-  int l0;
-  float a0, b0, cre, cim;
-};
-
-// Per-lane constants of the tap inputs.
-struct TapConst {
-  float es_scale;  // 2^-E
-  float eh32;      // E (2 / W) 2^-32: kernel argument per 2^-32 cell
-  float two_e;     // 2 E
-};
-
-template <bool INT_KC>
-__device__ __forceinline__ TapIn tap_inputs(const Anchor& A, const float* __restrict__ xs, int j, int l_base,
-                                            int W, const TapConst& k, const MixedArgs& a) {
-  uint32_t Psi;
-  float sn, cs;
-  if (INT_KC) {
-    // f_c t_coh = k_c is a whole number: f_c delta = k_c (delta / t_coh), so the
-    // demodulation phase is k_c * Psi modulo one cycle, exactly
-    Psi = mixed_psi(A, j - l_base);
-    __sincosf((float)(int32_t)(Psi * (uint32_t)a.kc_int) * 1.4629180792671596e-09f, &sn, &cs);  // 2 pi / 2^32
-  } else {
-    float th;
-    mixed_phase(A, j - l_base, a.kc, Psi, th);
-    __sincosf(6.28318530717958647692f * th, &sn, &cs);
-  }
-  const int n = a.n_fine;
-  // s = Psi n - W/2 cells in 32.32 fixed point; the first tap sits at cell
-  // l0 = ceil(s), and e = (l0 - s) 2^32 gives its kernel argument
-  // z0 = (e 2^-32 - W/2) (2/W)
-  const long long s = (long long)((unsigned long long)Psi * (uint32_t)n) - ((long long)W << 31);
-  const uint32_t e = 0u - (uint32_t)s;
-  int l0 = (int)(s >> 32) + (e != 0u ? 1 : 0);
-  if (l0 < 0) l0 += n; else if (l0 >= n) l0 -= n;
-  const float ef = (float)e;
-  const float xv = xs[j] * k.es_scale;
-  TapIn t;
-  t.l0 = l0;
-  t.b0 = k.eh32 * ef;                  // E (1 + z0)
-  t.a0 = fmaf(-k.eh32, ef, k.two_e);   // E (1 - z0)
-  t.cre = xv * cs;
-  t.cim = -xv * sn;
-  return t;
-}
-
-// Spread the samples [j_begin, j_end) of one lane into `grid`.  The lane keeps
-// the W cells [Bm, Bm + W) of its kernel footprint in registers.  The warp
-// walks cell by cell: each lane adds all of its samples whose first cell is
-// Bm, then every lane flushes cell Bm with a shared-memory atomic and moves
-// its window one cell on, so the step is warp-uniform.  The window is a ring:
-// the walk is unrolled W times so that, at step R of the unrolled loop, cell
-// Bm + t lives in register acc[(t + R) % W] and moving on renames registers
-// instead of copying them.
+// Spread the samples [j_begin, j_end) of one lane into `grid`.
+//
+// Time map.  The lane's phases come from a LaneMap seeded at its first sample
+// (64-bit fixed point, integer steps): Psi' = Psi - W/(2n) - base/n periods,
+// where base is the lane's base cell (one cell before its first sample's
+// first tap), so that s = Psi' n is the position of the first tap relative
+// to base and never wraps within the lane's run.  The demodulation phase is
+// k_c Psi mod 1 from the same Psi when k_c is a whole number, else a second
+// LaneMap.
+//
+// Taps.  The ES kernel is phi(z) = 2^(E sqrt(1 - z^2)) 2^-E with E = beta
+// log2 e; the constant 2^-E is left to the deconvolution factors.  With
+// Z = E z, E sqrt(1 - z^2) = sqrt(E^2 - Z^2), and tap t of a sample sits at
+// Z = Z0 + t H (H = 2E/W); taps are evaluated in pairs on the packed FP32x2
+// pipe.
+//
+// Cell walk.  The lane keeps the W cells [Bm, Bm + W) of its kernel
+// footprint in registers.  The warp walks cell by cell: each lane adds all
+// of its samples whose first tap is cell Bm, then every lane flushes cell Bm
+// with a shared-memory atomic and moves its window one cell on, so the step
+// is warp-uniform.  The window is a ring: the walk is unrolled W times so
+// that, at step R of the unrolled loop, cell Bm + t lives in register
+// acc[(t + R) % W] and moving on renames registers instead of copying them.
 template <int W, bool INT_KC>
 struct CellWalk {
   float2 acc[W];
-  TapIn p;
-  int j, j_end, l_base, Bm;
+  int l0;
+  float z0, cre, cim;
+  LaneMap m;
+  LaneMap mt;
+  uint32_t thofs, kc, n;
+  int base, j, j_end, Bm;
+  float x_next, H, eh32, E;
   bool live;
   unsigned mask;
-  float H;
-  TapConst kc;
-  Anchor A;
   const float* __restrict__ xs;
   float2* __restrict__ grid;
-  const MixedArgs* a;
 
-  // one cell of the walk at ring offset R; false once no lane has samples left
+  __device__ __forceinline__ void inputs(float x) {
+    const uint32_t ph = (uint32_t)(m.v >> 32), pl = (uint32_t)m.v;
+    uint32_t th;
+    if (INT_KC) {
+      th = ph * kc + __umulhi(pl, kc) + thofs;
+    } else {
+      th = (uint32_t)(mt.v >> 32);
+      mt.step();
+    }
+    float sn, cs;
+    __sincosf((float)(int32_t)th * 1.4629180792671596e-09f, &sn, &cs);
+    const unsigned long long sp = (unsigned long long)ph * n + __umulhi(pl, n);
+    const uint32_t sl = (uint32_t)sp;
+    l0 = (int)(sp >> 32) + (sl != 0u ? 1 : 0);
+    z0 = fmaf(eh32, (float)(0u - sl), -E);
+    cre = x * cs;
+    cim = -x * sn;
+    m.step();
+  }
+
+  __device__ __forceinline__ void next() {
+    ++j;
+    live = j < j_end;
+    if (live) {
+      const float x = x_next;
+      if (j + 1 < j_end) x_next = xs[j + 1];
+      inputs(x);
+    }
+  }
+
+  __device__ __forceinline__ void flush_cell(int c_rel, float2 v) {
+    int c = base + c_rel;
+    while (c >= (int)n) c -= n;
+    atomicAdd(&grid[c].x, v.x);
+    atomicAdd(&grid[c].y, v.y);
+  }
+
   template <int R>
   __device__ __forceinline__ bool cell() {
     if (!__any_sync(mask, live)) return false;
-    const float2 HH = make_float2(H, H), mHH = make_float2(-H, -H);
-    while (live && p.l0 == Bm) {
-      const float2 cv = make_float2(p.cre, p.cim);
-      const float2 aa = make_float2(p.a0, p.a0), bb = make_float2(p.b0, p.b0);
-      // taps in pairs on the packed FP32x2 pipe; |.| guards a rounding just below zero at the footprint's edge
+    const float2 HH = make_float2(H, H), mEE = make_float2(-E * E, -E * E);
+    while (live && l0 == Bm) {
+      const float2 ZZ = make_float2(z0, z0);
+      const float2 cv = make_float2(cre, cim);
 #pragma unroll
       for (int t = 0; t + 1 < W; t += 2) {
         const float2 tt = make_float2((float)t, (float)(t + 1));
-        const float2 q = __fmul2_rn(__ffma2_rn(tt, mHH, aa), __ffma2_rn(tt, HH, bb));
+        const float2 Z = __ffma2_rn(tt, HH, ZZ);
+        const float2 q = __ffma2_rn(Z, Z, mEE);
         const float p0 = ex2_approx(sqrt_approx(fabsf(q.x)));
         const float p1 = ex2_approx(sqrt_approx(fabsf(q.y)));
         acc[(t + R) % W] = __ffma2_rn(make_float2(p0, p0), cv, acc[(t + R) % W]);
         acc[(t + 1 + R) % W] = __ffma2_rn(make_float2(p1, p1), cv, acc[(t + 1 + R) % W]);
       }
       if (W & 1) {
-        const float tl = (float)(W - 1);
-        const float pl = ex2_approx(sqrt_approx(fabsf(fmaf(tl, -H, p.a0) * fmaf(tl, H, p.b0))));
+        const float Zl = fmaf((float)(W - 1), H, z0);
+        const float pl = ex2_approx(sqrt_approx(fabsf(fmaf(Zl, Zl, -E * E))));
         acc[(W - 1 + R) % W] = __ffma2_rn(make_float2(pl, pl), cv, acc[(W - 1 + R) % W]);
       }
-      ++j;
-      live = j < j_end;
-      if (live) p = tap_inputs<INT_KC>(A, xs, j, l_base, W, kc, *a);
+      next();
     }
-    // cell Bm is complete for this lane; its register becomes cell Bm + W
-    atomicAdd(&grid[Bm].x, acc[R % W].x);
-    atomicAdd(&grid[Bm].y, acc[R % W].y);
+    flush_cell(Bm, acc[R % W]);
     acc[R % W] = make_float2(0.f, 0.f);
-    Bm = (Bm + 1 == a->n_fine) ? 0 : Bm + 1;
+    ++Bm;
     return true;
   }
 
-  // the cells still in the window when the walk ends at ring offset R
   template <int R>
   __device__ __forceinline__ void flush() {
 #pragma unroll
     for (int t = 0; t < W - 1; ++t) {
-      int c = Bm + t;
-      if (c >= a->n_fine) c -= a->n_fine;
       const float2 v = acc[(t + R) % W];
-      if (v.x != 0.f || v.y != 0.f) {
-        atomicAdd(&grid[c].x, v.x);
-        atomicAdd(&grid[c].y, v.y);
-      }
+      if (v.x != 0.f || v.y != 0.f) flush_cell(Bm + t, v);
     }
   }
 
-  // ring offsets R .. W-1 of one turn; false once the walk has ended
   template <int R>
   __device__ __forceinline__ bool turn() {
     if constexpr (R == W) {
@@ -395,30 +385,44 @@ struct CellWalk {
 
 template <int W, bool INT_KC>
 __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2* __restrict__ grid,
-                                           const Anchor A, int j_begin, int j_end, int l_base,
+                                           const Anchor& A, int j_begin, int j_end, int l_base,
                                            const MixedArgs& a) {
   CellWalk<W, INT_KC> w;
 #pragma unroll
-  for (int t = 0; t < W; ++t) w.acc[t] = make_float2(0.f, 0.f);
-  // ES kernel in base 2: phi(z) = 2^(E sqrt(1 - z^2) - E); with Z = E z,
-  // E sqrt(1 - z^2) = sqrt((E - Z)(E + Z)), and tap t has Z = Z0 + t H.
+  for (int c = 0; c < W; ++c) w.acc[c] = make_float2(0.f, 0.f);
   const float E = a.es_beta_log2e;
+  w.E = E;
   w.H = E * a.two_over_w;
-  w.kc.es_scale = exp2f(-E);
-  w.kc.eh32 = w.H * 2.3283064365386963e-10f;
-  w.kc.two_e = 2.0f * E;
+  w.eh32 = w.H * 2.3283064365386963e-10f;
+  w.n = (uint32_t)a.n_fine;
+  w.kc = (uint32_t)a.kc_int;
   w.mask = __activemask();
-  w.A = A;
   w.xs = xs;
   w.grid = grid;
-  w.a = &a;
   w.j = j_begin;
   w.j_end = j_end;
-  w.l_base = l_base;
   w.live = j_begin < j_end;
-  w.p = {0, 0.f, 0.f, 0.f, 0.f};
-  if (w.live) w.p = tap_inputs<INT_KC>(A, xs, j_begin, l_base, W, w.kc, a);
-  w.Bm = w.p.l0;  // fine-grid cell of ring offset 0
+  w.Bm = 0;
+  if (w.live) {
+    const int l = j_begin - l_base;
+    // Psi - W/(2n) at the first sample, and the lane's base cell
+    w.m = lane_map(A, anchor_psi0(A), A.n1, A.p1lo, A.q2, 1.0f, l);
+    w.m.v -= a.wofs;
+    const uint32_t ph = (uint32_t)(w.m.v >> 32), pl = (uint32_t)w.m.v;
+    const unsigned long long sp = (unsigned long long)ph * w.n + __umulhi(pl, w.n);
+    int base = (int)(sp >> 32) - 1;
+    if (base < 0) base += (int)w.n;
+    w.base = base;
+    const unsigned long long off = (unsigned long long)base * a.inv_n64;   // base / n periods
+    w.m.v -= off;
+    const unsigned long long o = a.wofs + off;
+    w.thofs = (uint32_t)(o >> 32) * w.kc + __umulhi((uint32_t)o, w.kc);  // k_c (W/(2n) + base/n) mod 1
+    if (!INT_KC) w.mt = lane_map(A, anchor_th0(A), A.m1, A.m1lo, A.kq2, a.kc, l);
+    const float x0 = xs[j_begin];
+    w.x_next = j_begin + 1 < j_end ? xs[j_begin + 1] : 0.f;
+    w.inputs(x0);
+    w.Bm = w.l0;
+  }
   while (w.template turn<0>()) {
   }
 }
@@ -799,18 +803,42 @@ __global__ void k_keys_to_cands(const unsigned long long* __restrict__ keys, int
 // ---------------------------------------------------------------------------
 __global__ void k_time_map_mixed(const Anchor* __restrict__ anchors, int n_items, MixedArgs a,
                                  double* __restrict__ psi_out, double* __restrict__ th_out) {
-  const long long total = (long long)n_items * a.n_s;
+  // one thread per lane run of the spreader (samples [r run, (r + 1) run)),
+  // stepping the same LaneMaps: Psi' plus the offsets the spreader removed,
+  // and the demodulation phase exactly as the spreader forms it
+  const int runs = (a.n_s + a.run - 1) / a.run;
+  const long long total = (long long)n_items * runs;
+  const uint32_t n = (uint32_t)a.n_fine, kc = (uint32_t)a.kc_int;
   for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < total;
        f += (long long)gridDim.x * blockDim.x) {
-    const long long it = f / a.n_s;
-    const int j = (int)(f - it * a.n_s);
-    const int ai = j / a.span;
+    const long long it = f / runs;
+    const int r = (int)(f - it * runs);
+    const int j0 = r * a.run, j1 = min(j0 + a.run, a.n_s);
+    const int ai = j0 / a.span;
     const Anchor A = anchors[it * a.n_anchor + ai];
-    uint32_t Psi;
-    float th;
-    mixed_phase(A, j - ai * a.span, a.kc, Psi, th);
-    psi_out[f] = (double)Psi * 2.3283064365386962890625e-10;
-    th_out[f] = th < 0.f ? (double)th + 1.0 : (double)th;
+    const int l = j0 - ai * a.span;
+    LaneMap m = lane_map(A, anchor_psi0(A), A.n1, A.p1lo, A.q2, 1.0f, l);
+    m.v -= a.wofs;
+    const uint32_t ph0 = (uint32_t)(m.v >> 32), pl0 = (uint32_t)m.v;
+    const unsigned long long sp = (unsigned long long)ph0 * n + __umulhi(pl0, n);
+    int base = (int)(sp >> 32) - 1;
+    if (base < 0) base += (int)n;
+    const unsigned long long off = (unsigned long long)base * a.inv_n64;
+    m.v -= off;
+    const unsigned long long o = a.wofs + off;
+    const uint32_t thofs = (uint32_t)(o >> 32) * kc + __umulhi((uint32_t)o, kc);
+    LaneMap mt = lane_map(A, anchor_th0(A), A.m1, A.m1lo, A.kq2, a.kc, l);
+    for (int j = j0; j < j1; ++j) {
+      const unsigned long long v = m.v + o;           // Psi, 2^-64 periods
+      uint32_t th;
+      if (kc) th = (uint32_t)(m.v >> 32) * kc + __umulhi((uint32_t)m.v, kc) + thofs;
+      else th = (uint32_t)(mt.v >> 32);
+      const long long out = it * a.n_s + j;
+      psi_out[out] = (double)(v >> 11) * 1.1102230246251565404e-16;   // 2^-53
+      th_out[out] = (double)th * 2.3283064365386962890625e-10;
+      m.step();
+      mt.step();
+    }
   }
 }
 
@@ -1016,11 +1044,9 @@ cudaError_t launch_topk(const unsigned long long* keys, long long n, int k, unsi
   const unsigned long long* src = keys;
   unsigned long long* dst = buf_a;
   long long cur = n;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_topk_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, kTopkTile * 8);
-    attr_set = true;
-  }
+  // a tile's keys (kTopkTile x 8 B = 32 KB of dynamic shared memory) fit the
+  // default per-block limit, so no attribute is set
+  static_assert(kTopkTile * 8 <= 48 * 1024, "top-k tile beyond the default dynamic shared memory");
   for (;;) {
     const int tile = topk_tile(cur, k);
     const long long tiles = (cur + tile - 1) / tile;

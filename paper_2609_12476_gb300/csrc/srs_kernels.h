@@ -33,6 +33,8 @@ struct MixedArgs {
   float inv_ns;                   // 1 / n_s
   float es_beta_log2e;            // ES shape parameter * log2(e)
   float two_over_w;
+  unsigned long long wofs;        // W / (2 n_fine) periods in 2^-64 fixed point (half the kernel's footprint)
+  unsigned long long inv_n64;     // 2^64 / n_fine rounded: one fine-grid cell in 2^-64 periods
   const float* corr;              // [n_bins] deconvolution factors
   const float* tw;                // [2 n_fine] interleaved exp(-2 pi i m / n_fine)
   const int* order;               // [n_items] queue position -> item, or NULL (item order)
@@ -52,6 +54,16 @@ struct PlainArgs {
 };
 
 size_t mixed_smem_bytes(const MixedArgs& a);
+
+// The fixed-point constants of the mixed spreader's time map for a plan:
+// W / (2 n_fine) periods and one fine-grid cell (1 / n_fine periods), both in
+// 2^-64 periods, rounded to nearest.
+inline void mixed_fixed_point(const Plan& pl, MixedArgs& a) {
+  const unsigned __int128 one = (unsigned __int128)1 << 64;
+  const unsigned __int128 n = (unsigned __int128)pl.n_fine;
+  a.wofs = (unsigned long long)(((unsigned __int128)pl.w * one + n) / (2 * n));
+  a.inv_n64 = (unsigned long long)((2 * one + n) / (2 * n));
+}
 
 cudaError_t launch_anchors(const Item* items, int n_items, const double* betas, const AnchorArgs& aa,
                            Anchor* out, long long total, int n_sm, cudaStream_t st);

@@ -60,13 +60,16 @@ srs_status scratch_for_device(int dev, void** out, std::string& msg) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-bool is_device_pointer(const void* p) {
+// True when p is device (or managed) memory of device `dev`: the scratch, the
+// SM count and the launch all belong to the current device.
+bool is_device_pointer_on(const void* p, int dev) {
   cudaPointerAttributes attr;
   if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+  if (attr.type == cudaMemoryTypeManaged) return true;
+  return attr.type == cudaMemoryTypeDevice && attr.device == dev;
 }
 
 void put_msg(char* buf, size_t len, const std::string& m) {
@@ -82,8 +85,10 @@ srs_status run(void* stream_v, const void* strain, int64_t n_samples, int32_t dt
   if (!strain || !F || !params || !mc) { msg = "strain, mc, params and F are required"; return SRS_ERR_ARG; }
   if (dtype != SRS_F32 && dtype != SRS_F64) { msg = "dtype must be SRS_F32 or SRS_F64"; return SRS_ERR_ARG; }
   if (params->precision != SRS_MIXED) { msg = "the static-scratch call runs the mixed form only"; return SRS_ERR_ARG; }
-  if (!is_device_pointer(strain) || !is_device_pointer(F)) {
-    msg = "strain and F must be device pointers";
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); msg = "cudaGetDevice failed"; return SRS_ERR_CUDA; }
+  if (!is_device_pointer_on(strain, dev) || !is_device_pointer_on(F, dev)) {
+    msg = "strain and F must be device pointers on the current device";
     return SRS_ERR_ARG;
   }
   Plan pl;
@@ -92,7 +97,8 @@ srs_status run(void* stream_v, const void* strain, int64_t n_samples, int32_t dt
 
   // Layout of the scratch for this call.
   const size_t n_items = pl.items.size();
-  const int64_t samples = (int64_t)seg_end * pl.n_s;
+  // float64 strain: only the requested segments are converted to float32
+  const int64_t samples = (int64_t)(seg_end - seg_begin) * pl.n_s;
   size_t off = 0;
   const size_t o_flags = off; off = align256(off + 64 + 64);          // queue, error flag
   const size_t o_betas = off; off = align256(off + (size_t)n_templates * sizeof(double));
@@ -108,8 +114,6 @@ srs_status run(void* stream_v, const void* strain, int64_t n_samples, int32_t dt
     msg = b;
     return SRS_ERR_ARG;
   }
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); msg = "cudaGetDevice failed"; return SRS_ERR_CUDA; }
   void* base_v = nullptr;
   s = scratch_for_device(dev, &base_v, msg);
   if (s != SRS_OK) return s;
@@ -122,7 +126,7 @@ srs_status run(void* stream_v, const void* strain, int64_t n_samples, int32_t dt
   float* d_tw = reinterpret_cast<float*>(base + o_tw);
   float* d_x32 = reinterpret_cast<float*>(base + o_x32);
 
-  std::vector<float> corr(pl.corr.begin(), pl.corr.end());
+  const std::vector<float> corr = mixed_corr(pl);
   std::vector<float> tw(2 * (size_t)pl.n_fine);
   for (int m = 0; m < pl.n_fine; ++m) { tw[2 * m] = (float)pl.tw_re[m]; tw[2 * m + 1] = (float)pl.tw_im[m]; }
 
@@ -143,10 +147,15 @@ srs_status run(void* stream_v, const void* strain, int64_t n_samples, int32_t dt
   int n_sm = 0;
   if (!ck(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev), "SM count")) return SRS_ERR_CUDA;
   const float* x32 = nullptr;
-  int use_tma = (pl.n_s % 4) == 0;
+  // the same staging rule as srs_segment_spectra (SRS_NO_TMA=1: no TMA)
+  int use_tma = (pl.n_s % 4) == 0 && !tma_disabled();
   if (dtype == SRS_F64) {
-    if (!ck(launch_to_f32(static_cast<const double*>(strain), d_x32, samples, n_sm, st), "k_to_f32")) return SRS_ERR_CUDA;
-    x32 = d_x32;
+    const int64_t first = (int64_t)seg_begin * pl.n_s;
+    if (!ck(launch_to_f32(static_cast<const double*>(strain) + first, d_x32, samples, n_sm, st), "k_to_f32"))
+      return SRS_ERR_CUDA;
+    // the kernel reads segment i at x32 + i n_s, so the base sits seg_begin
+    // segments before the copy (integer arithmetic: no access lands there)
+    x32 = reinterpret_cast<const float*>(reinterpret_cast<uintptr_t>(d_x32) - (uintptr_t)first * sizeof(float));
   } else {
     x32 = static_cast<const float*>(strain);
     if (((uintptr_t)x32 % 16) != 0) use_tma = 0;
@@ -180,8 +189,9 @@ srs_status run(void* stream_v, const void* strain, int64_t n_samples, int32_t dt
   a.kc = (float)pl.k_c;
   a.kc_int = (pl.k_c >= 1.0 && pl.k_c < 1073741824.0 && pl.k_c == std::floor(pl.k_c)) ? (int)pl.k_c : 0;
   a.inv_ns = (float)(1.0 / (double)pl.n_s);
-  a.es_beta_log2e = (float)(pl.beta_es * 1.4426950408889634074);
+  a.es_beta_log2e = mixed_es_e(pl);
   a.two_over_w = (float)(2.0 / pl.w);
+  mixed_fixed_point(pl, a);
   a.corr = d_corr;
   a.tw = d_tw;
   for (size_t k = 0; k < pl.radices.size() && k < 16; ++k) a.radices[k] = (int8_t)pl.radices[k];

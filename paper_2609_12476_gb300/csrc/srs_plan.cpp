@@ -402,3 +402,17 @@ void fill_info(const Plan& pl, srs_plan_info* info) {
 }
 
 }  // namespace srs
+
+namespace srs {
+
+float mixed_es_e(const Plan& pl) { return (float)(pl.beta_es * 1.4426950408889634074); }
+
+std::vector<float> mixed_corr(const Plan& pl) {
+  // the spreader's taps are 2^(E sqrt(1 - z^2)), the ES kernel times 2^E
+  const double scale = std::exp2(-(double)mixed_es_e(pl));
+  std::vector<float> c(pl.corr.size());
+  for (size_t b = 0; b < c.size(); ++b) c[b] = (float)(pl.corr[b] * scale);
+  return c;
+}
+
+}  // namespace srs

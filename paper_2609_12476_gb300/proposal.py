@@ -267,19 +267,24 @@ def detection_threshold(nseg, p_fa):
 
 
 def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t_obs, n_real, per_real, seed,
-             p_fa=1e-6, amp_range=(0.01, 0.1), nms=NO_NMS, fine_rows=1, component_top=0, nms_by_nsigma=False):
-    """Recall of injections over the same realisations in four searches:
-      full            every fine template (the recall reference)
+             p_fa=1e-6, amp_range=(0.01, 0.1), nms=NO_NMS, fine_rows=1, component_top=0, nms_by_nsigma=False,
+             plain_subset=False, baselines=True):
+    """Recall of injections over the same realisations in these searches:
+      full            every fine template (the recall reference), mixed form
       proposal        the network's proposal at its noise-calibrated threshold
                       (the library's srs_search_proposed)
       nsigma_equal    the proposal without the network at equal cost: the same
                       number of coarse cells, the highest coarse n_sigma first
       nsigma_far      the proposal without the network at the same noise false-
                       alarm rate: coarse cells above the calibrated n_sigma threshold
+      plain_fp64      (plain_subset) the plain FP64 form of the full search on
+                      the fine templates within +-2 of each injection's own,
+                      the only templates that decide its recall
     An injection counts as recovered when a cell within +-2 fine templates and
     +-1 bin of its own (label) cell exceeds the detection threshold at
     per-cell false-alarm probability p_fa; in the proposal searches that cell
-    must also have been evaluated."""
+    must also have been evaluated.  baselines=False skips the two searches
+    without the network."""
     import torch
     rng = np.random.default_rng(seed)
     n = int(round(t_obs * params.fs))
@@ -287,9 +292,11 @@ def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t
     Mf = len(fine_mc)
     info, _, nseg_f = _capi.srs_plan(params, fine_mc, n)
     th_f = detection_threshold(nseg_f, p_fa)
-    keys = ("full", "proposal", "nsigma_equal", "nsigma_far")
+    keys = ("full", "proposal") + (("nsigma_equal", "nsigma_far") if baselines else ()) + \
+        (("plain_fp64",) if plain_subset else ())
     out = {"injections": 0, "full_ms": 0.0, "proposal_ms": 0.0, "full_spectra": 0, "proposal_coarse_spectra": 0,
-           "proposal_segment_bins": 0, "proposed_coarse": 0}
+           "proposal_segment_bins": 0, "proposed_coarse": 0, "plain_ms": 0.0, "plain_spectra": 0,
+           "plain_mixed_max_dnsigma": 0.0}
     for k in keys:
         out[k] = 0
         out[k + "_cells"] = 0
@@ -314,6 +321,32 @@ def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t
         out["proposed_coarse"] += pr["report"]["proposed_coarse"]
         out["proposal_cells"] += pr["n_cells"]
         found["proposal"] = {(int(m), int(b)): float(v) for (m, b), v in zip(pr["cells"], pr["nsigma"])}
+        if plain_subset:
+            # the plain FP64 form on the templates that decide recall
+            sub = sorted({m for I in inj for m in range(max(0, nearest_template(fine_mc, I["label"]) - 2),
+                                                        min(Mf, nearest_template(fine_mc, I["label"]) + 3))})
+            pp = Params(**{f: getattr(params, f) for f in params.__dataclass_fields__})
+            pp.precision = _capi.SRS_PLAIN_FP64
+            pmap = torch.empty((len(sub), n_bins), dtype=torch.float32, device=x.device)
+            _, prep = ctx.search(x, fine_mc[sub], pp, out={"map": pmap, "cands": torch.empty(
+                (params.top_k, 3), dtype=torch.int32, device=x.device)})
+            out["plain_ms"] += prep["device_ms"]
+            out["plain_spectra"] += prep["n_spectra"]
+            pm = pmap.cpu().numpy()
+            out["plain_mixed_max_dnsigma"] = max(out["plain_mixed_max_dnsigma"],
+                                                 float(np.max(np.abs(pm - fm[sub]))))
+            found["plain_fp64"] = {(sub[r], int(b)): float(pm[r, b]) for r, b in np.argwhere(pm > th_f[sub][:, None])}
+        if not baselines:
+            for I in inj:
+                out["injections"] += 1
+                mf = nearest_template(fine_mc, I["label"])
+                bf = int(round((I["f0"] - params.f_lo) * params.t_coh))
+                nb = [(m, b) for m in range(max(0, mf - 2), min(Mf, mf + 3))
+                      for b in range(max(0, bf - 1), min(n_bins, bf + 2))]
+                for key in keys:
+                    if any(found[key].get((m, b), -np.inf) > th_f[m] for m, b in nb):
+                        out[key] += 1
+            continue
         # proposals without the network
         cmap, _ = coarse_map(ctx, x, coarse_mc, params)
         cm = cmap.cpu().numpy()

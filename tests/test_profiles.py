@@ -17,6 +17,8 @@ CSRC = os.path.join(ROOT, "paper_2609_12476_gb300", "csrc")
 SUMMARIES = [
     ("k_mixed_semicoherent_2h.md", ("srs_kernels.cu", "srs_device.cuh"),
      ("traffic_bytes_per_launch", "inst_executed_per_launch")),
+    ("k_mixed_large_24h.md", ("srs_kernels.cu", "srs_device.cuh"),
+     ("traffic_bytes_per_launch", "inst_executed_per_launch")),
     ("two_stage_24h.md", ("srs_kernels.cu", "srs_device.cuh"), ("k_mixed cube traffic_bytes_per_launch",)),
     ("two_stage_24h.md", ("srs_slide.cu", "srs_device.cuh"), ("k_stack_slide traffic_bytes_per_launch",)),
 ]

@@ -54,3 +54,33 @@ def test_static_scratch_rejects_requests_beyond_its_size():
     with pytest.raises(SrsError) as e:
         segment_spectra_static(x, [5e-4], 0, 2880, Params(eps=1e-6))
     assert e.value.status == -1 and "static scratch" in str(e.value)
+
+
+def test_static_scratch_late_segments_of_long_float64_strain():
+    """Only the requested segments of float64 strain are converted into the
+    scratch, so a few segments far into a long series fit."""
+    torch = pytest.importorskip("torch")
+    fs = 256.0
+    x = srs_synth.white_noise(700 * 7680, seed=9)          # 43 MB of float64, beyond the scratch
+    mc = srs_synth.log_templates(5e-4, 2e-3, 2)
+    p = Params(eps=1e-6)
+    ctx = Context(0)
+    ref, _ = ctx.segment_spectra(x, mc, 650, 653, p)
+    ctx.close()
+    xd = torch.from_numpy(x).cuda()
+    for _ in range(2):
+        got = segment_spectra_static(xd, mc, 650, 653, p).cpu().numpy()
+        assert _rel_l2(got, ref).max() <= 1e-5
+
+
+def test_static_scratch_checks_the_output_tensor():
+    torch = pytest.importorskip("torch")
+    xd = torch.zeros(4 * 7680, dtype=torch.float32, device="cuda")
+    bad = [torch.empty((1, 2, 600), dtype=torch.complex64, device="cuda"),     # wrong dtype
+           torch.empty((1, 3, 600), dtype=torch.complex128, device="cuda"),    # wrong shape
+           torch.empty((1, 600, 2), dtype=torch.complex128, device="cuda").transpose(1, 2)]   # not contiguous
+    for F in bad:
+        with pytest.raises(ValueError):
+            segment_spectra_static(xd, [1e-2], 0, 2, Params(eps=1e-6), F=F)
+    with pytest.raises(ValueError):
+        segment_spectra_static(xd[::2], [1e-2], 0, 1, Params(eps=1e-6))
