@@ -106,23 +106,6 @@ __global__ void k_patches(const float* __restrict__ map, int n_templates, int n_
   }
 }
 
-// Patches of every cell of a map, cells [c0, c0 + n) in row-major order.
-__global__ void k_patches_all(const float* __restrict__ map, int n_templates, int n_bins, long long c0, int n,
-                              float* __restrict__ out) {
-  const long long total = (long long)n * kPatchSize;
-  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(f / kPatchSize);
-    const int e = (int)(f - (long long)k * kPatchSize);
-    const long long cell = c0 + k;
-    const int m0 = (int)(cell / n_bins), b0 = (int)(cell - (long long)m0 * n_bins);
-    const int r = e / kPatchBins, c = e - r * kPatchBins;
-    const int m = m0 + r - kPatchTemplates / 2, b = b0 + c - kPatchBins / 2;
-    float v = 0.f;
-    if (m >= 0 && m < n_templates && b >= 0 && b < n_bins) v = feature(map[(long long)m * n_bins + b]);
-    out[f] = v;
-  }
-}
-
 // Forward pass: four samples per 256-thread block, one hidden unit per thread.
 // z1 = W1 x + b1 (FP16 weights, FP32 sums), h = relu(z1), logit = w2 . h + b2.
 __global__ void __launch_bounds__(256)
@@ -348,16 +331,6 @@ cudaError_t launch_patches(const float* map, int n_templates, int n_bins, const 
   if (blocks > (long long)n_sm * 32) blocks = (long long)n_sm * 32;
   if (blocks < 1) blocks = 1;
   k_patches<<<(unsigned)blocks, 256, 0, st>>>(map, n_templates, n_bins, cm, cb, n, out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_patches_all(const float* map, int n_templates, int n_bins, long long c0, int n, float* out,
-                               int n_sm, cudaStream_t st) {
-  long long total = (long long)n * kPatchSize;
-  long long blocks = (total + 255) / 256;
-  if (blocks > (long long)n_sm * 32) blocks = (long long)n_sm * 32;
-  if (blocks < 1) blocks = 1;
-  k_patches_all<<<(unsigned)blocks, 256, 0, st>>>(map, n_templates, n_bins, c0, n, out);
   return cudaGetLastError();
 }
 

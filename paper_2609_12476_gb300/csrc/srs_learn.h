@@ -45,10 +45,16 @@ cudaError_t launch_make_strain(float* out, long long n, double fs, unsigned long
                                const InjectionDev* inj, int n_inj, int n_sm, cudaStream_t st);
 cudaError_t launch_patches(const float* map, int n_templates, int n_bins, const int* cm, const int* cb, int n,
                            float* out, int n_sm, cudaStream_t st);
-cudaError_t launch_patches_all(const float* map, int n_templates, int n_bins, long long c0, int n, float* out,
-                               int n_sm, cudaStream_t st);
 cudaError_t launch_mlp_forward(const float* X, int n, const __half* W1h, const float* b1, const __half* w2h,
                                const float* b2, float* logits, float* Z1, int n_sm, cudaStream_t st);
+// The network's logit for every cell of a [n_templates][n_bins] map on the
+// tensor cores (srs_score_tc.cu): one persistent CTA of 128 threads per SM,
+// score_tc_smem_bytes() of dynamic shared memory.  err[0] = 1 (err[1] = the
+// tile) if a wait for the tensor cores gave up.
+size_t score_tc_smem_bytes();
+cudaError_t launch_score_tc(const float* map, int n_templates, int n_bins, const __half* W1h, const float* b1,
+                            const __half* w2h, const float* b2, float* scores, int* err, int n_sm,
+                            cudaStream_t st);
 cudaError_t launch_bce(const float* logits, const float* y, int n, float* dz, float* loss_terms, cudaStream_t st);
 cudaError_t launch_mlp_grad(const float* X, int n, const float* Z1, const float* dz, const __half* w2h, float* g,
                             cudaStream_t st);

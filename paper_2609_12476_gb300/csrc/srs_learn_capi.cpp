@@ -80,16 +80,21 @@ srs_status forward(srs_ctx* ctx, const float* X, int32_t n, float* logits, float
   return SRS_OK;
 }
 
+// Every cell's logit on the tensor cores: the first layer as an implicit-GEMM
+// convolution over the map (k_score_tc), FP16 features and weights, FP32 sums.
 srs_status score_map_impl(srs_ctx* ctx, const float* map, int32_t n_templates, int32_t n_bins, float* scores) {
-  const long long cells = (long long)n_templates * n_bins;
-  const int chunk = 16384;
-  SRS_CK(ctx->patches.ensure((size_t)chunk * kPatchSize * 4), "alloc patches");
-  for (long long c0 = 0; c0 < cells; c0 += chunk) {
-    const int n = (int)std::min<long long>(chunk, cells - c0);
-    SRS_CK(launch_patches_all(map, n_templates, n_bins, c0, n, ctx->patches.as<float>(), ctx->n_sm, ctx->stream),
-           "k_patches_all");
-    srs_status s = forward(ctx, ctx->patches.as<float>(), n, scores + c0, nullptr);
-    if (s != SRS_OK) return s;
+  srs_status s = clear_err_flag(ctx);
+  if (s != SRS_OK) return s;
+  SRS_CK(launch_score_tc(map, n_templates, n_bins, ctx->w1h.as<__half>(), b1_ptr(ctx), ctx->w2h.as<__half>(),
+                         b2_ptr(ctx), scores, ctx->errflag.as<int>(), ctx->n_sm, ctx->stream),
+         "k_score_tc");
+  int flag[2] = {0, 0};
+  SRS_CK(cudaMemcpyAsync(flag, ctx->errflag.p, sizeof flag, cudaMemcpyDeviceToHost, ctx->stream), "read error flag");
+  SRS_CK(cudaStreamSynchronize(ctx->stream), "k_score_tc");
+  if (flag[0]) {
+    char b[128];
+    std::snprintf(b, sizeof b, "score_map: a wait for the tensor cores gave up (tile %d)", flag[1]);
+    return set_err(ctx, SRS_ERR_TIMEOUT, b);
   }
   return SRS_OK;
 }

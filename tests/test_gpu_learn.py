@@ -74,6 +74,30 @@ def test_forward_matches_reference_with_fp16_weights(ctx):
     assert np.max(np.abs(got - ref)) <= 1e-4 * (1 + np.max(np.abs(ref)))
 
 
+@pytest.mark.parametrize("shape", [(20, 600), (13, 130), (3, 40)])
+def test_score_map_on_tensor_cores_matches_reference(ctx, shape):
+    """Every cell's logit from the tensor-core scorer (implicit-GEMM first
+    layer, FP16 features and weights, FP32 sums) against the FP64 network on
+    the same FP16-rounded features and weights.  The shapes cover the map's
+    edges (zero padding), a last tile of partial rows (600 = 4 x 128 + 88) and
+    more tiles than SMs or fewer."""
+    r = np.random.default_rng(11 + shape[0])
+    smap = (r.normal(0, 2, shape) + 8 * (r.random(shape) < 0.01)).astype(np.float32)
+    _, _, p = _case(4, 8)
+    got = ctx.score_map(torch.from_numpy(smap).cuda(), p).cpu().numpy()
+    cells = [(m, b) for m in range(shape[0]) for b in range(shape[1])]
+    X = omlp.patches(smap.astype(np.float64), cells)
+    X16 = X.astype(np.float16).astype(np.float64)
+    p16 = omlp.fp16_weights(p)
+    ref, _ = omlp.forward(X16, p16)
+    W1, _, w2, _ = omlp.unpack(p16)
+    # FP32 accumulation over 297 terms, and asinh in FP32 before the FP16 rounding
+    # (one FP16 ulp, 2^-11 relative, where the two asinh round differently)
+    bound = 2.0 ** -11 * (np.abs(X16) @ np.abs(W1).T) @ np.abs(w2) + 1e-5 * (1 + np.abs(ref))
+    err = np.abs(got.ravel() - ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+
+
 def test_gradient_matches_reference(ctx):
     X, y, p = _case(2, 257)
     g, loss = ctx.mlp_grad(X, y, p)
