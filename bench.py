@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large_24h",
                     choices=sorted(srs_synth.WORKLOADS) + sorted(srs_synth.SLIDE_WORKLOADS) + ["learned_6h",
-                                                                                                  "learned_24h"])
+                                                                                                  "learned_24h",
+                                                                                                  "proposal_score"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 and cuFFT comparisons")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-two-stage", action="store_true", help="skip the two-stage (cube + stack-slide) measurement")
@@ -799,10 +800,61 @@ def run_learned(args):
     ctx.close()
 
 
+def run_proposal_score(args):
+    """The proposal network's inference kernel alone (k_score_tc, tcgen05):
+    logits of every cell of a coarse n_sigma map of 256 templates x 600 bins
+    (the learned workloads' coarse bank), seeded synthetic map and weights.
+    value = cells per second; roofline against the dense FP16 tensor peak
+    (the measured bf16 figure: same rate), algorithmic FLOPs 2 x 297 x 64 per
+    cell for the first layer plus 2 x 64 for the output layer."""
+    import torch
+    from paper_2609_12476_gb300 import Context, proposal
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(0)
+    torch.cuda.set_stream(stream)
+    ctx = Context(0, stream=stream.cuda_stream)
+    r = np.random.default_rng(7)
+    smap = torch.from_numpy((r.normal(0, 2, (256, 600)) + 8 * (r.random((256, 600)) < 0.01))
+                            .astype(np.float32)).cuda()
+    params = proposal.init_params(3)
+    for _ in range(args.warmup):
+        ctx.score_map(smap, params)
+    torch.cuda.synchronize()
+    ev = []
+    torch.cuda.nvtx.range_push("timed")
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.score_map(smap, params)
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+    cells = 256 * 600
+    flops = cells * (2 * 297 * 64 + 2 * 64)
+    pk = peaks()
+    peak = (pk or {}).get("bf16_tflops", 1900.0)
+    ach = flops / (ms * 1e-3) / 1e12
+    line = {"metric": "proposal network logits per second (coarse map cells)", "value": cells / (ms * 1e-3),
+            "unit": "cells/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
+            "data": "synthetic seeded n_sigma map and weights",
+            "config": {"workload": "proposal_score", "map": "256 x 600", "network": "297-64-1, FP16 weights"},
+            "roofline": {"kernel": "k_score_tc", "bound": "tensor", "achieved": ach, "peak": peak,
+                         "unit": "TFLOP/s", "frac": ach / peak,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (FP16 runs at the bf16 rate)",
+                         "note": "ms_per_step is the library call (launch, error-flag read, sync)"}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "proposal_score":
+        run_proposal_score(args)
     elif args.workload in LEARNED:
         run_learned(args)
     elif args.workload in srs_synth.SLIDE_WORKLOADS:

@@ -111,8 +111,11 @@ __global__ void k_slide_lengths(const int* __restrict__ cell, const float2* __re
 // chunk, first = n + [c > 0], and s < min(len_r, n_total - first).  The
 // row's track cells (and, WEIGHTED, their FMA coefficients) are staged in
 // shared memory; four accumulators keep four loads in flight per thread.
-// Without weights every term is P / 2 - 1.
-template <bool WEIGHTED>
+// Without weights every term is P / 2 - 1.  OFF32: the staged value is the
+// 32-bit cube offset cell_s * ld + s, and each thread adds it to its own
+// base cube + first - seg_begin, so a power read is one shared load, one
+// address multiply-add and the load.
+template <bool WEIGHTED, bool OFF32>
 __global__ void __launch_bounds__(kSlideThreads)
 k_stack_slide(const float* __restrict__ cube, const int* __restrict__ cell, const float2* __restrict__ coef,
               const int* __restrict__ len, const double* __restrict__ w2, const double* __restrict__ frac,
@@ -138,17 +141,46 @@ k_stack_slide(const float* __restrict__ cube, const int* __restrict__ cell, cons
   const float2* __restrict__ wrow = coef + (long long)r * a.n_total;
   // cube index of track step s: cell_s * ld + (first + s - seg_begin)
   const long long c0 = (long long)first - a.seg_begin;
+  // OFF32: this thread's base; every index it adds lands inside the cube
+  const float* __restrict__ cb = cube + c0;
+  const unsigned* __restrict__ so = reinterpret_cast<const unsigned*>(sc);
   float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
   for (int base = S_lo; base < S_hi; base += kSlideStage) {
     const int cnt = min(kSlideStage, S_hi - base);
     __syncthreads();
     for (int t = threadIdx.x; t < cnt; t += kSlideThreads) {
-      sc[t] = crow[base + t];
+      if (OFF32) sc[t] = (int)((unsigned)crow[base + t] * (unsigned)a.ld + (unsigned)(base + t));
+      else sc[t] = crow[base + t];
       if (WEIGHTED) sw[t] = wrow[base + t];
     }
     __syncthreads();
     const int lo = max(s_lo, base), hi = min(s_hi, base + cnt);
     int s = lo;
+    if (OFF32) {
+      for (; s + 3 < hi; s += 4) {
+        const float p0 = __ldg(cb + so[s - base]);
+        const float p1 = __ldg(cb + so[s + 1 - base]);
+        const float p2 = __ldg(cb + so[s + 2 - base]);
+        const float p3 = __ldg(cb + so[s + 3 - base]);
+        if (WEIGHTED) {
+          const float2 w0 = sw[s - base], w1 = sw[s + 1 - base], w2_ = sw[s + 2 - base], w3 = sw[s + 3 - base];
+          z0 += fmaf(p0, w0.x, -w0.y);
+          z1 += fmaf(p1, w1.x, -w1.y);
+          z2 += fmaf(p2, w2_.x, -w2_.y);
+          z3 += fmaf(p3, w3.x, -w3.y);
+        } else {
+          z0 += fmaf(p0, 0.5f, -1.0f);
+          z1 += fmaf(p1, 0.5f, -1.0f);
+          z2 += fmaf(p2, 0.5f, -1.0f);
+          z3 += fmaf(p3, 0.5f, -1.0f);
+        }
+      }
+      for (; s < hi; ++s) {
+        const float2 w = WEIGHTED ? sw[s - base] : make_float2(0.5f, 1.0f);
+        z0 += fmaf(__ldg(cb + so[s - base]), w.x, -w.y);
+      }
+      continue;
+    }
     // term of track step s: a_s (P / S_s - 2) / 2 = sw.x P - sw.y
     for (; s + 3 < hi; s += 4) {
       const float p0 = __ldg(cube + ((long long)sc[s - base] * a.ld + c0 + s));
@@ -293,10 +325,18 @@ cudaError_t launch_stack_slide(const float* cube, const int* cell, const float2*
   const long long tiles = (a.n_t0 + kSlideThreads - 1) / kSlideThreads;
   const long long blocks = tiles * a.n_rows;
   if (blocks <= 0) return cudaSuccess;
-  if (a.weighted)
-    k_stack_slide<true><<<(unsigned)blocks, kSlideThreads, 0, st>>>(cube, cell, coef, len, w2, frac, a, Z, map, keys);
+  if (a.weighted && a.off32)
+    k_stack_slide<true, true><<<(unsigned)blocks, kSlideThreads, 0, st>>>(cube, cell, coef, len, w2, frac, a, Z, map,
+                                                                         keys);
+  else if (a.weighted)
+    k_stack_slide<true, false><<<(unsigned)blocks, kSlideThreads, 0, st>>>(cube, cell, coef, len, w2, frac, a, Z, map,
+                                                                          keys);
+  else if (a.off32)
+    k_stack_slide<false, true><<<(unsigned)blocks, kSlideThreads, 0, st>>>(cube, cell, coef, len, w2, frac, a, Z, map,
+                                                                          keys);
   else
-    k_stack_slide<false><<<(unsigned)blocks, kSlideThreads, 0, st>>>(cube, cell, coef, len, w2, frac, a, Z, map, keys);
+    k_stack_slide<false, false><<<(unsigned)blocks, kSlideThreads, 0, st>>>(cube, cell, coef, len, w2, frac, a, Z, map,
+                                                                           keys);
   return cudaGetLastError();
 }
 

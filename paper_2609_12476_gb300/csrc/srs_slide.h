@@ -31,6 +31,7 @@ struct SlideArgs {
   int seg_begin, seg_end, ld;
   int first, last;
   int weighted;       // 0: equal weights and a white PSD (every coefficient is (1/2, 1))
+  int off32;          // 1: every cube index cell * ld + segment fits 32 bits (cube chunk < 2^32 elements)
 };
 
 // cell[r][s] = k_s n_bins + j_s of the s-th segment of row r's track, -1 past

@@ -199,7 +199,7 @@ srs_status prepare_out(srs_ctx* ctx, const srs_slide_grid* g, const srs_params* 
 // the map and the top-k keys).
 srs_status slide_pass(srs_ctx* ctx, const float* dcube, int32_t seg_begin, int32_t seg_end, int32_t n_total,
                       const srs_slide_grid* g, bool first, bool last, const SlideOut& o, int* launches,
-                      bool s_used) {
+                      bool s_used, long long n_cells) {
   SRS_CK(ctx->slide_Z.ensure((size_t)g->n_rows * g->n_t0 * 4), "alloc running sums");
   SlideArgs a;
   a.n_rows = g->n_rows;
@@ -211,6 +211,8 @@ srs_status slide_pass(srs_ctx* ctx, const float* dcube, int32_t seg_begin, int32
   a.first = first ? 1 : 0;
   a.last = last ? 1 : 0;
   a.weighted = (g->weighting != SRS_WEIGHT_EQUAL || s_used) ? 1 : 0;
+  // the kernel stages cell * ld + step as 32-bit offsets when they all fit
+  a.off32 = n_cells * (long long)a.ld + n_total < 4294967296LL ? 1 : 0;
   SRS_CK(launch_stack_slide(dcube, ctx->slide_cell.as<int>(), ctx->slide_coef.as<float2>(), ctx->slide_len.as<int>(),
                             ctx->slide_w2.as<double>(), ctx->slide_frac.as<double>(), a, ctx->slide_Z.as<float>(),
                             o.dmap, ctx->keys.as<unsigned long long>(), ctx->stream),
@@ -275,7 +277,8 @@ srs_status stack_slide_impl(srs_ctx* ctx, const float* cube, int32_t seg_begin, 
   }
   int launches = 0;
   SRS_CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
-  s = slide_pass(ctx, dcube, seg_begin, seg_end, n_total, g, first, last, o, &launches, g->s_eff != nullptr);
+  s = slide_pass(ctx, dcube, seg_begin, seg_end, n_total, g, first, last, o, &launches, g->s_eff != nullptr,
+                 (long long)bank->n_beta * n_bins);
   if (s != SRS_OK) return s;
   SRS_CK(cudaEventRecord(ctx->ev2, ctx->stream), "event");
   if (last && (s = slide_topk(ctx, g, o, &launches)) != SRS_OK) return s;
@@ -384,7 +387,8 @@ srs_status slide_search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples
       }
     }
     SRS_CK(cudaEventRecord(ctx->slide_ev[3 * c + 1], ctx->stream), "event");
-    s = slide_pass(ctx, ctx->cube.as<float>(), a, b, n_total, g, c == 0, c == n_chunks - 1, o, &launches, s_used);
+    s = slide_pass(ctx, ctx->cube.as<float>(), a, b, n_total, g, c == 0, c == n_chunks - 1, o, &launches, s_used,
+                   rows);
     if (s != SRS_OK) return s;
     SRS_CK(cudaEventRecord(ctx->slide_ev[3 * c + 2], ctx->stream), "event");
   }

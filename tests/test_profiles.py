@@ -21,6 +21,7 @@ SUMMARIES = [
      ("traffic_bytes_per_launch", "inst_executed_per_launch")),
     ("two_stage_24h.md", ("srs_kernels.cu", "srs_device.cuh"), ("k_mixed cube traffic_bytes_per_launch",)),
     ("two_stage_24h.md", ("srs_slide.cu", "srs_device.cuh"), ("k_stack_slide traffic_bytes_per_launch",)),
+    ("k_score_tc_proposal_score.md", ("srs_score_tc.cu",), ()),
 ]
 
 
