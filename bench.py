@@ -530,6 +530,15 @@ def two_stage_measure(ctx, stream, dev, flush, name, steps, warmup, pk, host_e2e
     n_tmpl = int(w["rows_mc"].size) * int(w["n_total"])
     sl = float(np.mean(slide_ms))
     cb = float(np.mean(cube_ms))
+    # the same search with the cube whitened (PSD estimated from the data,
+    # per-segment moments): the whitening passes' time is the cube stage's
+    # extra time (the library's cube events close after the whitening)
+    wh = []
+    for it in range(4):
+        flush.zero_()
+        _, rw = ctx.slide_search(xd, *args, want_map=False, whiten=True)
+        if it:
+            wh.append(rw["spread_ms"] - cb)
     sm_mhz = (ck or {}).get("sm_mhz") or (pk or {}).get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     n_s = int(round(w["t_coh"] * w["fs"]))
@@ -555,6 +564,10 @@ def two_stage_measure(ctx, stream, dev, flush, name, steps, warmup, pk, host_e2e
                             % (n_spec * 600 * 4 // (1 << 20))},
            "cube_ms": cb, "slide_ms": sl, "templates_per_s": n_tmpl / (sl * 1e-3),
            "slide_ms_amplitude_weights": float(np.mean(wsl)),
+           "whitening": {"ms": float(np.mean(wh)), "bytes": 4 * n_spec * n_b * 4,
+                         "achieved_gbs": 4 * n_spec * n_b * 4 / (float(np.mean(wh)) * 1e-3) / 1e9,
+                         "frac_hbm": 4 * n_spec * n_b * 4 / (float(np.mean(wh)) * 1e-3) / 1e9 / hbm_peak,
+                         "passes": "PSD estimate (read), per-segment moments (read), apply (read + write)"},
            "power_reads_per_step": reads,
            "roofline_cube": xu_roofline(n_spec, n_s, int(rep["w"]), cb, n_sm, sm_mhz,
                                         profile_traffic("two_stage_24h.md", ("srs_kernels.cu", "srs_device.cuh"),
@@ -646,7 +659,7 @@ def run_two_stage(args):
                 "slide_load_path": res["slide_load_path"], "clocks": res["clocks"],
                 "gpu_launches": res["gpu_launches"], "e2e": res.get("e2e"), "cpu_baseline": cpu,
                 "cube_ms": res["cube_ms"], "slide_ms": res["slide_ms"], "templates_per_s": res["templates_per_s"],
-                "slide_ms_amplitude_weights": res["slide_ms_amplitude_weights"],
+                "slide_ms_amplitude_weights": res["slide_ms_amplitude_weights"], "whitening": res["whitening"],
                 "power_reads_per_step": res["power_reads_per_step"]}
         print(json.dumps(line), flush=True)
     barrier(world)
