@@ -299,7 +299,11 @@ srs_status srs_segment_spectra_cufft(srs_ctx* ctx, const void* strain, int64_t n
  * evaluates it inside the spreader, for n_items (template, segment) pairs:
  *   psi_out   [n_items][n_s]  delta_j / t_coh modulo 1 (fine-grid phase, periods)
  *   theta_out [n_items][n_s]  f_c delta_j modulo 1, f_c = (f_lo + f_hi)/2 (cycles)
- * both host double arrays; item_m / item_i host int32 arrays. */
+ * both host double arrays; item_m / item_i host int32 arrays.  The mixed
+ * form steps each lane's 64-bit fixed-point phase from the lane's first
+ * sample; this call uses the lanes of the default 256-thread layout (a tuned
+ * search may start its lanes elsewhere, which moves the values by rounding
+ * only, below 1e-13 periods). */
 srs_status srs_time_map(srs_ctx* ctx, const double* mc, int32_t n_templates,
                         const int32_t* item_m, const int32_t* item_i, int32_t n_items,
                         const srs_params* params, int64_t n_samples, double* psi_out,
