@@ -269,6 +269,17 @@ srs_status get_plan(srs_ctx* ctx, int kind, const srs_params* params, const doub
 
 namespace srs {
 
+size_t alloc_limit() {
+  static const size_t limit = [] {
+    const char* v = std::getenv("SRS_ALLOC_LIMIT_BYTES");
+    if (!v || !*v) return (size_t)-1;
+    char* end = nullptr;
+    const unsigned long long b = std::strtoull(v, &end, 10);
+    return (end && *end == '\0' && b > 0) ? (size_t)b : (size_t)-1;
+  }();
+  return limit;
+}
+
 // The mixed form reads FP32 samples: convert FP64 strain once per call, and
 // use FP32 strain in place when TMA can read it (16-byte aligned, n_s % 4 == 0).
 bool tma_disabled() {

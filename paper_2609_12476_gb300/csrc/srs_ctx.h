@@ -13,11 +13,18 @@
 namespace srs {
 
 // A device buffer that only grows.
+// Largest single device allocation the library makes (SIZE_MAX unless
+// SRS_ALLOC_LIMIT_BYTES is set in the environment, read once per process): a
+// larger request fails as out of memory without calling cudaMalloc, which
+// lets tests drive the out-of-memory path without exhausting a GPU.
+size_t alloc_limit();
+
 struct DevBuf {
   void* p = nullptr;
   size_t cap = 0;
   cudaError_t ensure(size_t bytes) {
     if (bytes <= cap && p) return cudaSuccess;
+    if (bytes > alloc_limit()) return cudaErrorMemoryAllocation;
     if (p) cudaFree(p);
     p = nullptr;
     cap = 0;

@@ -59,6 +59,25 @@ def test_time_map_against_oracle(ctx, two_hours, precision, tol_psi, tol_th):
     print("time map (precision %d): max error %.3g periods (Psi), %.3g cycles (f_c delta)" % (precision, ep, et))
 
 
+def test_time_map_with_a_fractional_demodulation_frequency(ctx, two_hours):
+    """f_lo = 40.01 Hz makes k_c = f_c t_coh = 1500.3 non-integer: the mixed
+    spreader then steps the demodulation phase as a second 64-bit map instead
+    of deriving it from k_c Psi.  Same bars as the integer case."""
+    w = two_hours
+    p = Params(f_lo=40.01, f_hi=60.01, precision=SRS_MIXED)
+    mc = w["mc"]
+    _, beta, nseg = __import__("paper_2609_12476_gb300").srs_plan(p, mc, w["n_samples"])
+    items = [(0, 0), (0, 239), (63, int(nseg[63]) - 1), (31, 57)]
+    psi, th = ctx.time_map(mc, items, p, w["n_samples"])
+    et = 0.0
+    for k, (m, i) in enumerate(items):
+        rp, rt = _oracle_phase(beta[m], i, 7680, 256.0, 30.0, 50.01)
+        assert _cyc(psi[k], rp).max() < 1e-12, (m, i, _cyc(psi[k], rp).max())
+        et = max(et, _cyc(th[k], rt).max())
+    print("time map, k_c = 1500.3: max error %.3g cycles (f_c delta)" % et)
+    assert et < 2e-9
+
+
 def test_single_segment_full_band_plain_fp64(ctx):
     """Single segment, exact template, 3840 modes at eps = 1e-9 in FP64."""
     w = srs_synth.make_workload("single")
@@ -427,3 +446,49 @@ def test_cufft_comparison_path_matches_oracle_and_fused(ctx, two_hours):
     assert rel_l2(Fc2, Fc).max() <= 1e-6
     with pytest.raises(SrsError):
         ctx.segment_spectra(w["strain"], mc, 0, 1, Params(precision=SRS_PLAIN_FP64, eps=1e-6), via_cufft=True)
+
+
+_OOM_SCRIPT = r"""
+import sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle, srs_synth
+from paper_2609_12476_gb300 import Context, Params, SrsError
+w = srs_synth.make_workload("semicoherent_2h")
+ctx = Context(0)
+try:
+    ctx.search(w["strain"], w["mc"], Params(eps=1e-6))
+    print("NO-ERROR")
+except SrsError as e:
+    print("STATUS", e.status, str(e).replace("\n", " "))
+x = srs_synth.strain_with_chirps(4 * 7680, 256.0, 3, [{"mc": 8e-2, "f0": 50.0, "amp": 0.05}])
+c, m, rep = ctx.search(x, [8e-2], Params(eps=1e-6, top_k=4))
+b = oracle.beta(8e-2, 40.0)
+n = oracle.nseg(b, 40.0, 60.0, 30.0, 4)
+ref = oracle.n_sigma(oracle.power(oracle.spectra(x, 256.0, 30.0, 40.0, 600, [b], [(0, i) for i in range(n)]),
+                                  7680).sum(axis=0, keepdims=True), [n])
+print("AFTER", rep["n_spectra"], float(np.max(np.abs(m - ref))))
+ctx.close()
+"""
+
+
+def test_out_of_memory_is_a_status_and_the_context_recovers(tmp_path):
+    """An allocation the device cannot satisfy comes back as SRS_ERR_OOM with a
+    message, and the same context then runs a search that fits.  The failure
+    is made on the host: SRS_ALLOC_LIMIT_BYTES caps every device allocation
+    (here 4 MB, below the 2 h search's 7 MB float32 strain copy), so no GPU
+    memory is exhausted."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "oom.py"
+    script.write_text(_OOM_SCRIPT)
+    env = dict(os.environ, SRS_ALLOC_LIMIT_BYTES=str(4 << 20))
+    r = subprocess.run([sys.executable, str(script), root], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = r.stdout.split("\n")
+    status = [l for l in lines if l.startswith("STATUS")]
+    assert status and status[0].split()[1] == "-2", r.stdout          # SRS_ERR_OOM
+    after = [l for l in lines if l.startswith("AFTER")][0].split()
+    assert int(after[1]) >= 1 and float(after[2]) < 1e-3
