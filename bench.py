@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 and cuFFT comparisons")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-two-stage", action="store_true", help="skip the two-stage (cube + stack-slide) measurement")
+    ap.add_argument("--steps-only", action="store_true",
+                    help="learned workloads: stop after the timed proposal searches (for ncu launch lists)")
     ap.add_argument("--sweep", action="store_true",
                     help="learned workloads: also measure the other proposal rules (time and recall)")
     ap.add_argument("--templates-every", type=int, default=1,
@@ -748,13 +750,20 @@ def run_learned(args):
     for k in range(args.warmup, args.warmup + args.steps):
         x = strain_for(k)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed")        # the proposal searches, for ncu --nvtx-include "timed/"
         a.record(stream)
         r = ctx.search_proposed(x, coarse, fine, p, mlp, sth)
         b.record(stream)
+        torch.cuda.nvtx.range_pop()
         ev.append((a, b))
         reps.append(r["report"])
     torch.cuda.synchronize()
     ck = clocks.stop()
+    if args.steps_only:
+        print(json.dumps({"workload": args.workload, "proposal_ms_per_step": sum(a.elapsed_time(b) for a, b in ev)
+                          / args.steps}), flush=True)
+        ctx.close()
+        return
     ms = sum(a.elapsed_time(b) for a, b in ev)
     value = full_spec * args.steps / (ms * 1e-3)
     fmap = torch.empty((len(fine), 600), dtype=torch.float32, device="cuda")

@@ -580,10 +580,29 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
     if (pl.global_x) use_tma = 0;
   } else {
     ctx->ctas_per_sm = 0;
-    if (mixed && (pl.threads != kSpreadThreads || pl.global_x)) {
-      // an explicit chunk runs the default layout: 256 threads, TMA staging where possible
+    if (mixed && ctx->subset_layout && pl.allow_128) {
+      // a refinement's template subset: 128 threads and global sample loads,
+      // the tuner's choice for whole banks of the paper's search shape
+      if (pl.threads != 128 || !pl.global_x) {
+        set_cta(pl, 128);
+        pl.global_x = true;
+        make_items(pl, pl.chunk, false, 0, 0, tail_singles(ctx));
+        s = upload_items(ctx, pl);
+        if (s != SRS_OK) return s;
+        n_items = (long long)pl.items.size();
+        SRS_CK(ctx->partial.ensure(n_items * pl.n_bins * 4), "alloc partial");
+      }
+      use_tma = 0;
+    } else if (mixed && (pl.threads != kSpreadThreads || pl.global_x)) {
+      // an explicit chunk runs the default layout: 256 threads, TMA staging
+      // where possible (items rebuilt: their anchor rows follow the layout)
       set_cta(pl, kSpreadThreads);
       pl.global_x = false;
+      make_items(pl, pl.chunk, false, 0, 0, 0);
+      s = upload_items(ctx, pl);
+      if (s != SRS_OK) return s;
+      n_items = (long long)pl.items.size();
+      SRS_CK(ctx->partial.ensure(n_items * pl.n_bins * 4), "alloc partial");
     }
   }
   // The device part of a search: one stream-ordered sequence, replayed from a

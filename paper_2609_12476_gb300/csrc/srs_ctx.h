@@ -56,6 +56,10 @@ struct srs_ctx {
   srs::Plan plan;
   // the search's device sequence as a CUDA graph, and what it was captured for
   bool use_graphs = true;
+  // refinement of a fine-template subset: run the layout the tuner picks for
+  // whole banks of this shape (128 threads, global sample loads) instead of
+  // tuning every one-off subset
+  bool subset_layout = false;
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<unsigned char> graph_key;
   int graph_launches = 0;

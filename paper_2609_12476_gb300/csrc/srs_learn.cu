@@ -220,10 +220,14 @@ __global__ void k_gather_batch(const float* __restrict__ X, const float* __restr
 // ---------------------------------------------------------------------------
 // Refinement: direct sums at a few bins of one template, accumulated over
 // segments.  One CTA per work item (template, bin group, segment chunk); per
-// segment, each thread walks its samples with the same FP64-anchored phase as
-// the spreader and adds x_j exp(-2 pi i (f_c + k/t_coh) delta_j) for each bin
-// of the group; (P - 2) / 2 is summed over the chunk's segments.
+// segment, each lane walks a run of consecutive samples and steps the same
+// 64-bit fixed-point phase as the spreader (a LaneMap seeded from the warp's
+// FP64 anchor), adding x_j exp(-2 pi i (f_c + k/t_coh) delta_j) for each bin
+// of the group: the demodulation phase k_c Psi (or its own map when k_c is
+// not whole) plus k Psi, both mod 1 cycle; (P - 2) / 2 is summed over the
+// chunk's segments.
 // ---------------------------------------------------------------------------
+template <bool INT_KC>
 __global__ void __launch_bounds__(256)
 k_sparse_bins(const float* __restrict__ strain, const SparseItem* __restrict__ items, int n_items,
               const double* __restrict__ betas, const int* __restrict__ bins, SparseArgs a,
@@ -238,6 +242,9 @@ k_sparse_bins(const float* __restrict__ strain, const SparseItem* __restrict__ i
     int kk[kSparseMaxBins];
 #pragma unroll
     for (int u = 0; u < kSparseMaxBins; ++u) kk[u] = u < nb ? bins[it.b0 + u] - a.half_bins : 0;
+    bool adjacent = false;                  // the group holds two neighbouring bins (uniform over the block)
+#pragma unroll
+    for (int u = 1; u < kSparseMaxBins; ++u) adjacent = adjacent || (u < nb && kk[u] == kk[u - 1] + 1);
     __syncthreads();   // the previous item is done with anc and sZ
     {
       const double b = betas[it.m];
@@ -252,28 +259,44 @@ k_sparse_bins(const float* __restrict__ strain, const SparseItem* __restrict__ i
 #pragma unroll
       for (int u = 0; u < kSparseMaxBins; ++u) { re[u] = 0.f; im[u] = 0.f; }
       const float* x = strain + (long long)i * a.n_s;
-      // each warp walks its anchor span, lanes interleaved (coalesced loads)
+      // warp w walks anchor span w; lane l its run of consecutive samples
       const int j_lo = warp * a.span;
       const int j_hi = min(j_lo + a.span, a.n_s);
-      if (j_lo < a.n_s) {
+      const int j0 = j_lo + lane * a.run, j1 = min(j0 + a.run, j_hi);
+      if (j0 < j1) {
         const Anchor A = anc[i - it.i0][warp];
-        for (int j = j_lo + lane; j < j_hi; j += 32) {
-          uint32_t Psi;
-          float th;
-          mixed_phase(A, j - j_lo, a.kc, Psi, th);
-          // f_b delta = f_c delta + k delta / t_coh: the k-term is k * Psi exactly (mod 1)
-          const uint32_t T0 = (uint32_t)__float2int_rn(th * 4294967296.0f);
+        LaneMap m = lane_map(A, anchor_psi0(A), A.n1, A.p1lo, A.q2, 1.0f, j0 - j_lo);
+        LaneMap mt;
+        if (!INT_KC) mt = lane_map(A, anchor_th0(A), A.m1, A.m1lo, A.kq2, a.kc, j0 - j_lo);
+        const uint32_t kc = (uint32_t)a.kc_int;
+        for (int j = j0; j < j1; ++j) {
+          const uint32_t ph = (uint32_t)(m.v >> 32), pl = (uint32_t)m.v;
+          // f_b delta = f_c delta + k delta / t_coh: the k-term is k Psi (mod 1)
+          const uint32_t T0 = INT_KC ? ph * kc + __umulhi(pl, kc) : (uint32_t)(mt.v >> 32);
+          const uint32_t Psi = ph + (pl >> 31);            // rounded to 2^-32 periods
           const float xv = x[j];
+          // the phasor of a bin next to the previous one is the previous one
+          // turned by exp(-2 pi i Psi)
+          float s1 = 0.f, c1 = 1.f;
+          if (adjacent) __sincosf((float)(int32_t)Psi * 1.4629180792671596e-09f, &s1, &c1);  // 2 pi / 2^32
+          float sn = 0.f, cs = 1.f;
 #pragma unroll
           for (int u = 0; u < kSparseMaxBins; ++u) {
             if (u < nb) {
-              const uint32_t Tb = T0 + (uint32_t)kk[u] * Psi;
-              float sn, cs;
-              __sincosf((float)(int32_t)Tb * 1.4629180792671596e-09f, &sn, &cs);  // 2 pi / 2^32
+              if (u > 0 && kk[u] == kk[u - 1] + 1) {
+                const float c = cs * c1 - sn * s1;
+                sn = fmaf(sn, c1, cs * s1);
+                cs = c;
+              } else {
+                const uint32_t Tb = T0 + (uint32_t)kk[u] * Psi;
+                __sincosf((float)(int32_t)Tb * 1.4629180792671596e-09f, &sn, &cs);  // 2 pi / 2^32
+              }
               re[u] = fmaf(xv, cs, re[u]);
               im[u] = fmaf(-xv, sn, im[u]);
             }
           }
+          m.step();
+          if (!INT_KC) mt.step();
         }
       }
 #pragma unroll
@@ -380,7 +403,10 @@ cudaError_t launch_sparse_bins(const float* strain, const SparseItem* items, int
   long long blocks = n_items;
   if (blocks > (long long)n_sm * 8) blocks = (long long)n_sm * 8;
   if (blocks < 1) blocks = 1;
-  k_sparse_bins<<<(unsigned)blocks, 256, 0, st>>>(strain, items, n_items, betas, bins, a, partial);
+  if (a.kc_int)
+    k_sparse_bins<true><<<(unsigned)blocks, 256, 0, st>>>(strain, items, n_items, betas, bins, a, partial);
+  else
+    k_sparse_bins<false><<<(unsigned)blocks, 256, 0, st>>>(strain, items, n_items, betas, bins, a, partial);
   return cudaGetLastError();
 }
 

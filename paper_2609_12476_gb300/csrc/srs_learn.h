@@ -20,8 +20,11 @@ static_assert(kParams == kHidden * kPatchSize + 2 * kHidden + 1, "parameter coun
 constexpr int kSparseMaxBins = 8;                   // bins per refinement work item
 constexpr int kSparseChunk = 16;                    // segments per refinement work item
 // Above this many requested bins a template is refined through the NUFFT
-// (one spectrum gives every bin) instead of direct sums (one pass per bin).
-constexpr int kDirectMaxBins = 24;
+// (one spectrum gives every bin) instead of direct sums.  A direct-sum pass
+// over a segment costs about a sixth of a NUFFT spectrum plus, per bin, a
+// sine and cosine (or, for the next bin up, one complex rotation): two groups
+// of eight bins cost about as much as the spectrum.
+constexpr int kDirectMaxBins = 16;
 
 struct InjectionDev {
   double beta, f0, amp, phi0_cyc, t_end;
@@ -37,6 +40,8 @@ struct SparseItem {
 
 struct SparseArgs {
   int n_s, span, half_bins;
+  int run;                        // samples per lane (consecutive), span = 32 run
+  int kc_int;                     // f_c t_coh when it is a whole number in [1, 2^30), else 0
   float kc, inv_ns;
   AnchorArgs aa;
 };

@@ -149,7 +149,7 @@ srs_status refine_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
       srs_params ps = pc;
       ps.io_on_device = 1;
       ps.top_k = 1;
-      ps.chunk = 16;   // no autotuning of a one-off template subset
+      ps.chunk = 4;    // no autotuning of a one-off template subset: the full banks' tuned layout
       const void* dstrain_all = strain;
       if (!params->io_on_device) {
         const size_t bytes = (size_t)n_samples * (dtype == SRS_F64 ? 8 : 4);
@@ -165,8 +165,10 @@ srs_status refine_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
       // a one-off template subset: launched directly, not captured as a graph
       const bool graphs = ctx->use_graphs;
       ctx->use_graphs = false;
+      ctx->subset_layout = true;
       s = search_impl(ctx, dstrain_all, n_samples, dtype, dmc.data(), (int32_t)dense.size(), &ps,
                       ctx->S.as<float>(), ctx->ccands.as<srs_candidate>(), &nc, &rs);
+      ctx->subset_layout = false;
       ctx->use_graphs = graphs;
       if (s != SRS_OK) return s;
       std::vector<float> dmap(dense.size() * (size_t)pl.n_bins);
@@ -281,7 +283,9 @@ srs_status refine_impl(srs_ctx* ctx, const void* strain, int64_t n_samples, int3
   std::memset(&a, 0, sizeof a);
   a.n_s = (int)pl.n_s;
   a.span = pl.span;
+  a.run = pl.run;
   a.half_bins = pl.half_bins;
+  a.kc_int = (pl.k_c >= 1.0 && pl.k_c < 1073741824.0 && pl.k_c == std::floor(pl.k_c)) ? (int)pl.k_c : 0;
   a.kc = (float)pl.k_c;
   a.inv_ns = (float)(1.0 / (double)pl.n_s);
   a.aa.fs = pl.fs;
