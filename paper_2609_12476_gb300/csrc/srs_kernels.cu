@@ -10,7 +10,7 @@
 // Two forms:
 //   mixed  -- k_mixed: a persistent kernel over (template, segment-chunk)
 //             items with FP64 anchors of the time map (a few per segment),
-//             FP32 spreading, shared-memory Stockham FFT and FP32 power/sum;
+//             FP32 spreading, shared-memory FFT and FP32 power/sum;
 //             then an ordered FP64 reduction with the top-k
 //             (k_reduce_mixed_top32, or k_reduce_mixed + k_topk_tile);
 //   plain  -- k_plain: one CTA per spectrum, every step in FP64.
@@ -114,44 +114,45 @@ __device__ __forceinline__ void stockham_pass(const C* __restrict__ in, C* __res
   }
 }
 
-// One Stockham pass with the radix, stride and size known at compile time
-// (index arithmetic folds to multiplies and shifts).
-template <typename C, int R, int Ns, int N>
-__device__ __forceinline__ void stockham_pass_c(const C* __restrict__ in, C* __restrict__ out,
-                                                const C* __restrict__ tw) {
-  constexpr int nR = N / R;
-  constexpr int step = N / (Ns * R);
-  for (int j = threadIdx.x; j < nR; j += blockDim.x) {
-    const int jm = j % Ns;
+// One in-place decimation-in-frequency pass of radix R over sub-transforms of
+// length M (Gentleman-Sande): butterfly (block c, k < L = M / R) takes
+// x[cM + k + sL] for s < R, forms y_r = sum_s x_s exp(-2 pi i rs / R) and
+// writes y_r exp(-2 pi i rk / M) back to x[cM + k + rL].  Every butterfly
+// reads and writes its own R elements, so the pass needs no second buffer.
+template <typename C, int R, int M, int N>
+__device__ __forceinline__ void dif_pass(C* a, const C* __restrict__ tw) {
+  constexpr int L = M / R;
+  for (int j = threadIdx.x; j < N / R; j += blockDim.x) {
+    const int c = j / L, k = j - c * L;
+    const int base = c * M + k;
     C v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = in[j + r * nR];
-    if (Ns > 1) {
-#pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[jm * r * step]);
-    }
+    for (int r = 0; r < R; ++r) v[r] = a[base + r * L];
     Dft<C, R>::run(v);
-    const int idxD = (j - jm) * R + jm;
+    a[base] = v[0];
 #pragma unroll
-    for (int r = 0; r < R; ++r) out[idxD + r * Ns] = v[r];
+    for (int r = 1; r < R; ++r) a[base + r * L] = L > 1 ? cmul(v[r], tw[r * k * (N / M)]) : v[r];
   }
+  __syncthreads();
 }
 
-// n = 1200 = 4 * 4 * 3 * 5 * 5 (the 40-60 Hz band at oversampling 2), five
-// passes ending in b.
+// n = 1200 in place: DIF passes of radix 4, 4, 3, 5, 5.  Frequency f ends at
+// position dif_1200_pos(f): with f = r1 + 4 (r2 + 4 (r3 + 3 (r4 + 5 r5))),
+// the position is r1 300 + r2 75 + r3 25 + r4 5 + r5.
 template <typename C>
-__device__ __forceinline__ C* fft_1200(C* a, C* b, const C* __restrict__ tw) {
-  stockham_pass_c<C, 4, 1, 1200>(a, b, tw);
-  __syncthreads();
-  stockham_pass_c<C, 4, 4, 1200>(b, a, tw);
-  __syncthreads();
-  stockham_pass_c<C, 3, 16, 1200>(a, b, tw);
-  __syncthreads();
-  stockham_pass_c<C, 5, 48, 1200>(b, a, tw);
-  __syncthreads();
-  stockham_pass_c<C, 5, 240, 1200>(a, b, tw);
-  __syncthreads();
-  return b;
+__device__ __forceinline__ void fft_1200_dif(C* a, const C* __restrict__ tw) {
+  dif_pass<C, 4, 1200, 1200>(a, tw);
+  dif_pass<C, 4, 300, 1200>(a, tw);
+  dif_pass<C, 3, 75, 1200>(a, tw);
+  dif_pass<C, 5, 25, 1200>(a, tw);
+  dif_pass<C, 5, 5, 1200>(a, tw);
+}
+__device__ __forceinline__ int dif_1200_pos(int f) {
+  const int r1 = f & 3, f1 = f >> 2;
+  const int r2 = f1 & 3, f2 = f1 >> 2;
+  const int f3 = f2 / 3, r3 = f2 - 3 * f3;
+  const int r5 = f3 / 5, r4 = f3 - 5 * r5;
+  return r1 * 300 + r2 * 75 + r3 * 25 + r4 * 5 + r5;
 }
 
 // Forward FFT of a[0..n) in shared memory, ping-ponging with b.  Returns the
@@ -443,8 +444,9 @@ k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_
   // otherwise a TMA bulk copy stages each segment in shared memory
   float* xs = reinterpret_cast<float*>(smem);                       // [ns4] unless GLOBAL_X
   float2* g0 = reinterpret_cast<float2*>(xs + (GLOBAL_X ? 0 : a.ns4));  // [n_fine]
-  float2* g1 = g0 + a.n_fine;                                       // [n_fine]
-  float* Z = reinterpret_cast<float*>(g1 + a.n_fine);               // [nb4]
+  // the generic FFT ping-pongs with a second buffer; the 1200-point one runs in place
+  float2* g1 = g0 + a.n_fine;                                       // [n_fine] unless 1200
+  float* Z = reinterpret_cast<float*>(a.fft_fixed == 1200 ? g1 : g1 + a.n_fine);   // [nb4]
   Anchor* anc = reinterpret_cast<Anchor*>(Z + a.nb4);               // [chunk * n_anchor]
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_item, s_abort;
@@ -507,11 +509,14 @@ k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_
         __syncthreads();
         continue;
       }
-      float2* res = a.fft_fixed == 1200 ? fft_1200<float2>(g0, g1, tw)
-                                        : fft_smem<float2>(g0, g1, a.n_fine, s_rad, a.n_pass, tw);
+      const bool dif = a.fft_fixed == 1200;
+      float2* res = g0;
+      if (dif) fft_1200_dif<float2>(g0, tw);
+      else res = fft_smem<float2>(g0, g1, a.n_fine, s_rad, a.n_pass, tw);
       for (int b = tid; b < a.n_bins; b += blockDim.x) {
         int k = b - a.half_bins;
         int idx = k < 0 ? k + a.n_fine : k;
+        if (dif) idx = dif_1200_pos(idx);
         const float2 G = res[idx];
         const float c = a.corr[b];
         const float fx = G.x * c, fy = G.y * c;
@@ -866,7 +871,7 @@ __global__ void k_time_map_plain(const int* __restrict__ item_m, const int* __re
 // ---------------------------------------------------------------------------
 size_t mixed_smem_bytes(const MixedArgs& a) {
   size_t s = a.use_tma ? (size_t)a.ns4 * sizeof(float) : 0;
-  s += (size_t)a.n_fine * 2 * sizeof(float2);
+  s += (size_t)a.n_fine * (a.fft_fixed == 1200 ? 1 : 2) * sizeof(float2);
   s += (size_t)a.nb4 * sizeof(float);
   s += (size_t)a.chunk * a.n_anchor * sizeof(Anchor);
   return s;

@@ -212,9 +212,10 @@ srs_status make_plan(const srs_params& p, const double* mc, int32_t n_templates,
     es_params(pl.sigma, pl.w, pl.beta_es);
     if (pl.w > kMixedMaxW) return fail(SRS_ERR_UNSUPPORTED, "kernel width above the mixed form's maximum (raise eps or sigma)");
     pl.n_fine = next_smooth(std::max((int32_t)std::ceil(pl.sigma * pl.n_bins - 1e-9), 2 * pl.w));
-    // shared memory of the mixed spreader: staged samples + grid + FFT scratch + Z
+    // shared memory of the mixed spreader: staged samples + grid + FFT scratch
+    // (none for the in-place 1200-point FFT; counted here for any size) + Z
     // + anchors of one item (at most 16 segments)
-    size_t need = (size_t)pl.n_s * 4 + (size_t)pl.n_fine * 16 + (size_t)pl.n_bins * 4 + 16 * 8 * 48 + 1024;
+    size_t need = (size_t)pl.n_s * 4 + (size_t)pl.n_fine * 16 + (size_t)pl.n_bins * 4 + 16 * 8 * sizeof(Anchor) + 1024;
     if (need > smem_cap) return fail(SRS_ERR_UNSUPPORTED, "segment too long or band too wide for the mixed form's shared memory");
   } else {
     const double sig_try[3] = {2.0, 1.5, 1.25};
