@@ -89,6 +89,44 @@ template <typename C> struct Dft<C, 5> {
   }
 };
 
+// Composite radices by the prime-factor (Good-Thomas) map, N = N1 N2 with
+// gcd(N1, N2) = 1: x[(N2 n1 + N1 n2) mod N] forms an N1 x N2 array; DFT-N1
+// down its columns, then DFT-N2 along its rows, gives X[k] at
+// k = (N2 (N2^-1 mod N1) k1 + N1 (N1^-1 mod N2) k2) mod N.  The index maps
+// are compile-time register renamings: no twiddle factors between the two.
+template <typename C, int N1, int N2, int A1, int A2>
+__device__ __forceinline__ void dft_pfa(C* v) {
+  constexpr int N = N1 * N2;
+  C a[N1][N2];
+#pragma unroll
+  for (int n1 = 0; n1 < N1; ++n1)
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) a[n1][n2] = v[(N2 * n1 + N1 * n2) % N];
+#pragma unroll
+  for (int n2 = 0; n2 < N2; ++n2) {
+    C t[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) t[n1] = a[n1][n2];
+    Dft<C, N1>::run(t);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) a[k1][n2] = t[k1];
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) {
+    Dft<C, N2>::run(a[k1]);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) v[(A1 * k1 + A2 * k2) % N] = a[k1][k2];
+  }
+}
+// 12 = 4 x 3: 3^-1 mod 4 = 3, 4^-1 mod 3 = 1, so k = (9 k1 + 4 k2) mod 12.
+template <typename C> struct Dft<C, 12> {
+  static __device__ __forceinline__ void run(C* v) { dft_pfa<C, 4, 3, 9, 4>(v); }
+};
+// 10 = 5 x 2: 2^-1 mod 5 = 3, 5^-1 mod 2 = 1, so k = (6 k1 + 5 k2) mod 10.
+template <typename C> struct Dft<C, 10> {
+  static __device__ __forceinline__ void run(C* v) { dft_pfa<C, 5, 2, 6, 5>(v); }
+};
+
 // One Stockham autosort pass of radix R over n points (Ns = product of the
 // radices already applied).  Butterfly j reads in[j + r n/R], multiplies by
 // the twiddles exp(-2 pi i (j mod Ns) r / (Ns R)), transforms, and writes
@@ -136,23 +174,21 @@ __device__ __forceinline__ void dif_pass(C* a, const C* __restrict__ tw) {
   __syncthreads();
 }
 
-// n = 1200 in place: DIF passes of radix 4, 4, 3, 5, 5.  Frequency f ends at
-// position dif_1200_pos(f): with f = r1 + 4 (r2 + 4 (r3 + 3 (r4 + 5 r5))),
-// the position is r1 300 + r2 75 + r3 25 + r4 5 + r5.
+// n = 1200 in place: DIF passes of radix 10, 10, 12 (each a prime-factor
+// DFT in registers; three passes and two twiddle stages instead of five and
+// four with radices 4, 4, 3, 5, 5).  Frequency f ends at position
+// dif_1200_pos(f): with f = r1 + 10 (r2 + 10 r3), the position is
+// r1 120 + r2 12 + r3.
 template <typename C>
 __device__ __forceinline__ void fft_1200_dif(C* a, const C* __restrict__ tw) {
-  dif_pass<C, 4, 1200, 1200>(a, tw);
-  dif_pass<C, 4, 300, 1200>(a, tw);
-  dif_pass<C, 3, 75, 1200>(a, tw);
-  dif_pass<C, 5, 25, 1200>(a, tw);
-  dif_pass<C, 5, 5, 1200>(a, tw);
+  dif_pass<C, 10, 1200, 1200>(a, tw);
+  dif_pass<C, 10, 120, 1200>(a, tw);
+  dif_pass<C, 12, 12, 1200>(a, tw);
 }
 __device__ __forceinline__ int dif_1200_pos(int f) {
-  const int r1 = f & 3, f1 = f >> 2;
-  const int r2 = f1 & 3, f2 = f1 >> 2;
-  const int f3 = f2 / 3, r3 = f2 - 3 * f3;
-  const int r5 = f3 / 5, r4 = f3 - 5 * r5;
-  return r1 * 300 + r2 * 75 + r3 * 25 + r4 * 5 + r5;
+  const int f1 = f / 10, r1 = f - 10 * f1;
+  const int r3 = f1 / 10, r2 = f1 - 10 * r3;
+  return r1 * 120 + r2 * 12 + r3;
 }
 
 // Forward FFT of a[0..n) in shared memory, ping-ponging with b.  Returns the
@@ -262,7 +298,10 @@ __global__ void k_wait_selftest(int* __restrict__ err) {
 // (64-bit fixed point, integer steps): Psi' = Psi - W/(2n) - base/n periods,
 // where base is the lane's base cell (one cell before its first sample's
 // first tap), so that s = Psi' n is the position of the first tap relative
-// to base and never wraps within the lane's run.  The demodulation phase is
+// to base and never wraps within the lane's run.  A sample is keyed by
+// floor(s): its taps go to cells floor(s) + 1 ... floor(s) + W.  (At an
+// exact integer s, W + 1 cells are in reach and both end cells carry the
+// kernel's edge value 2^-E; the walk takes the last W.)  The demodulation phase is
 // k_c Psi mod 1 from the same Psi when k_c is a whole number, else a second
 // LaneMap.
 //
@@ -272,13 +311,15 @@ __global__ void k_wait_selftest(int* __restrict__ err) {
 // Z = Z0 + t H (H = 2E/W); taps are evaluated in pairs on the packed FP32x2
 // pipe.
 //
-// Cell walk.  The lane keeps the W cells [Bm, Bm + W) of its kernel
+// Cell walk.  The lane keeps the W cells [Bm + 1, Bm + 1 + W) of its kernel
 // footprint in registers.  The warp walks cell by cell: each lane adds all
-// of its samples whose first tap is cell Bm, then every lane flushes cell Bm
+// of its samples keyed Bm, then every lane flushes cell Bm + 1
 // with a shared-memory atomic and moves its window one cell on, so the step
 // is warp-uniform.  The window is a ring: the walk is unrolled W times so
-// that, at step R of the unrolled loop, cell Bm + t lives in register
+// that, at step R of the unrolled loop, cell Bm + 1 + t lives in register
 // acc[(t + R) % W] and moving on renames registers instead of copying them.
+// The per-sample step has no branch: the next sample's load index is clamped
+// to the run, and a step past the run's end computes inputs nobody reads.
 template <int W, bool INT_KC>
 struct CellWalk {
   float2 acc[W];
@@ -288,7 +329,7 @@ struct CellWalk {
   LaneMap mt;
   uint32_t thofs, kc, n;
   int base, j, j_end, Bm;
-  float x_next, H, eh32, E;
+  float x_next, H, eh32, E, EH1;
   bool live;
   unsigned mask;
   const float* __restrict__ xs;
@@ -307,8 +348,8 @@ struct CellWalk {
     __sincosf((float)(int32_t)th * 1.4629180792671596e-09f, &sn, &cs);
     const unsigned long long sp = (unsigned long long)ph * n + __umulhi(pl, n);
     const uint32_t sl = (uint32_t)sp;
-    l0 = (int)(sp >> 32) + (sl != 0u ? 1 : 0);
-    z0 = fmaf(eh32, (float)(0u - sl), -E);
+    l0 = (int)(sp >> 32);
+    z0 = fmaf(-eh32, (float)sl, EH1);
     cre = x * cs;
     cim = -x * sn;
     m.step();
@@ -317,11 +358,9 @@ struct CellWalk {
   __device__ __forceinline__ void next() {
     ++j;
     live = j < j_end;
-    if (live) {
-      const float x = x_next;
-      if (j + 1 < j_end) x_next = xs[j + 1];
-      inputs(x);
-    }
+    const float x = x_next;
+    x_next = xs[min(j + 1, j_end - 1)];
+    inputs(x);
   }
 
   __device__ __forceinline__ void flush_cell(int c_rel, float2 v) {
@@ -395,6 +434,7 @@ __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2*
   w.E = E;
   w.H = E * a.two_over_w;
   w.eh32 = w.H * 2.3283064365386963e-10f;
+  w.EH1 = w.H - E;
   w.n = (uint32_t)a.n_fine;
   w.kc = (uint32_t)a.kc_int;
   w.mask = __activemask();
@@ -418,6 +458,7 @@ __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2*
     w.m.v -= off;
     const unsigned long long o = a.wofs + off;
     w.thofs = (uint32_t)(o >> 32) * w.kc + __umulhi((uint32_t)o, w.kc);  // k_c (W/(2n) + base/n) mod 1
+    w.base = base + 1;   // flushes address cell base + 1 + c_rel: a sample keyed l0 has its first tap at l0 + 1
     if (!INT_KC) w.mt = lane_map(A, anchor_th0(A), A.m1, A.m1lo, A.kq2, a.kc, l);
     const float x0 = xs[j_begin];
     w.x_next = j_begin + 1 < j_end ? xs[j_begin + 1] : 0.f;

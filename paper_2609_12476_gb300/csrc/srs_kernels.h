@@ -25,7 +25,7 @@ struct MixedArgs {
   int use_tma;                    // 1: samples staged by TMA bulk copies (n_s % 4 == 0, 16-byte aligned strain);
                                   // 0: samples read straight from the strain in global memory
   int threads;                    // threads per CTA (128 or 256); run, span and n_anchor follow it
-  int fft_fixed;                  // 1200: the compile-time 4-4-3-5-5 plan applies; 0: generic passes
+  int fft_fixed;                  // 1200: the compile-time in-place 10-10-12 transform applies; 0: generic passes
   int seg_begin, seg_range;       // spectra output: first segment, segments per template
   AnchorArgs aa;                  // FP64 anchor inputs
   float kc;                       // f_c * t_coh
