@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsrs.so")
 SOURCES = ["srs_kernels.cu", "srs_capi.cpp", "srs_plan.cpp", "srs_noalloc.cu", "srs_learn.cu", "srs_learn_capi.cpp",
-           "srs_slide.cu", "srs_slide_capi.cpp", "srs_stats.cpp", "srs_score_tc.cu"]
+           "srs_slide.cu", "srs_slide_capi.cpp", "srs_stats.cpp", "srs_score_tc.cu", "srs_reduce.cu"]
 HEADERS = ["srs_internal.h", "srs_kernels.h", "srs_ctx.h", "srs_device.cuh", "srs_learn.h", "srs_slide.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
