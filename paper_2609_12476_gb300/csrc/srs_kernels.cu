@@ -308,7 +308,10 @@ __global__ void k_wait_selftest(int* __restrict__ err) {
 // log2 e; the constant 2^-E is left to the deconvolution factors.  With
 // Z = E z, E sqrt(1 - z^2) = sqrt(E^2 - Z^2), and tap t of a sample sits at
 // Z = Z0 + t H (H = 2E/W); taps are evaluated in pairs on the packed FP32x2
-// pipe.
+// pipe.  The first pair sits at (Z0, Z0 + H) and each further pair is one
+// packed add of 2H on, so every operand is an ordinary register: packed
+// multiply-adds by the tap numbers (Z = (t, t + 1) H + Z0) left the compiler
+// moving those constants out of uniform registers for every sample.
 //
 // Cell walk.  The lane keeps the W cells [Bm + 1, Bm + 1 + W) of its kernel
 // footprint in registers.  The warp walks cell by cell: each lane adds all
@@ -328,7 +331,7 @@ struct CellWalk {
   LaneMap mt;
   uint32_t thofs, kc, n;
   int base, j, j_end, Bm;
-  float x_next, H, eh32, E, EH1;
+  float x_next, H, eh32, E, EH1, H2, mE2;
   bool live;
   unsigned mask;
   const float* __restrict__ xs;
@@ -372,14 +375,13 @@ struct CellWalk {
   template <int R>
   __device__ __forceinline__ bool cell() {
     if (!__any_sync(mask, live)) return false;
-    const float2 HH = make_float2(H, H), mEE = make_float2(-E * E, -E * E);
+    const float2 H2H2 = make_float2(H2, H2), mEE = make_float2(mE2, mE2);
     while (live && l0 == Bm) {
-      const float2 ZZ = make_float2(z0, z0);
       const float2 cv = make_float2(cre, cim);
+      float2 Z = make_float2(z0, z0 + H);   // taps 0 and 1; each further pair 2H on
 #pragma unroll
       for (int t = 0; t + 1 < W; t += 2) {
-        const float2 tt = make_float2((float)t, (float)(t + 1));
-        const float2 Z = __ffma2_rn(tt, HH, ZZ);
+        if (t > 0) Z = __fadd2_rn(Z, H2H2);
         const float2 q = __ffma2_rn(Z, Z, mEE);
         const float p0 = ex2_approx(sqrt_approx(fabsf(q.x)));
         const float p1 = ex2_approx(sqrt_approx(fabsf(q.y)));
@@ -387,8 +389,8 @@ struct CellWalk {
         acc[(t + 1 + R) % W] = __ffma2_rn(make_float2(p1, p1), cv, acc[(t + 1 + R) % W]);
       }
       if (W & 1) {
-        const float Zl = fmaf((float)(W - 1), H, z0);
-        const float pl = ex2_approx(sqrt_approx(fabsf(fmaf(Zl, Zl, -E * E))));
+        const float Zl = W == 1 ? z0 : Z.x + H2;
+        const float pl = ex2_approx(sqrt_approx(fabsf(fmaf(Zl, Zl, mE2))));
         acc[(W - 1 + R) % W] = __ffma2_rn(make_float2(pl, pl), cv, acc[(W - 1 + R) % W]);
       }
       next();
@@ -434,6 +436,8 @@ __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2*
   w.H = E * a.two_over_w;
   w.eh32 = w.H * 2.3283064365386963e-10f;
   w.EH1 = w.H - E;
+  w.H2 = 2.f * w.H;
+  w.mE2 = -E * E;
   w.n = (uint32_t)a.n_fine;
   w.kc = (uint32_t)a.kc_int;
   w.mask = __activemask();
