@@ -701,6 +701,10 @@ SWEEP = [
      {"nms": (4, 16), "nms_by_nsigma": True, "fine_rows": 0}),
     ("coarse n_sigma peaks (+-8, +-32), FAR 1e-3, own row", 1e-3,
      {"nms": (8, 32), "nms_by_nsigma": True, "fine_rows": 0}),
+    ("every cell above threshold, FAR 1e-3, +-1 row, best 1024 fine templates", 1e-3, {"template_budget": 1024}),
+    ("every cell above threshold, FAR 1e-3, +-1 row, best 512 fine templates", 1e-3, {"template_budget": 512}),
+    ("every cell above threshold, FAR 1e-3, +-1 row, best 256 fine templates", 1e-3, {"template_budget": 256}),
+    ("every cell above threshold, FAR 1e-3, +-1 row, best 128 fine templates", 1e-3, {"template_budget": 128}),
 ]
 
 
@@ -788,18 +792,20 @@ def run_learned(args):
     pareto = None
     if args.sweep:
         pareto = []
-        n_real, per_real = L["evals"][-1]
         for name, far, kw in SWEEP:
             s_th, n_th = proposal.calibrate(ctx, mlp, coarse, p, t_obs, 10, seed=5, far=far,
                                             nms=kw.get("nms", proposal.NO_NMS),
                                             component_top=kw.get("component_top", 0),
                                             nms_by_nsigma=kw.get("nms_by_nsigma", False))
-            e = proposal.evaluate(ctx, mlp, s_th, n_th, coarse, fine, p, t_obs, n_real, per_real, seed=29,
-                                  baselines=False, **kw)
-            pareto.append({"rule": name, "proposal_ms_per_map": e["proposal_ms"] / n_real,
-                           "full_ms_per_map": e["full_ms"] / n_real, "recall_proposal": e["recall_proposal"],
-                           "recall_full": e["recall_full"], "proposal_cells": e["proposal_cells"] / n_real,
-                           "proposed_coarse": e["proposed_coarse"] / n_real})
+            # every rule on every injection density of the workload (sparse and crowded maps)
+            for n_real, per_real in L["evals"]:
+                e = proposal.evaluate(ctx, mlp, s_th, n_th, coarse, fine, p, t_obs, n_real, per_real, seed=29,
+                                      baselines=False, **kw)
+                pareto.append({"rule": name, "injections_per_map": per_real, "maps": n_real,
+                               "proposal_ms_per_map": e["proposal_ms"] / n_real,
+                               "full_ms_per_map": e["full_ms"] / n_real, "recall_proposal": e["recall_proposal"],
+                               "recall_full": e["recall_full"], "proposal_cells": e["proposal_cells"] / n_real,
+                               "proposed_coarse": e["proposed_coarse"] / n_real})
     line = {"metric": METRIC + " (full-grid equivalent, learned proposal)", "value": value, "unit": UNIT,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

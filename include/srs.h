@@ -518,6 +518,9 @@ typedef struct {
   int32_t component_top;   /* > 0: of each 8-connected group of cells above the threshold, propose only
                               the component_top cells with the highest coarse n_sigma (suppression off) */
   int32_t nms_by_nsigma;   /* 1: the suppression window compares coarse n_sigma instead of scores */
+  int32_t template_budget; /* > 0: refine at most this many fine templates -- those whose best proposing
+                              coarse cell has the highest score (ties: lower template index); the
+                              others' proposed cells are dropped.  0: no budget */
 } srs_proposal_params;
 
 /* The proposal search: the coarse search over coarse_mc, network scores of

@@ -90,7 +90,7 @@ class _TrainCfg(ctypes.Structure):
 class _ProposalParams(ctypes.Structure):
     _fields_ = [("score_threshold", ctypes.c_float), ("nms_templates", ctypes.c_int32),
                 ("nms_bins", ctypes.c_int32), ("fine_rows", ctypes.c_int32), ("component_top", ctypes.c_int32),
-                ("nms_by_nsigma", ctypes.c_int32)]
+                ("nms_by_nsigma", ctypes.c_int32), ("template_budget", ctypes.c_int32)]
 
 
 class _ProposalReport(ctypes.Structure):
@@ -679,14 +679,16 @@ class Context:
         return ns, _report_dict(rep)
 
     def search_proposed(self, strain, coarse_mc, fine_mc, params, mlp_params, threshold, max_cells=1 << 20,
-                        nms=(0, 0), fine_rows=1, component_top=0, nms_by_nsigma=False):
+                        nms=(0, 0), fine_rows=1, component_top=0, nms_by_nsigma=False, template_budget=0):
         """srs_search_proposed: returns dict(cells [n, 2], nsigma [n], cands,
         report).  nms = (templates, bins) half-window of the non-maximum
         suppression ((0, 0): off); fine_rows = coarse rows either side whose
         fine templates a proposal covers; component_top > 0: each connected
         group of above-threshold cells proposes its component_top cells of
         highest coarse n_sigma; nms_by_nsigma: the suppression window
-        compares coarse n_sigma instead of scores."""
+        compares coarse n_sigma instead of scores; template_budget > 0: only
+        the template_budget fine templates with the highest best proposing
+        score are refined."""
         cmc = np.ascontiguousarray(coarse_mc, dtype=np.float64)
         fmc = np.ascontiguousarray(fine_mc, dtype=np.float64)
         mp = np.ascontiguousarray(mlp_params, dtype=np.float32)
@@ -703,8 +705,10 @@ class Context:
             strain = np.ascontiguousarray(strain)
             p.io_on_device = 0
             ptr, n = strain.ctypes.data, strain.size
+        if int(template_budget) < 0:
+            raise ValueError("template_budget must be >= 0")
         pp = _ProposalParams(float(threshold), int(nms[0]), int(nms[1]), int(fine_rows), int(component_top),
-                             int(bool(nms_by_nsigma)))
+                             int(bool(nms_by_nsigma)), int(template_budget))
         st = self._lib.srs_search_proposed(self._h, ptr, n, _dtype_code(strain), cmc.ctypes.data, cmc.size,
                                            fmc.ctypes.data, fmc.size, ctypes.byref(p), mp.ctypes.data,
                                            ctypes.byref(pp), max_cells, cm.ctypes.data, cb.ctypes.data,

@@ -648,6 +648,8 @@ srs_status srs_search_proposed(srs_ctx* ctx, const void* strain, int64_t n_sampl
     std::vector<std::vector<int32_t>> children(n_coarse);
     for (int32_t f = 0; f < n_fine; ++f) children[parent[f]].push_back(f);
     std::vector<long long> fk;
+    // best score of the coarse cells proposing each fine template (for the budget)
+    std::vector<float> tbest(params_prop.template_budget > 0 ? n_fine : 0, -INFINITY);
     int32_t proposed = 0;
     const int32_t rt = std::max(0, params_prop.nms_templates), rb = std::max(0, params_prop.nms_bins);
     const int32_t rows = std::max(0, params_prop.fine_rows);
@@ -670,12 +672,31 @@ srs_status srs_search_proposed(srs_ctx* ctx, const void* strain, int64_t n_sampl
       }
       ++proposed;
       for (int32_t c = std::max(0, cm - rows); c <= std::min(n_coarse - 1, cm + rows); ++c)
-        for (int32_t f : children[c])
+        for (int32_t f : children[c]) {
+          if (!tbest.empty()) tbest[f] = std::max(tbest[f], scores[cell]);
           for (int32_t b = std::max(0, cb - 1); b <= std::min(n_bins - 1, cb + 1); ++b)
             fk.push_back((long long)f * n_bins + b);
+        }
     }
     std::sort(fk.begin(), fk.end());
     fk.erase(std::unique(fk.begin(), fk.end()), fk.end());
+    if (!tbest.empty()) {
+      // template budget: keep the cells of the template_budget fine templates
+      // with the highest best proposing score (ties: lower index first)
+      std::vector<int32_t> touched;
+      for (int32_t f = 0; f < n_fine; ++f)
+        if (tbest[f] > -INFINITY) touched.push_back(f);
+      if ((int64_t)touched.size() > params_prop.template_budget) {
+        std::partial_sort(touched.begin(), touched.begin() + params_prop.template_budget, touched.end(),
+                          [&](int32_t a, int32_t b) {
+                            if (tbest[a] != tbest[b]) return tbest[a] > tbest[b];
+                            return a < b;
+                          });
+        std::vector<unsigned char> kept(n_fine, 0);
+        for (int32_t u = 0; u < params_prop.template_budget; ++u) kept[touched[u]] = 1;
+        fk.erase(std::remove_if(fk.begin(), fk.end(), [&](long long v) { return !kept[v / n_bins]; }), fk.end());
+      }
+    }
     const int32_t nf = (int32_t)fk.size();
     std::vector<int32_t> fm(nf), fb(nf);
     for (int32_t k = 0; k < nf; ++k) { fm[k] = (int32_t)(fk[k] / n_bins); fb[k] = (int32_t)(fk[k] % n_bins); }

@@ -268,7 +268,7 @@ def detection_threshold(nseg, p_fa):
 
 def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t_obs, n_real, per_real, seed,
              p_fa=1e-6, amp_range=(0.01, 0.1), nms=NO_NMS, fine_rows=1, component_top=0, nms_by_nsigma=False,
-             plain_subset=False, baselines=True):
+             plain_subset=False, baselines=True, template_budget=0):
     """Recall of injections over the same realisations in these searches:
       full            every fine template (the recall reference), mixed form
       proposal        the network's proposal at its noise-calibrated threshold
@@ -284,7 +284,8 @@ def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t
     +-1 bin of its own (label) cell exceeds the detection threshold at
     per-cell false-alarm probability p_fa; in the proposal searches that cell
     must also have been evaluated.  baselines=False skips the two searches
-    without the network."""
+    without the network; template_budget > 0 caps the fine templates the
+    proposal refines (srs_proposal_params.template_budget)."""
     import torch
     rng = np.random.default_rng(seed)
     n = int(round(t_obs * params.fs))
@@ -314,7 +315,8 @@ def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t
         out["full_cells"] += fm.size
         # the network's proposal search
         pr = ctx.search_proposed(x, coarse_mc, fine_mc, params, mlp_params, score_th, nms=nms, fine_rows=fine_rows,
-                                 component_top=component_top, nms_by_nsigma=nms_by_nsigma)
+                                 component_top=component_top, nms_by_nsigma=nms_by_nsigma,
+                                 template_budget=template_budget)
         out["proposal_ms"] += pr["report"]["device_ms"]
         out["proposal_coarse_spectra"] += pr["report"]["coarse_spectra"]
         out["proposal_segment_bins"] += pr["report"]["fine_segment_bins"]
@@ -382,6 +384,20 @@ def evaluate(ctx, mlp_params, score_th, nsigma_th, coarse_mc, fine_mc, params, t
     for key in keys:
         out["recall_" + key] = out[key] / max(1, out["injections"])
     return out
+
+
+def budget_templates(coarse_cells, scores, coarse_mc, fine_mc, fine_rows, budget):
+    """The fine templates a template budget keeps: each fine template touched
+    by a proposed coarse cell ranks by the best score among the cells that
+    touch it (ties: lower index first); the first `budget` are kept."""
+    parent = np.array([nearest_template(coarse_mc, m) for m in fine_mc])
+    best = {}
+    for m, b in coarse_cells:
+        s = float(scores[int(m), int(b)])
+        for f in np.nonzero(np.abs(parent - int(m)) <= fine_rows)[0]:
+            best[int(f)] = max(best.get(int(f), -np.inf), s)
+    order = sorted(best, key=lambda f: (-best[f], f))
+    return set(order[:budget])
 
 
 def fine_cells_of(coarse_cells, coarse_mc, fine_mc, n_bins, fine_rows=1):

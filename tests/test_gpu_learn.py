@@ -215,3 +215,33 @@ def test_proposal_component_rule_matches_host_rule(ctx, top):
     expect = proposal.fine_cells_of(np.argwhere(keep), coarse, fine, 600, fine_rows=0)
     got = sorted(map(tuple, r["cells"].tolist()))
     assert got == [tuple(c) for c in expect]
+
+
+@pytest.mark.parametrize("budget", [1, 5, 1000])
+def test_proposal_template_budget_keeps_the_best_scored_templates(ctx, budget):
+    """template_budget: only the fine templates whose best proposing coarse
+    cell scores highest are refined; their cells are exactly the unbudgeted
+    proposal's cells of those templates, with the same n_sigma.  A budget
+    above the number of touched templates changes nothing."""
+    fs, nseg = 256.0, 24
+    coarse = srs_synth.log_templates(3e-2, 1e-1, 6)
+    fine = srs_synth.log_templates(3e-2, 1e-1, 24)
+    x = srs_synth.strain_with_chirps(nseg * 7680, fs, 4, [{"mc": 6e-2, "f0": 50.0, "amp": 0.08}])
+    p = Params(eps=1e-6, top_k=8)
+    params = proposal.init_params(0)
+    smap = torch.from_numpy(ctx.search(x, coarse, p)[1]).cuda()
+    sc = ctx.score_map(smap, params).cpu().numpy()
+    th = float(np.float32(np.quantile(sc, 0.99)))
+    full = ctx.search_proposed(x, coarse, fine, p, params, threshold=th, fine_rows=1)
+    r = ctx.search_proposed(x, coarse, fine, p, params, threshold=th, fine_rows=1, template_budget=budget)
+    kept = proposal.budget_templates(np.argwhere(sc > th), sc, coarse, fine, 1, budget)
+    touched = {int(m) for m in full["cells"][:, 0]}
+    assert len(kept) == min(budget, len(touched))
+    want = {(int(m), int(b)): v for (m, b), v in zip(full["cells"], full["nsigma"]) if int(m) in kept}
+    got = {(int(m), int(b)): v for (m, b), v in zip(r["cells"], r["nsigma"])}
+    assert sorted(got) == sorted(want)
+    assert r["report"]["proposed_coarse"] == full["report"]["proposed_coarse"]
+    for c, v in got.items():
+        assert v == pytest.approx(want[c], abs=2e-3)
+    if budget >= len(touched):
+        assert r["n_cells"] == full["n_cells"]
