@@ -64,3 +64,29 @@ def test_injections_on_grid_sit_in_their_cells():
 def test_detection_threshold_matches_the_library():
     for n in (1, 35, 240, 720):
         assert proposal.detection_threshold(n, 1e-6) == pytest.approx(nsigma_threshold(n, 1e-6), rel=1e-9)
+
+
+def test_budget_templates_against_brute_force():
+    """The template budget's host restatement: a fine template ranks by the
+    best score of the proposed coarse cells whose rows (within fine_rows of
+    its nearest coarse template) touch it; ties go to the lower index."""
+    rng = np.random.default_rng(3)
+    coarse = np.geomspace(1e-2, 1e-1, 7)
+    fine = np.geomspace(1e-2, 1e-1, 29)
+    scores = rng.integers(0, 5, size=(7, 40)).astype(np.float32)   # many ties
+    cells = np.argwhere(scores >= 3)
+    parent = [int(np.argmin(np.abs(np.log(coarse) - np.log(m)))) for m in fine]
+    for rows in (0, 1):
+        best = {}
+        for m, b in cells:
+            for f in range(len(fine)):
+                if abs(parent[f] - m) <= rows:
+                    best[f] = max(best.get(f, -np.inf), scores[m, b])
+        ranked = sorted(best, key=lambda f: (-best[f], f))
+        for budget in (1, 4, 11, 100):
+            got = proposal.budget_templates(cells, scores, coarse, fine, rows, budget)
+            assert got == set(ranked[:budget]), (rows, budget)
+    # a row that no proposed cell reaches contributes nothing
+    only = np.array([[0, 5]])
+    got = proposal.budget_templates(only, scores, coarse, fine, 0, 100)
+    assert got == {f for f in range(len(fine)) if parent[f] == 0}
