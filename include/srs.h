@@ -56,6 +56,11 @@
  *     more than 2^31 - 1 segment spectra in one call).
  *   - SRS_ERR_CUDA / SRS_ERR_OOM: a CUDA call failed / device memory ran out;
  *     the context stays usable for smaller problems.
+ *   - SRS_ERR_TIMEOUT: a device-side bound was reached and the kernel
+ *     returned instead of waiting on: a wait for a TMA copy gave up, or the
+ *     spreader's cell walk stopped at its cell bound (possible only with a
+ *     time map that steps back, which the planner's range excludes); the
+ *     message names the item and segment and the context stays usable.
  *   - Threading: one context per host thread.
  */
 #ifndef SRS_H

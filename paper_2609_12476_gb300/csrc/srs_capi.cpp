@@ -287,6 +287,15 @@ bool tma_disabled() {
   return no_tma && no_tma[0] == '1';
 }
 
+void err_flag_message(const int* f, char* buf, size_t n) {
+  if (f[0] == 2)
+    std::snprintf(buf, n, "the spreader's cell walk reached its bound with samples unused (a time map that steps "
+                  "back): item %d segment %d sample %d block %d", f[1], f[2], f[3], f[4]);
+  else
+    std::snprintf(buf, n, "a device wait gave up (TMA copy did not complete in time): item %d segment %d parity %d "
+                  "block %d", f[1], f[2], f[3], f[4]);
+}
+
 srs_status strain_f32(srs_ctx* ctx, const void* dstrain, int32_t dtype, int64_t samples, int64_t n_s,
                       const float** out, int* use_tma) {
   // SRS_NO_TMA=1 in the environment selects plain shared-memory staging.
@@ -445,9 +454,8 @@ srs_status check_err_flag(srs_ctx* ctx) {
   int flag[5] = {0, 0, 0, 0, 0};
   SRS_CK(cudaMemcpy(flag, ctx->errflag.p, sizeof flag, cudaMemcpyDeviceToHost), "read error flag");
   if (flag[0]) {
-    char buf[200];
-    std::snprintf(buf, sizeof buf, "a device wait gave up (TMA copy did not complete in time): item %d segment %d parity %d block %d",
-                  flag[1], flag[2], flag[3], flag[4]);
+    char buf[240];
+    err_flag_message(flag, buf, sizeof buf);
     return set_err(ctx, SRS_ERR_TIMEOUT, buf);
   }
   return SRS_OK;
@@ -762,9 +770,8 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
   }
   SRS_CK(cudaStreamSynchronize(ctx->stream), "search");
   if (mixed && ctx->hflag[0]) {
-    char b[200];
-    std::snprintf(b, sizeof b, "a device wait gave up (TMA copy did not complete in time): item %d segment %d parity %d block %d",
-                  ctx->hflag[1], ctx->hflag[2], ctx->hflag[3], ctx->hflag[4]);
+    char b[240];
+    err_flag_message(ctx->hflag, b, sizeof b);
     return set_err(ctx, SRS_ERR_TIMEOUT, b);
   }
   *n_cands = k;
@@ -797,10 +804,9 @@ srs_status srs::sync_impl(srs_ctx* ctx, srs_report* report) {
   for (int k = 0; k < n; ++k) {
     int* f = ctx->hflag + 8 * (1 + k);
     if (f[0] && st == SRS_OK) {
-      char b[220];
-      std::snprintf(b, sizeof b,
-                    "asynchronous search %d: a device wait gave up (TMA copy did not complete in time): item %d "
-                    "segment %d parity %d block %d", k, f[1], f[2], f[3], f[4]);
+      char d[240], b[280];
+      err_flag_message(f, d, sizeof d);
+      std::snprintf(b, sizeof b, "asynchronous search %d: %s", k, d);
       st = SRS_ERR_TIMEOUT;
       msg = b;
     }

@@ -91,6 +91,12 @@ double chirp_beta(double mc, double f);
 // stages samples without TMA bulk copies (srs_capi.cpp).
 bool tma_disabled();
 
+// Message for k_mixed's error flag (srs_capi.cpp): flag[0] = 1 when a wait for
+// a TMA copy gave up (flag[1..4]: item, segment, parity, block), 2 when the
+// spreader's cell walk stopped at its bound with samples unused (item,
+// segment, the lane's first sample, block).
+void err_flag_message(const int* flag, char* buf, size_t n);
+
 // Host planner (srs_plan.cpp).  Returns SRS_OK or an error with `msg` set.
 // With betas_in != NULL the templates are given by their chirp parameters
 // (mc is ignored); with local = true every segment is resampled with a 0PN

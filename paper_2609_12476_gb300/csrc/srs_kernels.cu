@@ -322,6 +322,13 @@ __global__ void k_wait_selftest(int* __restrict__ err) {
 // acc[(t + R) % W] and moving on renames registers instead of copying them.
 // The per-sample step has no branch: the next sample's load index is clamped
 // to the run, and a step past the run's end computes inputs nobody reads.
+//
+// The walk ends when every lane has used its run.  That needs a time map that
+// never steps back a cell, which the planner's range guarantees; as a guard
+// against anything else spread_run also stops the walk once no live lane is
+// below cell n + W + 2 (a lane's run spans about n / threads + W cells),
+// checked once per turn of the ring so the check stays off the per-cell path,
+// and reports the lanes left with samples.
 template <int W, bool INT_KC>
 struct CellWalk {
   float2 acc[W];
@@ -424,8 +431,9 @@ struct CellWalk {
   }
 };
 
+// Returns false when the walk stopped at its cell bound with samples unused.
 template <int W, bool INT_KC>
-__device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2* __restrict__ grid,
+__device__ __forceinline__ bool spread_run(const float* __restrict__ xs, float2* __restrict__ grid,
                                            const Anchor& A, int j_begin, int j_end, int l_base,
                                            const MixedArgs& a) {
   CellWalk<W, INT_KC> w;
@@ -468,8 +476,16 @@ __device__ __forceinline__ void spread_run(const float* __restrict__ xs, float2*
     w.inputs(x0);
     w.Bm = w.l0;
   }
+  // each turn walks W cells; the bound is checked once per turn, and leaving
+  // there flushes the window as the walk's own end (cell<0> finding no live
+  // lane) would
   while (w.template turn<0>()) {
+    if (!__any_sync(w.mask, w.live && w.Bm < a.n_fine + W + 2)) {
+      w.template flush<0>();
+      break;
+    }
   }
+  return !w.live;
 }
 
 // Persistent CTAs take (template, segment-chunk) items from `queue` (in the
@@ -525,7 +541,7 @@ k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_
         if (tid == 0 && !mbar_wait(&s_bar, parity)) {
           // record where the wait gave up: flag, item, segment, parity, block
           s_abort = 1;
-          if (atomicExch(err, 1) == 0) { err[1] = q; err[2] = i; err[3] = (int)parity; err[4] = blockIdx.x; }
+          if (atomicCAS(err, 0, 1) == 0) { err[1] = q; err[2] = i; err[3] = (int)parity; err[4] = blockIdx.x; }
         }
         parity ^= 1u;
       }
@@ -542,7 +558,11 @@ k_mixed(const float* __restrict__ strain, const Item* __restrict__ items, int n_
         const float* xsrc = GLOBAL_X ? strain + (long long)i * a.n_s : xs;
         // the anchor of this lane's span (one per warp, or per half-warp)
         const int ai = j0 / a.span;
-        if (j0 < a.n_s) spread_run<W, INT_KC>(xsrc, g0, anc[(i - it.i0) * a.n_anchor + ai], j0, j1, ai * a.span, a);
+        if (j0 < a.n_s && !spread_run<W, INT_KC>(xsrc, g0, anc[(i - it.i0) * a.n_anchor + ai], j0, j1, ai * a.span, a)
+            && atomicCAS(err, 0, 2) == 0) {
+          // the cell walk hit its bound: flag 2, item, segment, first sample of the lane, block
+          err[1] = q; err[2] = i; err[3] = j0; err[4] = blockIdx.x;
+        }
       }
       __syncthreads();
       if (!GLOBAL_X && tid == 0 && i + 1 < it.i1) bulk_load(xs, strain + (long long)(i + 1) * a.n_s, seg_bytes, &s_bar);

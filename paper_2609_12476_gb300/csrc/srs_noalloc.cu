@@ -204,7 +204,9 @@ srs_status run(void* stream_v, const void* strain, int64_t n_samples, int32_t dt
       !ck(cudaStreamSynchronize(st), "k_mixed"))
     return SRS_ERR_CUDA;
   if (flag[0]) {
-    msg = "a device wait gave up (TMA copy did not complete in time)";
+    char buf[240];
+    err_flag_message(flag, buf, sizeof buf);
+    msg = buf;
     return SRS_ERR_TIMEOUT;
   }
   return SRS_OK;
