@@ -544,7 +544,7 @@ srs_status srs::search_impl(srs_ctx* ctx, const void* strain, int64_t n_samples,
   SRS_CK(ctx->keys.ensure(n_map * 8), "alloc keys");
   // k <= 32 (mixed form): the reduction selects the top k itself
   const bool top32 = mixed && k <= 32;
-  const long long scratch = std::max(topk_scratch_keys(n_map, k), 4LL * ctx->n_sm * 32);
+  const long long scratch = std::max(topk_scratch_keys(n_map, k), (long long)kTop32BlocksPerSm * ctx->n_sm * 32);
   SRS_CK(ctx->topk_a.ensure(scratch * 8), "alloc topk");
   SRS_CK(ctx->topk_b.ensure(scratch * 8), "alloc topk");
   srs_candidate* dc = on_dev ? cands : nullptr;

@@ -9,6 +9,9 @@
 namespace srs {
 
 constexpr int kTopkTile = 4096;  // keys per top-k tile (k <= kTopkTile / 2)
+// at most this many k_reduce_mixed_top32 blocks per SM; each leaves 32 keys in
+// the caller's scratch, which must hold kTop32BlocksPerSm * n_sm * 32 keys
+constexpr int kTop32BlocksPerSm = 8;
 
 struct AnchorArgs {
   double fs, t_coh, f_c;

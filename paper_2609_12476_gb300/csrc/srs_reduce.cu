@@ -232,7 +232,10 @@ cudaError_t launch_reduce_mixed_top32(const float* partial, const int* item_off,
   if (k < 1 || k > 32) return cudaErrorInvalidValue;
   long long total = (long long)n_templates * n_bins;
   long long blocks = (total + 255) / 256;
-  if (blocks > (long long)n_sm * 4) blocks = (long long)n_sm * 4;
+  // kTop32BlocksPerSm = 8 blocks of 256 per SM fill it: the pass streams the
+  // partial sums from HBM, and the loads in flight (eight per thread) bound it;
+  // the scratch holds 32 keys per block
+  if (blocks > (long long)n_sm * kTop32BlocksPerSm) blocks = (long long)n_sm * kTop32BlocksPerSm;
   k_reduce_mixed_top32<<<(unsigned)blocks, 256, 0, st>>>(partial, item_off, nseg, n_templates, n_bins, map, k,
                                                           scratch, ticket, cands);
   return cudaGetLastError();

@@ -184,7 +184,7 @@ srs_status prepare_out(srs_ctx* ctx, const srs_slide_grid* g, const srs_params* 
     }
   }
   SRS_CK(ctx->keys.ensure(o->n_map * 8), "alloc keys");
-  const long long scratch = std::max(topk_scratch_keys(o->n_map, o->k), 4LL * ctx->n_sm * 32);
+  const long long scratch = std::max(topk_scratch_keys(o->n_map, o->k), (long long)kTop32BlocksPerSm * ctx->n_sm * 32);
   SRS_CK(ctx->topk_a.ensure(scratch * 8), "alloc topk");
   SRS_CK(ctx->topk_b.ensure(scratch * 8), "alloc topk");
   o->dc = on_dev ? cands : nullptr;
