@@ -292,6 +292,40 @@ def _dtype_code(x):
         return SRS_F32
     raise TypeError("strain must be float32 or float64")
 
+def _dev_in(x, device, name, dtypes=None, ndim=None):
+    """A torch CUDA input of a Context call: on the context's device and
+    contiguous (the library reads it as a flat array), of one of `dtypes` and
+    with `ndim` dimensions when given."""
+    if x.device.index != device:
+        raise ValueError("%s is on %s; the context runs on cuda:%d" % (name, x.device, device))
+    if not x.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if dtypes is not None and x.dtype not in dtypes:
+        raise TypeError("%s must be of dtype %s" % (name, " or ".join(str(d) for d in dtypes)))
+    if ndim is not None and x.dim() != ndim:
+        raise ValueError("%s must have %d dimensions" % (name, ndim))
+
+
+def _dev_out(x, shape, dtype, device, name):
+    """A caller-supplied torch CUDA output: exactly the shape and dtype the
+    library writes, contiguous, on the context's device (None: not wanted)."""
+    if x is None:
+        return
+    if (not _is_torch_cuda(x) or x.dtype != dtype or tuple(x.shape) != tuple(shape) or not x.is_contiguous()
+            or x.device.index != device):
+        raise ValueError("%s must be a contiguous %s CUDA tensor of shape %s on cuda:%d"
+                         % (name, dtype, tuple(shape), device))
+
+
+def _host_out(x, shape, dtype, name):
+    """A caller-supplied numpy output: exactly the shape and dtype the library
+    writes, C-contiguous and writeable (None: not wanted)."""
+    if x is None:
+        return
+    if (not isinstance(x, np.ndarray) or x.dtype != dtype or x.shape != tuple(shape)
+            or not x.flags["C_CONTIGUOUS"] or not x.flags["WRITEABLE"]):
+        raise ValueError("%s must be a writeable C-contiguous %s array of shape %s" % (name, dtype, tuple(shape)))
+
 
 class Context:
     """srs_ctx: one CUDA device, one stream, a reusable device workspace."""
@@ -302,7 +336,7 @@ class Context:
         st = self._lib.srs_create(ctypes.byref(self._h), int(device), stream)
         if st != SRS_OK:
             raise SrsError(st, "srs_create failed (no CUDA device?)")
-        self.device = device
+        self.device = int(device)
 
     def close(self):
         if self._h:
@@ -319,6 +353,15 @@ class Context:
         if st != SRS_OK:
             raise SrsError(st, self._lib.srs_last_error(self._h).decode())
 
+    def _check_dev_search_out(self, out, map_shape, top_k):
+        """The device outputs of a search: {"map": float32 [templates, n_bins]
+        or None, "cands": int32 [top_k, 3]} on this context's device."""
+        import torch
+        if out.get("cands") is None:
+            raise ValueError("out['cands'] is required")
+        _dev_out(out.get("map"), map_shape, torch.float32, self.device, "out['map']")
+        _dev_out(out["cands"], (top_k, 3), torch.int32, self.device, "out['cands']")
+
     def search(self, strain, mc, params, stat_map=True, out=None):
         """srs_search.  Host numpy strain (params.io_on_device = 0) returns numpy
         results; a torch CUDA tensor (io_on_device = 1) returns torch tensors on
@@ -331,12 +374,15 @@ class Context:
         rep = _Report()
         if _is_torch_cuda(strain):
             import torch
+            _dev_in(strain, self.device, "strain")
             p.io_on_device = 1
             n_bins = int(round((params.f_hi - params.f_lo) * params.t_coh))
             if out is None:
                 out = {"map": torch.empty((mc.size, n_bins), dtype=torch.float32, device=strain.device)
                        if stat_map else None,
                        "cands": torch.empty((params.top_k, 3), dtype=torch.int32, device=strain.device)}
+            else:
+                self._check_dev_search_out(out, (mc.size, n_bins), params.top_k)
             mp = out["map"].data_ptr() if out.get("map") is not None else None
             st = self._lib.srs_search(self._h, strain.data_ptr(), strain.numel(), dt, mc.ctypes.data, mc.size,
                                       ctypes.byref(p), mp, out["cands"].data_ptr(), ctypes.byref(n_cands),
@@ -365,7 +411,10 @@ class Context:
         mc = np.ascontiguousarray(mc, dtype=np.float64)
         p = params.c()
         n_cands = ctypes.c_int32(0)
+        n_bins = int(round((params.f_hi - params.f_lo) * params.t_coh))
         if _is_torch_cuda(strain):
+            _dev_in(strain, self.device, "strain")
+            self._check_dev_search_out(out, (mc.size, n_bins), params.top_k)
             p.io_on_device = 1
             mp = out["map"].data_ptr() if out.get("map") is not None else None
             st = self._lib.srs_search_async(self._h, strain.data_ptr(), strain.numel(), _dtype_code(strain),
@@ -376,9 +425,11 @@ class Context:
                 raise ValueError("a host strain must be a C-contiguous numpy array (kept alive until sync)")
             p.io_on_device = 0
             c = out["cands"]
-            if c.dtype != CAND_DTYPE or c.size < params.top_k or not c.flags["C_CONTIGUOUS"]:
+            if (not isinstance(c, np.ndarray) or c.dtype != CAND_DTYPE or c.size < params.top_k
+                    or not c.flags["C_CONTIGUOUS"] or not c.flags["WRITEABLE"]):
                 raise ValueError("out['cands'] must be a contiguous CAND_DTYPE array of top_k entries")
             m = out.get("map")
+            _host_out(m, (mc.size, n_bins), np.float32, "out['map']")
             st = self._lib.srs_search_async(self._h, strain.ctypes.data, strain.size, _dtype_code(strain),
                                             mc.ctypes.data, mc.size, ctypes.byref(p),
                                             m.ctypes.data if m is not None else None, c.ctypes.data,
@@ -407,6 +458,7 @@ class Context:
         shape = (mc.size, seg_end - seg_begin, n_bins)
         if _is_torch_cuda(strain):
             import torch
+            _dev_in(strain, self.device, "strain")
             p.io_on_device = 1
             F = torch.empty(shape, dtype=torch.complex128, device=strain.device)
             st = fn(self._h, strain.data_ptr(), strain.numel(), dt, mc.ctypes.data, mc.size, int(seg_begin),
@@ -454,6 +506,7 @@ class Context:
         b = self._bank(bank)
         if _is_torch_cuda(strain):
             import torch
+            _dev_in(strain, self.device, "strain")
             p.io_on_device = 1
             out = torch.empty(shape, dtype=torch.float32, device=strain.device)
             st = self._lib.srs_power_cube(self._h, strain.data_ptr(), strain.numel(), dt, ctypes.byref(b),
@@ -487,6 +540,8 @@ class Context:
             raise ValueError("cube must be [n_beta, n_bins, segments]")
         if _is_torch_cuda(cube) and (cube.dtype != __import__("torch").float32 or not cube.is_contiguous()):
             raise ValueError("a device cube must be a contiguous float32 tensor")
+        if _is_torch_cuda(cube):
+            _dev_in(cube, self.device, "cube")
         seg_end = int(seg_begin) + int(cube.shape[2])
         R = keep[0].size
         if _is_torch_cuda(cube):
@@ -520,6 +575,7 @@ class Context:
         import torch
         if not (_is_torch_cuda(cube) and cube.dtype == torch.float32 and cube.is_contiguous() and cube.dim() == 3):
             raise ValueError("cube must be a contiguous float32 CUDA tensor [n_beta, n_bins, n_seg]")
+        _dev_in(cube, self.device, "cube")
         K, B, N = (int(v) for v in cube.shape)
         est = s_eff is None
         S = torch.empty((K, B), dtype=torch.float32, device=cube.device) if est else \
@@ -545,11 +601,14 @@ class Context:
         R = keep[0].size
         if _is_torch_cuda(strain):
             import torch
+            _dev_in(strain, self.device, "strain")
             p.io_on_device = 1
             if out is None:
                 out = {"map": torch.empty((R, int(n_t0)), dtype=torch.float32, device=strain.device)
                        if want_map else None,
                        "cands": torch.empty((params.top_k, 3), dtype=torch.int32, device=strain.device)}
+            else:
+                self._check_dev_search_out(out, (R, int(n_t0)), params.top_k)
             mp = out["map"].data_ptr() if out.get("map") is not None else None
             st = self._lib.srs_slide_search(self._h, strain.data_ptr(), strain.numel(), dt, ctypes.byref(b),
                                             ctypes.byref(g), ctypes.byref(p), int(cube_budget_bytes), mp,
@@ -574,6 +633,8 @@ class Context:
         import torch
         if out is None:
             out = torch.empty(int(n), dtype=torch.float32, device="cuda:%d" % self.device)
+        else:
+            _dev_out(out, (int(n),), torch.float32, self.device, "out")
         arr = (_Injection * max(1, len(injections)))()
         for k, inj in enumerate(injections):
             arr[k] = _Injection(inj["mc"], inj["f0"], inj["amp"], inj.get("phi0", 0.0))
@@ -590,6 +651,7 @@ class Context:
         n = cells.shape[0]
         if _is_torch_cuda(stat_map):
             import torch
+            _dev_in(stat_map, self.device, "stat_map", (torch.float32,), 2)
             M, NB = stat_map.shape
             cm = torch.from_numpy(np.ascontiguousarray(cells[:, 0])).to(stat_map.device)
             cb = torch.from_numpy(np.ascontiguousarray(cells[:, 1])).to(stat_map.device)
@@ -613,6 +675,9 @@ class Context:
         params = np.ascontiguousarray(params, dtype=np.float32)
         if _is_torch_cuda(X):
             import torch
+            _dev_in(X, self.device, "X", (torch.float32,), 2)
+            if X.shape[1] != MLP_INPUTS:
+                raise ValueError("X must be [n, %d]" % MLP_INPUTS)
             out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
             st = self._lib.srs_mlp_forward(self._h, X.data_ptr(), X.shape[0], params.ctypes.data, out.data_ptr(), 1)
             self._check(st)
@@ -638,6 +703,13 @@ class Context:
     def mlp_train(self, X, y, params, epochs=20, batch=256, lr=1e-3, seed=0, beta1=0.9, beta2=0.999, eps=1e-8):
         """srs_mlp_train on a CUDA training set X [n, 297], y [n]; returns
         (trained FP32 parameters, mean loss of each epoch)."""
+        import torch
+        if not (_is_torch_cuda(X) and _is_torch_cuda(y)):
+            raise TypeError("X and y must be CUDA tensors")
+        _dev_in(X, self.device, "X", (torch.float32,), 2)
+        _dev_in(y, self.device, "y", (torch.float32,), 1)
+        if X.shape[1] != MLP_INPUTS or y.shape[0] != X.shape[0]:
+            raise ValueError("X must be [n, %d] and y [n]" % MLP_INPUTS)
         p = np.array(params, dtype=np.float32)
         losses = np.zeros(epochs, dtype=np.float32)
         cfg = _TrainCfg(int(epochs), int(batch), float(lr), float(beta1), float(beta2), float(eps),
@@ -651,6 +723,9 @@ class Context:
         """srs_score_map: logits of every cell of a CUDA map [templates, bins]."""
         import torch
         params = np.ascontiguousarray(params, dtype=np.float32)
+        if not _is_torch_cuda(stat_map):
+            raise TypeError("stat_map must be a CUDA tensor")
+        _dev_in(stat_map, self.device, "stat_map", (torch.float32,), 2)
         M, NB = stat_map.shape
         out = torch.empty((M, NB), dtype=torch.float32, device=stat_map.device)
         st = self._lib.srs_score_map(self._h, stat_map.data_ptr(), M, NB, params.ctypes.data, out.data_ptr())
@@ -666,6 +741,7 @@ class Context:
         p = params.c()
         rep = _Report()
         if _is_torch_cuda(strain):
+            _dev_in(strain, self.device, "strain")
             p.io_on_device = 1
             ptr, n = strain.data_ptr(), strain.numel()
         else:
@@ -699,6 +775,7 @@ class Context:
         rep = _ProposalReport()
         p = params.c()
         if _is_torch_cuda(strain):
+            _dev_in(strain, self.device, "strain")
             p.io_on_device = 1
             ptr, n = strain.data_ptr(), strain.numel()
         else:

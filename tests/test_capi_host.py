@@ -226,3 +226,17 @@ def test_plan_refuses_more_spectra_than_32_bit_items_hold():
     assert e.value.status == -5
     info, _, _ = srs_plan(Params(), np.full(fit // 64, 5e-4), n)
     assert info["n_spectra"] == (fit // 64) * per
+
+
+def test_host_output_buffers_are_checked_before_the_call():
+    """A caller's numpy output must be exactly what the library writes
+    (dtype, shape, C order) and writeable: a smaller or transposed array would
+    take out-of-bounds or misplaced host writes."""
+    _capi._host_out(None, (2, 3), np.float32, "m")
+    _capi._host_out(np.empty((2, 3), np.float32), (2, 3), np.float32, "m")
+    ro = np.empty((2, 3), np.float32)
+    ro.flags.writeable = False
+    for bad in (np.empty((2, 4), np.float32), np.empty((2, 3), np.float64), np.empty((3, 2), np.float32).T, ro,
+                [[0.0] * 3] * 2):
+        with pytest.raises(ValueError):
+            _capi._host_out(bad, (2, 3), np.float32, "m")

@@ -239,6 +239,47 @@ def test_errors_are_status_codes(ctx):
     assert len(c) == 4 and np.isfinite(m).all()
 
 
+def test_binding_rejects_mismatched_buffers(ctx):
+    """The binding checks caller-supplied tensors before any device work: the
+    library writes exactly [templates, n_bins] float32 and [top_k, 3] int32 and
+    reads the strain as one flat array on the context's device."""
+    torch = pytest.importorskip("torch")
+    from paper_2609_12476_gb300 import CAND_DTYPE
+    mc = srs_synth.log_templates(2e-2, 5e-2, 2)
+    p = Params(eps=1e-6, top_k=4)
+    xh = srs_synth.white_noise(4 * 7680, 5)
+    x = torch.from_numpy(xh).cuda()
+    good = {"map": torch.empty((2, 600), dtype=torch.float32, device="cuda"),
+            "cands": torch.empty((4, 3), dtype=torch.int32, device="cuda")}
+    bad = [dict(good, map=torch.empty((2, 599), dtype=torch.float32, device="cuda")),
+           dict(good, map=torch.empty((2, 600), dtype=torch.float64, device="cuda")),
+           dict(good, map=torch.empty((600, 2), dtype=torch.float32, device="cuda").t()),
+           dict(good, map=torch.empty((2, 600), dtype=torch.float32)),
+           dict(good, cands=torch.empty((3, 3), dtype=torch.int32, device="cuda")),
+           {"map": good["map"]}]
+    for o in bad:
+        with pytest.raises(ValueError):
+            ctx.search(x, mc, p, out=o)
+        with pytest.raises(ValueError):
+            ctx.search_async(x, mc, p, o)
+    xs = torch.from_numpy(np.repeat(xh, 2)).cuda()[::2]        # the same samples, strided
+    with pytest.raises(ValueError):
+        ctx.search(xs, mc, p)
+    with pytest.raises(ValueError):
+        ctx.segment_spectra(xs, mc, 0, 1, p)
+    with pytest.raises(ValueError):
+        ctx.search_async(xh, mc, p, {"map": np.empty((2, 599), np.float32), "cands": np.zeros(4, CAND_DTYPE)})
+    with pytest.raises(ValueError):
+        ctx.make_strain(100, 256.0, 1, out=torch.empty(99, dtype=torch.float32, device="cuda"))
+    with pytest.raises(TypeError):
+        ctx.score_map(torch.zeros((4, 600), dtype=torch.float64, device="cuda"), np.zeros(1, np.float32))
+    # the right buffers still work, and give the map of a search with its own outputs
+    out, _ = ctx.search(x, mc, p, out=good)
+    ref, _ = ctx.search(x, mc, p)
+    torch.cuda.synchronize()
+    assert torch.allclose(out["map"], ref["map"], rtol=1e-5, atol=1e-5)
+
+
 def test_bounded_wait_gives_up_with_a_status(ctx):
     """The spreader's staging wait, armed for a transfer that never comes,
     gives up after its cycle limit: the call returns SRS_ERR_TIMEOUT with the
